@@ -1,0 +1,60 @@
+"""Named synthetic workloads shaped like the paper's CUBE experiments.
+
+Each entry fixes the mesh (grid size, perturbation bound and seed), the
+degree k, the viscosity, the load and the partition.  ``make_config``
+returns the arrays; nothing here computes anything of the method.
+"""
+import numpy as np
+
+from .mesh import cube_mesh, box_partition, greedy_partition, element_vertex_average
+from .fields import manufactured_f, sinker_centres, sinker_viscosity, sinker_load
+
+CONFIGS = {
+    # 4^3 exact cubes, k=2, 2x2x2 box subdomains (smallest full case)
+    "cube4_k2": dict(n=4, perturb=0.0, seed=None, k=2, parts=(2, 2, 2), load="manufactured"),
+    # 32^3 perturbed (+-0.2h) triangulated hexes, k=2, 4x4x4 subdomains
+    "tri32_k2": dict(n=32, perturb=0.2, seed=2, k=2, parts=(4, 4, 4), load="manufactured"),
+    # 48^3 perturbed (+-0.15h), 512 uneven greedy subdomains
+    "tri48_greedy": dict(n=48, perturb=0.15, seed=3, k=2, greedy=(512, 31), load="manufactured"),
+    # 16^3 perturbed (+-0.2h), 4x4x4 subdomains, degree sweep
+    "tri16_k2": dict(n=16, perturb=0.2, seed=4, k=2, parts=(4, 4, 4), load="manufactured"),
+    "tri16_k3": dict(n=16, perturb=0.2, seed=4, k=3, parts=(4, 4, 4), load="manufactured"),
+    "tri16_k4": dict(n=16, perturb=0.2, seed=4, k=4, parts=(4, 4, 4), load="manufactured"),
+    # 32^3 cubes with 8 sinkers, contrast 1e4 and 1e6
+    "sinker32_dr1e4": dict(n=32, perturb=0.0, seed=None, k=2, parts=(4, 4, 4), load="sinker",
+                           sinkers=(8, 5), dr=1e4),
+    "sinker32_dr1e6": dict(n=32, perturb=0.0, seed=None, k=2, parts=(4, 4, 4), load="sinker",
+                           sinkers=(8, 5), dr=1e6),
+    # small cases used by the parity tests
+    "tri4_k2": dict(n=4, perturb=0.2, seed=7, k=2, parts=(2, 2, 2), load="manufactured"),
+    "tri6_k2": dict(n=6, perturb=0.2, seed=8, k=2, parts=(3, 2, 2), load="manufactured"),
+    "tri4_k3": dict(n=4, perturb=0.2, seed=9, k=3, parts=(2, 2, 2), load="manufactured"),
+    "tri4_k4": dict(n=4, perturb=0.2, seed=10, k=4, parts=(2, 2, 1), load="manufactured"),
+    "cube6_k2": dict(n=6, perturb=0.0, seed=None, k=2, parts=(3, 3, 3), load="manufactured"),
+    "sinker8": dict(n=8, perturb=0.0, seed=None, k=2, parts=(2, 2, 2), load="sinker",
+                    sinkers=(8, 5), dr=1e4),
+}
+
+
+def make_config(name, **override):
+    c = dict(CONFIGS[name])
+    c.update(override)
+    mesh = cube_mesh(c["n"], c["perturb"], c["seed"])
+    ne = c["n"] ** 3
+    xk = element_vertex_average(mesh)
+    if c["load"] == "sinker":
+        centres = sinker_centres(*c["sinkers"])
+        nu = sinker_viscosity(xk, centres, nu_min=1.0, nu_max=c["dr"])
+
+        def f(x, centres=centres):
+            return sinker_load(x, centres)
+    else:
+        nu = np.ones(ne)
+
+        def f(x):
+            return manufactured_f(x, 1.0)
+    if "greedy" in c:
+        part = greedy_partition(mesh, c["greedy"][0], c["greedy"][1])
+    else:
+        part = box_partition(mesh, c["parts"])
+    return dict(name=name, mesh=mesh, k=c["k"], nu=nu, f=f, part=part, spec=c)

@@ -1,0 +1,242 @@
+"""Seeded polyhedral meshes of the unit cube and subdomain partitions.
+
+Mesh layout (the one the library's ``vem_mesh`` takes):
+
+* ``xyz``      float64 [nV, 3]  vertex coordinates.
+* ``face_ptr`` int32 [nF+1], ``face_vtx`` int32: each face is a planar
+  vertex loop; its orientation (right-hand rule) fixes the global face
+  normal.
+* ``elem_ptr`` int32 [nE+1], ``elem_face`` int32: signed face references,
+  ``+(f+1)`` if the global normal of face ``f`` points out of the element,
+  ``-(f+1)`` otherwise.
+
+The CUBE family is an ``n x n x n`` grid of hexahedra (each a VEM polyhedron
+with 6 quadrilateral faces).  Interior vertices may be moved by i.i.d.
+uniform offsets in ``[-a h, a h]^3`` drawn in lexicographic vertex order
+(x, then y, then z of each vertex).  A moved hexahedron has non-planar
+quadrilaterals, so every quadrilateral is then split into two triangles
+along the diagonal through its smallest-index vertex, giving polyhedra with
+8 vertices, 18 edges and 12 triangular faces.
+"""
+import numpy as np
+
+
+def _vid(n, i, j, l):
+    return i + (n + 1) * (j + (n + 1) * l)
+
+
+def cube_mesh(n, perturb=0.0, seed=None, split_quads=None):
+    """Uniform ``n^3`` hexahedral mesh of [0,1]^3, optionally perturbed.
+
+    ``perturb`` is the offset bound as a fraction of h = 1/n.  ``split_quads``
+    defaults to ``perturb > 0``.
+    """
+    if split_quads is None:
+        split_quads = perturb > 0.0
+    h = 1.0 / n
+    idx = np.arange(n + 1)
+    L, J, I = np.meshgrid(idx, idx, idx, indexing="ij")
+    xyz = np.stack([I.ravel(), J.ravel(), L.ravel()], axis=1).astype(np.float64) * h
+    if perturb > 0.0:
+        rng = np.random.default_rng(seed)
+        off = rng.uniform(-perturb * h, perturb * h, size=xyz.shape)
+        ii, jj, ll = I.ravel(), J.ravel(), L.ravel()
+        interior = (ii > 0) & (ii < n) & (jj > 0) & (jj < n) & (ll > 0) & (ll < n)
+        xyz[interior] += off[interior]
+
+    quads = []
+    # x-normal faces at i = 0..n, normal +x
+    fx = {}
+    for l in range(n):
+        for j in range(n):
+            for i in range(n + 1):
+                fx[(i, j, l)] = len(quads)
+                quads.append((_vid(n, i, j, l), _vid(n, i, j + 1, l),
+                              _vid(n, i, j + 1, l + 1), _vid(n, i, j, l + 1)))
+    fy = {}
+    for l in range(n):
+        for j in range(n + 1):
+            for i in range(n):
+                fy[(i, j, l)] = len(quads)
+                quads.append((_vid(n, i, j, l), _vid(n, i, j, l + 1),
+                              _vid(n, i + 1, j, l + 1), _vid(n, i + 1, j, l)))
+    fz = {}
+    for l in range(n + 1):
+        for j in range(n):
+            for i in range(n):
+                fz[(i, j, l)] = len(quads)
+                quads.append((_vid(n, i, j, l), _vid(n, i + 1, j, l),
+                              _vid(n, i + 1, j + 1, l), _vid(n, i, j + 1, l)))
+
+    faces = []
+    quad_to_faces = []
+    for q in quads:
+        if split_quads:
+            p = int(np.argmin(q))
+            a, b, c, d = q[p], q[(p + 1) % 4], q[(p + 2) % 4], q[(p + 3) % 4]
+            quad_to_faces.append((len(faces), len(faces) + 1))
+            faces.append((a, b, c))
+            faces.append((a, c, d))
+        else:
+            quad_to_faces.append((len(faces),))
+            faces.append(tuple(q))
+
+    elem_faces = []
+    elem_ijk = []
+    for l in range(n):
+        for j in range(n):
+            for i in range(n):
+                ef = []
+                for q, s in ((fx[(i, j, l)], -1), (fx[(i + 1, j, l)], 1),
+                             (fy[(i, j, l)], -1), (fy[(i, j + 1, l)], 1),
+                             (fz[(i, j, l)], -1), (fz[(i, j, l + 1)], 1)):
+                    for f in quad_to_faces[q]:
+                        ef.append(s * (f + 1))
+                elem_faces.append(ef)
+                elem_ijk.append((i, j, l))
+
+    face_ptr = np.zeros(len(faces) + 1, dtype=np.int32)
+    face_ptr[1:] = np.cumsum([len(f) for f in faces])
+    face_vtx = np.array([v for f in faces for v in f], dtype=np.int32)
+    elem_ptr = np.zeros(len(elem_faces) + 1, dtype=np.int32)
+    elem_ptr[1:] = np.cumsum([len(e) for e in elem_faces])
+    elem_face = np.array([f for e in elem_faces for f in e], dtype=np.int32)
+    return {
+        "n": n, "h": h, "xyz": xyz,
+        "face_ptr": face_ptr, "face_vtx": face_vtx,
+        "elem_ptr": elem_ptr, "elem_face": elem_face,
+        "elem_ijk": np.array(elem_ijk, dtype=np.int32),
+    }
+
+
+def element_vertex_average(mesh):
+    """Vertex average of each element (used to sample fields per element)."""
+    fp, fv = mesh["face_ptr"], mesh["face_vtx"]
+    ep, ef = mesh["elem_ptr"], mesh["elem_face"]
+    out = np.zeros((len(ep) - 1, 3))
+    for e in range(len(ep) - 1):
+        vs = set()
+        for sf in ef[ep[e]:ep[e + 1]]:
+            f = abs(int(sf)) - 1
+            vs.update(int(v) for v in fv[fp[f]:fp[f + 1]])
+        out[e] = mesh["xyz"][sorted(vs)].mean(axis=0)
+    return out
+
+
+def box_partition(mesh, parts):
+    """Split the element grid into ``px x py x pz`` boxes of whole elements."""
+    n = mesh["n"]
+    px, py, pz = parts
+    ijk = mesh["elem_ijk"]
+    bi = ijk[:, 0] * px // n
+    bj = ijk[:, 1] * py // n
+    bl = ijk[:, 2] * pz // n
+    return (bi + px * (bj + py * bl)).astype(np.int32)
+
+
+def _grid_neighbours(n):
+    nb = [[] for _ in range(n ** 3)]
+    for l in range(n):
+        for j in range(n):
+            for i in range(n):
+                e = i + n * (j + n * l)
+                for di, dj, dl in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    a, b, c = i + di, j + dj, l + dl
+                    if 0 <= a < n and 0 <= b < n and 0 <= c < n:
+                        nb[e].append(a + n * (b + n * c))
+    return nb
+
+
+def greedy_partition(mesh, nparts, seed, size_range=(0.5, 2.0)):
+    """Seeded greedy graph-growing partition with uneven target sizes.
+
+    Targets are drawn U(size_range) times the mean size and rescaled to sum
+    to the element count.  Seeds: one random element, then farthest-point
+    picks over element centres.  Subdomains grow round-robin by breadth-first
+    search over face neighbours until they reach their target; elements left
+    over join the smallest adjacent subdomain; disconnected pieces of a
+    subdomain other than its largest join the smallest adjacent subdomain.
+    """
+    n = mesh["n"]
+    ne = n ** 3
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(size_range[0], size_range[1], size=nparts)
+    target = np.maximum(1, np.round(t / t.sum() * ne)).astype(np.int64)
+    ijk = mesh["elem_ijk"].astype(np.float64)
+    nb = _grid_neighbours(n)
+    seeds = [int(rng.integers(ne))]
+    d = np.linalg.norm(ijk - ijk[seeds[0]], axis=1)
+    for _ in range(1, nparts):
+        s = int(np.argmax(d))
+        seeds.append(s)
+        d = np.minimum(d, np.linalg.norm(ijk - ijk[s], axis=1))
+    part = -np.ones(ne, dtype=np.int64)
+    fronts = []
+    size = np.zeros(nparts, dtype=np.int64)
+    for p, s in enumerate(seeds):
+        part[s] = p
+        size[p] = 1
+        fronts.append([s])
+    active = True
+    while active:
+        active = False
+        for p in range(nparts):
+            if size[p] >= target[p] or not fronts[p]:
+                continue
+            newf = []
+            grown = False
+            for e in fronts[p]:
+                for q in nb[e]:
+                    if part[q] < 0 and size[p] < target[p]:
+                        part[q] = p
+                        size[p] += 1
+                        newf.append(q)
+                        grown = True
+            fronts[p] = newf
+            active = active or grown
+    while (part < 0).any():
+        changed = False
+        for e in np.nonzero(part < 0)[0]:
+            cand = [part[q] for q in nb[e] if part[q] >= 0]
+            if cand:
+                p = min(cand, key=lambda c: (size[c], c))
+                part[e] = p
+                size[p] += 1
+                changed = True
+        if not changed:
+            break
+    # merge disconnected pieces into a neighbour
+    for p in range(nparts):
+        members = np.nonzero(part == p)[0]
+        if len(members) == 0:
+            continue
+        seen = {}
+        comps = []
+        for e in members:
+            if e in seen:
+                continue
+            comp = [e]
+            seen[e] = True
+            stack = [e]
+            while stack:
+                x = stack.pop()
+                for q in nb[x]:
+                    if part[q] == p and q not in seen:
+                        seen[q] = True
+                        comp.append(q)
+                        stack.append(q)
+            comps.append(comp)
+        if len(comps) > 1:
+            comps.sort(key=len, reverse=True)
+            for comp in comps[1:]:
+                cand = [part[q] for x in comp for q in nb[x] if part[q] != p]
+                r = min(cand, key=lambda c: (size[c], c))
+                for x in comp:
+                    part[x] = r
+                size[r] += len(comp)
+                size[p] -= len(comp)
+    # relabel to consecutive ids
+    used = np.unique(part)
+    remap = -np.ones(nparts, dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    return remap[part].astype(np.int32)
