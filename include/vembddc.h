@@ -1,0 +1,129 @@
+/*
+ * vembddc -- BDDC-preconditioned CG for the divergence-free virtual element
+ * discretization of the 3D Stokes equations, on one GPU (sm_103a).
+ *
+ * Method: T. Bevilacqua, F. Dassi, S. Zampini, S. Scacchi, "BDDC
+ * preconditioners for virtual element approximations of the
+ * three-dimensional Stokes equations".  Section, equation and table names
+ * below refer to that paper.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Status: every call returns a vem_status (0 = success, < 0 = error); no call
+ * aborts, traps or exits.  vem_last_error() returns a message for the last
+ * failure in the calling thread.
+ *
+ * Pointers: "host" arrays are read during the call only and copied; the
+ * library never keeps them.  "device" arrays are caller-owned CUDA device
+ * memory (for example torch tensors) that must stay valid for the call; the
+ * library works on the stream set with vem_set_stream (default: the legacy
+ * default stream) and returns once its work on that stream is enqueued,
+ * except where a call says it synchronizes.
+ *
+ * Global DOF order (Sec. 3, DOFs D1-D5; one number per velocity component):
+ *   vertex v            : 3 v + c                                   (D1)
+ *   edge e, point j     : nV*3 + (e*(k-1) + j)*3 + c                (D2)
+ *   face f, monomial b  : off_f + (f*dim P_{k-2}(2D) + b)*3 + t     (D3)
+ *   element K           : off_k + K*(n4+n5) + (D4 then D5)          (D4,D5)
+ * with c = x,y,z; t = 0 normal, 1 first tangent, 2 second tangent.
+ * Edges are numbered in order of first appearance when the face loops are
+ * read face by face; edge points are the interior Gauss-Lobatto nodes,
+ * ordered from the lower-numbered vertex.  Face frames: n = the face's
+ * global normal (loop orientation), t1 = unit first loop edge, t2 = n x t1;
+ * moments are averages (1/|f|) int over the face against the scaled
+ * monomials of P_{k-2} in the face frame centred at the vertex average.
+ * D4: averages (1/|K|) int v . (xi ^ m_b e_c), xi = (x - x_K)/h_K (x_K the
+ * vertex average, h_K the diameter), b over P_{k-3} and c = x,y,z, graded
+ * monomial order, minus the dependent generator (b = xi_3, c = z) at k = 4.
+ * D5: averages (1/|K|) int div v m_a for the scaled monomials of degree
+ * 1..k-1.  Pressure: per element, the coefficients of the scaled monomials
+ * of P_{k-1}(K).  Vectors passed to the solver calls ("system vectors")
+ * hold the free (non-Dirichlet) velocity DOFs in increasing global order,
+ * then all element pressures (element-major).
+ */
+#ifndef VEMBDDC_H
+#define VEMBDDC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VEM_OK = 0,
+  VEM_EINVAL = -1,     /* bad argument (null pointer, size, mesh topology) */
+  VEM_ENOMEM = -2,     /* device or host allocation failed */
+  VEM_ECUDA = -3,      /* a CUDA call failed */
+  VEM_ESINGULAR = -4,  /* zero or wrong-signed pivot in a local or coarse factorization */
+  VEM_EBREAKDOWN = -5, /* CG breakdown (p^T S p <= 0 or a non-finite value) */
+  VEM_ENOTCONV = -6,   /* CG reached maxit above rtol */
+  VEM_ETIMEOUT = -7    /* a bounded device wait gave up */
+} vem_status;
+
+/* Polyhedral mesh (Sec. 3, "Mesh construction").  All host arrays.
+ * Faces are planar vertex loops; a loop's orientation fixes the face's
+ * global normal.  elem_face holds +(f+1) when the global normal of face f
+ * points out of the element and -(f+1) otherwise. */
+typedef struct {
+  int32_t nV;
+  const double* xyz;        /* [nV*3] */
+  int32_t nF;
+  const int32_t* face_ptr;  /* [nF+1] */
+  const int32_t* face_vtx;  /* [face_ptr[nF]] */
+  int32_t nE;
+  const int32_t* elem_ptr;  /* [nE+1] */
+  const int32_t* elem_face; /* [elem_ptr[nE]] signed, 1-based */
+} vem_mesh;
+
+typedef struct vem_system vem_system;
+typedef struct bddc bddc;
+
+/* Builds the VEM discretization of degree k (2 <= k <= 4) of the Stokes
+ * problem with homogeneous Dirichlet velocity on the boundary (Eq.
+ * DiscProblem): per-element projectors and local matrices on the GPU
+ * (Eq. discreteA with nu_K as factor, B_K exact from the DOFs) and the global
+ * CSR matrix K = [A B^T; B 0] over the free velocity DOFs and all element
+ * pressures (Eq. MatrixForm).  nu_per_element: host [nE].  Synchronizes. */
+int vem_assemble(const vem_mesh* mesh, int k, const double* nu_per_element, vem_system** out);
+
+/* Sizes: free velocity DOFs, element pressures, all velocity DOFs. */
+int vem_dof_layout(const vem_system* sys, int64_t* n_vel_free, int64_t* n_press, int64_t* n_vel_all);
+
+/* Host copy of the map free-velocity index -> global velocity DOF number. */
+int vem_free_dofs(const vem_system* sys, int64_t* free_to_global /* host [n_vel_free] */);
+
+/* Quadrature points of the load rule of exactness `degree` (collapsed Gauss
+ * product rule with (degree+3)/2+1 points per direction on each tetrahedron
+ * (x_K, face fan triangle); point order: element, face, fan triangle, then
+ * the rule's points).  With xyz_out == NULL only *n is set.  xyz_out: host
+ * [n*3]. */
+int vem_quad_points(vem_system* sys, int degree, int64_t* n, double* xyz_out);
+
+/* Load vector (Eq. discreteF): rhs = [int Pi^0_k f . phi_i ; 0] over the
+ * system vector layout, from f sampled at the points of vem_quad_points with
+ * the same degree.  f_at_quad: host [n*3]; rhs_dev: device [n_free+n_press]. */
+int vem_load(vem_system* sys, int degree, const double* f_at_quad, double* rhs_dev);
+
+/* y = K x over the system vector layout (Eq. MatrixForm).  Device arrays. */
+int vem_apply(vem_system* sys, const double* x_dev, double* y_dev);
+
+/* Test access: copies the local matrices of `count` elements to the host.
+ * A: [count * nK * nK] row-major (nK = velocity DOFs of the element, in
+ * the order vertices (increasing), edges (increasing), faces (element
+ * order), D4, D5); B: [count * nP * nK]; dofs: [count * nK] global velocity
+ * numbers.  Elements must all have the same nK (returned in *nK). */
+int vem_element_matrices(vem_system* sys, const int32_t* elems, int32_t count, int32_t* nK,
+                         double* A, double* B, int64_t* dofs);
+
+/* Test access: CSR of K (system layout).  With vals == NULL only sizes. */
+int vem_csr(vem_system* sys, int64_t* n, int64_t* nnz, int64_t* row_ptr, int32_t* col, double* vals);
+
+int vem_set_stream(vem_system* sys, void* cuda_stream);
+void vem_free(vem_system* sys);
+const char* vem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,888 @@
+// Per-element VEM construction (Sec. 3): face projectors Pi^nabla_{k,f},
+// Pi^0_{k+1,f} (Eq. faceSpace), element divergence, Pi^nabla_{k,K},
+// Pi^0_{k-1} grad, Pi^0_k (Eq. velSpace), the local stiffness
+// a_h^K = consistency + stabilization (Eq. discreteA) and B_K.
+//
+// One cooperating group of `nt` threads (a CTA) builds one element.  The
+// body is written against a tiny execution interface (thread id, count,
+// barrier) so that it also runs with a single host thread.
+//
+// Polynomial facts used (all in scaled monomials xi = (x - x_K)/h_K):
+//  * any homogeneous w in [P_d]^3 splits as
+//      w = grad( (xi.w)/(d+1) ) - xi ^ (curl w)/(d+1),
+//    which gives the moments int v.w from divergence/boundary data and from
+//    moments against xi ^ [P_{d-1}]^3 (D4 for d-1 <= k-3, enhancement of
+//    Eq. velSpace for d-1 in {k-2, k-1});
+//  * int_K v.grad q = -int_K div v q + int_dK (v.n) q, and boundary traces are
+//    replaced by Pi^0_{k+1,f} v on each face (exact against P_{k+1}(f)).
+#pragma once
+#include <cmath>
+#include "common.h"
+#include "system.h"
+
+#ifdef __CUDACC__
+#define VB_HD __host__ __device__
+#else
+#define VB_HD
+#endif
+
+namespace vb {
+
+struct Exec {
+  int tid, nt;
+#ifdef __CUDA_ARCH__
+  __device__ void sync() const { __syncthreads(); }
+#else
+  VB_HD void sync() const {}
+#endif
+};
+
+// element-independent tables (quadrature rules, monomial exponents)
+struct ElemTables {
+  Exp3 e3[kMaxMono3];
+  Exp2 e2[kMaxMono2];
+  double gl[4];            // interior Gauss-Lobatto nodes (k-1 used)
+  int nq_edge;
+  double qe_x[8], qe_w[8];     // edge rule on [0,1]
+  int nq_face;
+  double qf_x[8], qf_w[8];     // 1D Gauss nodes for the collapsed triangle rule
+  int nq_vol;
+  double qv_x[8], qv_w[8];     // 1D Gauss nodes for the collapsed tetrahedron rule
+};
+
+template <int K>
+struct ElemSizes {
+  static constexpr int NP0 = pdim3(K - 1);     // pressure / divergence space
+  static constexpr int NP1 = pdim3(K);
+  static constexpr int NP2 = pdim3(K + 1);
+  static constexpr int NMOM = pdim3(2 * K);    // volume moments needed
+  static constexpr int NF1 = pdim2(K);
+  static constexpr int NF2 = pdim2(K + 1);
+  static constexpr int NFM = pdim2(K - 2);
+  static constexpr int NFMOM = pdim2(2 * K + 2);
+  static constexpr int NL = pdim3(K - 2);
+  static constexpr int NQ3 = pdim3(K - 3);
+  static constexpr int N4 = n_d4(K);
+  static constexpr int N5 = n_d5(K);
+  static constexpr int NSMAX = kMaxFaceVerts * K + NFM;   // face-local DOFs per component
+};
+
+// shared (fast) working set of one element
+template <int K>
+struct ElemShared {
+  using S = ElemSizes<K>;
+  double X[kMaxElemVerts][3];
+  double xK[3], hK, vol;
+  double fn[kMaxElemFaces][3], ft1[kMaxElemFaces][3], ft2[kMaxElemFaces][3], fxc[kMaxElemFaces][3];
+  double fh[kMaxElemFaces], farea[kMaxElemFaces];
+  double mu[S::NMOM];
+  double Minv0[S::NP0 * S::NP0];   // inverse mass on P_{k-1}
+  double Minv1[S::NP1 * S::NP1];   // inverse mass on P_k
+  double Ginv[S::NP1 * S::NP1];    // inverse of the Pi^nabla_k system
+  double bndm[S::NP1];             // int_dK m_g
+  double big[S::NP1 * S::NP1];     // temporary for the inversions
+  // per-face work
+  double nu2[S::NFMOM];
+  double G2[S::NF1 * S::NF1];
+  double MF[S::NF2 * S::NF2];
+  double W[S::NP2 * S::NF2];
+  double PiN[S::NF1 * S::NSMAX];
+  double Pi0[S::NF2 * S::NSMAX];
+  double rhs[S::NF2 * S::NSMAX];
+  double red[256];
+};
+
+// global scratch layout of one element (sizes in doubles)
+template <int K>
+struct ElemScratch {
+  using S = ElemSizes<K>;
+  static VB_HD size_t face_block() { return (size_t)S::NP2 * S::NSMAX; }
+  static VB_HD size_t size(int nK) {
+    return kMaxElemFaces * face_block() + (size_t)nK *
+               (S::NP0 + S::NP2 + 3 * S::NL + 3 * S::NP1 + 12 * S::NP0 + 3 * S::NP1 + 3 * S::NP1) +
+           2 * (size_t)nK * nK;
+  }
+};
+
+VB_HD inline void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+VB_HD inline double ipow(double x, int p) {
+  double r = 1.0;
+  for (int i = 0; i < p; ++i) r *= x;
+  return r;
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting of an n x n row-major
+// matrix (one thread).  Returns false on a zero pivot.
+VB_HD inline bool small_inverse(double* M, double* Inv, int n) {
+  for (int i = 0; i < n * n; ++i) Inv[i] = 0.0;
+  for (int i = 0; i < n; ++i) Inv[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    double best = M[c * n + c] < 0 ? -M[c * n + c] : M[c * n + c];
+    for (int r = c + 1; r < n; ++r) {
+      double v = M[r * n + c] < 0 ? -M[r * n + c] : M[r * n + c];
+      if (v > best) { best = v; p = r; }
+    }
+    if (best == 0.0) return false;
+    if (p != c)
+      for (int j = 0; j < n; ++j) {
+        double t = M[c * n + j]; M[c * n + j] = M[p * n + j]; M[p * n + j] = t;
+        t = Inv[c * n + j]; Inv[c * n + j] = Inv[p * n + j]; Inv[p * n + j] = t;
+      }
+    double d = 1.0 / M[c * n + c];
+    for (int j = 0; j < n; ++j) { M[c * n + j] *= d; Inv[c * n + j] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = M[r * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) { M[r * n + j] -= f * M[c * n + j]; Inv[r * n + j] -= f * Inv[c * n + j]; }
+    }
+  }
+  return true;
+}
+
+template <int K>
+struct ElemBuilder {
+  using S = ElemSizes<K>;
+  const ElemRec& R;
+  const double* xyz;
+  const ElemTables& T;
+  ElemShared<K>& sh;
+  double* scr;
+  int nK;
+  int off_e, off_f, off_4, off_5;
+  Exec ex;
+  // scratch views
+  double *Y, *DIV, *GM, *VML, *PiN, *Rs, *E, *VMH, *Dm, *Pm;
+
+  VB_HD ElemBuilder(const ElemRec& r, const double* x, const ElemTables& t, ElemShared<K>& s, double* sc, Exec e)
+      : R(r), xyz(x), T(t), sh(s), scr(sc), ex(e) {
+    nK = R.nK;
+    off_e = 3 * R.nv;
+    off_f = off_e + R.ne * 3 * (K - 1);
+    off_4 = off_f + R.nf * 3 * S::NFM;
+    off_5 = off_4 + S::N4;
+    size_t o = 0;
+    Y = scr + o;   o += kMaxElemFaces * ElemScratch<K>::face_block();
+    DIV = scr + o; o += (size_t)S::NP0 * nK;
+    GM = scr + o;  o += (size_t)S::NP2 * nK;
+    VML = scr + o; o += (size_t)3 * S::NL * nK;
+    PiN = scr + o; o += (size_t)3 * S::NP1 * nK;
+    Rs = scr + o;  o += (size_t)6 * S::NP0 * nK;
+    E = scr + o;   o += (size_t)6 * S::NP0 * nK;
+    VMH = scr + o; o += (size_t)3 * S::NP1 * nK;
+    Dm = scr + o;  o += (size_t)3 * S::NP1 * nK;
+    Pm = scr + o;  o += (size_t)2 * nK * nK;
+  }
+
+  VB_HD double mu(int a, int b, int c) const { return sh.mu[idx3(a, b, c)]; }
+  // int_K m_p m_q
+  VB_HD double mass(int p, int q) const {
+    const Exp3 &A = T.e3[p], &B = T.e3[q];
+    return mu(A.a + B.a, A.b + B.b, A.c + B.c);
+  }
+  VB_HD int ns(int f) const { return R.fnv[f] * K + S::NFM; }
+
+  // ---------------------------------------------------------------- geometry
+  VB_HD void geometry() {
+    if (ex.tid == 0) {
+      double c[3] = {0, 0, 0};
+      for (int i = 0; i < R.nv; ++i)
+        for (int d = 0; d < 3; ++d) {
+          sh.X[i][d] = xyz[3 * R.vert[i] + d];
+          c[d] += sh.X[i][d];
+        }
+      for (int d = 0; d < 3; ++d) sh.xK[d] = c[d] / R.nv;
+      double h2 = 0;
+      for (int i = 0; i < R.nv; ++i)
+        for (int j = i + 1; j < R.nv; ++j) {
+          double s = 0;
+          for (int d = 0; d < 3; ++d) s += (sh.X[i][d] - sh.X[j][d]) * (sh.X[i][d] - sh.X[j][d]);
+          h2 = s > h2 ? s : h2;
+        }
+      sh.hK = sqrt(h2);
+      for (int f = 0; f < R.nf; ++f) {
+        int m = R.fnv[f];
+        double nrm[3] = {0, 0, 0}, xc[3] = {0, 0, 0}, h2f = 0;
+        for (int i = 0; i < m; ++i) {
+          const double* a = sh.X[R.floopv[f][i]];
+          const double* b = sh.X[R.floopv[f][(i + 1) % m]];
+          double cr[3];
+          cross3(a, b, cr);
+          for (int d = 0; d < 3; ++d) { nrm[d] += cr[d]; xc[d] += a[d]; }
+          for (int j = i + 1; j < m; ++j) {
+            const double* bb = sh.X[R.floopv[f][j]];
+            double s = 0;
+            for (int d = 0; d < 3; ++d) s += (a[d] - bb[d]) * (a[d] - bb[d]);
+            h2f = s > h2f ? s : h2f;
+          }
+        }
+        double ln = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        sh.farea[f] = 0.5 * ln;
+        sh.fh[f] = sqrt(h2f);
+        const double* p0 = sh.X[R.floopv[f][0]];
+        const double* p1 = sh.X[R.floopv[f][1]];
+        double t1[3], dd = 0;
+        for (int d = 0; d < 3; ++d) { sh.fn[f][d] = nrm[d] / ln; t1[d] = p1[d] - p0[d]; }
+        for (int d = 0; d < 3; ++d) dd += t1[d] * sh.fn[f][d];
+        double lt = 0;
+        for (int d = 0; d < 3; ++d) { t1[d] -= dd * sh.fn[f][d]; lt += t1[d] * t1[d]; }
+        lt = sqrt(lt);
+        for (int d = 0; d < 3; ++d) { sh.ft1[f][d] = t1[d] / lt; sh.fxc[f][d] = xc[d] / m; }
+        cross3(sh.fn[f], sh.ft1[f], sh.ft2[f]);
+      }
+    }
+    ex.sync();
+  }
+
+  // ------------------------------------------------ volume moments mu_a = int xi^a
+  VB_HD void volume_moments() {
+    const int nq = T.nq_vol;
+    double hinv = 1.0 / sh.hK;
+    for (int a = ex.tid; a < S::NMOM; a += ex.nt) {
+      const Exp3 ea = T.e3[a];
+      double acc = 0.0;
+      for (int f = 0; f < R.nf; ++f) {
+        int m = R.fnv[f];
+        // outward loop: reverse when the global normal points inwards
+        for (int t = 1; t < m - 1; ++t) {
+          int i0 = 0, i1 = t, i2 = t + 1;
+          if (R.fsign[f] < 0) { i0 = m - 1; i1 = m - 1 - t; i2 = m - 2 - t; }
+          const double* A = sh.X[R.floopv[f][i0]];
+          const double* B = sh.X[R.floopv[f][i1]];
+          const double* C = sh.X[R.floopv[f][i2]];
+          double a1[3], b1[3], c1[3];
+          for (int d = 0; d < 3; ++d) { a1[d] = A[d] - sh.xK[d]; b1[d] = B[d] - sh.xK[d]; c1[d] = C[d] - sh.xK[d]; }
+          double cr[3];
+          cross3(b1, c1, cr);
+          double det = a1[0] * cr[0] + a1[1] * cr[1] + a1[2] * cr[2];
+          for (int iu = 0; iu < nq; ++iu)
+            for (int iv = 0; iv < nq; ++iv)
+              for (int iw = 0; iw < nq; ++iw) {
+                double U = T.qv_x[iu], V = T.qv_x[iv], Wd = T.qv_x[iw];
+                double x = U, y = V * (1 - U), z = Wd * (1 - U) * (1 - V);
+                double w = T.qv_w[iu] * T.qv_w[iv] * T.qv_w[iw] * (1 - U) * (1 - U) * (1 - V) * det;
+                double p[3];
+                for (int d = 0; d < 3; ++d) p[d] = (x * a1[d] + y * b1[d] + z * c1[d]) * hinv;
+                acc += w * ipow(p[0], ea.a) * ipow(p[1], ea.b) * ipow(p[2], ea.c);
+              }
+        }
+      }
+      sh.mu[a] = acc;
+    }
+    ex.sync();
+    if (ex.tid == 0) sh.vol = sh.mu[0];
+    ex.sync();
+  }
+
+  // inverse mass matrices and the Pi^nabla_k system
+  VB_HD bool volume_systems() {
+    double* tmp = sh.big;
+    bool ok = true;
+    if (ex.tid == 0) {
+      for (int p = 0; p < S::NP0; ++p)
+        for (int q = 0; q < S::NP0; ++q) tmp[p * S::NP0 + q] = mass(p, q);
+      ok = small_inverse(tmp, sh.Minv0, S::NP0);
+    }
+    ex.sync();
+    if (ex.tid == 0 && ok) {
+      for (int p = 0; p < S::NP1; ++p)
+        for (int q = 0; q < S::NP1; ++q) tmp[p * S::NP1 + q] = mass(p, q);
+      ok = small_inverse(tmp, sh.Minv1, S::NP1);
+    }
+    ex.sync();
+    return ok;
+  }
+
+  // ------------------------------------------------ faces
+  VB_HD bool face(int f) {
+    const int m = R.fnv[f];
+    const int nsf = ns(f);
+    const double hf = sh.fh[f], hfi = 1.0 / hf;
+    const double* xc = sh.fxc[f];
+    const double *t1 = sh.ft1[f], *t2 = sh.ft2[f];
+    // face quadrature (fan from loop vertex 0, collapsed Gauss); 2D moments
+    // nu_g = int_f s^g1 t^g2 and W[a][b] = int_f m3_a m2_b
+    const int nq = T.nq_face;
+    for (int idx = ex.tid; idx < S::NFMOM + S::NP2 * S::NF2; idx += ex.nt) {
+      int g1 = 0, g2 = 0, a = -1, b = -1;
+      if (idx < S::NFMOM) { g1 = T.e2[idx].a; g2 = T.e2[idx].b; }
+      else { a = (idx - S::NFMOM) / S::NF2; b = (idx - S::NFMOM) % S::NF2; }
+      double acc = 0.0;
+      const double* P0 = sh.X[R.floopv[f][0]];
+      for (int t = 1; t < m - 1; ++t) {
+        const double* P1 = sh.X[R.floopv[f][t]];
+        const double* P2 = sh.X[R.floopv[f][t + 1]];
+        double u1[3], u2[3], cr[3];
+        for (int d = 0; d < 3; ++d) { u1[d] = P1[d] - P0[d]; u2[d] = P2[d] - P0[d]; }
+        cross3(u1, u2, cr);
+        double J = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        for (int iu = 0; iu < nq; ++iu)
+          for (int iv = 0; iv < nq; ++iv) {
+            double U = T.qf_x[iu], V = T.qf_x[iv] * (1 - U);
+            double w = T.qf_w[iu] * T.qf_w[iv] * (1 - U) * J;
+            double x[3];
+            for (int d = 0; d < 3; ++d) x[d] = P0[d] + U * u1[d] + V * u2[d];
+            double dx[3] = {x[0] - xc[0], x[1] - xc[1], x[2] - xc[2]};
+            double s = (dx[0] * t1[0] + dx[1] * t1[1] + dx[2] * t1[2]) * hfi;
+            double tt = (dx[0] * t2[0] + dx[1] * t2[1] + dx[2] * t2[2]) * hfi;
+            if (a < 0) {
+              acc += w * ipow(s, g1) * ipow(tt, g2);
+            } else {
+              const Exp3 ea = T.e3[a];
+              const Exp2 eb = T.e2[b];
+              double hk = 1.0 / sh.hK;
+              double px = (x[0] - sh.xK[0]) * hk, py = (x[1] - sh.xK[1]) * hk, pz = (x[2] - sh.xK[2]) * hk;
+              acc += w * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c) * ipow(s, eb.a) * ipow(tt, eb.b);
+            }
+          }
+      }
+      if (a < 0) sh.nu2[idx] = acc;
+      else sh.W[a * S::NF2 + b] = acc;
+    }
+    ex.sync();
+    // Pi^nabla_{k,f}: G2 c = rhs, rows b >= 1: int grad m_b . grad m_g;
+    // row 0: int_df m_g.  rhs: -int Lap m_b v + sum_e int_e d_n m_b v; row 0 int_df v
+    for (int idx = ex.tid; idx < S::NF1 * S::NF1; idx += ex.nt) {
+      int b = idx / S::NF1, g = idx % S::NF1;
+      const Exp2 eb = T.e2[b], eg = T.e2[g];
+      double v = 0.0;
+      if (b > 0) {
+        if (eb.a > 0 && eg.a > 0) v += eb.a * eg.a * sh.nu2[idx2(eb.a + eg.a - 2, eb.b + eg.b)];
+        if (eb.b > 0 && eg.b > 0) v += eb.b * eg.b * sh.nu2[idx2(eb.a + eg.a, eb.b + eg.b - 2)];
+        v *= hfi * hfi;
+      }
+      sh.G2[idx] = v;
+    }
+    for (int idx = ex.tid; idx < S::NF1 * nsf; idx += ex.nt) sh.rhs[idx] = 0.0;
+    ex.sync();
+    if (ex.tid == 0) {
+      // interior moments: -int_f Lap m_b v = -|f| sum_g L[g][b] s_g
+      for (int b = 1; b < S::NF1; ++b) {
+        const Exp2 eb = T.e2[b];
+        if (eb.a >= 2) sh.rhs[b * nsf + m * K + idx2(eb.a - 2, eb.b)] -= sh.farea[f] * eb.a * (eb.a - 1) * hfi * hfi;
+        if (eb.b >= 2) sh.rhs[b * nsf + m * K + idx2(eb.a, eb.b - 2)] -= sh.farea[f] * eb.b * (eb.b - 1) * hfi * hfi;
+      }
+      for (int g = 0; g < S::NF1; ++g) sh.G2[g] = 0.0;
+      // edges: Gauss points, Lagrange basis on (0, interior GL nodes, 1)
+      double nodes[K + 1];
+      nodes[0] = 0.0;
+      for (int j = 0; j < K - 1; ++j) nodes[1 + j] = T.gl[j];
+      nodes[K] = 1.0;
+      for (int i = 0; i < m; ++i) {
+        const double* A = sh.X[R.floopv[f][i]];
+        const double* B = sh.X[R.floopv[f][(i + 1) % m]];
+        double dvec[3], le = 0;
+        for (int d = 0; d < 3; ++d) { dvec[d] = B[d] - A[d]; le += dvec[d] * dvec[d]; }
+        le = sqrt(le);
+        double du[3] = {dvec[0] / le, dvec[1] / le, dvec[2] / le};
+        double ne[3];
+        cross3(du, sh.fn[f], ne);
+        double n1 = ne[0] * t1[0] + ne[1] * t1[1] + ne[2] * t1[2];
+        double n2 = ne[0] * t2[0] + ne[1] * t2[1] + ne[2] * t2[2];
+        int sidx[K + 1];
+        sidx[0] = i;
+        for (int j = 0; j < K - 1; ++j) sidx[1 + j] = m + i * (K - 1) + j;
+        sidx[K] = (i + 1) % m;
+        for (int q = 0; q < T.nq_edge; ++q) {
+          double tq = T.qe_x[q], wq = T.qe_w[q] * le;
+          double x[3];
+          for (int d = 0; d < 3; ++d) x[d] = A[d] + tq * dvec[d];
+          double dx[3] = {x[0] - xc[0], x[1] - xc[1], x[2] - xc[2]};
+          double s = (dx[0] * t1[0] + dx[1] * t1[1] + dx[2] * t1[2]) * hfi;
+          double tt = (dx[0] * t2[0] + dx[1] * t2[1] + dx[2] * t2[2]) * hfi;
+          double lag[K + 1];
+          for (int aa = 0; aa <= K; ++aa) {
+            double l = 1.0;
+            for (int bb = 0; bb <= K; ++bb)
+              if (bb != aa) l *= (tq - nodes[bb]) / (nodes[aa] - nodes[bb]);
+            lag[aa] = l;
+          }
+          for (int b = 0; b < S::NF1; ++b) {
+            const Exp2 eb = T.e2[b];
+            double mb = ipow(s, eb.a) * ipow(tt, eb.b);
+            if (b == 0) {
+              for (int aa = 0; aa <= K; ++aa) sh.rhs[sidx[aa]] += wq * lag[aa];
+            } else {
+              double ds = eb.a > 0 ? eb.a * ipow(s, eb.a - 1) * ipow(tt, eb.b) : 0.0;
+              double dt = eb.b > 0 ? eb.b * ipow(s, eb.a) * ipow(tt, eb.b - 1) : 0.0;
+              double dn = (ds * n1 + dt * n2) * hfi;
+              for (int aa = 0; aa <= K; ++aa) sh.rhs[b * nsf + sidx[aa]] += wq * dn * lag[aa];
+            }
+            sh.G2[b] += wq * mb;     // row 0 of G2: int_df m_b
+          }
+        }
+      }
+    }
+    ex.sync();
+    // solve (one thread inverts; all apply)
+    double* G2inv = sh.MF;   // borrowed until the face mass is formed
+    bool ok = true;
+    if (ex.tid == 0) ok = small_inverse(sh.G2, G2inv, S::NF1);
+    ex.sync();
+    for (int idx = ex.tid; idx < S::NF1 * nsf; idx += ex.nt) {
+      int b = idx / nsf, s = idx % nsf;
+      double acc = 0.0;
+      for (int g = 0; g < S::NF1; ++g) acc += G2inv[b * S::NF1 + g] * sh.rhs[g * nsf + s];
+      sh.PiN[idx] = acc;
+    }
+    ex.sync();
+    // Pi^0_{k+1,f}: face mass; rhs rows < NFM from the moments, others from Pi^nabla
+    double* MFm = sh.rhs;    // rhs consumed: reuse for the face mass
+    for (int idx = ex.tid; idx < S::NF2 * S::NF2; idx += ex.nt) {
+      int b = idx / S::NF2, g = idx % S::NF2;
+      MFm[idx] = sh.nu2[idx2(T.e2[b].a + T.e2[g].a, T.e2[b].b + T.e2[g].b)];
+    }
+    ex.sync();
+    if (ex.tid == 0) ok = ok && small_inverse(MFm, sh.MF, S::NF2);
+    ex.sync();
+    // rhs for Pi^0 into Pi0 (temporarily), then multiply by MF^{-1} into rhs
+    for (int idx = ex.tid; idx < S::NF2 * nsf; idx += ex.nt) {
+      int b = idx / nsf, s = idx % nsf;
+      double v = 0.0;
+      if (b < S::NFM) {
+        v = (s == m * K + b) ? sh.farea[f] : 0.0;
+      } else {
+        for (int g = 0; g < S::NF1; ++g)
+          v += sh.nu2[idx2(T.e2[b].a + T.e2[g].a, T.e2[b].b + T.e2[g].b)] * sh.PiN[g * nsf + s];
+      }
+      sh.Pi0[idx] = v;
+    }
+    ex.sync();
+    for (int idx = ex.tid; idx < S::NF2 * nsf; idx += ex.nt) {
+      int b = idx / nsf, s = idx % nsf;
+      double acc = 0.0;
+      for (int g = 0; g < S::NF2; ++g) acc += sh.MF[b * S::NF2 + g] * sh.Pi0[g * nsf + s];
+      sh.rhs[idx] = acc;
+    }
+    ex.sync();
+    // Y_f = W Pi0_f : int_f m3_a (Pi^0_{k+1,f} v)  for a in P_{k+1}
+    double* Yf = Y + (size_t)f * ElemScratch<K>::face_block();
+    for (int idx = ex.tid; idx < S::NP2 * nsf; idx += ex.nt) {
+      int a = idx / nsf, s = idx % nsf;
+      double acc = 0.0;
+      for (int b = 0; b < S::NF2; ++b) acc += sh.W[a * S::NF2 + b] * sh.rhs[b * nsf + s];
+      Yf[idx] = acc;
+    }
+    // int_f m3_g for g in P_k (row 0 of the Pi^nabla_K system)
+    if (ex.tid == 0) {
+      for (int g = 0; g < S::NP1; ++g) sh.bndm[g] += sh.W[g * S::NF2 + 0];
+    }
+    ex.sync();
+    return ok;
+  }
+
+  // boundary functional entry: column `col` of  int_dK v_c m_a (n_j)  (j < 0: no normal)
+  VB_HD double bnd(int col, int c, int a, int j) const {
+    double acc = 0.0;
+    // decode the entity of col
+    if (col < off_e) {
+      int lv = col / 3, cc = col % 3;
+      if (cc != c) return 0.0;
+      for (int f = 0; f < R.nf; ++f) {
+        int m = R.fnv[f];
+        for (int i = 0; i < m; ++i)
+          if (R.floopv[f][i] == lv) {
+            double cf = j < 0 ? 1.0 : R.fsign[f] * sh.fn[f][j];
+            acc += cf * Y[(size_t)f * ElemScratch<K>::face_block() + a * ns(f) + i];
+          }
+      }
+      return acc;
+    }
+    if (col < off_f) {
+      int r = col - off_e;
+      int le = r / (3 * (K - 1));
+      int jj = (r / 3) % (K - 1), cc = r % 3;
+      if (cc != c) return 0.0;
+      for (int f = 0; f < R.nf; ++f) {
+        int m = R.fnv[f];
+        for (int i = 0; i < m; ++i)
+          if (R.floope[f][i] == le) {
+            int jt = R.floopdir[f][i] ? jj : (K - 2 - jj);
+            double cf = j < 0 ? 1.0 : R.fsign[f] * sh.fn[f][j];
+            acc += cf * Y[(size_t)f * ElemScratch<K>::face_block() + a * ns(f) + m + i * (K - 1) + jt];
+          }
+      }
+      return acc;
+    }
+    if (col < off_4) {
+      int r = col - off_f;
+      int f = r / (3 * S::NFM);
+      int b = (r / 3) % S::NFM, t = r % 3;
+      double wv = t == 0 ? sh.fn[f][c] : (t == 1 ? sh.ft1[f][c] : sh.ft2[f][c]);
+      double cf = j < 0 ? 1.0 : R.fsign[f] * sh.fn[f][j];
+      return cf * wv * Y[(size_t)f * ElemScratch<K>::face_block() + a * ns(f) + R.fnv[f] * K + b];
+    }
+    return 0.0;
+  }
+
+  // D4 functional: column pattern of  int_K v . (xi ^ (m_b e_i)), b in P_{k-3}
+  // (dependent generator (xi_3, z) at k = 4 replaced by minus the other two)
+  VB_HD double d4(int col, int b, int i) const {
+    if (col < off_4 || col >= off_5) return 0.0;
+    int jcol = col - off_4;
+    int g = b * 3 + i;
+    if (K == 4 && g == 3 * 3 + 2) {
+      // -(g(xi_1, x) + g(xi_2, y)) : generators 3*1+0 and 3*2+1
+      double v = 0.0;
+      if (jcol == 3) v -= 1.0;
+      if (jcol == 7) v -= 1.0;
+      return v * sh.vol;
+    }
+    return (jcol == g) ? sh.vol : 0.0;
+  }
+
+  // moment of v against xi ^ (m_b e_i) for deg(b) >= k-2 via Pi^nabla (enhancement)
+  VB_HD double enh(int col, int b, int i) const {
+    // (xi ^ e_i m_b)_comp = eps(comp, j, i) xi_j m_b
+    double acc = 0.0;
+    for (int comp = 0; comp < 3; ++comp)
+      for (int jd = 0; jd < 3; ++jd) {
+        int eps = 0;
+        if (comp == jd || jd == i || comp == i) continue;
+        eps = ((comp + 1) % 3 == jd) ? 1 : -1;   // cyclic (comp, jd, i)
+        const Exp3 eb = T.e3[b];
+        for (int g = 0; g < S::NP1; ++g) {
+          const Exp3 eg = T.e3[g];
+          int ea = eg.a + eb.a + (jd == 0), ebb = eg.b + eb.b + (jd == 1), ec = eg.c + eb.c + (jd == 2);
+          acc += eps * PiN[((size_t)comp * S::NP1 + g) * nK + col] * mu(ea, ebb, ec);
+        }
+      }
+    return acc;
+  }
+
+  // int_K v . (m_b e_c) for the vector monomial of degree d = |b|, column col
+  VB_HD double vecmom(int col, int c, int b, bool use_enh) const {
+    const Exp3 eb = T.e3[b];
+    int d = eb.a + eb.b + eb.c;
+    double hK = sh.hK;
+    // gradient part: Q = xi_c m_b / (d+1);  int v . grad_xi Q = h int v . grad_x Q
+    int qa = eb.a + (c == 0), qb = eb.b + (c == 1), qc = eb.c + (c == 2);
+    double acc = hK / (d + 1) * GM[(size_t)idx3(qa, qb, qc) * nK + col];
+    if (d == 0) return acc;
+    // curl part: R = -(grad m_b x e_c)/(d+1), components R_i = -(1/(d+1)) eps(i,j,c) d_j m_b
+    for (int i = 0; i < 3; ++i)
+      for (int jd = 0; jd < 3; ++jd) {
+        if (i == jd || jd == c || i == c) continue;
+        int eps = ((i + 1) % 3 == jd) ? 1 : -1;   // eps(i, jd, c) with c the third index
+        int pj = jd == 0 ? eb.a : (jd == 1 ? eb.b : eb.c);
+        if (pj == 0) continue;
+        int ra = eb.a - (jd == 0), rb = eb.b - (jd == 1), rc = eb.c - (jd == 2);
+        int rb_idx = idx3(ra, rb, rc);
+        double coef = -(double)eps * pj / (d + 1);
+        double mom;
+        if (d - 1 <= K - 3) mom = d4(col, rb_idx, i);
+        else mom = use_enh ? enh(col, rb_idx, i) : 0.0;
+        acc += coef * mom;
+      }
+    return acc;
+  }
+
+  VB_HD bool build(double nu, double* Aout, double* Bout, double* P0out) {
+    geometry();
+    for (int g = ex.tid; g < S::NP1; g += ex.nt) sh.bndm[g] = 0.0;
+    ex.sync();
+    volume_moments();
+    bool ok = volume_systems();
+    for (int f = 0; f < R.nf; ++f) ok = face(f) && ok;
+    const double hK = sh.hK, vol = sh.vol;
+    // (1) divergence: mom rows -> DIV = Minv0 mom
+    for (int idx = ex.tid; idx < S::NP0 * nK; idx += ex.nt) {
+      int g = idx / nK, col = idx % nK;
+      double v = 0.0;
+      // mom row 0 : sum_f sgn |f| (normal D3, b = 0)
+      double m0 = 0.0;
+      if (col >= off_f && col < off_4) {
+        int r = col - off_f;
+        int f = r / (3 * S::NFM), b = (r / 3) % S::NFM, t = r % 3;
+        if (b == 0 && t == 0) m0 = R.fsign[f] * sh.farea[f];
+      }
+      v += sh.Minv0[g * S::NP0 + 0] * m0;
+      if (col >= off_5) v += sh.Minv0[g * S::NP0 + (col - off_5 + 1)] * vol;
+      DIV[idx] = v;
+    }
+    ex.sync();
+    // (2) GM[a] = int v . grad_x m_a  for a in P_{k+1}
+    for (int idx = ex.tid; idx < S::NP2 * nK; idx += ex.nt) {
+      int a = idx / nK, col = idx % nK;
+      // -int div v m_a
+      double v = 0.0;
+      for (int g = 0; g < S::NP0; ++g) v -= mass(g, a) * DIV[(size_t)g * nK + col];
+      for (int c = 0; c < 3; ++c) v += bnd(col, c, a, c);
+      GM[idx] = v;
+    }
+    ex.sync();
+    // note: GM holds int v.grad_x Q when multiplied by ... (grad_x m_a = (1/h) grad_xi m_a)
+    // vecmom uses h * int v . grad_x Q with Q in xi; int v.grad_x m_a as computed
+    // above is int v . grad_x (m_a(xi)) = (1/h) int v . grad_xi m_a -- consistent.
+    // (3) low moments (degree <= k-2), no enhancement
+    for (int idx = ex.tid; idx < 3 * S::NL * nK; idx += ex.nt) {
+      int c = idx / (S::NL * nK), r = idx % (S::NL * nK);
+      int b = r / nK, col = r % nK;
+      VML[idx] = vecmom(col, c, b, false);
+    }
+    ex.sync();
+    // (4) Pi^nabla_k : G c = rhs
+    if (ex.tid == 0) {
+      double* Gm = sh.big;
+      for (int p = 0; p < S::NP1; ++p)
+        for (int q = 0; q < S::NP1; ++q) {
+          double v = 0.0;
+          if (p == 0) v = sh.bndm[q];
+          else {
+            const Exp3 ep = T.e3[p], eq = T.e3[q];
+            if (ep.a && eq.a) v += ep.a * eq.a * mu(ep.a + eq.a - 2, ep.b + eq.b, ep.c + eq.c);
+            if (ep.b && eq.b) v += ep.b * eq.b * mu(ep.a + eq.a, ep.b + eq.b - 2, ep.c + eq.c);
+            if (ep.c && eq.c) v += ep.c * eq.c * mu(ep.a + eq.a, ep.b + eq.b, ep.c + eq.c - 2);
+            v /= hK * hK;
+          }
+          Gm[p * S::NP1 + q] = v;
+        }
+      ok = small_inverse(Gm, sh.Ginv, S::NP1) && ok;
+    }
+    ex.sync();
+    // rhs into VMH (temporary), then PiN = Ginv rhs
+    for (int idx = ex.tid; idx < 3 * S::NP1 * nK; idx += ex.nt) {
+      int c = idx / (S::NP1 * nK), r = idx % (S::NP1 * nK);
+      int a = r / nK, col = r % nK;
+      double v;
+      if (a == 0) {
+        v = bnd(col, c, 0, -1);
+      } else {
+        const Exp3 ea = T.e3[a];
+        v = 0.0;
+        // -int v_c Lap m_a, Lap_x m_a = (1/h^2) sum_j a_j (a_j - 1) m_{a - 2 e_j}
+        if (ea.a >= 2) v -= ea.a * (ea.a - 1) * VML[((size_t)c * S::NL + idx3(ea.a - 2, ea.b, ea.c)) * nK + col];
+        if (ea.b >= 2) v -= ea.b * (ea.b - 1) * VML[((size_t)c * S::NL + idx3(ea.a, ea.b - 2, ea.c)) * nK + col];
+        if (ea.c >= 2) v -= ea.c * (ea.c - 1) * VML[((size_t)c * S::NL + idx3(ea.a, ea.b, ea.c - 2)) * nK + col];
+        v /= hK * hK;
+        // + int_dK v_c grad m_a . n = (1/h) sum_j a_j int_dK v_c m_{a-e_j} n_j
+        if (ea.a) v += ea.a / hK * bnd(col, c, idx3(ea.a - 1, ea.b, ea.c), 0);
+        if (ea.b) v += ea.b / hK * bnd(col, c, idx3(ea.a, ea.b - 1, ea.c), 1);
+        if (ea.c) v += ea.c / hK * bnd(col, c, idx3(ea.a, ea.b, ea.c - 1), 2);
+      }
+      VMH[idx] = v;
+    }
+    ex.sync();
+    for (int idx = ex.tid; idx < 3 * S::NP1 * nK; idx += ex.nt) {
+      int c = idx / (S::NP1 * nK), r = idx % (S::NP1 * nK);
+      int a = r / nK, col = r % nK;
+      double acc = 0.0;
+      for (int g = 0; g < S::NP1; ++g) acc += sh.Ginv[a * S::NP1 + g] * VMH[((size_t)c * S::NP1 + g) * nK + col];
+      PiN[idx] = acc;
+    }
+    ex.sync();
+    // (5) Pi^0_{k-1} grad v, symmetrized: Rs_ij = (rhs_ij + rhs_ji)/2, E_ij = Minv0 Rs_ij
+    //     rhs_ij[a] = -(a_j/h) int v_i m_{a-e_j} + int_dK v_i m_a n_j
+    for (int idx = ex.tid; idx < 6 * S::NP0 * nK; idx += ex.nt) {
+      int pr = idx / (S::NP0 * nK), r = idx % (S::NP0 * nK);
+      int a = r / nK, col = r % nK;
+      const int PI[6] = {0, 1, 2, 0, 0, 1}, PJ[6] = {0, 1, 2, 1, 2, 2};
+      int i = PI[pr], j = PJ[pr];
+      const Exp3 ea = T.e3[a];
+      double v = 0.0;
+      for (int s = 0; s < 2; ++s) {
+        int ii = s ? j : i, jj = s ? i : j;
+        int pj = jj == 0 ? ea.a : (jj == 1 ? ea.b : ea.c);
+        if (pj > 0) {
+          int bidx = idx3(ea.a - (jj == 0), ea.b - (jj == 1), ea.c - (jj == 2));
+          v -= (double)pj / hK * VML[((size_t)ii * S::NL + bidx) * nK + col];
+        }
+        v += bnd(col, ii, a, jj);
+      }
+      Rs[idx] = 0.5 * v;
+    }
+    ex.sync();
+    for (int idx = ex.tid; idx < 6 * S::NP0 * nK; idx += ex.nt) {
+      int pr = idx / (S::NP0 * nK), r = idx % (S::NP0 * nK);
+      int a = r / nK, col = r % nK;
+      double acc = 0.0;
+      for (int g = 0; g < S::NP0; ++g) acc += sh.Minv0[a * S::NP0 + g] * Rs[((size_t)pr * S::NP0 + g) * nK + col];
+      E[idx] = acc;
+    }
+    ex.sync();
+    // (6) DOFs of the [P_k]^3 basis: Dm[row][c*NP1 + a]
+    const int nb = 3 * S::NP1;
+    for (int idx = ex.tid; idx < nK * nb; idx += ex.nt) {
+      int row = idx / nb, cb = idx % nb;
+      int c = cb / S::NP1, a = cb % S::NP1;
+      const Exp3 ea = T.e3[a];
+      double v = 0.0;
+      double hi = 1.0 / hK;
+      if (row < off_e) {
+        if (row % 3 == c) {
+          const double* X = sh.X[row / 3];
+          v = ipow((X[0] - sh.xK[0]) * hi, ea.a) * ipow((X[1] - sh.xK[1]) * hi, ea.b) * ipow((X[2] - sh.xK[2]) * hi, ea.c);
+        }
+      } else if (row < off_f) {
+        int r = row - off_e;
+        int le = r / (3 * (K - 1)), jj = (r / 3) % (K - 1), cc = r % 3;
+        if (cc == c) {
+          // edge from its lower vertex: vertices are stored sorted, so locate them
+          int a0 = R.edge_a[le], b0 = R.edge_b[le];
+          const double *PA = nullptr, *PB = nullptr;
+          for (int q = 0; q < R.nv; ++q) {
+            if (R.vert[q] == a0) PA = sh.X[q];
+            if (R.vert[q] == b0) PB = sh.X[q];
+          }
+          double t = T.gl[jj];
+          double x[3];
+          for (int d = 0; d < 3; ++d) x[d] = PA[d] + t * (PB[d] - PA[d]);
+          v = ipow((x[0] - sh.xK[0]) * hi, ea.a) * ipow((x[1] - sh.xK[1]) * hi, ea.b) * ipow((x[2] - sh.xK[2]) * hi, ea.c);
+        }
+      } else if (row < off_4) {
+        int r = row - off_f;
+        int f = r / (3 * S::NFM), b = (r / 3) % S::NFM, t = r % 3;
+        double wv = t == 0 ? sh.fn[f][c] : (t == 1 ? sh.ft1[f][c] : sh.ft2[f][c]);
+        // (1/|f|) int_f m3_a m2_b : recomputed from the face quadrature table W is
+        // per face and gone; use Y? no -- evaluate with the stored face moments
+        v = wv * facemom_(f, a, b) / sh.farea[f];
+      } else if (row < off_5) {
+        int jcol = row - off_4;
+        // generator number g (kept ones in order, the dropped one skipped)
+        int g = jcol;
+        if (K == 4 && g >= 11) g += 1;
+        int bb = g / 3, i = g % 3;
+        // (1/|K|) int m_a e_c . (xi ^ (m_bb e_i)) = (1/|K|) int m_a eps(c,j,i) xi_j m_bb
+        const Exp3 eb = T.e3[bb];
+        for (int jd = 0; jd < 3; ++jd) {
+          if (c == jd || jd == i || c == i) continue;
+          int eps = ((c + 1) % 3 == jd) ? 1 : -1;
+          v += eps * mu(ea.a + eb.a + (jd == 0), ea.b + eb.b + (jd == 1), ea.c + eb.c + (jd == 2));
+        }
+        v /= vol;
+      } else {
+        int al = row - off_5 + 1;
+        // (1/|K|) int div(m_a e_c) m_al = (1/|K|) (p_c/h) int m_{a-e_c} m_al
+        int pc = c == 0 ? ea.a : (c == 1 ? ea.b : ea.c);
+        if (pc > 0) {
+          const Exp3 el = T.e3[al];
+          v = pc * hi * mu(ea.a - (c == 0) + el.a, ea.b - (c == 1) + el.b, ea.c - (c == 2) + el.c) / vol;
+        }
+      }
+      Dm[idx] = v;
+    }
+    ex.sync();
+    // (7) consistency Ac = sum_ij Rs_ij^T E_ij (off-diagonal pairs twice), into Pm[nK*nK ..]
+    double* Ac = Pm + (size_t)nK * nK;
+    for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
+      int r = idx / nK, c = idx % nK;
+      double acc = 0.0;
+      for (int pr = 0; pr < 6; ++pr) {
+        double w = pr < 3 ? 1.0 : 2.0;
+        double s = 0.0;
+        for (int g = 0; g < S::NP0; ++g)
+          s += Rs[((size_t)pr * S::NP0 + g) * nK + r] * E[((size_t)pr * S::NP0 + g) * nK + c];
+        acc += w * s;
+      }
+      Ac[idx] = acc;
+    }
+    ex.sync();
+    // symmetrize the consistency part (rounding)
+    for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
+      int r = idx / nK, c = idx % nK;
+      if (r < c) {
+        double m = 0.5 * (Ac[(size_t)r * nK + c] + Ac[(size_t)c * nK + r]);
+        Ac[(size_t)r * nK + c] = m;
+        Ac[(size_t)c * nK + r] = m;
+      }
+    }
+    ex.sync();
+    // (8) P = I - Dm PiN
+    for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
+      int r = idx / nK, c = idx % nK;
+      double acc = (r == c) ? 1.0 : 0.0;
+      for (int q = 0; q < nb; ++q) acc -= Dm[(size_t)r * nb + q] * PiN[(size_t)q * nK + c];
+      Pm[idx] = acc;
+    }
+    ex.sync();
+    // (9) A = nu (Ac + P^T diag(s) P), s_i = max(Ac_ii, h_K)
+    for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
+      int r = idx / nK, c = idx % nK;
+      if (r > c) continue;
+      double acc = 0.0;
+      for (int q = 0; q < nK; ++q) {
+        double s = Ac[(size_t)q * nK + q];
+        s = s > hK ? s : hK;
+        acc += Pm[(size_t)q * nK + r] * s * Pm[(size_t)q * nK + c];
+      }
+      double v = nu * (Ac[idx] + acc);
+      Aout[(size_t)r * nK + c] = v;
+      Aout[(size_t)c * nK + r] = v;
+    }
+    // (10) B_K rows: row 0 flux, rows a >= 1: |K| on D5
+    for (int idx = ex.tid; idx < S::NP0 * nK; idx += ex.nt) {
+      int a = idx / nK, col = idx % nK;
+      double v = 0.0;
+      if (a == 0) {
+        if (col >= off_f && col < off_4) {
+          int r = col - off_f;
+          int f = r / (3 * S::NFM), b = (r / 3) % S::NFM, t = r % 3;
+          if (b == 0 && t == 0) v = R.fsign[f] * sh.farea[f];
+        }
+      } else if (col == off_5 + a - 1) {
+        v = vol;
+      }
+      Bout[idx] = v;
+    }
+    ex.sync();
+    // (11) Pi^0_k : VMH[c][a] = int v . m_a e_c (with enhancement), P0 = Minv1 VMH
+    for (int idx = ex.tid; idx < 3 * S::NP1 * nK; idx += ex.nt) {
+      int c = idx / (S::NP1 * nK), r = idx % (S::NP1 * nK);
+      int a = r / nK, col = r % nK;
+      VMH[idx] = vecmom(col, c, a, true);
+    }
+    ex.sync();
+    for (int idx = ex.tid; idx < 3 * S::NP1 * nK; idx += ex.nt) {
+      int c = idx / (S::NP1 * nK), r = idx % (S::NP1 * nK);
+      int a = r / nK, col = r % nK;
+      double acc = 0.0;
+      for (int g = 0; g < S::NP1; ++g) acc += sh.Minv1[a * S::NP1 + g] * VMH[((size_t)c * S::NP1 + g) * nK + col];
+      P0out[idx] = acc;
+    }
+    ex.sync();
+    return ok;
+  }
+
+  // (1/|f|)-free face moment int_f m3_a m2_b, recomputed by quadrature
+  VB_HD double facemom_(int f, int a, int b) const {
+    const int m = R.fnv[f];
+    const double hfi = 1.0 / sh.fh[f];
+    const double* xc = sh.fxc[f];
+    const double *t1 = sh.ft1[f], *t2 = sh.ft2[f];
+    const int nq = T.nq_face;
+    const Exp3 ea = T.e3[a];
+    const Exp2 eb = T.e2[b];
+    double hk = 1.0 / sh.hK;
+    double acc = 0.0;
+    const double* P0 = sh.X[R.floopv[f][0]];
+    for (int t = 1; t < m - 1; ++t) {
+      const double* P1 = sh.X[R.floopv[f][t]];
+      const double* P2 = sh.X[R.floopv[f][t + 1]];
+      double u1[3], u2[3], cr[3];
+      for (int d = 0; d < 3; ++d) { u1[d] = P1[d] - P0[d]; u2[d] = P2[d] - P0[d]; }
+      cross3(u1, u2, cr);
+      double J = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+      for (int iu = 0; iu < nq; ++iu)
+        for (int iv = 0; iv < nq; ++iv) {
+          double U = T.qf_x[iu], V = T.qf_x[iv] * (1 - U);
+          double w = T.qf_w[iu] * T.qf_w[iv] * (1 - U) * J;
+          double x[3];
+          for (int d = 0; d < 3; ++d) x[d] = P0[d] + U * u1[d] + V * u2[d];
+          double dx[3] = {x[0] - xc[0], x[1] - xc[1], x[2] - xc[2]};
+          double s = (dx[0] * t1[0] + dx[1] * t1[1] + dx[2] * t1[2]) * hfi;
+          double tt = (dx[0] * t2[0] + dx[1] * t2[1] + dx[2] * t2[2]) * hfi;
+          double px = (x[0] - sh.xK[0]) * hk, py = (x[1] - sh.xK[1]) * hk, pz = (x[2] - sh.xK[2]) * hk;
+          acc += w * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c) * ipow(s, eb.a) * ipow(tt, eb.b);
+        }
+    }
+    return acc;
+  }
+};
+
+}  // namespace vb

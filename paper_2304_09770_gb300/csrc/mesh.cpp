@@ -1,0 +1,253 @@
+// Host preprocessing: mesh topology, DOF numbering (Sec. 3, D1-D5) and the
+// fixed-size element records the element kernel reads.
+#include "system.h"
+
+#include <algorithm>
+#include <cmath>
+#include <unordered_map>
+
+namespace vb {
+
+thread_local std::string g_last_error;
+void set_last_error(const std::string& m) { g_last_error = m; }
+
+void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
+  // roots of the Legendre polynomial P_n by Newton iteration from the
+  // Chebyshev-like first guess; weights 2 / ((1 - z^2) P_n'(z)^2)
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double pp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 2; j <= n; ++j) {
+        double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      pp = n * (z * p1 - p0) / (z * z - 1.0);
+      double z1 = z;
+      z = z1 - p1 / pp;
+      if (std::fabs(z - z1) < 1e-15) break;
+    }
+    // derivative at the converged root
+    double p0 = 1.0, p1 = z;
+    for (int j = 2; j <= n; ++j) {
+      double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+      p0 = p1;
+      p1 = p2;
+    }
+    pp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+  std::vector<std::pair<double, double>> xw(n);
+  for (int i = 0; i < n; ++i) xw[i] = {0.5 * (x[i] + 1.0), 0.5 * w[i]};
+  std::sort(xw.begin(), xw.end());
+  for (int i = 0; i < n; ++i) { x[i] = xw[i].first; w[i] = xw[i].second; }
+}
+
+std::vector<double> lobatto_interior(int k) {
+  // the k-1 roots of P_k' on (-1,1), mapped to (0,1)
+  std::vector<double> r;
+  if (k == 2) r = {0.5};
+  else if (k == 3) r = {0.5 * (1.0 - 1.0 / std::sqrt(5.0)), 0.5 * (1.0 + 1.0 / std::sqrt(5.0))};
+  else if (k == 4) r = {0.5 * (1.0 - std::sqrt(3.0 / 7.0)), 0.5, 0.5 * (1.0 + std::sqrt(3.0 / 7.0))};
+  else throw Error(VEM_EINVAL, "degree k must be 2, 3 or 4");
+  return r;
+}
+
+void build_topology(const vem_mesh* m, Topo& t) {
+  VB_CHECK(m && m->xyz && m->face_ptr && m->face_vtx && m->elem_ptr && m->elem_face, VEM_EINVAL,
+           "vem_mesh has a null array");
+  VB_CHECK(m->nV > 0 && m->nF > 0 && m->nE > 0, VEM_EINVAL, "empty mesh");
+  t.nV = m->nV;
+  t.nF = m->nF;
+  t.nE = m->nE;
+  t.xyz.assign(m->xyz, m->xyz + 3 * (size_t)m->nV);
+  t.face_ptr.assign(m->face_ptr, m->face_ptr + m->nF + 1);
+  t.face_vtx.assign(m->face_vtx, m->face_vtx + t.face_ptr[m->nF]);
+  t.elem_ptr.assign(m->elem_ptr, m->elem_ptr + m->nE + 1);
+  t.elem_face.assign(m->elem_face, m->elem_face + t.elem_ptr[m->nE]);
+  for (int f = 0; f < t.nF; ++f) {
+    int nv = t.face_ptr[f + 1] - t.face_ptr[f];
+    VB_CHECK(nv >= 3 && nv <= kMaxFaceVerts, VEM_EINVAL, "face with unsupported vertex count");
+    for (int i = t.face_ptr[f]; i < t.face_ptr[f + 1]; ++i)
+      VB_CHECK(t.face_vtx[i] >= 0 && t.face_vtx[i] < t.nV, VEM_EINVAL, "face vertex out of range");
+  }
+  // edges by first appearance in the face loops
+  std::unordered_map<uint64_t, int> eid;
+  t.face_edges_ptr.assign(t.nF + 1, 0);
+  t.face_edges.clear();
+  for (int f = 0; f < t.nF; ++f) {
+    int b = t.face_ptr[f], nv = t.face_ptr[f + 1] - b;
+    for (int i = 0; i < nv; ++i) {
+      int va = t.face_vtx[b + i], vb_ = t.face_vtx[b + (i + 1) % nv];
+      int lo = std::min(va, vb_), hi = std::max(va, vb_);
+      uint64_t key = ((uint64_t)lo << 32) | (uint32_t)hi;
+      auto it = eid.find(key);
+      int id;
+      if (it == eid.end()) {
+        id = (int)t.edge_a.size();
+        eid.emplace(key, id);
+        t.edge_a.push_back(lo);
+        t.edge_b.push_back(hi);
+      } else {
+        id = it->second;
+      }
+      t.face_edges.push_back(id);
+    }
+    t.face_edges_ptr[f + 1] = (int)t.face_edges.size();
+  }
+  t.nEd = (int)t.edge_a.size();
+  std::vector<int> cnt(t.nF, 0);
+  for (int e = 0; e < t.nE; ++e)
+    for (int i = t.elem_ptr[e]; i < t.elem_ptr[e + 1]; ++i) {
+      int s = t.elem_face[i];
+      int f = std::abs(s) - 1;
+      VB_CHECK(s != 0 && f < t.nF, VEM_EINVAL, "element face reference out of range");
+      cnt[f]++;
+    }
+  t.bnd_f.assign(t.nF, 0);
+  t.bnd_v.assign(t.nV, 0);
+  t.bnd_e.assign(t.nEd, 0);
+  for (int f = 0; f < t.nF; ++f) {
+    VB_CHECK(cnt[f] == 1 || cnt[f] == 2, VEM_EINVAL, "face shared by more than two elements or unused");
+    if (cnt[f] == 1) {
+      t.bnd_f[f] = 1;
+      for (int i = t.face_ptr[f]; i < t.face_ptr[f + 1]; ++i) t.bnd_v[t.face_vtx[i]] = 1;
+      for (int i = t.face_edges_ptr[f]; i < t.face_edges_ptr[f + 1]; ++i) t.bnd_e[t.face_edges[i]] = 1;
+    }
+  }
+  t.elem_verts.assign(t.nE, {});
+  t.elem_edges.assign(t.nE, {});
+  for (int e = 0; e < t.nE; ++e) {
+    auto& vs = t.elem_verts[e];
+    auto& es = t.elem_edges[e];
+    for (int i = t.elem_ptr[e]; i < t.elem_ptr[e + 1]; ++i) {
+      int f = std::abs(t.elem_face[i]) - 1;
+      for (int j = t.face_ptr[f]; j < t.face_ptr[f + 1]; ++j) vs.push_back(t.face_vtx[j]);
+      for (int j = t.face_edges_ptr[f]; j < t.face_edges_ptr[f + 1]; ++j) es.push_back(t.face_edges[j]);
+    }
+    std::sort(vs.begin(), vs.end());
+    vs.erase(std::unique(vs.begin(), vs.end()), vs.end());
+    std::sort(es.begin(), es.end());
+    es.erase(std::unique(es.begin(), es.end()), es.end());
+    VB_CHECK((int)vs.size() <= kMaxElemVerts && (int)es.size() <= kMaxElemEdges &&
+                 t.elem_ptr[e + 1] - t.elem_ptr[e] <= kMaxElemFaces,
+             VEM_EINVAL, "element too large for the element kernel");
+  }
+}
+
+void number_dofs(const Topo& t, int k, DofNumbering& d) {
+  VB_CHECK(k >= 2 && k <= 4, VEM_EINVAL, "degree k must be 2, 3 or 4");
+  d.k = k;
+  d.ce = 3 * (k - 1);
+  d.cf = 3 * pdim2(k - 2);
+  d.n4 = n_d4(k);
+  d.n5 = n_d5(k);
+  d.np = pdim3(k - 1);
+  d.off_e = 3LL * t.nV;
+  d.off_f = d.off_e + (int64_t)t.nEd * d.ce;
+  d.off_k = d.off_f + (int64_t)t.nF * d.cf;
+  d.nvel = d.off_k + (int64_t)t.nE * (d.n4 + d.n5);
+  std::vector<char> fixed(d.nvel, 0);
+  for (int v = 0; v < t.nV; ++v)
+    if (t.bnd_v[v]) fixed[3 * v] = fixed[3 * v + 1] = fixed[3 * v + 2] = 1;
+  for (int e = 0; e < t.nEd; ++e)
+    if (t.bnd_e[e]) for (int j = 0; j < d.ce; ++j) fixed[d.off_e + (int64_t)e * d.ce + j] = 1;
+  for (int f = 0; f < t.nF; ++f)
+    if (t.bnd_f[f]) for (int j = 0; j < d.cf; ++j) fixed[d.off_f + (int64_t)f * d.cf + j] = 1;
+  d.free_index.assign(d.nvel, -1);
+  d.free_to_global.clear();
+  for (int64_t g = 0; g < d.nvel; ++g)
+    if (!fixed[g]) {
+      d.free_index[g] = (int64_t)d.free_to_global.size();
+      d.free_to_global.push_back(g);
+    }
+  d.nvf = (int64_t)d.free_to_global.size();
+  d.npress = (int64_t)t.nE * d.np;
+}
+
+void element_global_dofs(const Topo& t, const DofNumbering& d, int e, std::vector<int64_t>& out) {
+  out.clear();
+  for (int v : t.elem_verts[e]) for (int c = 0; c < 3; ++c) out.push_back(3LL * v + c);
+  for (int ed : t.elem_edges[e])
+    for (int j = 0; j < d.ce; ++j) out.push_back(d.off_e + (int64_t)ed * d.ce + j);
+  for (int i = t.elem_ptr[e]; i < t.elem_ptr[e + 1]; ++i) {
+    int f = std::abs(t.elem_face[i]) - 1;
+    for (int j = 0; j < d.cf; ++j) out.push_back(d.off_f + (int64_t)f * d.cf + j);
+  }
+  for (int j = 0; j < d.n4 + d.n5; ++j) out.push_back(d.off_k + (int64_t)e * (d.n4 + d.n5) + j);
+}
+
+void build_elem_records(const Topo& t, const DofNumbering& d, std::vector<ElemRec>& recs) {
+  recs.assign(t.nE, ElemRec{});
+  for (int e = 0; e < t.nE; ++e) {
+    ElemRec& r = recs[e];
+    const auto& vs = t.elem_verts[e];
+    const auto& es = t.elem_edges[e];
+    r.nv = (int)vs.size();
+    r.ne = (int)es.size();
+    r.nf = t.elem_ptr[e + 1] - t.elem_ptr[e];
+    for (int i = 0; i < r.nv; ++i) r.vert[i] = vs[i];
+    for (int i = 0; i < r.ne; ++i) { r.edge_a[i] = t.edge_a[es[i]]; r.edge_b[i] = t.edge_b[es[i]]; }
+    for (int fi = 0; fi < r.nf; ++fi) {
+      int s = t.elem_face[t.elem_ptr[e] + fi];
+      int f = std::abs(s) - 1;
+      r.face[fi] = f;
+      r.fsign[fi] = s > 0 ? 1 : -1;
+      int b = t.face_ptr[f], nv = t.face_ptr[f + 1] - b;
+      r.fnv[fi] = nv;
+      for (int i = 0; i < nv; ++i) {
+        int va = t.face_vtx[b + i], vbb = t.face_vtx[b + (i + 1) % nv];
+        r.floopv[fi][i] = (int)(std::lower_bound(vs.begin(), vs.end(), va) - vs.begin());
+        int ed = t.face_edges[t.face_edges_ptr[f] + i];
+        r.floope[fi][i] = (int)(std::lower_bound(es.begin(), es.end(), ed) - es.begin());
+        r.floopdir[fi][i] = va < vbb ? 1 : 0;
+      }
+    }
+    r.nK = 3 * r.nv + r.ne * d.ce + r.nf * d.cf + d.n4 + d.n5;
+  }
+}
+
+}  // namespace vb
+
+#include "elem_body.cuh"
+namespace vb {
+
+void make_elem_tables(int k, ElemTables& T) {
+  T = ElemTables{};
+  int i = 0;
+  for (int d = 0; i < kMaxMono3; ++d)
+    for (int a = d; a >= 0 && i < kMaxMono3; --a)
+      for (int b = d - a; b >= 0 && i < kMaxMono3; --b) {
+        T.e3[i] = Exp3{(unsigned char)a, (unsigned char)b, (unsigned char)(d - a - b), (unsigned char)d};
+        ++i;
+      }
+  i = 0;
+  for (int d = 0; i < kMaxMono2; ++d)
+    for (int a = d; a >= 0 && i < kMaxMono2; --a) {
+      T.e2[i] = Exp2{(unsigned char)a, (unsigned char)(d - a), (unsigned char)d, 0};
+      ++i;
+    }
+  std::vector<double> gl = lobatto_interior(k);
+  for (size_t j = 0; j < gl.size(); ++j) T.gl[j] = gl[j];
+  std::vector<double> x, w;
+  // edges: exact to degree 2k+3
+  T.nq_edge = k + 2;
+  gauss01(T.nq_edge, x, w);
+  for (int j = 0; j < T.nq_edge; ++j) { T.qe_x[j] = x[j]; T.qe_w[j] = w[j]; }
+  // faces: collapsed triangle rule exact to degree 2k+2
+  T.nq_face = (2 * k + 5) / 2;
+  gauss01(T.nq_face, x, w);
+  for (int j = 0; j < T.nq_face; ++j) { T.qf_x[j] = x[j]; T.qf_w[j] = w[j]; }
+  // volume: collapsed tetrahedron rule exact to degree 2k
+  T.nq_vol = k + 2;
+  gauss01(T.nq_vol, x, w);
+  for (int j = 0; j < T.nq_vol; ++j) { T.qv_x[j] = x[j]; T.qv_w[j] = w[j]; }
+}
+
+}  // namespace vb

@@ -1,0 +1,521 @@
+// vem_system: element construction on the GPU (one CTA per element), the
+// deterministic CSR assembly of K = [A B^T; B 0] (Eq. MatrixForm), the load
+// (Eq. discreteF) and the operator apply.
+#include "system.h"
+#include "elem_body.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace vb {
+
+__constant__ ElemTables c_tab;
+
+template <int K>
+__global__ void __launch_bounds__(128) k_element(const ElemRec* __restrict__ rec, const double* __restrict__ xyz,
+                                                 const double* __restrict__ nu, const int64_t* __restrict__ offK,
+                                                 const int64_t* __restrict__ offK2, double* A, double* B, double* P0,
+                                                 double* scratch, size_t stride, int nE, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ElemShared<K>& sh = *reinterpret_cast<ElemShared<K>*>(smem_raw);
+  __shared__ ElemRec R;
+  double* scr = scratch + (size_t)blockIdx.x * stride;
+  for (int e = blockIdx.x; e < nE; e += gridDim.x) {
+    {
+      const int* src = reinterpret_cast<const int*>(rec + e);
+      int* dst = reinterpret_cast<int*>(&R);
+      for (int i = threadIdx.x; i < (int)(sizeof(ElemRec) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    ElemBuilder<K> b(R, xyz, c_tab, sh, scr, Exec{(int)threadIdx.x, (int)blockDim.x});
+    const int np = pdim3(K - 1);
+    bool ok = b.build(nu[e], A + offK2[e], B + (size_t)np * offK[e], P0 + (size_t)3 * pdim3(K) * offK[e]);
+    if (!ok && threadIdx.x == 0) atomicExch(status, 1);
+    __syncthreads();
+  }
+}
+
+// CSR assembly: one warp per system row, contributions gathered element by
+// element in a fixed order (deterministic sums, no atomics).
+__global__ void k_assemble(int64_t nrows, int64_t nvf, int np, const int64_t* __restrict__ rowptr,
+                           const int* __restrict__ col, double* __restrict__ val, const int64_t* __restrict__ adj_ptr,
+                           const int* __restrict__ adj_elem, const int* __restrict__ adj_loc,
+                           const int64_t* __restrict__ offK, const int64_t* __restrict__ offK2,
+                           const int64_t* __restrict__ sysdof, const double* __restrict__ A,
+                           const double* __restrict__ B) {
+  int lane = threadIdx.x & 31;
+  int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nrows) return;
+  const int64_t r0 = rowptr[r], r1 = rowptr[r + 1];
+  for (int64_t p = r0 + lane; p < r1; p += 32) val[p] = 0.0;
+  __syncwarp();
+  for (int64_t q = adj_ptr[r]; q < adj_ptr[r + 1]; ++q) {
+    const int e = adj_elem[q], loc = adj_loc[q];
+    const int nK = (int)(offK[e + 1] - offK[e]);
+    const int64_t* sd = sysdof + offK[e];
+    const double* Ae = A + offK2[e];
+    const double* Be = B + (int64_t)np * offK[e];
+    const int ncols = loc < nK ? nK + np : nK;
+    for (int b = lane; b < ncols; b += 32) {
+      int64_t c;
+      double v;
+      if (loc < nK) {
+        if (b < nK) { c = sd[b]; v = Ae[(int64_t)loc * nK + b]; }
+        else { c = nvf + (int64_t)e * np + (b - nK); v = Be[(int64_t)(b - nK) * nK + loc]; }
+      } else {
+        c = sd[b];
+        v = Be[(int64_t)(loc - nK) * nK + b];
+      }
+      if (c < 0) continue;
+      // binary search of column c in row r
+      int64_t lo = r0, hi = r1 - 1;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < c) lo = mid + 1; else hi = mid;
+      }
+      val[lo] += v;
+    }
+    __syncwarp();
+  }
+}
+
+// y = K x, one warp per row
+__global__ void k_spmv(int64_t nrows, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+  int lane = threadIdx.x & 31;
+  int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nrows) return;
+  double acc = 0.0;
+  for (int64_t p = rowptr[r] + lane; p < rowptr[r + 1]; p += 32) acc += val[p] * __ldg(x + col[p]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[r] = acc;
+}
+
+// load-rule points of element e (tetrahedra x_K + outward fan triangles)
+struct LoadRule {
+  int nq;
+  double x[16], w[16];
+};
+__constant__ LoadRule c_load;
+
+__device__ inline void elem_centroid(const ElemRec& R, const double* xyz, double* xK) {
+  xK[0] = xK[1] = xK[2] = 0.0;
+  for (int i = 0; i < R.nv; ++i)
+    for (int d = 0; d < 3; ++d) xK[d] += xyz[3 * R.vert[i] + d];
+  for (int d = 0; d < 3; ++d) xK[d] /= R.nv;
+}
+
+// point p (of this element's list) -> physical point and weight
+__device__ inline void load_point(const ElemRec& R, const double* xyz, const double* xK, int p, double* x,
+                                  double* w) {
+  const int nq = c_load.nq, nq3 = nq * nq * nq;
+  int tet = p / nq3, q = p % nq3;
+  int iu = q / (nq * nq), iv = (q / nq) % nq, iw = q % nq;
+  int f = 0, t = 0, cnt = 0;
+  for (f = 0; f < R.nf; ++f) {
+    int nt = R.fnv[f] - 2;
+    if (tet < cnt + nt) { t = tet - cnt + 1; break; }
+    cnt += nt;
+  }
+  int m = R.fnv[f];
+  int i0 = 0, i1 = t, i2 = t + 1;
+  if (R.fsign[f] < 0) { i0 = m - 1; i1 = m - 1 - t; i2 = m - 2 - t; }
+  const int* lv = R.floopv[f];
+  double a1[3], b1[3], c1[3];
+  for (int d = 0; d < 3; ++d) {
+    a1[d] = xyz[3 * R.vert[lv[i0]] + d] - xK[d];
+    b1[d] = xyz[3 * R.vert[lv[i1]] + d] - xK[d];
+    c1[d] = xyz[3 * R.vert[lv[i2]] + d] - xK[d];
+  }
+  double cr[3];
+  cross3(b1, c1, cr);
+  double det = a1[0] * cr[0] + a1[1] * cr[1] + a1[2] * cr[2];
+  double U = c_load.x[iu], V = c_load.x[iv], W = c_load.x[iw];
+  double px = U, py = V * (1 - U), pz = W * (1 - U) * (1 - V);
+  *w = c_load.w[iu] * c_load.w[iv] * c_load.w[iw] * (1 - U) * (1 - U) * (1 - V) * det;
+  for (int d = 0; d < 3; ++d) x[d] = xK[d] + px * a1[d] + py * b1[d] + pz * c1[d];
+}
+
+__global__ void k_quad_points(const ElemRec* __restrict__ rec, const double* __restrict__ xyz,
+                              const int64_t* __restrict__ qoff, int nE, double* out) {
+  int e = blockIdx.x;
+  if (e >= nE) return;
+  const ElemRec& R = rec[e];
+  double xK[3];
+  elem_centroid(R, xyz, xK);
+  int npts = (int)(qoff[e + 1] - qoff[e]);
+  for (int p = threadIdx.x; p < npts; p += blockDim.x) {
+    double x[3], w;
+    load_point(R, xyz, xK, p, x, &w);
+    for (int d = 0; d < 3; ++d) out[3 * (qoff[e] + p) + d] = x[d];
+  }
+}
+
+// per element: F[c][a] = sum_p w f_c m_a(xi), local rhs = P0^T F (Eq. discreteF)
+template <int K>
+__global__ void k_load_local(const ElemRec* __restrict__ rec, const double* __restrict__ xyz,
+                             const int64_t* __restrict__ qoff, const double* __restrict__ fq,
+                             const int64_t* __restrict__ offK, const double* __restrict__ P0, int nE,
+                             double* __restrict__ rloc) {
+  constexpr int NP1 = pdim3(K);
+  __shared__ double Fm[3 * NP1];
+  __shared__ double xK[3], hK;
+  int e = blockIdx.x;
+  if (e >= nE) return;
+  const ElemRec& R = rec[e];
+  if (threadIdx.x == 0) {
+    elem_centroid(R, xyz, xK);
+    double h2 = 0;
+    for (int i = 0; i < R.nv; ++i)
+      for (int j = i + 1; j < R.nv; ++j) {
+        double s = 0;
+        for (int d = 0; d < 3; ++d) {
+          double t = xyz[3 * R.vert[i] + d] - xyz[3 * R.vert[j] + d];
+          s += t * t;
+        }
+        h2 = s > h2 ? s : h2;
+      }
+    hK = sqrt(h2);
+  }
+  __syncthreads();
+  int npts = (int)(qoff[e + 1] - qoff[e]);
+  for (int idx = threadIdx.x; idx < 3 * NP1; idx += blockDim.x) {
+    int c = idx / NP1, a = idx % NP1;
+    const Exp3 ea = c_tab.e3[a];
+    double acc = 0.0;
+    for (int p = 0; p < npts; ++p) {
+      double x[3], w;
+      load_point(R, xyz, xK, p, x, &w);
+      double px = (x[0] - xK[0]) / hK, py = (x[1] - xK[1]) / hK, pz = (x[2] - xK[2]) / hK;
+      acc += w * fq[3 * (qoff[e] + p) + c] * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c);
+    }
+    Fm[idx] = acc;
+  }
+  __syncthreads();
+  int nK = (int)(offK[e + 1] - offK[e]);
+  const double* P = P0 + (size_t)3 * NP1 * offK[e];
+  for (int col = threadIdx.x; col < nK; col += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < 3 * NP1; ++q) acc += P[(size_t)q * nK + col] * Fm[q];
+    rloc[offK[e] + col] = acc;
+  }
+}
+
+// system rhs from the per-element local vectors (velocity rows), zero pressure rows
+__global__ void k_gather_rhs(int64_t nrows, int64_t nvf, const int64_t* __restrict__ adj_ptr,
+                             const int* __restrict__ adj_elem, const int* __restrict__ adj_loc,
+                             const int64_t* __restrict__ offK, const double* __restrict__ rloc,
+                             double* __restrict__ rhs) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  double acc = 0.0;
+  if (r < nvf)
+    for (int64_t q = adj_ptr[r]; q < adj_ptr[r + 1]; ++q) acc += rloc[offK[adj_elem[q]] + adj_loc[q]];
+  rhs[r] = acc;
+}
+
+template <int K>
+static void launch_elements(vem_system* s, const std::vector<ElemRec>& recs, const DBuf<int64_t>& offK,
+                            const DBuf<int64_t>& offK2) {
+  const int nE = s->topo.nE;
+  const int grid = std::min(nE, 152 * (K == 2 ? 8 : (K == 3 ? 4 : 2)));
+  size_t stride = ElemScratch<K>::size(s->nKmax);
+  DBuf<double> scratch((size_t)grid * stride);
+  DBuf<int> status(1);
+  status.zero(s->stream);
+  size_t smem = sizeof(ElemShared<K>);
+  VB_CUDA(cudaFuncSetAttribute(k_element<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_element<K><<<grid, 128, smem, s->stream>>>(s->d_rec.p, s->d_xyz.p, s->d_nu.p, offK.p, offK2.p, s->d_A.p,
+                                               s->d_B.p, s->d_P0.p, scratch.p, stride, nE, status.p);
+  VB_KERNEL_CHECK();
+  auto st = status.download(s->stream);
+  VB_CHECK(st[0] == 0, VEM_ESINGULAR, "element projector system singular (degenerate element)");
+}
+
+static void load_tables(vem_system* s) {
+  ElemTables T;
+  make_elem_tables(s->dof.k, T);
+  VB_CUDA(cudaMemcpyToSymbolAsync(c_tab, &T, sizeof(T), 0, cudaMemcpyHostToDevice, s->stream));
+}
+
+}  // namespace vb
+
+using namespace vb;
+
+static int fail(const Error& e) {
+  set_last_error(e.what());
+  return e.status;
+}
+
+extern "C" const char* vem_last_error(void) { return vb::g_last_error.c_str(); }
+
+extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_system** out) {
+  if (!out || !nu) { set_last_error("vem_assemble: null argument"); return VEM_EINVAL; }
+  *out = nullptr;
+  vem_system* s = new vem_system();
+  try {
+    build_topology(mesh, s->topo);
+    number_dofs(s->topo, k, s->dof);
+    const Topo& t = s->topo;
+    const DofNumbering& d = s->dof;
+    std::vector<ElemRec> recs;
+    build_elem_records(t, d, recs);
+    // per-element offsets and system DOF maps
+    std::vector<int64_t> offK(t.nE + 1, 0), offK2(t.nE + 1, 0);
+    for (int e = 0; e < t.nE; ++e) {
+      offK[e + 1] = offK[e] + recs[e].nK;
+      offK2[e + 1] = offK2[e] + (int64_t)recs[e].nK * recs[e].nK;
+      s->nKmax = std::max(s->nKmax, recs[e].nK);
+    }
+    s->h_eoff = offK;
+    s->h_sysdof.assign(offK[t.nE], -1);
+    std::vector<int64_t> g;
+    for (int e = 0; e < t.nE; ++e) {
+      element_global_dofs(t, d, e, g);
+      VB_CHECK((int)g.size() == recs[e].nK, VEM_EINVAL, "element DOF count mismatch");
+      for (size_t i = 0; i < g.size(); ++i) s->h_sysdof[offK[e] + i] = d.free_index[g[i]];
+    }
+    // upload element data, build element matrices
+    s->d_rec.alloc(t.nE);
+    VB_CUDA(cudaMemcpyAsync(s->d_rec.p, recs.data(), recs.size() * sizeof(ElemRec), cudaMemcpyHostToDevice, s->stream));
+    s->d_xyz.upload(t.xyz, s->stream);
+    s->d_nu.upload(std::vector<double>(nu, nu + t.nE), s->stream);
+    DBuf<int64_t> dK, dK2;
+    dK.upload(offK, s->stream);
+    dK2.upload(offK2, s->stream);
+    s->d_A.alloc(offK2[t.nE]);
+    s->d_B.alloc((size_t)d.np * offK[t.nE]);
+    s->d_P0.alloc((size_t)3 * pdim3(k) * offK[t.nE]);
+    s->d_sysdof.upload(s->h_sysdof, s->stream);
+    load_tables(s);
+    if (k == 2) launch_elements<2>(s, recs, dK, dK2);
+    else if (k == 3) launch_elements<3>(s, recs, dK, dK2);
+    else launch_elements<4>(s, recs, dK, dK2);
+    // CSR pattern and row adjacency (host)
+    const int64_t nvf = d.nvf, np = d.np;
+    s->n = nvf + d.npress;
+    std::vector<int64_t> cnt(s->n + 1, 0);
+    for (int e = 0; e < t.nE; ++e)
+      for (int i = 0; i < recs[e].nK; ++i) {
+        int64_t r = s->h_sysdof[offK[e] + i];
+        if (r >= 0) cnt[r + 1]++;
+      }
+    for (int64_t r = nvf; r < s->n; ++r) cnt[r + 1] = 1;
+    for (int64_t r = 0; r < s->n; ++r) cnt[r + 1] += cnt[r];
+    s->h_adj_ptr = cnt;
+    s->h_adj_elem.assign(cnt[s->n], 0);
+    s->h_adj_loc.assign(cnt[s->n], 0);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int e = 0; e < t.nE; ++e)
+      for (int i = 0; i < recs[e].nK; ++i) {
+        int64_t r = s->h_sysdof[offK[e] + i];
+        if (r >= 0) { s->h_adj_elem[fill[r]] = e; s->h_adj_loc[fill[r]] = i; fill[r]++; }
+      }
+    for (int e = 0; e < t.nE; ++e)
+      for (int a = 0; a < np; ++a) {
+        int64_t r = nvf + (int64_t)e * np + a;
+        s->h_adj_elem[fill[r]] = e;
+        s->h_adj_loc[fill[r]] = recs[e].nK + a;
+        fill[r]++;
+      }
+    std::vector<int64_t> rowptr(s->n + 1, 0);
+    std::vector<int> cols;
+    std::vector<int> buf;
+    for (int64_t r = 0; r < s->n; ++r) {
+      buf.clear();
+      for (int64_t q = cnt[r]; q < cnt[r + 1]; ++q) {
+        int e = s->h_adj_elem[q], loc = s->h_adj_loc[q];
+        int nK = recs[e].nK;
+        for (int b = 0; b < nK; ++b) {
+          int64_t c = s->h_sysdof[offK[e] + b];
+          if (c >= 0) buf.push_back((int)c);
+        }
+        if (loc < nK)
+          for (int a = 0; a < np; ++a) buf.push_back((int)(nvf + (int64_t)e * np + a));
+      }
+      std::sort(buf.begin(), buf.end());
+      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+      cols.insert(cols.end(), buf.begin(), buf.end());
+      rowptr[r + 1] = (int64_t)cols.size();
+    }
+    VB_CHECK(s->n < (int64_t)INT32_MAX, VEM_EINVAL, "system too large for 32-bit column indices");
+    s->nnz = rowptr[s->n];
+    s->d_rowptr.upload(rowptr, s->stream);
+    s->d_col.upload(cols, s->stream);
+    s->d_val.alloc(s->nnz);
+    s->d_adj_ptr.upload(s->h_adj_ptr, s->stream);
+    s->d_adj_elem.upload(s->h_adj_elem, s->stream);
+    s->d_adj_loc.upload(s->h_adj_loc, s->stream);
+    s->d_eoff.upload(offK, s->stream);
+    DBuf<int64_t>& offKd = s->d_eoff;
+    int64_t threads = s->n * 32;
+    k_assemble<<<(unsigned)((threads + 255) / 256), 256, 0, s->stream>>>(
+        s->n, nvf, (int)np, s->d_rowptr.p, s->d_col.p, s->d_val.p, s->d_adj_ptr.p, s->d_adj_elem.p,
+        s->d_adj_loc.p, offKd.p, dK2.p, s->d_sysdof.p, s->d_A.p, s->d_B.p);
+    VB_KERNEL_CHECK();
+    s->d_eoffK2 = std::move(dK2);
+    VB_CUDA(cudaStreamSynchronize(s->stream));
+    *out = s;
+    return VEM_OK;
+  } catch (const Error& e) {
+    delete s;
+    return fail(e);
+  } catch (const std::exception& e) {
+    delete s;
+    set_last_error(e.what());
+    return VEM_ENOMEM;
+  }
+}
+
+extern "C" int vem_dof_layout(const vem_system* s, int64_t* nvf, int64_t* np, int64_t* nvel) {
+  if (!s) { set_last_error("null system"); return VEM_EINVAL; }
+  if (nvf) *nvf = s->dof.nvf;
+  if (np) *np = s->dof.npress;
+  if (nvel) *nvel = s->dof.nvel;
+  return VEM_OK;
+}
+
+extern "C" int vem_free_dofs(const vem_system* s, int64_t* out) {
+  if (!s || !out) { set_last_error("null argument"); return VEM_EINVAL; }
+  std::memcpy(out, s->dof.free_to_global.data(), s->dof.nvf * sizeof(int64_t));
+  return VEM_OK;
+}
+
+static void load_offsets(vem_system* s, int degree, std::vector<int64_t>& qoff) {
+  VB_CHECK(degree >= 0 && degree <= 24, VEM_EINVAL, "load degree out of range");
+  int nq = (degree + 3) / 2 + 1;
+  LoadRule L{};
+  L.nq = nq;
+  std::vector<double> x, w;
+  gauss01(nq, x, w);
+  for (int i = 0; i < nq; ++i) { L.x[i] = x[i]; L.w[i] = w[i]; }
+  VB_CUDA(cudaMemcpyToSymbolAsync(c_load, &L, sizeof(L), 0, cudaMemcpyHostToDevice, s->stream));
+  const Topo& t = s->topo;
+  qoff.assign(t.nE + 1, 0);
+  for (int e = 0; e < t.nE; ++e) {
+    int ntets = 0;
+    for (int i = t.elem_ptr[e]; i < t.elem_ptr[e + 1]; ++i) {
+      int f = std::abs(t.elem_face[i]) - 1;
+      ntets += t.face_ptr[f + 1] - t.face_ptr[f] - 2;
+    }
+    qoff[e + 1] = qoff[e] + (int64_t)ntets * nq * nq * nq;
+  }
+}
+
+extern "C" int vem_quad_points(vem_system* s, int degree, int64_t* n, double* xyz_out) {
+  if (!s || !n) { set_last_error("null argument"); return VEM_EINVAL; }
+  try {
+    std::vector<int64_t> qoff;
+    load_offsets(s, degree, qoff);
+    *n = qoff.back();
+    if (!xyz_out) return VEM_OK;
+    DBuf<int64_t> dq;
+    dq.upload(qoff, s->stream);
+    DBuf<double> pts(3 * (size_t)qoff.back());
+    k_quad_points<<<s->topo.nE, 128, 0, s->stream>>>(s->d_rec.p, s->d_xyz.p, dq.p, s->topo.nE, pts.p);
+    VB_KERNEL_CHECK();
+    VB_CUDA(cudaMemcpyAsync(xyz_out, pts.p, pts.n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    VB_CUDA(cudaStreamSynchronize(s->stream));
+    return VEM_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
+
+extern "C" int vem_load(vem_system* s, int degree, const double* fq, double* rhs) {
+  if (!s || !fq || !rhs) { set_last_error("null argument"); return VEM_EINVAL; }
+  try {
+    std::vector<int64_t> qoff;
+    load_offsets(s, degree, qoff);
+    DBuf<int64_t> dq;
+    dq.upload(qoff, s->stream);
+    DBuf<double> df(3 * (size_t)qoff.back());
+    VB_CUDA(cudaMemcpyAsync(df.p, fq, df.n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    DBuf<double> rloc(s->h_eoff.back());
+    const int nE = s->topo.nE;
+    if (s->dof.k == 2) k_load_local<2><<<nE, 128, 0, s->stream>>>(s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, nE, rloc.p);
+    else if (s->dof.k == 3) k_load_local<3><<<nE, 128, 0, s->stream>>>(s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, nE, rloc.p);
+    else k_load_local<4><<<nE, 128, 0, s->stream>>>(s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, nE, rloc.p);
+    VB_KERNEL_CHECK();
+    k_gather_rhs<<<(unsigned)((s->n + 255) / 256), 256, 0, s->stream>>>(s->n, s->dof.nvf, s->d_adj_ptr.p,
+                                                                           s->d_adj_elem.p, s->d_adj_loc.p,
+                                                                           s->d_eoff.p, rloc.p, rhs);
+    VB_KERNEL_CHECK();
+    VB_CUDA(cudaStreamSynchronize(s->stream));
+    return VEM_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
+
+namespace vb {
+void spmv(vem_system* s, const double* x, double* y, cudaStream_t st) {
+  int64_t threads = s->n * 32;
+  k_spmv<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(s->n, s->d_rowptr.p, s->d_col.p, s->d_val.p, x, y);
+  VB_KERNEL_CHECK();
+}
+}  // namespace vb
+
+extern "C" int vem_apply(vem_system* s, const double* x, double* y) {
+  if (!s || !x || !y) { set_last_error("null argument"); return VEM_EINVAL; }
+  try {
+    spmv(s, x, y, s->stream);
+    return VEM_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
+
+extern "C" int vem_element_matrices(vem_system* s, const int32_t* elems, int32_t count, int32_t* nKout, double* A,
+                                    double* B, int64_t* dofs) {
+  if (!s || !elems || !nKout || count <= 0) { set_last_error("bad argument"); return VEM_EINVAL; }
+  try {
+    const auto& off = s->h_eoff;
+    int nK = (int)(off[elems[0] + 1] - off[elems[0]]);
+    const int np = s->dof.np;
+    std::vector<int64_t> g;
+    for (int i = 0; i < count; ++i) {
+      int e = elems[i];
+      VB_CHECK(e >= 0 && e < s->topo.nE, VEM_EINVAL, "element index out of range");
+      VB_CHECK(off[e + 1] - off[e] == nK, VEM_EINVAL, "elements with different DOF counts");
+      int64_t o2 = 0;
+      // offset of A: prefix sum of nK^2
+      for (int q = 0; q < e; ++q) { int64_t a = off[q + 1] - off[q]; o2 += a * a; }
+      if (A) VB_CUDA(cudaMemcpyAsync(A + (size_t)i * nK * nK, s->d_A.p + o2, sizeof(double) * nK * nK, cudaMemcpyDeviceToHost, s->stream));
+      if (B) VB_CUDA(cudaMemcpyAsync(B + (size_t)i * np * nK, s->d_B.p + (size_t)np * off[e], sizeof(double) * np * nK, cudaMemcpyDeviceToHost, s->stream));
+      if (dofs) {
+        element_global_dofs(s->topo, s->dof, e, g);
+        for (int j = 0; j < nK; ++j) dofs[(size_t)i * nK + j] = g[j];
+      }
+    }
+    VB_CUDA(cudaStreamSynchronize(s->stream));
+    *nKout = nK;
+    return VEM_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
+
+extern "C" int vem_csr(vem_system* s, int64_t* n, int64_t* nnz, int64_t* row_ptr, int32_t* col, double* vals) {
+  if (!s || !n || !nnz) { set_last_error("null argument"); return VEM_EINVAL; }
+  *n = s->n;
+  *nnz = s->nnz;
+  if (!vals) return VEM_OK;
+  try {
+    VB_CUDA(cudaMemcpyAsync(row_ptr, s->d_rowptr.p, sizeof(int64_t) * (s->n + 1), cudaMemcpyDeviceToHost, s->stream));
+    VB_CUDA(cudaMemcpyAsync(col, s->d_col.p, sizeof(int) * s->nnz, cudaMemcpyDeviceToHost, s->stream));
+    VB_CUDA(cudaMemcpyAsync(vals, s->d_val.p, sizeof(double) * s->nnz, cudaMemcpyDeviceToHost, s->stream));
+    VB_CUDA(cudaStreamSynchronize(s->stream));
+    return VEM_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
+
+extern "C" int vem_set_stream(vem_system* s, void* st) {
+  if (!s) { set_last_error("null system"); return VEM_EINVAL; }
+  s->stream = (cudaStream_t)st;
+  return VEM_OK;
+}
+
+extern "C" void vem_free(vem_system* s) { delete s; }
