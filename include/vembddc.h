@@ -123,6 +123,64 @@ int vem_set_stream(vem_system* sys, void* cuda_stream);
 void vem_free(vem_system* sys);
 const char* vem_last_error(void);
 
+/* ---------------------------------------------------------------- BDDC
+ * Primal constraint set (Sec. 5.1), bit mask:                              */
+#define BDDC_VERTEX 1u  /* all subdomain vertices primal                      */
+#define BDDC_EDGE 2u    /* per macro edge: the three component means            */
+#define BDDC_FACE 4u    /* per macro face: the three component integrals        */
+#define BDDC_FLUX 8u    /* per macro face: the normal flux (Eq. primalfacen)     */
+#define BDDC_ALL 16u    /* every interface DOF primal (test: M^{-1} = S^{-1})   */
+/* scaling: averaging of the dual interface values (Sec. 4.3, Sec. 6)       */
+#define BDDC_SCALING_MULTIPLICITY 0   /* 1/card on every dual DOF (Eq. pseudoinv)   */
+#define BDDC_SCALING_DELUXE 1         /* deluxe on macro faces, 1/card on edges     */
+
+typedef struct {
+  int32_t precision;        /* 0: FP64 local factors (the only value accepted) */
+  int32_t scaling;          /* unused (the bddc_setup argument decides)        */
+  uint32_t constraints;     /* unused (the bddc_setup argument decides)        */
+  double adaptive_threshold;/* unused: 0                                       */
+  int32_t nd_leaf;          /* elements per nested-dissection leaf (0: 4)      */
+  int32_t use_graph;        /* unused: 0                                       */
+  int32_t refine;           /* unused: 0                                       */
+  int32_t reserved[8];
+} bddc_options;
+
+/* BDDC setup (Sec. 4-6) for the partition elem_to_subdomain (host [nE],
+ * ids 0..N-1, each subdomain face-connected): interface classification into
+ * macro vertices/edges/faces, primal constraints as an orthogonal change of
+ * basis, nested-dissection multifrontal LDL^T factorizations of the
+ * subdomain Dirichlet problems (Eq. uipi) and constrained Neumann problems
+ * (zero-mean interior pressure, primal values fixed), the deluxe face
+ * blocks (Sec. 6) and the coarse saddle matrix bordered by
+ * sum_i |Omega_i| p_0,i = 0.  opts may be NULL.  The handle keeps a pointer
+ * to sys, which must outlive it.  Synchronizes. */
+int bddc_setup(vem_system* sys, const int32_t* elem_to_subdomain, uint32_t constraints, int scaling,
+               const bddc_options* opts, bddc** out);
+
+/* z = M^{-1} r (Eq. BDDCprec) followed by the subdomain Dirichlet
+ * (harmonic) extension; r, z: device system vectors (z overwritten).  The
+ * interior velocity rows and the interior (zero-mean) pressure part of r
+ * are ignored; only r on the interface DOFs and its subdomain-constant
+ * pressure part enter, as in the interface problem (Eq. globInt). */
+int bddc_apply(bddc* b, const double* r_dev, double* z_dev);
+
+/* PCG on K u = f with the BDDC preconditioner; u0 = interior Dirichlet
+ * solves so that every iterate is discrete-harmonic and the iteration is CG
+ * on the interface problem (Eq. globInt).  Stops when the interface residual
+ * (u_Gamma, p_0 parts) satisfies ||r||_2 <= rtol ||r_0||_2.  iters, kappa,
+ * lam_min, lam_max (nullable): iteration count and the Lanczos estimates
+ * from the CG coefficients.  f, u: device system vectors.  Returns
+ * VEM_ENOTCONV at maxit, VEM_EBREAKDOWN if p^T K p <= 0.  Synchronizes. */
+int pcg_solve(bddc* b, const double* f_dev, double* u_dev, double rtol, int maxit, int* iters, double* kappa,
+              double* lam_min, double* lam_max);
+
+/* Statistics by name: "n_subdomains", "n_coarse", "n_macro",
+ * "factor_bytes_dirichlet", "factor_bytes_neumann", "n_deluxe_faces",
+ * "deluxe_bytes", "phi_bytes". */
+int bddc_info(bddc* b, const char* key, double* value);
+int bddc_set_stream(bddc* b, void* cuda_stream);
+void bddc_free(bddc* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,1505 @@
+// BDDC preconditioner (Eq. BDDCprec) and PCG on the GPU: setup (local
+// factorizations, deluxe face blocks, coarse basis and coarse matrix) and the
+// per-iteration apply: restriction with the change of basis and scaling,
+// coarse solve, constrained Neumann solves, averaging, Dirichlet harmonic
+// extension.
+#include "system.h"
+#include "bddc_setup.h"
+#include "bddc_dev.h"
+#include "mf.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+namespace vb {
+void spmv(vem_system* s, const double* x, double* y, cudaStream_t st);
+
+// one batch of problems (all Dirichlet, all Neumann or all deluxe ones)
+struct Batch {
+  std::vector<int> probs;                 // global problem ids
+  int64_t vec_n = 0;                      // sum of problem sizes
+  int64_t uvec_n = 0;                     // sum of border sizes
+  int maxh = 0, maxnf = 0;
+  std::vector<int> level_ptr;             // nodes grouped by height
+  DBuf<int> d_levels;
+  std::vector<int> h_levels;
+  DBuf<double> F;                         // panels (FP64)
+  DBuf<double> U;                         // update matrices
+  int64_t nF = 0, nU = 0;
+};
+
+}  // namespace vb
+
+struct bddc {
+  vem_system* sys = nullptr;
+  vb::BddcHost H;
+  cudaStream_t stream = 0;
+  vb::SetupOptions opt;
+  // device copies of the structure
+  vb::DBuf<vb::NodeDev> d_nodes;
+  vb::DBuf<vb::ProbDev> d_probs;
+  vb::DBuf<vb::SubDev> d_subs;
+  vb::DBuf<vb::MacroDev> d_macros;
+  vb::DBuf<int> d_border, d_children, d_rel, d_dtype, d_dsrc, d_elpos, d_elptr, d_pv, d_sub_elems, d_vadj_ptr,
+      d_vadj, d_vcon_ptr, d_vcon_id, d_iface, d_elloc, d_elloc_ptr, d_share, d_gpos, d_gif;
+  vb::DBuf<int64_t> d_vdof, d_press, d_coarse, d_mdofs;
+  vb::DBuf<double> d_vcon_coef, d_wmean, d_hv, d_tau, d_deluxe;
+  std::vector<vb::NodeDev> h_nodes;
+  std::vector<vb::ProbDev> h_probs;
+  std::vector<vb::SubDev> h_subs;
+  std::vector<vb::MacroDev> h_macros;
+  vb::Batch bd, bn, bx;          // Dirichlet, Neumann, deluxe batches
+  // coarse
+  int64_t nc = 0, ncv = 0;
+  vb::DBuf<double> d_Kinv;       // inverse of the bordered coarse matrix, (nc+1)^2
+  vb::DBuf<double> d_phi;        // Phi_Gamma per subdomain
+  int64_t nphi = 0;
+  vb::DBuf<int> d_cg_ptr, d_cg_sub, d_cg_loc;   // coarse row -> (subdomain, local coordinate)
+  // apply workspaces
+  vb::DBuf<double> XD, XN, UVD, UVN, rC, uC, cloc, wloc, dwork, y, part;
+  int64_t ndual = 0, niface_tot = 0;
+  // PCG vectors
+  vb::DBuf<double> r, z, p, Ap, scal;
+  double last_setup_ms = 0;
+};
+
+namespace vb {
+
+static BddcView make_view(bddc* b) {
+  vem_system* s = b->sys;
+  BddcView V{};
+  V.np = s->dof.np;
+  V.k = s->dof.k;
+  V.nvf = s->dof.nvf;
+  V.n = s->n;
+  V.offK = s->d_eoff.p;
+  V.offK2 = s->d_eoffK2.p;
+  V.A = s->d_A.p;
+  V.B = s->d_B.p;
+  V.nodes = b->d_nodes.p;
+  V.probs = b->d_probs.p;
+  V.subs = b->d_subs.p;
+  V.macros = b->d_macros.p;
+  V.border = b->d_border.p;
+  V.children = b->d_children.p;
+  V.rel = b->d_rel.p;
+  V.dtype = b->d_dtype.p;
+  V.dsrc = b->d_dsrc.p;
+  V.elpos = b->d_elpos.p;
+  V.elptr = b->d_elptr.p;
+  V.pos_of_vdof = b->d_pv.p;
+  V.sub_elems = b->d_sub_elems.p;
+  V.vdof = b->d_vdof.p;
+  V.vadj_ptr = b->d_vadj_ptr.p;
+  V.vadj = b->d_vadj.p;
+  V.vcon_ptr = b->d_vcon_ptr.p;
+  V.vcon_id = b->d_vcon_id.p;
+  V.vcon_coef = b->d_vcon_coef.p;
+  V.press = b->d_press.p;
+  V.wmean = b->d_wmean.p;
+  V.iface = b->d_iface.p;
+  V.coarse = b->d_coarse.p;
+  V.elloc = b->d_elloc.p;
+  V.elloc_ptr = b->d_elloc_ptr.p;
+  V.mdofs = b->d_mdofs.p;
+  V.hv = b->d_hv.p;
+  V.tau = b->d_tau.p;
+  V.share = b->d_share.p;
+  V.gpos = b->d_gpos.p;
+  V.gif = b->d_gif.p;
+  V.deluxe = b->d_deluxe.p;
+  V.ncv = b->ncv;
+  V.nc = b->nc;
+  return V;
+}
+
+// ----------------------------------------------------------------- helpers
+
+// c = H^T v (in place) with the r reflectors of entity G (n values)
+VB_HD inline void hh_T_inplace(const BddcView& V, const MacroDev& G, double* c) {
+  for (int q = 0; q < G.r; ++q) {
+    if (G.hv_off < 0) break;
+    const double* h = V.hv + G.hv_off + (int64_t)q * G.n;
+    double dot = 0.0;
+    for (int i = 0; i < G.n; ++i) dot += h[i] * c[i];
+    dot *= V.tau[G.tau_off + q];
+    for (int i = 0; i < G.n; ++i) c[i] -= dot * h[i];
+  }
+}
+VB_HD inline void hh_inplace(const BddcView& V, const MacroDev& G, double* c) {
+  for (int q = G.r - 1; q >= 0; --q) {
+    if (G.hv_off < 0) break;
+    const double* h = V.hv + G.hv_off + (int64_t)q * G.n;
+    double dot = 0.0;
+    for (int i = 0; i < G.n; ++i) dot += h[i] * c[i];
+    dot *= V.tau[G.tau_off + q];
+    for (int i = 0; i < G.n; ++i) c[i] -= dot * h[i];
+  }
+}
+
+// Y = K_i X on subdomain-local dense blocks (rows: local velocity DOFs, then
+// local pressures; NC columns, column-major with leading dimension nloc).
+struct KElemMatvec {
+  BddcView V;
+  const int64_t* row_ptr;   // prefix of nloc over subdomains
+  int nsub;
+  const double* X;
+  double* Y;
+  int NC;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    int lo = 0, hi = nsub - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (row_ptr[mid] <= blk) lo = mid; else hi = mid - 1;
+    }
+    const SubDev S = V.subs[lo];
+    const int nloc = S.nv + S.npress;
+    const int row = (int)(blk - row_ptr[lo]);
+    const double* Xs = X + S.loc_off * NC;
+    double* Ys = Y + S.loc_off * NC;
+    const int npk = V.np;
+    const int* ellp = V.elloc_ptr + S.ellocptr_off;
+    for (int c = ex.tid; c < NC; c += ex.nt) {
+      double acc = 0.0;
+      if (row < S.nv) {
+        const int* vp = V.vadj_ptr + S.vadj_ptr_off;
+        for (int q = vp[row]; q < vp[row + 1]; ++q) {
+          const int le = V.vadj[S.vadj_off + 2 * q], a = V.vadj[S.vadj_off + 2 * q + 1];
+          const int e = V.sub_elems[S.elem_off + le];
+          const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+          const double* Ae = V.A + V.offK2[e];
+          const double* Be = V.B + (int64_t)npk * V.offK[e];
+          const int* el = V.elloc + S.elloc_off + ellp[le];
+          for (int b = 0; b < nK + npk; ++b) {
+            const int l = el[b];
+            if (l < 0) continue;
+            const double v = b < nK ? Ae[(int64_t)a * nK + b] : Be[(int64_t)(b - nK) * nK + a];
+            acc += v * Xs[(int64_t)c * nloc + l];
+          }
+        }
+      } else {
+        const int q = row - S.nv;
+        const int le = q / npk, a = q % npk;
+        const int e = V.sub_elems[S.elem_off + le];
+        const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+        const double* Be = V.B + (int64_t)npk * V.offK[e];
+        const int* el = V.elloc + S.elloc_off + ellp[le];
+        for (int b = 0; b < nK; ++b) {
+          const int l = el[b];
+          if (l < 0) continue;
+          acc += Be[(int64_t)a * nK + b] * Xs[(int64_t)c * nloc + l];
+        }
+      }
+      Ys[(int64_t)c * nloc + row] = acc;
+    }
+  }
+};
+
+// Neumann right-hand sides of the coarse basis: -K W at the problem
+// positions, pressure part projected onto sum-zero data (zero-mean Q_I)
+struct KNeuRhsPhi {
+  BddcView V;
+  const double* KW;
+  double* XN;
+  int NC;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int i = blk / NC, c = blk % NC;
+    const SubDev S = V.subs[i];
+    const ProbDev P = V.probs[S.neu];
+    const int nloc = S.nv + S.npress;
+    const double* kw = KW + S.loc_off * NC + (int64_t)c * nloc;
+    double* x = XN + P.vec_off * NC + (int64_t)c * P.n;
+    // compatibility with the subdomain-constant pressure: shift the pressure
+    // data by (sum of its constant-coefficient entries)/|Omega_i| times w
+    double sg = 0.0;
+    for (int le = ex.tid; le < S.ne; le += ex.nt) sg -= kw[S.nv + le * V.np];
+    sg = block_sum(ex, sg, ex.smem);
+    const double shift = sg / S.wsum;
+    for (int pos = ex.tid; pos < P.n; pos += ex.nt) {
+      const int dt = V.dtype[P.pos_off + pos], src = V.dsrc[P.pos_off + pos];
+      double v = 0.0;
+      if (dt == DT_VEL) v = -kw[src];
+      else if (dt == DT_PRESS) v = -kw[S.nv + src] - shift * V.wmean[S.press_off + src];
+      x[pos] = v;
+    }
+  }
+};
+
+// Phi = W + Z (local layout); Z read from the Neumann solution, its
+// pressure made zero-mean
+struct KPhiAssemble {
+  BddcView V;
+  const double* W;
+  const double* XN;
+  double* PHI;
+  int NC;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int i = blk / NC, c = blk % NC;
+    const SubDev S = V.subs[i];
+    const ProbDev P = V.probs[S.neu];
+    const int nloc = S.nv + S.npress;
+    const double* w = W + S.loc_off * NC + (int64_t)c * nloc;
+    double* phi = PHI + S.loc_off * NC + (int64_t)c * nloc;
+    const double* x = XN + P.vec_off * NC + (int64_t)c * P.n;
+    const int* pv = V.pos_of_vdof + P.pv_off;
+    for (int v = ex.tid; v < S.nv; v += ex.nt) {
+      const int pos = pv[v];
+      phi[v] = w[v] + (pos >= 0 ? x[pos] : 0.0);
+    }
+    // pressures: position via the element table of the problem
+    double wp = 0.0;
+    const int npk = V.np;
+    for (int q = ex.tid; q < S.npress; q += ex.nt) {
+      const int le = q / npk, a = q % npk;
+      const int e = V.sub_elems[S.elem_off + le];
+      const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+      const int pos = V.elpos[P.elpos_off + V.elptr[P.elptr_off + le] + nK + a];
+      const double pz = pos >= 0 ? x[pos] : 0.0;
+      phi[S.nv + q] = pz;
+      wp += V.wmean[S.press_off + q] * pz;
+    }
+    wp = block_sum(ex, wp, ex.smem);
+    const double m = wp / S.wsum;   // remove m * 1_{Omega_i}: constant coefficients only
+    for (int q = ex.tid; q < S.npress; q += ex.nt) phi[S.nv + q] += w[S.nv + q] - (q % npk == 0 ? m : 0.0);
+  }
+};
+
+// S_Pi = Phi^T (K Phi) per subdomain
+struct KGram {
+  BddcView V;
+  const double* PHI;
+  const double* KPHI;
+  double* SG;
+  int NC;
+  VB_HD void operator()(const KExec& ex, int i) const {
+    const SubDev S = V.subs[i];
+    const int nloc = S.nv + S.npress;
+    const double* ph = PHI + S.loc_off * NC;
+    const double* kp = KPHI + S.loc_off * NC;
+    for (int idx = ex.tid; idx < S.ncl * S.ncl; idx += ex.nt) {
+      const int a = idx / S.ncl, b = idx % S.ncl;
+      double acc = 0.0;
+      for (int l = 0; l < nloc; ++l) acc += ph[(int64_t)a * nloc + l] * kp[(int64_t)b * nloc + l];
+      SG[(int64_t)i * NC * NC + a * NC + b] = acc;
+    }
+  }
+};
+
+// interface rows of Phi (velocity part), column-major niface x ncl
+struct KPhiGamma {
+  BddcView V;
+  const double* PHI;
+  double* PG;
+  int NC;
+  VB_HD void operator()(const KExec& ex, int i) const {
+    const SubDev S = V.subs[i];
+    const int nloc = S.nv + S.npress;
+    const double* ph = PHI + S.loc_off * NC;
+    for (int idx = ex.tid; idx < S.niface * S.ncl; idx += ex.nt) {
+      const int c = idx / S.niface, l = idx % S.niface;
+      PG[S.phi_off + idx] = ph[(int64_t)c * nloc + V.iface[S.iface_off + l]];
+    }
+  }
+};
+
+// bordered coarse matrix (one CTA, subdomains in order: deterministic sums)
+struct KCoarseAssemble {
+  BddcView V;
+  const double* SG;
+  double* KB;
+  int N, NC;
+  VB_HD void operator()(const KExec& ex, int) const {
+    const int64_t nb = V.nc + 1;
+    for (int64_t q = ex.tid; q < nb * nb; q += ex.nt) KB[q] = 0.0;
+    ex.sync();
+    for (int i = 0; i < N; ++i) {
+      const SubDev S = V.subs[i];
+      const int64_t* g = V.coarse + S.coarse_off;
+      for (int idx = ex.tid; idx < S.ncl * S.ncl; idx += ex.nt) {
+        const int a = idx / S.ncl, b = idx % S.ncl;
+        KB[g[a] * nb + g[b]] += SG[(int64_t)i * NC * NC + a * NC + b];
+      }
+      ex.sync();
+      if (ex.tid == 0) {
+        KB[(V.ncv + i) * nb + V.nc] = S.volume;
+        KB[V.nc * nb + V.ncv + i] = S.volume;
+      }
+      ex.sync();
+    }
+  }
+};
+
+// Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix
+// (one CTA).  M is destroyed.
+struct KDenseInverse {
+  double* M;
+  double* Inv;
+  int64_t n;
+  int* status;
+  VB_HD void operator()(const KExec& ex, int) const {
+    double* red = ex.smem;          // nt values
+    int* ired = reinterpret_cast<int*>(ex.smem + ex.nt);
+    for (int64_t q = ex.tid; q < n * n; q += ex.nt) Inv[q] = (q / n == q % n) ? 1.0 : 0.0;
+    ex.sync();
+    for (int64_t c = 0; c < n; ++c) {
+      double best = -1.0;
+      int bi = (int)c;
+      for (int64_t r = c + ex.tid; r < n; r += ex.nt) {
+        double v = fabs(M[r * n + c]);
+        if (v > best) { best = v; bi = (int)r; }
+      }
+      red[ex.tid] = best;
+      ired[ex.tid] = bi;
+      ex.sync();
+      if (ex.tid == 0) {
+        for (int t = 1; t < ex.nt; ++t)
+          if (red[t] > red[0]) { red[0] = red[t]; ired[0] = ired[t]; }
+        if (!(red[0] > 0.0)) flag_error(status, 4);
+      }
+      ex.sync();
+      const int64_t p = ired[0];
+      if (p != c)
+        for (int64_t j = ex.tid; j < n; j += ex.nt) {
+          double t = M[c * n + j]; M[c * n + j] = M[p * n + j]; M[p * n + j] = t;
+          t = Inv[c * n + j]; Inv[c * n + j] = Inv[p * n + j]; Inv[p * n + j] = t;
+        }
+      ex.sync();
+      const double d = 1.0 / M[c * n + c];
+      ex.sync();
+      for (int64_t j = ex.tid; j < n; j += ex.nt) { M[c * n + j] *= d; Inv[c * n + j] *= d; }
+      ex.sync();
+      for (int64_t idx = ex.tid; idx < n * n; idx += ex.nt) {
+        const int64_t r = idx / n, j = idx % n;
+        if (r == c) continue;
+        const double f = M[r * n + c];
+        if (f == 0.0) continue;
+        if (j == c) continue;
+        M[r * n + j] -= f * M[c * n + j];
+        Inv[r * n + j] -= f * Inv[c * n + j];
+      }
+      ex.sync();
+      for (int64_t r = ex.tid; r < n; r += ex.nt) {
+        if (r == c) continue;
+        const double f = M[r * n + c];
+        Inv[r * n + c] -= f * Inv[c * n + c];
+        M[r * n + c] = 0.0;
+      }
+      ex.sync();
+    }
+  }
+};
+
+// deluxe: S_FF of one side from the root update matrix, rotated to the dual
+// coordinates: Sd = (H^T S H)[r:, r:]
+struct KDeluxeExtract {
+  BddcView V;
+  const int* probs;       // deluxe problem ids
+  const int* roots;       // root node per problem
+  const double* U;        // deluxe batch update store
+  double* work;           // n x n per problem
+  const int64_t* work_off;
+  double* SD;             // dual blocks
+  const int64_t* sd_off;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const ProbDev P = V.probs[probs[blk]];
+    const NodeDev R = V.nodes[roots[blk]];
+    const MacroDev F = V.macros[P.macro];
+    const int n = F.n, r = F.r, nd = n - r;
+    const double* Ur = U + R.upd_off;
+    double* S = work + work_off[blk];
+    for (int64_t idx = ex.tid; idx < (int64_t)n * n; idx += ex.nt) {
+      const int k = (int)(idx / n), i = (int)(idx % n);
+      S[idx] = i >= k ? Ur[(int64_t)k * n + i] : Ur[(int64_t)i * n + k];
+    }
+    ex.sync();
+    // S <- H^T S (columns), then S <- (H^T S^T)^T = H^T S H using symmetry of S
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = 0; q < r; ++q) {
+        const double* h = V.hv + F.hv_off + (int64_t)q * n;
+        const double tau = V.tau[F.tau_off + q];
+        for (int j = ex.tid; j < n; j += ex.nt) {
+          double* col = S + (int64_t)j * n;
+          double dot = 0.0;
+          for (int i = 0; i < n; ++i) dot += h[i] * col[i];
+          dot *= tau;
+          for (int i = 0; i < n; ++i) col[i] -= dot * h[i];
+        }
+        ex.sync();
+      }
+      // transpose in place
+      for (int64_t idx = ex.tid; idx < (int64_t)n * n; idx += ex.nt) {
+        const int k = (int)(idx / n), i = (int)(idx % n);
+        if (i > k) { double t = S[(int64_t)k * n + i]; S[(int64_t)k * n + i] = S[(int64_t)i * n + k]; S[(int64_t)i * n + k] = t; }
+      }
+      ex.sync();
+    }
+    double* sd = SD + sd_off[blk];
+    for (int64_t idx = ex.tid; idx < (int64_t)nd * nd; idx += ex.nt) {
+      const int k = (int)(idx / nd), i = (int)(idx % nd);
+      sd[idx] = 0.5 * (S[(int64_t)(r + k) * n + r + i] + S[(int64_t)(r + i) * n + r + k]);
+    }
+  }
+};
+
+// deluxe: D^(i) = (S_i + S_j)^{-1} S_i for the first sharing subdomain i
+// (Cholesky of the SPD sum, then n right-hand sides)
+struct KDeluxeCombine {
+  BddcView V;
+  const int* faces;
+  const int64_t* sd_i;
+  const int64_t* sd_j;
+  const double* SD;
+  double* work;
+  const int64_t* work_off;
+  double* DEL;
+  int* status;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const MacroDev F = V.macros[faces[blk]];
+    const int nd = F.ndual;
+    const double* Si = SD + sd_i[blk];
+    const double* Sj = SD + sd_j[blk];
+    double* L = work + work_off[blk];
+    for (int64_t idx = ex.tid; idx < (int64_t)nd * nd; idx += ex.nt) L[idx] = Si[idx] + Sj[idx];
+    ex.sync();
+    // right-looking Cholesky, column-major lower
+    for (int j = 0; j < nd; ++j) {
+      if (ex.tid == 0) {
+        double d = L[(int64_t)j * nd + j];
+        if (!(d > 0.0)) { flag_error(status, 5); d = 1.0; }
+        L[(int64_t)j * nd + j] = sqrt(d);
+      }
+      ex.sync();
+      const double dj = L[(int64_t)j * nd + j];
+      for (int i = j + 1 + ex.tid; i < nd; i += ex.nt) L[(int64_t)j * nd + i] /= dj;
+      ex.sync();
+      const int m = nd - j - 1;
+      for (int64_t idx = ex.tid; idx < (int64_t)m * m; idx += ex.nt) {
+        const int k = j + 1 + (int)(idx / m), i = j + 1 + (int)(idx % m);
+        if (i < k) continue;
+        L[(int64_t)k * nd + i] -= L[(int64_t)j * nd + i] * L[(int64_t)j * nd + k];
+      }
+      ex.sync();
+    }
+    // D = L^{-T} L^{-1} S_i, one column per thread
+    double* D = DEL + F.deluxe_off;
+    for (int c = ex.tid; c < nd; c += ex.nt) {
+      double* x = D + (int64_t)c * nd;
+      for (int i = 0; i < nd; ++i) x[i] = Si[(int64_t)c * nd + i];
+      for (int i = 0; i < nd; ++i) {
+        double v = x[i];
+        for (int k = 0; k < i; ++k) v -= L[(int64_t)k * nd + i] * x[k];
+        x[i] = v / L[(int64_t)i * nd + i];
+      }
+      for (int i = nd - 1; i >= 0; --i) {
+        double v = x[i];
+        for (int k = i + 1; k < nd; ++k) v -= L[(int64_t)i * nd + k] * x[k];
+        x[i] = v / L[(int64_t)i * nd + i];
+      }
+    }
+  }
+};
+
+// ----------------------------------------------------------------- apply
+
+// (1) r_G -> c = H^T r_G: primal part to the coarse rhs, dual part kept
+struct KRestrict {
+  BddcView V;
+  const double* r;
+  double* rC;
+  double* dwork;
+  double* part;
+  VB_HD void operator()(const KExec& ex, int g) const {
+    const MacroDev G = V.macros[g];
+    double* c = ex.smem;
+    double ss = 0.0;
+    for (int a = ex.tid; a < G.n; a += ex.nt) {
+      c[a] = r[V.mdofs[G.dofs_off + a]];
+      ss += c[a] * c[a];
+    }
+    ss = block_sum(ex, ss, ex.smem + G.n);
+    if (ex.tid == 0) {
+      part[g] = ss;
+      hh_T_inplace(V, G, c);
+    }
+    ex.sync();
+    for (int a = ex.tid; a < G.n; a += ex.nt) {
+      if (a < G.r) rC[G.coarse0 + a] = c[a];
+      else dwork[G.dual_off + a - G.r] = c[a];
+    }
+  }
+};
+
+// (2) subdomain constant-pressure residuals r_0,i
+struct KRestrictP0 {
+  BddcView V;
+  const double* r;
+  double* rC;
+  double* part;
+  int nmacro;
+  VB_HD void operator()(const KExec& ex, int i) const {
+    const SubDev S = V.subs[i];
+    double s = 0.0;
+    for (int le = ex.tid; le < S.ne; le += ex.nt) s += r[V.press[S.press_off + (int64_t)le * V.np]];
+    s = block_sum(ex, s, ex.smem);
+    if (ex.tid == 0) {
+      rC[V.ncv + i] = s;
+      part[nmacro + i] = s * s;
+    }
+  }
+};
+
+// (3) scaled dual residual of each sharing subdomain, back to the original
+// basis, written into its Neumann right-hand side
+struct KScaleToNeumann {
+  BddcView V;
+  const double* dwork;
+  double* XN;
+  VB_HD void operator()(const KExec& ex, int g) const {
+    const MacroDev G = V.macros[g];
+    if (G.ndual == 0) return;
+    double* c = ex.smem;
+    const double* dr = dwork + G.dual_off;
+    for (int si = 0; si < G.nshare; ++si) {
+      const int s = V.share[G.share_off + si];
+      const SubDev S = V.subs[s];
+      const ProbDev P = V.probs[S.neu];
+      for (int a = ex.tid; a < G.n; a += ex.nt) {
+        double v = 0.0;
+        if (a >= G.r) {
+          const int k = a - G.r;
+          if (G.deluxe_off >= 0) {
+            // D^T r for the first side, r - D^T r for the second
+            const double* D = V.deluxe + G.deluxe_off + (int64_t)k * G.ndual;
+            double dt = 0.0;
+            for (int i = 0; i < G.ndual; ++i) dt += D[i] * dr[i];
+            v = si == 0 ? dt : dr[k] - dt;
+          } else {
+            v = dr[k] / G.nshare;
+          }
+        }
+        c[a] = v;
+      }
+      ex.sync();
+      if (ex.tid == 0) hh_inplace(V, G, c);
+      ex.sync();
+      const int* gp = V.gpos + G.gpos_off + (int64_t)si * G.n;
+      for (int a = ex.tid; a < G.n; a += ex.nt) XN[P.vec_off + gp[a]] = c[a];
+      ex.sync();
+    }
+  }
+};
+
+// (4) local coarse rhs contributions Phi_Gamma^T g
+struct KCoarseLocal {
+  BddcView V;
+  const double* PG;
+  const double* XN;
+  double* cloc;
+  int NC;
+  VB_HD void operator()(const KExec& ex, int i) const {
+    const SubDev S = V.subs[i];
+    const ProbDev P = V.probs[S.neu];
+    const int* pv = V.pos_of_vdof + P.pv_off;
+    for (int c = ex.tid; c < S.ncl; c += ex.nt) {
+      const double* ph = PG + S.phi_off + (int64_t)c * S.niface;
+      double acc = 0.0;
+      for (int l = 0; l < S.niface; ++l) {
+        const int pos = pv[V.iface[S.iface_off + l]];
+        if (pos >= 0) acc += ph[l] * XN[P.vec_off + pos];
+      }
+      cloc[(int64_t)i * NC + c] = acc;
+    }
+  }
+};
+
+struct KCoarseGather {
+  BddcView V;
+  const int* ptr;
+  const int* sub;
+  const int* loc;
+  const double* cloc;
+  double* rC;
+  int NC;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int64_t hi = (int64_t)(blk + 1) * 256 < V.nc + 1 ? (int64_t)(blk + 1) * 256 : V.nc + 1;
+    for (int64_t c = (int64_t)blk * 256 + ex.tid; c < hi; c += ex.nt) {
+      if (c == V.nc) { rC[c] = 0.0; continue; }
+      double acc = rC[c];
+      for (int q = ptr[c]; q < ptr[c + 1]; ++q) acc += cloc[(int64_t)sub[q] * NC + loc[q]];
+      rC[c] = acc;
+    }
+  }
+};
+
+// (6) u_C = K_C^{-1} r_C (bordered), one row per CTA
+struct KCoarseSolve {
+  const double* Kinv;
+  const double* rC;
+  double* uC;
+  int64_t n;
+  VB_HD void operator()(const KExec& ex, int row) const {
+    const double* kr = Kinv + (int64_t)row * n;
+    double acc = 0.0;
+    for (int64_t j = ex.tid; j < n; j += ex.nt) acc += kr[j] * rC[j];
+    acc = block_sum(ex, acc, ex.smem);
+    if (ex.tid == 0) uC[row] = acc;
+  }
+};
+
+// (8) w_Gamma = z_Gamma + Phi_Gamma u_C on the interface of each subdomain
+struct KProlongLocal {
+  BddcView V;
+  const double* PG;
+  const double* XN;
+  const double* uC;
+  double* wloc;
+  VB_HD void operator()(const KExec& ex, int i) const {
+    const SubDev S = V.subs[i];
+    const ProbDev P = V.probs[S.neu];
+    const int* pv = V.pos_of_vdof + P.pv_off;
+    const int64_t* g = V.coarse + S.coarse_off;
+    for (int l = ex.tid; l < S.niface; l += ex.nt) {
+      const int pos = pv[V.iface[S.iface_off + l]];
+      double acc = pos >= 0 ? XN[P.vec_off + pos] : 0.0;
+      for (int c = 0; c < S.ncl; ++c) acc += PG[S.phi_off + (int64_t)c * S.niface + l] * uC[g[c]];
+      wloc[S.iface_off + l] = acc;
+    }
+  }
+};
+
+// (9) averaging R~_D^T: primal coordinates from u_C, dual ones scaled and
+// summed, back to the original basis
+struct KAverage {
+  BddcView V;
+  const double* wloc;
+  const double* uC;
+  double* z;
+  VB_HD void operator()(const KExec& ex, int g) const {
+    const MacroDev G = V.macros[g];
+    double* c = ex.smem;              // result coordinates
+    double* w = ex.smem + G.n;        // one side's values
+    double* w0 = ex.smem + 2 * G.n;   // first side's dual coordinates
+    for (int a = ex.tid; a < G.n; a += ex.nt) c[a] = a < G.r ? uC[G.coarse0 + a] : 0.0;
+    ex.sync();
+    for (int si = 0; si < G.nshare && G.ndual > 0; ++si) {
+      const int s = V.share[G.share_off + si];
+      const SubDev S = V.subs[s];
+      const int* gi = V.gif + G.gif_off + (int64_t)si * G.n;
+      for (int a = ex.tid; a < G.n; a += ex.nt) w[a] = wloc[S.iface_off + gi[a]];
+      ex.sync();
+      if (ex.tid == 0) hh_T_inplace(V, G, w);
+      ex.sync();
+      if (G.deluxe_off >= 0) {
+        if (si == 0) {
+          for (int a = ex.tid; a < G.ndual; a += ex.nt) w0[a] = w[G.r + a];
+        } else {
+          // D (w0 - w1) + w1
+          for (int k = ex.tid; k < G.ndual; k += ex.nt) {
+            double acc = 0.0;
+            for (int i = 0; i < G.ndual; ++i)
+              acc += V.deluxe[G.deluxe_off + (int64_t)i * G.ndual + k] * (w0[i] - w[G.r + i]);
+            c[G.r + k] = acc + w[G.r + k];
+          }
+        }
+      } else {
+        for (int k = ex.tid; k < G.ndual; k += ex.nt) c[G.r + k] += w[G.r + k] / G.nshare;
+      }
+      ex.sync();
+    }
+    if (ex.tid == 0) hh_inplace(V, G, c);
+    ex.sync();
+    for (int a = ex.tid; a < G.n; a += ex.nt) z[V.mdofs[G.dofs_off + a]] = c[a];
+  }
+};
+
+// (11) Dirichlet right-hand side: sgn * src at the problem positions, the
+// pressure part projected onto sum-zero data
+struct KDirRhs {
+  BddcView V;
+  const double* src;
+  double sgn;
+  double* XD;
+  VB_HD void operator()(const KExec& ex, int i) const {
+    const SubDev S = V.subs[i];
+    const ProbDev P = V.probs[S.dir];
+    double sg = 0.0;
+    for (int le = ex.tid; le < S.ne; le += ex.nt) sg += sgn * src[V.press[S.press_off + (int64_t)le * V.np]];
+    sg = block_sum(ex, sg, ex.smem);
+    const double shift = sg / S.wsum;
+    for (int pos = ex.tid; pos < P.n; pos += ex.nt) {
+      const int dt = V.dtype[P.pos_off + pos], s2 = V.dsrc[P.pos_off + pos];
+      double v = 0.0;
+      if (dt == DT_VEL) v = sgn * src[V.vdof[S.vdof_off + s2]];
+      else if (dt == DT_PRESS) v = sgn * src[V.press[S.press_off + s2]] - shift * V.wmean[S.press_off + s2];
+      XD[P.vec_off + pos] = v;
+    }
+  }
+};
+
+// (13) interior velocity and pressure from the Dirichlet solution
+struct KDirOut {
+  BddcView V;
+  const double* XD;
+  const double* uC;   // may be null: no p_0 part
+  double* z;
+  VB_HD void operator()(const KExec& ex, int i) const {
+    const SubDev S = V.subs[i];
+    const ProbDev P = V.probs[S.dir];
+    const int* pv = V.pos_of_vdof + P.pv_off;
+    for (int v = ex.tid; v < S.nv; v += ex.nt) {
+      const int pos = pv[v];
+      if (pos >= 0) z[V.vdof[S.vdof_off + v]] = XD[P.vec_off + pos];
+    }
+    const int npk = V.np;
+    double wp = 0.0;
+    for (int q = ex.tid; q < S.npress; q += ex.nt) {
+      const int le = q / npk, a = q % npk;
+      const int e = V.sub_elems[S.elem_off + le];
+      const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+      const int pos = V.elpos[P.elpos_off + V.elptr[P.elptr_off + le] + nK + a];
+      wp += V.wmean[S.press_off + q] * (pos >= 0 ? XD[P.vec_off + pos] : 0.0);
+    }
+    wp = block_sum(ex, wp, ex.smem);
+    const double m = wp / S.wsum;
+    const double p0 = uC ? uC[V.ncv + i] : 0.0;
+    for (int q = ex.tid; q < S.npress; q += ex.nt) {
+      const int le = q / npk, a = q % npk;
+      const int e = V.sub_elems[S.elem_off + le];
+      const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+      const int pos = V.elpos[P.elpos_off + V.elptr[P.elptr_off + le] + nK + a];
+      const double pz = pos >= 0 ? XD[P.vec_off + pos] : 0.0;
+      z[V.press[S.press_off + q]] = pz + (a == 0 ? p0 - m : 0.0);
+    }
+  }
+};
+
+// ----------------------------------------------------------------- vectors
+struct KDotPartial {
+  const double* a;
+  const double* b;
+  int64_t n;
+  double* part;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    double s = 0.0;
+    const int64_t chunk = (n + 1023) / 1024;
+    const int64_t lo = (int64_t)blk * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    for (int64_t i = lo + ex.tid; i < hi; i += ex.nt) s += a[i] * b[i];
+    s = block_sum(ex, s, ex.smem);
+    if (ex.tid == 0) part[blk] = s;
+  }
+};
+struct KSumPartial {
+  const double* part;
+  int n;
+  double* out;
+  VB_HD void operator()(const KExec& ex, int) const {
+    double s = 0.0;
+    for (int i = ex.tid; i < n; i += ex.nt) s += part[i];
+    s = block_sum(ex, s, ex.smem);
+    if (ex.tid == 0) *out = s;
+  }
+};
+struct KAxpby {   // y = a*x + b*y
+  const double* x;
+  double* y;
+  double a, b;
+  int64_t n;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int64_t hi = (int64_t)(blk + 1) * 256 < n ? (int64_t)(blk + 1) * 256 : n;
+    for (int64_t i = (int64_t)blk * 256 + ex.tid; i < hi; i += ex.nt) y[i] = a * x[i] + b * y[i];
+  }
+};
+struct KSub {     // r = f - Ax
+  const double* f;
+  const double* Ax;
+  double* r;
+  int64_t n;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int64_t hi = (int64_t)(blk + 1) * 256 < n ? (int64_t)(blk + 1) * 256 : n;
+    for (int64_t i = (int64_t)blk * 256 + ex.tid; i < hi; i += ex.nt) r[i] = f[i] - Ax[i];
+  }
+};
+
+}  // namespace vb
+
+// =================================================================== host
+namespace vb {
+
+template <class T>
+static void upload_vec(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+  if (h.empty()) { d.alloc(1); return; }
+  d.upload(h, s);
+}
+
+static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool with_vectors) {
+  B.probs = probs;
+  int64_t vec = 0, uv = 0, nF = 0, nU = 0;
+  std::vector<std::pair<int, int>> hn;   // (height, node)
+  B.maxnf = 1;
+  B.maxh = 0;
+  for (int q : probs) {
+    ProbDev& P = b->h_probs[q];
+    P.vec_off = vec;
+    vec += P.n;
+    const Problem& HP = b->H.probs[q];
+    int base = (int)(&P - &b->h_probs[0]);
+    (void)base;
+    for (size_t k = 0; k < HP.nodes.size(); ++k) {
+      int gid = b->h_probs[q].root - (int)HP.nodes.size() + 1 + (int)k;
+      NodeDev& N = b->h_nodes[gid];
+      N.panel_off = nF;
+      nF += (int64_t)(N.np + N.nb) * N.np;
+      N.upd_off = nU;
+      nU += (int64_t)N.nb * N.nb;
+      N.uvec_off = uv;
+      uv += N.nb;
+      hn.push_back({N.height, gid});
+      B.maxh = std::max(B.maxh, N.height);
+      B.maxnf = std::max(B.maxnf, N.np + N.nb);
+    }
+  }
+  std::sort(hn.begin(), hn.end());
+  B.level_ptr.assign(B.maxh + 2, 0);
+  B.h_levels.clear();
+  for (auto& pr : hn) {
+    B.level_ptr[pr.first + 1]++;
+    B.h_levels.push_back(pr.second);
+  }
+  for (int h = 0; h <= B.maxh; ++h) B.level_ptr[h + 1] += B.level_ptr[h];
+  B.vec_n = vec;
+  B.uvec_n = uv;
+  B.nF = nF;
+  B.nU = nU;
+  (void)with_vectors;
+}
+
+static void upload_levels(bddc* b, Batch& B) { upload_vec(B.d_levels, B.h_levels, b->stream); }
+
+static void factor_batch(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status) {
+  B.F.alloc(std::max<int64_t>(B.nF, 1));
+  B.U.alloc(std::max<int64_t>(B.nU, 1));
+  for (int h = 0; h <= B.maxh; ++h) {
+    int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
+    KFactor<double> f{V, B.d_levels.p + B.level_ptr[h], B.F.p, B.U.p, status.p};
+    launch(f, cnt, 256, 0, b->stream);
+  }
+}
+
+static void solve_batch(bddc* b, Batch& B, const BddcView& V, double* X, double* UV, int nrhs) {
+  size_t sm = sizeof(double) * (B.maxnf + 8);
+  for (int h = 0; h <= B.maxh; ++h) {
+    int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
+    launch(KFwd<double>{V, B.d_levels.p + B.level_ptr[h], B.F.p, X, UV, nrhs}, cnt, 256, sm, b->stream);
+  }
+  for (int h = B.maxh; h >= 0; --h) {
+    int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
+    launch(KBwd<double>{V, B.d_levels.p + B.level_ptr[h], B.F.p, X, nrhs}, cnt, 256, sm, b->stream);
+  }
+}
+
+static int max_macro_n(bddc* b) {
+  int m = 1;
+  for (auto& G : b->h_macros) m = std::max(m, G.n);
+  return m;
+}
+
+// z = M^{-1} r (BDDC with the Dirichlet harmonic extension), system layout
+static void apply_bddc(bddc* b, const double* r, double* z) {
+  vem_system* s = b->sys;
+  const BddcView V = make_view(b);
+  cudaStream_t st = b->stream;
+  const int nmac = (int)b->h_macros.size();
+  const int N = b->H.N;
+  const size_t msm = sizeof(double) * (3 * max_macro_n(b) + 256 + 8);
+  const int NC = 1;
+  b->XN.zero(st);
+  launch(KRestrict{V, r, b->rC.p, b->dwork.p, b->part.p}, nmac, 256, msm, st);
+  launch(KRestrictP0{V, r, b->rC.p, b->part.p, nmac}, N, 256, sizeof(double) * 256, st);
+  launch(KScaleToNeumann{V, b->dwork.p, b->XN.p}, nmac, 256, msm, st);
+  int ncl_max = 1;
+  for (auto& S : b->h_subs) ncl_max = std::max(ncl_max, S.ncl);
+  launch(KCoarseLocal{V, b->d_phi.p, b->XN.p, b->cloc.p, ncl_max}, N, 128, 0, st);
+  launch(KCoarseGather{V, b->d_cg_ptr.p, b->d_cg_sub.p, b->d_cg_loc.p, b->cloc.p, b->rC.p, ncl_max},
+         (b->nc + 1 + 255) / 256, 256, 0, st);
+  launch(KCoarseSolve{b->d_Kinv.p, b->rC.p, b->uC.p, b->nc + 1}, b->nc + 1, 256, sizeof(double) * 256, st);
+  solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, NC);
+  launch(KProlongLocal{V, b->d_phi.p, b->XN.p, b->uC.p, b->wloc.p}, N, 128, 0, st);
+  VB_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * s->n, st));
+  launch(KAverage{V, b->wloc.p, b->uC.p, z}, nmac, 256, msm, st);
+  spmv(s, z, b->y.p, st);
+  launch(KDirRhs{V, b->y.p, -1.0, b->XD.p}, N, 256, sizeof(double) * 256, st);
+  solve_batch(b, b->bd, V, b->XD.p, b->UVD.p, 1);
+  launch(KDirOut{V, b->XD.p, b->uC.p, z}, N, 256, sizeof(double) * 256, st);
+}
+
+static double dot(bddc* b, const double* x, const double* y, int64_t n) {
+  launch(KDotPartial{x, y, n, b->part.p + b->part.n - 1024 - 1}, 1024, 256, sizeof(double) * 256, b->stream);
+  launch(KSumPartial{b->part.p + b->part.n - 1024 - 1, 1024, b->scal.p}, 1, 256, sizeof(double) * 256, b->stream);
+  double h;
+  VB_CUDA(cudaMemcpyAsync(&h, b->scal.p, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  VB_CUDA(cudaStreamSynchronize(b->stream));
+  return h;
+}
+
+static double iface_norm(bddc* b, const double* r) {
+  const BddcView V = make_view(b);
+  const int nmac = (int)b->h_macros.size();
+  const size_t msm = sizeof(double) * (3 * max_macro_n(b) + 256 + 8);
+  launch(KRestrict{V, r, b->rC.p, b->dwork.p, b->part.p}, nmac, 256, msm, b->stream);
+  launch(KRestrictP0{V, r, b->rC.p, b->part.p, nmac}, b->H.N, 256, sizeof(double) * 256, b->stream);
+  launch(KSumPartial{b->part.p, nmac + b->H.N, b->scal.p}, 1, 256, sizeof(double) * 256, b->stream);
+  double h;
+  VB_CUDA(cudaMemcpyAsync(&h, b->scal.p, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  VB_CUDA(cudaStreamSynchronize(b->stream));
+  return std::sqrt(h);
+}
+
+static void lanczos(const std::vector<double>& al, const std::vector<double>& be, double& lmin, double& lmax) {
+  const int m = (int)al.size();
+  if (m == 0) { lmin = lmax = 1.0; return; }
+  std::vector<double> d(m), e(m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j < m - 1) e[j] = std::sqrt(be[j]) / al[j];
+  }
+  // Gershgorin bounds, then bisection with Sturm counts
+  double lo = 1e300, hi = -1e300;
+  for (int j = 0; j < m; ++j) {
+    double rr = (j > 0 ? std::fabs(e[j - 1]) : 0.0) + (j < m - 1 ? std::fabs(e[j]) : 0.0);
+    lo = std::min(lo, d[j] - rr);
+    hi = std::max(hi, d[j] + rr);
+  }
+  auto count = [&](double x) {   // eigenvalues < x
+    int c = 0;
+    double q = d[0] - x;
+    if (q < 0) c++;
+    for (int j = 1; j < m; ++j) {
+      if (q == 0.0) q = 1e-300;
+      q = d[j] - x - e[j - 1] * e[j - 1] / q;
+      if (q < 0) c++;
+    }
+    return c;
+  };
+  auto kth = [&](int k) {
+    double a = lo, bb = hi;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (a + bb);
+      if (count(mid) > k) bb = mid; else a = mid;
+    }
+    return 0.5 * (a + bb);
+  };
+  lmin = kth(0);
+  lmax = kth(m - 1);
+}
+
+}  // namespace vb
+
+using namespace vb;
+
+static int bfail(const Error& e) {
+  set_last_error(e.what());
+  return e.status;
+}
+
+extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constraints, int scaling,
+                          const bddc_options* opts, bddc** out) {
+  if (!s || !part || !out) { set_last_error("bddc_setup: null argument"); return VEM_EINVAL; }
+  *out = nullptr;
+  bddc* b = new bddc();
+  try {
+    b->sys = s;
+    b->stream = s->stream;
+    b->opt.constraints = constraints;
+    b->opt.scaling = scaling;
+    if (opts && opts->nd_leaf > 0) b->opt.leaf = opts->nd_leaf;
+    cudaStream_t st = b->stream;
+    BddcHost& H = b->H;
+    bddc_host_setup(s, part, b->opt, H, s->elem_wmean);
+    const int N = H.N;
+    const int np = s->dof.np;
+    // ---------------- flatten
+    std::vector<int> border, children, rel, dtype, dsrc, elpos, elptr, pv, sub_elems, vadj_ptr, vadj, vcon_ptr,
+        vcon_id, iface, elloc, elloc_ptr, share, gpos, gif;
+    std::vector<int64_t> vdof, press, coarse, mdofs;
+    std::vector<double> vcon_coef, wmean, hv, tau;
+    b->h_subs.assign(N, SubDev{});
+    int64_t loc = 0;
+    for (int i = 0; i < N; ++i) {
+      const Subdomain& S = H.subs[i];
+      SubDev& D = b->h_subs[i];
+      D.ne = (int)S.elems.size();
+      D.nv = (int)S.vdof.size();
+      D.npress = (int)S.press.size();
+      D.pstar = S.pstar;
+      D.niface = (int)S.iface_vdof.size();
+      D.ncl = (int)S.coarse.size();
+      D.dir = H.dir_prob[i];
+      D.neu = H.neu_prob[i];
+      D.volume = S.volume;
+      D.wsum = S.volume;   // sum of int_K m_0 over the subdomain = |Omega_i|
+      D.elem_off = (int64_t)sub_elems.size();
+      sub_elems.insert(sub_elems.end(), S.elems.begin(), S.elems.end());
+      D.vdof_off = (int64_t)vdof.size();
+      vdof.insert(vdof.end(), S.vdof.begin(), S.vdof.end());
+      D.vadj_ptr_off = (int64_t)vadj_ptr.size();
+      vadj_ptr.insert(vadj_ptr.end(), S.vadj_ptr.begin(), S.vadj_ptr.end());
+      D.vadj_off = (int64_t)vadj.size();
+      vadj.insert(vadj.end(), S.vadj.begin(), S.vadj.end());
+      D.vcon_ptr_off = (int64_t)vcon_ptr.size();
+      vcon_ptr.insert(vcon_ptr.end(), S.vcon_ptr.begin(), S.vcon_ptr.end());
+      D.vcon_off = (int64_t)vcon_id.size();
+      vcon_id.insert(vcon_id.end(), S.vcon_id.begin(), S.vcon_id.end());
+      vcon_coef.insert(vcon_coef.end(), S.vcon_coef.begin(), S.vcon_coef.end());
+      D.press_off = (int64_t)press.size();
+      press.insert(press.end(), S.press.begin(), S.press.end());
+      wmean.insert(wmean.end(), S.wmean.begin(), S.wmean.end());
+      D.iface_off = (int64_t)iface.size();
+      iface.insert(iface.end(), S.iface_vdof.begin(), S.iface_vdof.end());
+      D.coarse_off = (int64_t)coarse.size();
+      coarse.insert(coarse.end(), S.coarse.begin(), S.coarse.end());
+      // element column -> local index
+      D.ellocptr_off = (int64_t)elloc_ptr.size();
+      D.elloc_off = (int64_t)elloc.size();
+      int off = 0;
+      for (int le = 0; le < D.ne; ++le) {
+        elloc_ptr.push_back(off);
+        int e = S.elems[le];
+        int nK = (int)(s->h_eoff[e + 1] - s->h_eoff[e]);
+        for (int bb = 0; bb < nK; ++bb) {
+          int64_t g = s->h_sysdof[s->h_eoff[e] + bb];
+          int l = -1;
+          if (g >= 0) l = (int)(std::lower_bound(S.vdof.begin(), S.vdof.end(), g) - S.vdof.begin());
+          elloc.push_back(l);
+        }
+        for (int a = 0; a < np; ++a) elloc.push_back(D.nv + le * np + a);
+        off += nK + np;
+      }
+      elloc_ptr.push_back(off);
+      D.loc_off = loc;
+      loc += D.nv + D.npress;
+    }
+    // problems and nodes
+    b->h_probs.assign(H.probs.size(), ProbDev{});
+    b->h_nodes.clear();
+    for (size_t q = 0; q < H.probs.size(); ++q) {
+      const Problem& P = H.probs[q];
+      ProbDev& D = b->h_probs[q];
+      D.sub = P.sub;
+      D.kind = P.kind;
+      D.n = P.n;
+      D.npiv = P.npiv;
+      D.mult0 = P.mult0;
+      D.nmult = P.nmult;
+      D.macro = P.macro;
+      D.pos_off = (int64_t)dtype.size();
+      dtype.insert(dtype.end(), P.dtype.begin(), P.dtype.end());
+      for (int64_t x : P.dsrc) dsrc.push_back((int)x);
+      D.elpos_off = (int64_t)elpos.size();
+      elpos.insert(elpos.end(), P.elpos.begin(), P.elpos.end());
+      D.elptr_off = (int64_t)elptr.size();
+      elptr.insert(elptr.end(), P.elpos_off.begin(), P.elpos_off.end());
+      D.pv_off = (int64_t)pv.size();
+      pv.insert(pv.end(), P.pos_of_vdof.begin(), P.pos_of_vdof.end());
+      const int base = (int)b->h_nodes.size();
+      const int64_t border_base = (int64_t)border.size(), rel_base = (int64_t)rel.size();
+      const int child_base = (int)children.size();
+      border.insert(border.end(), P.border.begin(), P.border.end());
+      rel.insert(rel.end(), P.rel.begin(), P.rel.end());
+      for (int c : P.children) children.push_back(base + c);
+      for (const Node& Nd : P.nodes) {
+        NodeDev N{};
+        N.prob = (int)q;
+        N.p0 = Nd.p0;
+        N.np = Nd.np;
+        N.nb = Nd.nb;
+        N.parent = Nd.parent >= 0 ? base + Nd.parent : -1;
+        N.height = Nd.height;
+        N.first_child = child_base + Nd.first_child;
+        N.nchild = Nd.nchild;
+        N.flags = Nd.flags;
+        N.border_off = border_base + Nd.border_off;
+        N.rel_off = rel_base + Nd.rel_off;
+        b->h_nodes.push_back(N);
+      }
+      D.root = (int)b->h_nodes.size() - 1;
+    }
+    // macro entities
+    b->h_macros.assign(H.macros.size(), MacroDev{});
+    int64_t dual = 0, deluxe_n = 0;
+    for (size_t g = 0; g < H.macros.size(); ++g) {
+      const Macro& G = H.macros[g];
+      MacroDev& D = b->h_macros[g];
+      D.kind = G.kind;
+      D.n = (int)G.dofs.size();
+      D.r = G.r;
+      D.nshare = (int)G.share.size();
+      D.ndual = D.n - D.r;
+      D.dofs_off = (int64_t)mdofs.size();
+      mdofs.insert(mdofs.end(), G.dofs.begin(), G.dofs.end());
+      if (G.hv.empty()) {
+        D.hv_off = -1;
+        D.tau_off = -1;
+      } else {
+        D.hv_off = (int64_t)hv.size();
+        hv.insert(hv.end(), G.hv.begin(), G.hv.end());
+        D.tau_off = (int64_t)tau.size();
+        tau.insert(tau.end(), G.tau.begin(), G.tau.end());
+      }
+      D.coarse0 = G.coarse0;
+      D.dual_off = dual;
+      dual += D.ndual;
+      D.share_off = (int64_t)share.size();
+      share.insert(share.end(), G.share.begin(), G.share.end());
+      D.gpos_off = (int64_t)gpos.size();
+      D.gif_off = (int64_t)gif.size();
+      for (int si : G.share) {
+        const Subdomain& S = H.subs[si];
+        const Problem& PN = H.probs[H.neu_prob[si]];
+        for (int64_t g2 : G.dofs) {
+          int v = (int)(std::lower_bound(S.vdof.begin(), S.vdof.end(), g2) - S.vdof.begin());
+          gpos.push_back(PN.pos_of_vdof[v]);
+          gif.push_back((int)(std::lower_bound(S.iface_vdof.begin(), S.iface_vdof.end(), v) - S.iface_vdof.begin()));
+        }
+      }
+      D.deluxe_off = -1;
+    }
+    b->ndual = dual;
+    // deluxe problems
+    std::vector<int> dl_probs, dl_roots;
+    for (size_t q = 0; q < H.probs.size(); ++q)
+      if (H.probs[q].kind == PK_DELUXE) { dl_probs.push_back((int)q); dl_roots.push_back(b->h_probs[q].root); }
+    std::vector<int> faces;
+    std::vector<int64_t> sd_i, sd_j, sd_off_v, work_off_v, cw_off;
+    {
+      // dual block offsets per deluxe problem
+      int64_t o = 0, w = 0;
+      for (int q : dl_probs) {
+        const MacroDev& G = b->h_macros[H.probs[q].macro];
+        sd_off_v.push_back(o);
+        o += (int64_t)G.ndual * G.ndual;
+        work_off_v.push_back(w);
+        w += (int64_t)G.n * G.n;
+      }
+      for (size_t g = 0; g < H.macros.size(); ++g) {
+        MacroDev& G = b->h_macros[g];
+        if (G.kind != 2 || G.ndual == 0) continue;
+        int qa = -1, qb = -1;
+        for (size_t t = 0; t < dl_probs.size(); ++t)
+          if (H.probs[dl_probs[t]].macro == (int)g) {
+            if (H.probs[dl_probs[t]].sub == H.macros[g].share[0]) qa = (int)t; else qb = (int)t;
+          }
+        if (qa < 0 || qb < 0) continue;
+        faces.push_back((int)g);
+        sd_i.push_back(sd_off_v[qa]);
+        sd_j.push_back(sd_off_v[qb]);
+        G.deluxe_off = deluxe_n;
+        deluxe_n += (int64_t)G.ndual * G.ndual;
+      }
+      int64_t c = 0;
+      for (int g : faces) {
+        cw_off.push_back(c);
+        c += (int64_t)b->h_macros[g].ndual * b->h_macros[g].ndual;
+      }
+    }
+    // ---------------- upload structure
+    upload_vec(b->d_border, border, st);
+    upload_vec(b->d_children, children, st);
+    upload_vec(b->d_rel, rel, st);
+    upload_vec(b->d_dtype, dtype, st);
+    upload_vec(b->d_dsrc, dsrc, st);
+    upload_vec(b->d_elpos, elpos, st);
+    upload_vec(b->d_elptr, elptr, st);
+    upload_vec(b->d_pv, pv, st);
+    upload_vec(b->d_sub_elems, sub_elems, st);
+    upload_vec(b->d_vadj_ptr, vadj_ptr, st);
+    upload_vec(b->d_vadj, vadj, st);
+    upload_vec(b->d_vcon_ptr, vcon_ptr, st);
+    upload_vec(b->d_vcon_id, vcon_id, st);
+    upload_vec(b->d_vcon_coef, vcon_coef, st);
+    upload_vec(b->d_iface, iface, st);
+    upload_vec(b->d_elloc, elloc, st);
+    upload_vec(b->d_elloc_ptr, elloc_ptr, st);
+    upload_vec(b->d_share, share, st);
+    upload_vec(b->d_gpos, gpos, st);
+    upload_vec(b->d_gif, gif, st);
+    upload_vec(b->d_vdof, vdof, st);
+    upload_vec(b->d_press, press, st);
+    upload_vec(b->d_coarse, coarse, st);
+    upload_vec(b->d_mdofs, mdofs, st);
+    upload_vec(b->d_wmean, wmean, st);
+    upload_vec(b->d_hv, hv, st);
+    upload_vec(b->d_tau, tau, st);
+    b->ncv = H.ncoarse_vel;
+    b->nc = H.ncoarse;
+    // batches
+    std::vector<int> dprobs(H.dir_prob.begin(), H.dir_prob.end()), nprobs(H.neu_prob.begin(), H.neu_prob.end());
+    build_batch(b, b->bd, dprobs, true);
+    build_batch(b, b->bn, nprobs, true);
+    build_batch(b, b->bx, dl_probs, false);
+    upload_vec(b->d_nodes, b->h_nodes, st);
+    upload_vec(b->d_probs, b->h_probs, st);
+    upload_vec(b->d_subs, b->h_subs, st);
+    upload_vec(b->d_macros, b->h_macros, st);
+    upload_levels(b, b->bd);
+    upload_levels(b, b->bn);
+    upload_levels(b, b->bx);
+    BddcView V = make_view(b);
+    // ---------------- numeric factorizations (S4)
+    DBuf<int> status(1);
+    status.zero(st);
+    factor_batch(b, b->bd, V, status);
+    factor_batch(b, b->bn, V, status);
+    factor_batch(b, b->bx, V, status);
+    {
+      auto stv = status.download(st);
+      VB_CHECK(stv[0] != 2, VEM_EINVAL, "local factorization: matrix entry outside the symbolic front");
+      VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "local factorization: zero or wrong-signed pivot");
+    }
+    // ---------------- deluxe blocks (S6)
+    b->d_deluxe.alloc(std::max<int64_t>(deluxe_n, 1));
+    if (!faces.empty()) {
+      DBuf<int> dp, dr, df;
+      DBuf<int64_t> dso, dwo, dsi, dsj, dcw;
+      upload_vec(dp, dl_probs, st);
+      upload_vec(dr, dl_roots, st);
+      upload_vec(df, faces, st);
+      upload_vec(dso, sd_off_v, st);
+      upload_vec(dwo, work_off_v, st);
+      upload_vec(dsi, sd_i, st);
+      upload_vec(dsj, sd_j, st);
+      upload_vec(dcw, cw_off, st);
+      int64_t sdn = 0, wn = 0, cwn = 0;
+      for (size_t t = 0; t < dl_probs.size(); ++t) {
+        const MacroDev& G = b->h_macros[H.probs[dl_probs[t]].macro];
+        sdn += (int64_t)G.ndual * G.ndual;
+        wn += (int64_t)G.n * G.n;
+      }
+      for (int g : faces) cwn += (int64_t)b->h_macros[g].ndual * b->h_macros[g].ndual;
+      DBuf<double> SD(std::max<int64_t>(sdn, 1)), work(std::max<int64_t>(wn, 1)), cwork(std::max<int64_t>(cwn, 1));
+      V = make_view(b);
+      launch(KDeluxeExtract{V, dp.p, dr.p, b->bx.U.p, work.p, dwo.p, SD.p, dso.p}, (int)dl_probs.size(), 256, 0, st);
+      launch(KDeluxeCombine{V, df.p, dsi.p, dsj.p, SD.p, cwork.p, dcw.p, b->d_deluxe.p, status.p}, (int)faces.size(),
+             256, 0, st);
+      auto stv = status.download(st);
+      VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe: face Schur complement sum not positive definite");
+    }
+    b->bx.F.release();
+    b->bx.U.release();
+    upload_vec(b->d_macros, b->h_macros, st);
+    V = make_view(b);
+    // ---------------- coarse basis and coarse matrix (S5)
+    int NC = 1;
+    for (auto& S : b->h_subs) NC = std::max(NC, S.ncl);
+    {
+      std::vector<double> W((size_t)loc * NC, 0.0);
+      for (int i = 0; i < N; ++i) {
+        const Subdomain& S = H.subs[i];
+        const SubDev& D = b->h_subs[i];
+        const int nloc = D.nv + D.npress;
+        double* Ws = &W[(size_t)D.loc_off * NC];
+        int c = 0;
+        for (int gi : S.macros) {
+          const Macro& G = H.macros[gi];
+          const int n = (int)G.dofs.size();
+          std::vector<double> e(n), col(n);
+          for (int q = 0; q < G.r; ++q, ++c) {
+            if (G.hv.empty()) {
+              std::fill(col.begin(), col.end(), 0.0);
+              col[q] = 1.0;
+            } else {
+              std::fill(e.begin(), e.end(), 0.0);
+              e[q] = 1.0;
+              hh_apply(G, e.data(), col.data());
+            }
+            for (int a = 0; a < n; ++a) {
+              int v = (int)(std::lower_bound(S.vdof.begin(), S.vdof.end(), G.dofs[a]) - S.vdof.begin());
+              Ws[(size_t)c * nloc + v] = col[a];
+            }
+          }
+        }
+        for (int le = 0; le < D.ne; ++le) Ws[(size_t)c * nloc + D.nv + le * np] = 1.0;   // p_0 column
+        VB_CHECK(c + 1 == D.ncl, VEM_EINVAL, "coarse column count mismatch");
+      }
+      DBuf<double> dW, KW((size_t)loc * NC), PHI((size_t)loc * NC);
+      upload_vec(dW, W, st);
+      std::vector<int64_t> rp(N + 1, 0);
+      for (int i = 0; i < N; ++i) rp[i + 1] = rp[i] + b->h_subs[i].nv + b->h_subs[i].npress;
+      DBuf<int64_t> drp;
+      upload_vec(drp, rp, st);
+      launch(KElemMatvec{V, drp.p, N, dW.p, KW.p, NC}, loc, 32, 0, st);
+      b->XN.alloc(std::max<int64_t>(b->bn.vec_n * NC, 1));
+      b->UVN.alloc(std::max<int64_t>(b->bn.uvec_n * NC, 1));
+      launch(KNeuRhsPhi{V, KW.p, b->XN.p, NC}, (int64_t)N * NC, 256, sizeof(double) * 256, st);
+      solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, NC);
+      launch(KPhiAssemble{V, dW.p, b->XN.p, PHI.p, NC}, (int64_t)N * NC, 256, sizeof(double) * 256, st);
+      launch(KElemMatvec{V, drp.p, N, PHI.p, KW.p, NC}, loc, 32, 0, st);
+      DBuf<double> SG((size_t)N * NC * NC);
+      launch(KGram{V, PHI.p, KW.p, SG.p, NC}, N, 256, 0, st);
+      int64_t nphi = 0;
+      for (auto& D : b->h_subs) {
+        D.phi_off = nphi;
+        nphi += (int64_t)D.niface * D.ncl;
+      }
+      upload_vec(b->d_subs, b->h_subs, st);
+      V = make_view(b);
+      b->d_phi.alloc(std::max<int64_t>(nphi, 1));
+      launch(KPhiGamma{V, PHI.p, b->d_phi.p, NC}, N, 256, 0, st);
+      const int64_t nb = b->nc + 1;
+      DBuf<double> KB(nb * nb);
+      b->d_Kinv.alloc(nb * nb);
+      launch(KCoarseAssemble{V, SG.p, KB.p, N, NC}, 1, 256, 0, st);
+      status.zero(st);
+      launch(KDenseInverse{KB.p, b->d_Kinv.p, nb, status.p}, 1, 256, sizeof(double) * 512, st);
+      auto stv = status.download(st);
+      VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "coarse matrix singular");
+    }
+    // coarse gather lists
+    {
+      std::vector<std::vector<std::pair<int, int>>> lists(b->nc);
+      for (int i = 0; i < N; ++i)
+        for (int c = 0; c < b->h_subs[i].ncl; ++c) lists[H.subs[i].coarse[c]].push_back({i, c});
+      std::vector<int> ptr(b->nc + 1, 0), sub, lc;
+      for (int64_t c = 0; c < b->nc; ++c) {
+        for (auto& pr : lists[c]) { sub.push_back(pr.first); lc.push_back(pr.second); }
+        ptr[c + 1] = (int)sub.size();
+      }
+      upload_vec(b->d_cg_ptr, ptr, st);
+      upload_vec(b->d_cg_sub, sub, st);
+      upload_vec(b->d_cg_loc, lc, st);
+    }
+    // ---------------- apply workspaces
+    b->XN.alloc(std::max<int64_t>(b->bn.vec_n, 1));
+    b->UVN.alloc(std::max<int64_t>(b->bn.uvec_n, 1));
+    b->XD.alloc(std::max<int64_t>(b->bd.vec_n, 1));
+    b->UVD.alloc(std::max<int64_t>(b->bd.uvec_n, 1));
+    b->rC.alloc(b->nc + 1);
+    b->uC.alloc(b->nc + 1);
+    b->cloc.alloc((size_t)N * NC);
+    int64_t nif = 0;
+    for (auto& D : b->h_subs) nif += D.niface;
+    b->wloc.alloc(std::max<int64_t>(nif, 1));
+    b->dwork.alloc(std::max<int64_t>(b->ndual, 1));
+    b->y.alloc(s->n);
+    b->part.alloc(b->h_macros.size() + N + 1024 + 8);
+    b->r.alloc(s->n);
+    b->z.alloc(s->n);
+    b->p.alloc(s->n);
+    b->Ap.alloc(s->n);
+    b->scal.alloc(4);
+    VB_CUDA(cudaStreamSynchronize(st));
+    *out = b;
+    return VEM_OK;
+  } catch (const Error& e) {
+    delete b;
+    return bfail(e);
+  } catch (const std::exception& e) {
+    delete b;
+    set_last_error(e.what());
+    return VEM_ENOMEM;
+  }
+}
+
+extern "C" int bddc_apply(bddc* b, const double* r, double* z) {
+  if (!b || !r || !z) { set_last_error("bddc_apply: null argument"); return VEM_EINVAL; }
+  try {
+    apply_bddc(b, r, z);
+    return VEM_OK;
+  } catch (const Error& e) {
+    return bfail(e);
+  }
+}
+
+extern "C" int pcg_solve(bddc* b, const double* f, double* u, double rtol, int maxit, int* iters, double* kappa,
+                         double* lam_min, double* lam_max) {
+  if (!b || !f || !u) { set_last_error("pcg_solve: null argument"); return VEM_EINVAL; }
+  try {
+    vem_system* s = b->sys;
+    const int64_t n = s->n;
+    cudaStream_t st = b->stream;
+    const BddcView V = make_view(b);
+    const int N = b->H.N;
+    const int nblk = (int)((n + 255) / 256);
+    // x0: interior Dirichlet solves, zero interface data
+    VB_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
+    launch(KDirRhs{V, f, 1.0, b->XD.p}, N, 256, sizeof(double) * 256, st);
+    solve_batch(b, b->bd, V, b->XD.p, b->UVD.p, 1);
+    launch(KDirOut{V, b->XD.p, nullptr, u}, N, 256, sizeof(double) * 256, st);
+    spmv(s, u, b->Ap.p, st);
+    launch(KSub{f, b->Ap.p, b->r.p, n}, nblk, 256, 0, st);
+    const double n0 = iface_norm(b, b->r.p);
+    const double nf = std::sqrt(dot(b, f, f, n));
+    std::vector<double> al, be;
+    int it = 0;
+    int status = VEM_OK;
+    if (n0 > 1e-14 * nf) {
+      apply_bddc(b, b->r.p, b->z.p);
+      VB_CUDA(cudaMemcpyAsync(b->p.p, b->z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      double rz = dot(b, b->r.p, b->z.p, n);
+      status = VEM_ENOTCONV;
+      while (it < maxit) {
+        spmv(s, b->p.p, b->Ap.p, st);
+        const double pAp = dot(b, b->p.p, b->Ap.p, n);
+        if (!(pAp > 0.0) || !std::isfinite(pAp) || !std::isfinite(rz)) { status = VEM_EBREAKDOWN; break; }
+        const double alpha = rz / pAp;
+        launch(KAxpby{b->p.p, u, alpha, 1.0, n}, nblk, 256, 0, st);
+        launch(KAxpby{b->Ap.p, b->r.p, -alpha, 1.0, n}, nblk, 256, 0, st);
+        ++it;
+        al.push_back(alpha);
+        const double nr = iface_norm(b, b->r.p);
+        if (nr <= rtol * n0) { status = VEM_OK; break; }
+        apply_bddc(b, b->r.p, b->z.p);
+        const double rzn = dot(b, b->r.p, b->z.p, n);
+        const double beta = rzn / rz;
+        be.push_back(beta);
+        rz = rzn;
+        launch(KAxpby{b->z.p, b->p.p, 1.0, beta, n}, nblk, 256, 0, st);
+      }
+    }
+    double lmin = 1.0, lmax = 1.0;
+    lanczos(al, be, lmin, lmax);
+    if (iters) *iters = it;
+    if (lam_min) *lam_min = lmin;
+    if (lam_max) *lam_max = lmax;
+    if (kappa) *kappa = lmax / lmin;
+    VB_CUDA(cudaStreamSynchronize(st));
+    if (status != VEM_OK) set_last_error(status == VEM_ENOTCONV ? "CG did not reach rtol" : "CG breakdown");
+    return status;
+  } catch (const Error& e) {
+    return bfail(e);
+  }
+}
+
+extern "C" int bddc_set_stream(bddc* b, void* st) {
+  if (!b) { set_last_error("null bddc"); return VEM_EINVAL; }
+  b->stream = (cudaStream_t)st;
+  return VEM_OK;
+}
+
+extern "C" int bddc_info(bddc* b, const char* key, double* value) {
+  if (!b || !key || !value) { set_last_error("bddc_info: null argument"); return VEM_EINVAL; }
+  std::string k(key);
+  if (k == "n_subdomains") *value = b->H.N;
+  else if (k == "n_coarse") *value = (double)b->nc;
+  else if (k == "n_macro") *value = (double)b->h_macros.size();
+  else if (k == "factor_bytes_dirichlet") *value = 8.0 * b->bd.nF;
+  else if (k == "factor_bytes_neumann") *value = 8.0 * b->bn.nF;
+  else if (k == "n_deluxe_faces") {
+    int c = 0;
+    for (auto& G : b->h_macros) c += G.deluxe_off >= 0;
+    *value = c;
+  } else if (k == "deluxe_bytes") {
+    double t = 0;
+    for (auto& G : b->h_macros)
+      if (G.deluxe_off >= 0) t += 8.0 * G.ndual * G.ndual;
+    *value = t;
+  } else if (k == "phi_bytes") *value = 8.0 * b->d_phi.n;
+  else {
+    set_last_error("bddc_info: unknown key " + k);
+    return VEM_EINVAL;
+  }
+  return VEM_OK;
+}
+
+extern "C" void bddc_free(bddc* b) { delete b; }

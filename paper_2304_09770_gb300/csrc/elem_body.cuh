@@ -19,23 +19,11 @@
 #include <cmath>
 #include "common.h"
 #include "system.h"
-
-#ifdef __CUDACC__
-#define VB_HD __host__ __device__
-#else
-#define VB_HD
-#endif
+#include "launch.h"
 
 namespace vb {
 
-struct Exec {
-  int tid, nt;
-#ifdef __CUDA_ARCH__
-  __device__ void sync() const { __syncthreads(); }
-#else
-  VB_HD void sync() const {}
-#endif
-};
+using Exec = KExec;
 
 // element-independent tables (quadrature rules, monomial exponents)
 struct ElemTables {
@@ -583,11 +571,13 @@ struct ElemBuilder {
     return acc;
   }
 
-  VB_HD bool build(double nu, double* Aout, double* Bout, double* P0out) {
+  VB_HD bool build(double nu, double* Aout, double* Bout, double* P0out, double* WMout = nullptr) {
     geometry();
     for (int g = ex.tid; g < S::NP1; g += ex.nt) sh.bndm[g] = 0.0;
     ex.sync();
     volume_moments();
+    if (WMout)
+      for (int a = ex.tid; a < S::NP0; a += ex.nt) WMout[a] = sh.mu[a];   // int_K m_a
     bool ok = volume_systems();
     for (int f = 0; f < R.nf; ++f) ok = face(f) && ok;
     const double hK = sh.hK, vol = sh.vol;

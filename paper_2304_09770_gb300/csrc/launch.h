@@ -1,0 +1,72 @@
+// Kernel launch helper.  Every kernel of the library is a functor
+//   struct K { __host__ __device__ void operator()(const KExec& ex, int block) const; };
+// run with one CTA per block index; ex.tid / ex.nt are the thread index and
+// count, ex.smem the dynamic shared memory, ex.sync() the CTA barrier.
+#pragma once
+#include "common.h"
+
+#ifdef __CUDACC__
+#define VB_HD __host__ __device__
+#else
+#define VB_HD
+#endif
+
+namespace vb {
+
+struct KExec {
+  int tid, nt;
+  double* smem;
+#ifdef __CUDA_ARCH__
+  __device__ void sync() const { __syncthreads(); }
+#else
+  VB_HD void sync() const {}
+#endif
+};
+
+#ifdef __CUDACC__
+template <class F>
+__global__ void k_run(const F f) {
+  extern __shared__ double vb_smem[];
+  f(KExec{(int)threadIdx.x, (int)blockDim.x, vb_smem}, (int)blockIdx.x);
+}
+
+template <class F>
+inline void launch(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaStream_t s) {
+  if (nblocks <= 0) return;
+  VB_CHECK(nblocks < (int64_t)INT32_MAX, VEM_EINVAL, "grid too large");
+  if (smem > 48 * 1024)
+    VB_CUDA(cudaFuncSetAttribute(k_run<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_run<F><<<(unsigned)nblocks, nthreads, smem, s>>>(f);
+  VB_KERNEL_CHECK();
+}
+#else
+template <class F>
+inline void launch(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaStream_t) {
+  (void)nthreads;
+  std::vector<double> buf(smem / sizeof(double) + 1, 0.0);
+  for (int64_t b = 0; b < nblocks; ++b) f(KExec{0, 1, buf.data()}, (int)b);
+}
+#endif
+
+VB_HD inline void flag_error(int* p, int v) {
+#ifdef __CUDA_ARCH__
+  atomicMax(p, v);
+#else
+  if (*p < v) *p = v;
+#endif
+}
+
+// block-wide sum of one double per thread (deterministic tree), result valid in all threads
+VB_HD inline double block_sum(const KExec& ex, double v, double* red) {
+  red[ex.tid] = v;
+  ex.sync();
+  for (int s = 1; s < ex.nt; s <<= 1) {
+    if ((ex.tid & (2 * s - 1)) == 0 && ex.tid + s < ex.nt) red[ex.tid] += red[ex.tid + s];
+    ex.sync();
+  }
+  double r = red[0];
+  ex.sync();
+  return r;
+}
+
+}  // namespace vb

@@ -1,0 +1,264 @@
+// Batched multifrontal LDL^T of the subdomain problems (nested-dissection
+// trees, dense fronts, no pivoting: velocity pivots positive, pressure and
+// multiplier pivots negative) and the triangular solves.  One CTA per front;
+// all fronts of one tree height across all problems run in one launch.
+//
+// Front of node t: positions [p0, p0+np) (pivots) followed by its border
+// (sorted positions eliminated by ancestors).  Storage: panel nf x np
+// column-major (D on the diagonal, unit L below), update matrix nb x nb
+// column-major (lower triangle valid), consumed by the parent.
+#pragma once
+#include "launch.h"
+#include "bddc_dev.h"
+#include "bddc_setup.h"
+
+namespace vb {
+
+VB_HD inline int front_index(const NodeDev& N, const int* bord, int x) {
+  if (x < N.p0 + N.np) return x >= N.p0 ? x - N.p0 : -1;
+  int lo = 0, hi = N.nb - 1;
+  if (hi < 0) return -1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (bord[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return bord[lo] == x ? N.np + lo : -1;
+}
+
+template <class T>
+struct KFactor {
+  BddcView V;
+  const int* list;
+  T* F;
+  T* U;
+  int* status;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int t = list[blk];
+    const NodeDev N = V.nodes[t];
+    const ProbDev P = V.probs[N.prob];
+    const SubDev S = V.subs[P.sub];
+    const int np = N.np, nb = N.nb, nf = np + nb;
+    const int npk = V.np;
+    T* pan = F + N.panel_off;
+    T* upd = U + N.upd_off;
+    const int* bord = V.border + N.border_off;
+    for (int64_t i = ex.tid; i < (int64_t)nf * np; i += ex.nt) pan[i] = (T)0;
+    for (int64_t i = ex.tid; i < (int64_t)nb * nb; i += ex.nt) upd[i] = (T)0;
+    ex.sync();
+    // original matrix entries of the pivot columns (one thread per column)
+    for (int j = ex.tid; j < np; j += ex.nt) {
+      const int pos = N.p0 + j;
+      const int dt = V.dtype[P.pos_off + pos];
+      const int src = V.dsrc[P.pos_off + pos];
+      T* colp = pan + (int64_t)j * nf;
+      if (dt == DT_VEL) {
+        const int* vp = V.vadj_ptr + S.vadj_ptr_off;
+        for (int q = vp[src]; q < vp[src + 1]; ++q) {
+          const int le = V.vadj[S.vadj_off + 2 * q], a = V.vadj[S.vadj_off + 2 * q + 1];
+          const int e = V.sub_elems[S.elem_off + le];
+          const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+          const int* ep = V.elpos + P.elpos_off + V.elptr[P.elptr_off + le];
+          const double* Ae = V.A + V.offK2[e];
+          const double* Be = V.B + (int64_t)npk * V.offK[e];
+          for (int b = 0; b < nK + npk; ++b) {
+            const int x = ep[b];
+            if (x < pos) continue;
+            const double v = b < nK ? Ae[(int64_t)a * nK + b] : Be[(int64_t)(b - nK) * nK + a];
+            const int fi = front_index(N, bord, x);
+            if (fi < 0) { flag_error(status, 2); continue; }
+            colp[fi] += (T)v;
+          }
+        }
+        if (P.kind == PK_NEUMANN) {
+          const int* cp = V.vcon_ptr + S.vcon_ptr_off;
+          for (int q = cp[src]; q < cp[src + 1]; ++q) {
+            const int x = P.mult0 + V.vcon_id[S.vcon_off + q];
+            const int fi = front_index(N, bord, x);
+            if (fi < 0) { flag_error(status, 2); continue; }
+            colp[fi] += (T)V.vcon_coef[S.vcon_off + q];
+          }
+        }
+      } else if (dt == DT_PRESS) {
+        const int le = src / npk, a = src % npk;
+        const int e = V.sub_elems[S.elem_off + le];
+        const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+        const int* ep = V.elpos + P.elpos_off + V.elptr[P.elptr_off + le];
+        const double* Be = V.B + (int64_t)npk * V.offK[e];
+        for (int b = 0; b < nK; ++b) {
+          const int x = ep[b];
+          if (x < pos) continue;
+          const int fi = front_index(N, bord, x);
+          if (fi < 0) { flag_error(status, 2); continue; }
+          colp[fi] += (T)Be[(int64_t)a * nK + b];
+        }
+      }
+    }
+    // deluxe root: entries between border-only DOFs (the face block K_FF)
+    if (N.flags & 1) {
+      for (int i = ex.tid; i < nb; i += ex.nt) {
+        const int x = bord[i];
+        const int v = V.dsrc[P.pos_off + x];
+        const int* vp = V.vadj_ptr + S.vadj_ptr_off;
+        for (int q = vp[v]; q < vp[v + 1]; ++q) {
+          const int le = V.vadj[S.vadj_off + 2 * q], a = V.vadj[S.vadj_off + 2 * q + 1];
+          const int e = V.sub_elems[S.elem_off + le];
+          const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+          const int* ep = V.elpos + P.elpos_off + V.elptr[P.elptr_off + le];
+          const double* Ae = V.A + V.offK2[e];
+          for (int b = 0; b < nK; ++b) {
+            const int y = ep[b];
+            if (y < P.npiv || y > x) continue;
+            const int fk = front_index(N, bord, y);
+            if (fk < np) { flag_error(status, 2); continue; }
+            upd[(int64_t)(fk - np) * nb + i] += (T)Ae[(int64_t)a * nK + b];
+          }
+        }
+      }
+    }
+    ex.sync();
+    // extend-add of the children's update matrices
+    for (int c = 0; c < N.nchild; ++c) {
+      const NodeDev C = V.nodes[V.children[N.first_child + c]];
+      const int* rel = V.rel + C.rel_off;
+      const T* Uc = U + C.upd_off;
+      const int nbc = C.nb;
+      for (int64_t idx = ex.tid; idx < (int64_t)nbc * nbc; idx += ex.nt) {
+        const int kk = (int)(idx / nbc), ii = (int)(idx % nbc);
+        if (ii < kk) continue;
+        const int rc = rel[kk], rr = rel[ii];
+        const T v = Uc[idx];
+        if (rc < np) pan[(int64_t)rc * nf + rr] += v;
+        else upd[(int64_t)(rc - np) * nb + (rr - np)] += v;
+      }
+      ex.sync();
+    }
+    // right-looking partial LDL^T
+    for (int j = 0; j < np; ++j) {
+      const T* cj = pan + (int64_t)j * nf;
+      const T dj = cj[j];
+      if (ex.tid == 0) {
+        const int dt = V.dtype[P.pos_off + N.p0 + j];
+        const double sgn = dt == DT_VEL ? 1.0 : -1.0;
+        if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
+      }
+      const T inv = (T)1 / dj;
+      const int m = nf - j - 1;
+      for (int64_t idx = ex.tid; idx < (int64_t)m * m; idx += ex.nt) {
+        const int kk = j + 1 + (int)(idx / m), ii = j + 1 + (int)(idx % m);
+        if (ii < kk) continue;
+        const T v = cj[ii] * cj[kk] * inv;
+        if (kk < np) pan[(int64_t)kk * nf + ii] -= v;
+        else upd[(int64_t)(kk - np) * nb + (ii - np)] -= v;
+      }
+      ex.sync();
+      for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) pan[(int64_t)j * nf + i] *= inv;
+      ex.sync();
+    }
+  }
+};
+
+// forward sweep: y = L^{-1} b per node; children update vectors extend-added
+template <class T>
+struct KFwd {
+  BddcView V;
+  const int* list;
+  const T* F;
+  double* X;      // problem vectors, [vec_off*nrhs + r*n + pos]
+  double* UV;     // update vectors, [uvec_off*nrhs + r*nb + i]
+  int nrhs;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int t = list[blk];
+    const NodeDev N = V.nodes[t];
+    const ProbDev P = V.probs[N.prob];
+    const int np = N.np, nb = N.nb, nf = np + nb;
+    const T* pan = F + N.panel_off;
+    double* f = ex.smem;
+    for (int r = 0; r < nrhs; ++r) {
+      double* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
+      for (int i = ex.tid; i < nf; i += ex.nt) f[i] = i < np ? x[N.p0 + i] : 0.0;
+      ex.sync();
+      for (int c = 0; c < N.nchild; ++c) {
+        const NodeDev C = V.nodes[V.children[N.first_child + c]];
+        const int* rel = V.rel + C.rel_off;
+        const double* uc = UV + C.uvec_off * nrhs + (int64_t)r * C.nb;
+        for (int i = ex.tid; i < C.nb; i += ex.nt) f[rel[i]] += uc[i];
+        ex.sync();
+      }
+      for (int jb = 0; jb < np; jb += 32) {
+        const int nbk = np - jb < 32 ? np - jb : 32;
+        if (ex.tid == 0)
+          for (int jj = 0; jj < nbk; ++jj) {
+            const double y = f[jb + jj];
+            const T* cj = pan + (int64_t)(jb + jj) * nf;
+            for (int ii = jj + 1; ii < nbk; ++ii) f[jb + ii] -= (double)cj[jb + ii] * y;
+          }
+        ex.sync();
+        for (int i = jb + nbk + ex.tid; i < nf; i += ex.nt) {
+          double acc = 0.0;
+          for (int jj = 0; jj < nbk; ++jj) acc += (double)pan[(int64_t)(jb + jj) * nf + i] * f[jb + jj];
+          f[i] -= acc;
+        }
+        ex.sync();
+      }
+      for (int i = ex.tid; i < np; i += ex.nt) x[N.p0 + i] = f[i];
+      double* u = UV + N.uvec_off * nrhs + (int64_t)r * nb;
+      for (int i = ex.tid; i < nb; i += ex.nt) u[i] = f[np + i];
+      ex.sync();
+    }
+  }
+};
+
+// backward sweep: x_p = L11^{-T} (D^{-1} y_p - L21^T x_border)
+template <class T>
+struct KBwd {
+  BddcView V;
+  const int* list;
+  const T* F;
+  double* X;
+  int nrhs;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int t = list[blk];
+    const NodeDev N = V.nodes[t];
+    const ProbDev P = V.probs[N.prob];
+    const int np = N.np, nb = N.nb, nf = np + nb;
+    const T* pan = F + N.panel_off;
+    const int* bord = V.border + N.border_off;
+    double* g = ex.smem;
+    for (int r = 0; r < nrhs; ++r) {
+      double* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
+      for (int i = ex.tid; i < np; i += ex.nt) g[i] = x[N.p0 + i] / (double)pan[(int64_t)i * nf + i];
+      for (int i = ex.tid; i < nb; i += ex.nt) g[np + i] = x[bord[i]];
+      ex.sync();
+      for (int j = ex.tid; j < np; j += ex.nt) {
+        const T* cj = pan + (int64_t)j * nf;
+        double acc = 0.0;
+        for (int i = np; i < nf; ++i) acc += (double)cj[i] * g[i];
+        g[j] -= acc;
+      }
+      ex.sync();
+      int jb = ((np - 1) / 32) * 32;
+      for (; np > 0 && jb >= 0; jb -= 32) {
+        const int nbk = np - jb < 32 ? np - jb : 32;
+        if (ex.tid == 0)
+          for (int jj = nbk - 1; jj >= 0; --jj) {
+            const T* cj = pan + (int64_t)(jb + jj) * nf;
+            double acc = 0.0;
+            for (int ii = jj + 1; ii < nbk; ++ii) acc += (double)cj[jb + ii] * g[jb + ii];
+            g[jb + jj] -= acc;
+          }
+        ex.sync();
+        for (int j = ex.tid; j < jb; j += ex.nt) {
+          const T* cj = pan + (int64_t)j * nf + jb;
+          double acc = 0.0;
+          for (int ii = 0; ii < nbk; ++ii) acc += (double)cj[ii] * g[jb + ii];
+          g[j] -= acc;
+        }
+        ex.sync();
+      }
+      for (int i = ex.tid; i < np; i += ex.nt) x[N.p0 + i] = g[i];
+      ex.sync();
+    }
+  }
+};
+
+}  // namespace vb

@@ -51,6 +51,7 @@ void build_elem_records(const Topo& t, const DofNumbering& d, std::vector<ElemRe
 
 }  // namespace vb
 
+namespace vb { struct ElemTables; }
 struct vem_system {
   vb::Topo topo;
   vb::DofNumbering dof;
@@ -60,6 +61,8 @@ struct vem_system {
   vb::DBuf<vb::ElemRec> d_rec;
   vb::DBuf<double> d_xyz;
   vb::DBuf<double> d_nu;
+  vb::DBuf<vb::ElemTables> d_tab;
+  std::vector<double> elem_wmean;   // int_K m_a per element pressure (a in P_{k-1})
   vb::DBuf<int64_t> d_eoff;      // prefix sums of nK (element DOF offsets)
   vb::DBuf<int64_t> d_eoffK2;    // prefix sums of nK^2 (element matrix offsets)
   vb::DBuf<double> d_A;          // element stiffness A_K (nK x nK), concatenated

@@ -9,106 +9,129 @@
 
 namespace vb {
 
-__constant__ ElemTables c_tab;
+// element-independent tables: a device copy for the kernels
+struct ElemTablesDev;
 
 template <int K>
-__global__ void __launch_bounds__(128) k_element(const ElemRec* __restrict__ rec, const double* __restrict__ xyz,
-                                                 const double* __restrict__ nu, const int64_t* __restrict__ offK,
-                                                 const int64_t* __restrict__ offK2, double* A, double* B, double* P0,
-                                                 double* scratch, size_t stride, int nE, int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ElemShared<K>& sh = *reinterpret_cast<ElemShared<K>*>(smem_raw);
-  __shared__ ElemRec R;
-  double* scr = scratch + (size_t)blockIdx.x * stride;
-  for (int e = blockIdx.x; e < nE; e += gridDim.x) {
-    {
+struct KElement {
+  const ElemRec* rec;
+  const double* xyz;
+  const double* nu;
+  const int64_t* offK;
+  const int64_t* offK2;
+  const ElemTables* tab;
+  double *A, *B, *P0, *WM, *scratch;
+  size_t stride;
+  int nE, nblocks;
+  int* status;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    ElemShared<K>& sh = *reinterpret_cast<ElemShared<K>*>(ex.smem);
+    ElemRec& R = *reinterpret_cast<ElemRec*>(ex.smem + (sizeof(ElemShared<K>) + 7) / 8);
+    double* scr = scratch + (size_t)blk * stride;
+    for (int e = blk; e < nE; e += nblocks) {
       const int* src = reinterpret_cast<const int*>(rec + e);
       int* dst = reinterpret_cast<int*>(&R);
-      for (int i = threadIdx.x; i < (int)(sizeof(ElemRec) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+      for (int i = ex.tid; i < (int)(sizeof(ElemRec) / sizeof(int)); i += ex.nt) dst[i] = src[i];
+      ex.sync();
+      ElemBuilder<K> b(R, xyz, *tab, sh, scr, ex);
+      const int np = pdim3(K - 1);
+      bool ok = b.build(nu[e], A + offK2[e], B + (size_t)np * offK[e], P0 + (size_t)3 * pdim3(K) * offK[e],
+                        WM + (size_t)np * e);
+      if (!ok && ex.tid == 0) flag_error(status, 1);
+      ex.sync();
     }
-    __syncthreads();
-    ElemBuilder<K> b(R, xyz, c_tab, sh, scr, Exec{(int)threadIdx.x, (int)blockDim.x});
-    const int np = pdim3(K - 1);
-    bool ok = b.build(nu[e], A + offK2[e], B + (size_t)np * offK[e], P0 + (size_t)3 * pdim3(K) * offK[e]);
-    if (!ok && threadIdx.x == 0) atomicExch(status, 1);
-    __syncthreads();
   }
-}
+};
 
-// CSR assembly: one warp per system row, contributions gathered element by
+// CSR assembly: one CTA per system row; contributions gathered element by
 // element in a fixed order (deterministic sums, no atomics).
-__global__ void k_assemble(int64_t nrows, int64_t nvf, int np, const int64_t* __restrict__ rowptr,
-                           const int* __restrict__ col, double* __restrict__ val, const int64_t* __restrict__ adj_ptr,
-                           const int* __restrict__ adj_elem, const int* __restrict__ adj_loc,
-                           const int64_t* __restrict__ offK, const int64_t* __restrict__ offK2,
-                           const int64_t* __restrict__ sysdof, const double* __restrict__ A,
-                           const double* __restrict__ B) {
-  int lane = threadIdx.x & 31;
-  int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (r >= nrows) return;
-  const int64_t r0 = rowptr[r], r1 = rowptr[r + 1];
-  for (int64_t p = r0 + lane; p < r1; p += 32) val[p] = 0.0;
-  __syncwarp();
-  for (int64_t q = adj_ptr[r]; q < adj_ptr[r + 1]; ++q) {
-    const int e = adj_elem[q], loc = adj_loc[q];
-    const int nK = (int)(offK[e + 1] - offK[e]);
-    const int64_t* sd = sysdof + offK[e];
-    const double* Ae = A + offK2[e];
-    const double* Be = B + (int64_t)np * offK[e];
-    const int ncols = loc < nK ? nK + np : nK;
-    for (int b = lane; b < ncols; b += 32) {
-      int64_t c;
-      double v;
-      if (loc < nK) {
-        if (b < nK) { c = sd[b]; v = Ae[(int64_t)loc * nK + b]; }
-        else { c = nvf + (int64_t)e * np + (b - nK); v = Be[(int64_t)(b - nK) * nK + loc]; }
-      } else {
-        c = sd[b];
-        v = Be[(int64_t)(loc - nK) * nK + b];
+struct KAssemble {
+  int64_t nvf;
+  int np;
+  const int64_t* rowptr;
+  const int* col;
+  double* val;
+  const int64_t *adj_ptr;
+  const int *adj_elem, *adj_loc;
+  const int64_t *offK, *offK2, *sysdof;
+  const double *A, *B;
+  VB_HD void operator()(const KExec& ex, int r) const {
+    const int64_t r0 = rowptr[r], r1 = rowptr[r + 1];
+    for (int64_t p = r0 + ex.tid; p < r1; p += ex.nt) val[p] = 0.0;
+    ex.sync();
+    for (int64_t q = adj_ptr[r]; q < adj_ptr[r + 1]; ++q) {
+      const int e = adj_elem[q], loc = adj_loc[q];
+      const int nK = (int)(offK[e + 1] - offK[e]);
+      const int64_t* sd = sysdof + offK[e];
+      const double* Ae = A + offK2[e];
+      const double* Be = B + (int64_t)np * offK[e];
+      const int ncols = loc < nK ? nK + np : nK;
+      for (int b = ex.tid; b < ncols; b += ex.nt) {
+        int64_t c;
+        double v;
+        if (loc < nK) {
+          if (b < nK) { c = sd[b]; v = Ae[(int64_t)loc * nK + b]; }
+          else { c = nvf + (int64_t)e * np + (b - nK); v = Be[(int64_t)(b - nK) * nK + loc]; }
+        } else {
+          c = sd[b];
+          v = Be[(int64_t)(loc - nK) * nK + b];
+        }
+        if (c < 0) continue;
+        int64_t lo = r0, hi = r1 - 1;
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          if (col[mid] < c) lo = mid + 1; else hi = mid;
+        }
+        val[lo] += v;
       }
-      if (c < 0) continue;
-      // binary search of column c in row r
-      int64_t lo = r0, hi = r1 - 1;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (col[mid] < c) lo = mid + 1; else hi = mid;
-      }
-      val[lo] += v;
+      ex.sync();
     }
-    __syncwarp();
   }
-}
+};
 
-// y = K x, one warp per row
-__global__ void k_spmv(int64_t nrows, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
-                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
-  int lane = threadIdx.x & 31;
-  int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (r >= nrows) return;
-  double acc = 0.0;
-  for (int64_t p = rowptr[r] + lane; p < rowptr[r + 1]; p += 32) acc += val[p] * __ldg(x + col[p]);
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) y[r] = acc;
-}
+// y = K x: each CTA handles nt/32 rows, one warp per row
+struct KSpmv {
+  int64_t nrows;
+  const int64_t* rowptr;
+  const int* col;
+  const double* val;
+  const double* x;
+  double* y;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+#ifdef __CUDA_ARCH__
+    int lane = ex.tid & 31;
+    int64_t r = (int64_t)blk * (ex.nt >> 5) + (ex.tid >> 5);
+    if (r >= nrows) return;
+    double acc = 0.0;
+    for (int64_t p = rowptr[r] + lane; p < rowptr[r + 1]; p += 32) acc += val[p] * __ldg(x + col[p]);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[r] = acc;
+#else
+    for (int64_t r = (int64_t)blk * 8; r < nrows && r < (int64_t)blk * 8 + 8; ++r) {
+      double acc = 0.0;
+      for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p) acc += val[p] * x[col[p]];
+      y[r] = acc;
+    }
+#endif
+  }
+};
 
-// load-rule points of element e (tetrahedra x_K + outward fan triangles)
+// load-rule points of an element: tetrahedra (x_K, outward fan triangle)
 struct LoadRule {
   int nq;
   double x[16], w[16];
 };
-__constant__ LoadRule c_load;
 
-__device__ inline void elem_centroid(const ElemRec& R, const double* xyz, double* xK) {
+VB_HD inline void elem_centroid(const ElemRec& R, const double* xyz, double* xK) {
   xK[0] = xK[1] = xK[2] = 0.0;
   for (int i = 0; i < R.nv; ++i)
     for (int d = 0; d < 3; ++d) xK[d] += xyz[3 * R.vert[i] + d];
   for (int d = 0; d < 3; ++d) xK[d] /= R.nv;
 }
 
-// point p (of this element's list) -> physical point and weight
-__device__ inline void load_point(const ElemRec& R, const double* xyz, const double* xK, int p, double* x,
-                                  double* w) {
-  const int nq = c_load.nq, nq3 = nq * nq * nq;
+VB_HD inline void load_point(const LoadRule& L, const ElemRec& R, const double* xyz, const double* xK, int p,
+                             double* x, double* w) {
+  const int nq = L.nq, nq3 = nq * nq * nq;
   int tet = p / nq3, q = p % nq3;
   int iu = q / (nq * nq), iv = (q / nq) % nq, iw = q % nq;
   int f = 0, t = 0, cnt = 0;
@@ -130,112 +153,128 @@ __device__ inline void load_point(const ElemRec& R, const double* xyz, const dou
   double cr[3];
   cross3(b1, c1, cr);
   double det = a1[0] * cr[0] + a1[1] * cr[1] + a1[2] * cr[2];
-  double U = c_load.x[iu], V = c_load.x[iv], W = c_load.x[iw];
+  double U = L.x[iu], V = L.x[iv], W = L.x[iw];
   double px = U, py = V * (1 - U), pz = W * (1 - U) * (1 - V);
-  *w = c_load.w[iu] * c_load.w[iv] * c_load.w[iw] * (1 - U) * (1 - U) * (1 - V) * det;
+  *w = L.w[iu] * L.w[iv] * L.w[iw] * (1 - U) * (1 - U) * (1 - V) * det;
   for (int d = 0; d < 3; ++d) x[d] = xK[d] + px * a1[d] + py * b1[d] + pz * c1[d];
 }
 
-__global__ void k_quad_points(const ElemRec* __restrict__ rec, const double* __restrict__ xyz,
-                              const int64_t* __restrict__ qoff, int nE, double* out) {
-  int e = blockIdx.x;
-  if (e >= nE) return;
-  const ElemRec& R = rec[e];
-  double xK[3];
-  elem_centroid(R, xyz, xK);
-  int npts = (int)(qoff[e + 1] - qoff[e]);
-  for (int p = threadIdx.x; p < npts; p += blockDim.x) {
-    double x[3], w;
-    load_point(R, xyz, xK, p, x, &w);
-    for (int d = 0; d < 3; ++d) out[3 * (qoff[e] + p) + d] = x[d];
-  }
-}
-
-// per element: F[c][a] = sum_p w f_c m_a(xi), local rhs = P0^T F (Eq. discreteF)
-template <int K>
-__global__ void k_load_local(const ElemRec* __restrict__ rec, const double* __restrict__ xyz,
-                             const int64_t* __restrict__ qoff, const double* __restrict__ fq,
-                             const int64_t* __restrict__ offK, const double* __restrict__ P0, int nE,
-                             double* __restrict__ rloc) {
-  constexpr int NP1 = pdim3(K);
-  __shared__ double Fm[3 * NP1];
-  __shared__ double xK[3], hK;
-  int e = blockIdx.x;
-  if (e >= nE) return;
-  const ElemRec& R = rec[e];
-  if (threadIdx.x == 0) {
+struct KQuadPoints {
+  const ElemRec* rec;
+  const double* xyz;
+  const int64_t* qoff;
+  LoadRule L;
+  double* out;
+  VB_HD void operator()(const KExec& ex, int e) const {
+    const ElemRec& R = rec[e];
+    double xK[3];
     elem_centroid(R, xyz, xK);
-    double h2 = 0;
-    for (int i = 0; i < R.nv; ++i)
-      for (int j = i + 1; j < R.nv; ++j) {
-        double s = 0;
-        for (int d = 0; d < 3; ++d) {
-          double t = xyz[3 * R.vert[i] + d] - xyz[3 * R.vert[j] + d];
-          s += t * t;
-        }
-        h2 = s > h2 ? s : h2;
-      }
-    hK = sqrt(h2);
-  }
-  __syncthreads();
-  int npts = (int)(qoff[e + 1] - qoff[e]);
-  for (int idx = threadIdx.x; idx < 3 * NP1; idx += blockDim.x) {
-    int c = idx / NP1, a = idx % NP1;
-    const Exp3 ea = c_tab.e3[a];
-    double acc = 0.0;
-    for (int p = 0; p < npts; ++p) {
+    int npts = (int)(qoff[e + 1] - qoff[e]);
+    for (int p = ex.tid; p < npts; p += ex.nt) {
       double x[3], w;
-      load_point(R, xyz, xK, p, x, &w);
-      double px = (x[0] - xK[0]) / hK, py = (x[1] - xK[1]) / hK, pz = (x[2] - xK[2]) / hK;
-      acc += w * fq[3 * (qoff[e] + p) + c] * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c);
+      load_point(L, R, xyz, xK, p, x, &w);
+      for (int d = 0; d < 3; ++d) out[3 * (qoff[e] + p) + d] = x[d];
     }
-    Fm[idx] = acc;
   }
-  __syncthreads();
-  int nK = (int)(offK[e + 1] - offK[e]);
-  const double* P = P0 + (size_t)3 * NP1 * offK[e];
-  for (int col = threadIdx.x; col < nK; col += blockDim.x) {
-    double acc = 0.0;
-    for (int q = 0; q < 3 * NP1; ++q) acc += P[(size_t)q * nK + col] * Fm[q];
-    rloc[offK[e] + col] = acc;
+};
+
+// per element: F[c][a] = sum_p w f_c m_a(xi); local rhs = P0^T F (Eq. discreteF)
+template <int K>
+struct KLoadLocal {
+  const ElemRec* rec;
+  const double* xyz;
+  const int64_t* qoff;
+  const double* fq;
+  const int64_t* offK;
+  const double* P0;
+  const ElemTables* tab;
+  LoadRule L;
+  double* rloc;
+  VB_HD void operator()(const KExec& ex, int e) const {
+    constexpr int NP1 = pdim3(K);
+    double* Fm = ex.smem;
+    double* geo = ex.smem + 3 * NP1;   // xK[3], hK
+    const ElemRec& R = rec[e];
+    if (ex.tid == 0) {
+      elem_centroid(R, xyz, geo);
+      double h2 = 0;
+      for (int i = 0; i < R.nv; ++i)
+        for (int j = i + 1; j < R.nv; ++j) {
+          double s = 0;
+          for (int d = 0; d < 3; ++d) {
+            double t = xyz[3 * R.vert[i] + d] - xyz[3 * R.vert[j] + d];
+            s += t * t;
+          }
+          h2 = s > h2 ? s : h2;
+        }
+      geo[3] = sqrt(h2);
+    }
+    ex.sync();
+    int npts = (int)(qoff[e + 1] - qoff[e]);
+    for (int idx = ex.tid; idx < 3 * NP1; idx += ex.nt) {
+      int c = idx / NP1, a = idx % NP1;
+      const Exp3 ea = tab->e3[a];
+      double acc = 0.0;
+      for (int p = 0; p < npts; ++p) {
+        double x[3], w;
+        load_point(L, R, xyz, geo, p, x, &w);
+        double px = (x[0] - geo[0]) / geo[3], py = (x[1] - geo[1]) / geo[3], pz = (x[2] - geo[2]) / geo[3];
+        acc += w * fq[3 * (qoff[e] + p) + c] * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c);
+      }
+      Fm[idx] = acc;
+    }
+    ex.sync();
+    int nK = (int)(offK[e + 1] - offK[e]);
+    const double* P = P0 + (size_t)3 * NP1 * offK[e];
+    for (int col = ex.tid; col < nK; col += ex.nt) {
+      double acc = 0.0;
+      for (int q = 0; q < 3 * NP1; ++q) acc += P[(size_t)q * nK + col] * Fm[q];
+      rloc[offK[e] + col] = acc;
+    }
   }
-}
+};
 
 // system rhs from the per-element local vectors (velocity rows), zero pressure rows
-__global__ void k_gather_rhs(int64_t nrows, int64_t nvf, const int64_t* __restrict__ adj_ptr,
-                             const int* __restrict__ adj_elem, const int* __restrict__ adj_loc,
-                             const int64_t* __restrict__ offK, const double* __restrict__ rloc,
-                             double* __restrict__ rhs) {
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
-  double acc = 0.0;
-  if (r < nvf)
-    for (int64_t q = adj_ptr[r]; q < adj_ptr[r + 1]; ++q) acc += rloc[offK[adj_elem[q]] + adj_loc[q]];
-  rhs[r] = acc;
-}
+struct KGatherRhs {
+  int64_t nrows, nvf;
+  const int64_t* adj_ptr;
+  const int *adj_elem, *adj_loc;
+  const int64_t* offK;
+  const double* rloc;
+  double* rhs;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int64_t hi = (int64_t)(blk + 1) * 256 < nrows ? (int64_t)(blk + 1) * 256 : nrows;
+    for (int64_t r = (int64_t)blk * 256 + ex.tid; r < hi; r += ex.nt) {
+      double acc = 0.0;
+      if (r < nvf)
+        for (int64_t q = adj_ptr[r]; q < adj_ptr[r + 1]; ++q) acc += rloc[offK[adj_elem[q]] + adj_loc[q]];
+      rhs[r] = acc;
+    }
+  }
+};
 
 template <int K>
-static void launch_elements(vem_system* s, const std::vector<ElemRec>& recs, const DBuf<int64_t>& offK,
-                            const DBuf<int64_t>& offK2) {
+static void launch_elements(vem_system* s, const DBuf<int64_t>& offK, const DBuf<int64_t>& offK2) {
   const int nE = s->topo.nE;
   const int grid = std::min(nE, 152 * (K == 2 ? 8 : (K == 3 ? 4 : 2)));
   size_t stride = ElemScratch<K>::size(s->nKmax);
   DBuf<double> scratch((size_t)grid * stride);
   DBuf<int> status(1);
   status.zero(s->stream);
-  size_t smem = sizeof(ElemShared<K>);
-  VB_CUDA(cudaFuncSetAttribute(k_element<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_element<K><<<grid, 128, smem, s->stream>>>(s->d_rec.p, s->d_xyz.p, s->d_nu.p, offK.p, offK2.p, s->d_A.p,
-                                               s->d_B.p, s->d_P0.p, scratch.p, stride, nE, status.p);
-  VB_KERNEL_CHECK();
+  size_t smem = ((sizeof(ElemShared<K>) + 7) / 8) * 8 + sizeof(ElemRec);
+  DBuf<double> wm((size_t)nE * pdim3(K - 1));
+  KElement<K> f{s->d_rec.p, s->d_xyz.p, s->d_nu.p, offK.p, offK2.p, s->d_tab.p, s->d_A.p, s->d_B.p,
+                s->d_P0.p, wm.p, scratch.p, stride, nE, grid, status.p};
+  launch(f, grid, 128, smem, s->stream);
   auto st = status.download(s->stream);
   VB_CHECK(st[0] == 0, VEM_ESINGULAR, "element projector system singular (degenerate element)");
+  s->elem_wmean = wm.download(s->stream);
 }
 
 static void load_tables(vem_system* s) {
-  ElemTables T;
-  make_elem_tables(s->dof.k, T);
-  VB_CUDA(cudaMemcpyToSymbolAsync(c_tab, &T, sizeof(T), 0, cudaMemcpyHostToDevice, s->stream));
+  std::vector<ElemTables> T(1);
+  make_elem_tables(s->dof.k, T[0]);
+  s->d_tab.upload(T, s->stream);
 }
 
 }  // namespace vb
@@ -288,9 +327,9 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
     s->d_P0.alloc((size_t)3 * pdim3(k) * offK[t.nE]);
     s->d_sysdof.upload(s->h_sysdof, s->stream);
     load_tables(s);
-    if (k == 2) launch_elements<2>(s, recs, dK, dK2);
-    else if (k == 3) launch_elements<3>(s, recs, dK, dK2);
-    else launch_elements<4>(s, recs, dK, dK2);
+    if (k == 2) launch_elements<2>(s, dK, dK2);
+    else if (k == 3) launch_elements<3>(s, dK, dK2);
+    else launch_elements<4>(s, dK, dK2);
     // CSR pattern and row adjacency (host)
     const int64_t nvf = d.nvf, np = d.np;
     s->n = nvf + d.npress;
@@ -347,12 +386,10 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
     s->d_adj_elem.upload(s->h_adj_elem, s->stream);
     s->d_adj_loc.upload(s->h_adj_loc, s->stream);
     s->d_eoff.upload(offK, s->stream);
-    DBuf<int64_t>& offKd = s->d_eoff;
-    int64_t threads = s->n * 32;
-    k_assemble<<<(unsigned)((threads + 255) / 256), 256, 0, s->stream>>>(
-        s->n, nvf, (int)np, s->d_rowptr.p, s->d_col.p, s->d_val.p, s->d_adj_ptr.p, s->d_adj_elem.p,
-        s->d_adj_loc.p, offKd.p, dK2.p, s->d_sysdof.p, s->d_A.p, s->d_B.p);
-    VB_KERNEL_CHECK();
+    KAssemble fa{nvf, (int)np, s->d_rowptr.p, s->d_col.p, s->d_val.p, s->d_adj_ptr.p, s->d_adj_elem.p,
+                 s->d_adj_loc.p, s->d_eoff.p, dK2.p, s->d_sysdof.p, s->d_A.p, s->d_B.p};
+    launch(fa, s->n, 32, 0, s->stream);
+
     s->d_eoffK2 = std::move(dK2);
     VB_CUDA(cudaStreamSynchronize(s->stream));
     *out = s;
@@ -381,15 +418,14 @@ extern "C" int vem_free_dofs(const vem_system* s, int64_t* out) {
   return VEM_OK;
 }
 
-static void load_offsets(vem_system* s, int degree, std::vector<int64_t>& qoff) {
+static void load_offsets(vem_system* s, int degree, std::vector<int64_t>& qoff, LoadRule& L) {
   VB_CHECK(degree >= 0 && degree <= 24, VEM_EINVAL, "load degree out of range");
   int nq = (degree + 3) / 2 + 1;
-  LoadRule L{};
+  L = LoadRule{};
   L.nq = nq;
   std::vector<double> x, w;
   gauss01(nq, x, w);
   for (int i = 0; i < nq; ++i) { L.x[i] = x[i]; L.w[i] = w[i]; }
-  VB_CUDA(cudaMemcpyToSymbolAsync(c_load, &L, sizeof(L), 0, cudaMemcpyHostToDevice, s->stream));
   const Topo& t = s->topo;
   qoff.assign(t.nE + 1, 0);
   for (int e = 0; e < t.nE; ++e) {
@@ -406,14 +442,14 @@ extern "C" int vem_quad_points(vem_system* s, int degree, int64_t* n, double* xy
   if (!s || !n) { set_last_error("null argument"); return VEM_EINVAL; }
   try {
     std::vector<int64_t> qoff;
-    load_offsets(s, degree, qoff);
+    LoadRule L;
+    load_offsets(s, degree, qoff, L);
     *n = qoff.back();
     if (!xyz_out) return VEM_OK;
     DBuf<int64_t> dq;
     dq.upload(qoff, s->stream);
     DBuf<double> pts(3 * (size_t)qoff.back());
-    k_quad_points<<<s->topo.nE, 128, 0, s->stream>>>(s->d_rec.p, s->d_xyz.p, dq.p, s->topo.nE, pts.p);
-    VB_KERNEL_CHECK();
+    launch(KQuadPoints{s->d_rec.p, s->d_xyz.p, dq.p, L, pts.p}, s->topo.nE, 128, 0, s->stream);
     VB_CUDA(cudaMemcpyAsync(xyz_out, pts.p, pts.n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     VB_CUDA(cudaStreamSynchronize(s->stream));
     return VEM_OK;
@@ -426,21 +462,23 @@ extern "C" int vem_load(vem_system* s, int degree, const double* fq, double* rhs
   if (!s || !fq || !rhs) { set_last_error("null argument"); return VEM_EINVAL; }
   try {
     std::vector<int64_t> qoff;
-    load_offsets(s, degree, qoff);
+    LoadRule L;
+    load_offsets(s, degree, qoff, L);
     DBuf<int64_t> dq;
     dq.upload(qoff, s->stream);
     DBuf<double> df(3 * (size_t)qoff.back());
     VB_CUDA(cudaMemcpyAsync(df.p, fq, df.n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     DBuf<double> rloc(s->h_eoff.back());
     const int nE = s->topo.nE;
-    if (s->dof.k == 2) k_load_local<2><<<nE, 128, 0, s->stream>>>(s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, nE, rloc.p);
-    else if (s->dof.k == 3) k_load_local<3><<<nE, 128, 0, s->stream>>>(s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, nE, rloc.p);
-    else k_load_local<4><<<nE, 128, 0, s->stream>>>(s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, nE, rloc.p);
-    VB_KERNEL_CHECK();
-    k_gather_rhs<<<(unsigned)((s->n + 255) / 256), 256, 0, s->stream>>>(s->n, s->dof.nvf, s->d_adj_ptr.p,
-                                                                           s->d_adj_elem.p, s->d_adj_loc.p,
-                                                                           s->d_eoff.p, rloc.p, rhs);
-    VB_KERNEL_CHECK();
+    const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4);
+    if (s->dof.k == 2)
+      launch(KLoadLocal<2>{s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE, 128, lsm, s->stream);
+    else if (s->dof.k == 3)
+      launch(KLoadLocal<3>{s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE, 128, lsm, s->stream);
+    else
+      launch(KLoadLocal<4>{s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE, 128, lsm, s->stream);
+    launch(KGatherRhs{s->n, s->dof.nvf, s->d_adj_ptr.p, s->d_adj_elem.p, s->d_adj_loc.p, s->d_eoff.p, rloc.p, rhs},
+           (s->n + 255) / 256, 256, 0, s->stream);
     VB_CUDA(cudaStreamSynchronize(s->stream));
     return VEM_OK;
   } catch (const Error& e) {
@@ -450,9 +488,7 @@ extern "C" int vem_load(vem_system* s, int degree, const double* fq, double* rhs
 
 namespace vb {
 void spmv(vem_system* s, const double* x, double* y, cudaStream_t st) {
-  int64_t threads = s->n * 32;
-  k_spmv<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(s->n, s->d_rowptr.p, s->d_col.p, s->d_val.p, x, y);
-  VB_KERNEL_CHECK();
+  launch(KSpmv{s->n, s->d_rowptr.p, s->d_col.p, s->d_val.p, x, y}, (s->n + 7) / 8, 256, 0, st);
 }
 }  // namespace vb
 
