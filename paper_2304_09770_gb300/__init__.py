@@ -57,9 +57,6 @@ def lib():
         L.vem_free.argtypes = [P]
         L.vem_free.restype = None
         L.vem_last_error.restype = ctypes.c_char_p
-        for name in ("bddc_setup", "bddc_apply", "pcg_solve", "bddc_free", "bddc_info", "bddc_set_stream"):
-            if not hasattr(L, name):
-                continue
         if hasattr(L, "bddc_setup"):
             L.bddc_setup.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_int,
                                      ctypes.POINTER(BddcOptions), ctypes.POINTER(P)]
@@ -178,3 +175,47 @@ class VemSystem:
 
     def set_stream(self, stream):
         _check(lib().vem_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)))
+
+
+class Bddc:
+    """bddc_setup + bddc_apply + pcg_solve over a VemSystem."""
+
+    def __init__(self, system, part, constraints=15, scaling=1, leaf=0):
+        L = lib()
+        self.sys = system
+        part = np.ascontiguousarray(part, dtype=np.int32)
+        opts = BddcOptions()
+        opts.nd_leaf = int(leaf)
+        h = ctypes.c_void_p()
+        _check(L.bddc_setup(system.h, part.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(constraints),
+                            int(scaling), ctypes.byref(opts), ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.bddc_free(self.h)
+            self.h = None
+
+    def apply(self, r, z=None):
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        _check(lib().bddc_apply(self.h, _dptr(r), _dptr(z)))
+        return z
+
+    def solve(self, f, u, rtol=1e-8, maxit=500):
+        it = ctypes.c_int()
+        ka, lmi, lma = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        st = lib().pcg_solve(self.h, _dptr(f), _dptr(u), float(rtol), int(maxit), ctypes.byref(it),
+                             ctypes.byref(ka), ctypes.byref(lmi), ctypes.byref(lma))
+        if st not in (0, -6):
+            _check(st)
+        return dict(status=st, iters=it.value, kappa=ka.value, lam_min=lmi.value, lam_max=lma.value)
+
+    def info(self, key):
+        v = ctypes.c_double()
+        _check(lib().bddc_info(self.h, key.encode(), ctypes.byref(v)))
+        return v.value
+
+    def set_stream(self, stream):
+        _check(lib().bddc_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)))

@@ -1,0 +1,106 @@
+"""GPU parity of BDDC-PCG against the CPU oracle, through the C-ABI: the same
+iteration count and Lanczos estimates, solution difference <= 1e-10 relative
+to the oracle's PCG solution at the same rtol, lambda_min >= 1, the
+preconditioner itself, and properties at the full benchmark size."""
+import numpy as np
+import pytest
+
+from synth import make_config
+from oracle.vem import System
+from oracle.bddc import BDDC
+
+pytestmark = pytest.mark.gpu
+
+CONS = {"vertex": 1, "edge": 2, "face": 4, "flux": 8}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2304_09770_gb300 as p
+    p.lib()
+    return p
+
+
+def _setup(pkg, name, deg=None):
+    cfg = make_config(name)
+    k = cfg["k"]
+    deg = deg if deg is not None else (k + 9 if cfg["spec"]["load"] == "manufactured" else 2 * k + 2)
+    g = pkg.VemSystem(cfg["mesh"], k, cfg["nu"])
+    rhs = g.load(deg, cfg["f"](g.quad_points(deg)))
+    S = System(cfg["mesh"], k, cfg["nu"], f=cfg["f"], load_deg=deg)
+    F = np.concatenate([S.F[S.dm.free], np.zeros(S.dm.npress)])
+    return cfg, g, rhs, S, F
+
+
+CASES = [("cube4_k2", "deluxe"), ("tri4_k2", "deluxe"), ("tri6_k2", "deluxe"), ("tri6_k2", "multiplicity"),
+         ("tri4_k3", "deluxe"), ("cube6_k2", "deluxe"), ("sinker8", "deluxe")]
+
+
+@pytest.mark.parametrize("name,scaling", CASES)
+def test_pcg_matches_oracle(pkg, name, scaling):
+    import torch
+    cfg, g, rhs, S, F = _setup(pkg, name)
+    bd = pkg.Bddc(g, cfg["part"], constraints=15, scaling=1 if scaling == "deluxe" else 0)
+    u = torch.zeros_like(rhs)
+    res = bd.solve(rhs, u, rtol=1e-8, maxit=300)
+    assert res["status"] == 0
+    ob = BDDC(S, cfg["part"], scaling=scaling)
+    ro = ob.pcg(F, rtol=1e-8)
+    assert abs(res["iters"] - ro["iters"]) <= 1
+    assert res["lam_min"] > 1.0 - 1e-8
+    assert abs(res["lam_max"] - ro["lam_max"]) <= 1e-6 * ro["lam_max"]
+    x = u.cpu().numpy()
+    xo = ro["x"]
+    nvf = len(S.dm.free)
+    assert np.linalg.norm(x[:nvf] - xo[:nvf]) <= 1e-10 * np.linalg.norm(xo[:nvf])
+    pz = lambda p: p - (S.wmean @ p) / S.wmean.sum()
+    assert np.linalg.norm(pz(x[nvf:]) - pz(xo[nvf:])) <= 1e-8 * np.linalg.norm(pz(xo[nvf:]))
+    # against the direct solve of the saddle system, within the CG tolerance
+    ud, pd = S.solve_direct(F=S.F)
+    assert np.linalg.norm(x[:nvf] - ud[S.dm.free]) <= 1e-6 * np.linalg.norm(ud[S.dm.free])
+
+
+def test_all_interface_primal_is_one_iteration(pkg):
+    import torch
+    cfg, g, rhs, S, F = _setup(pkg, "tri4_k2")
+    bd = pkg.Bddc(g, cfg["part"], constraints=16, scaling=0)
+    u = torch.zeros_like(rhs)
+    res = bd.solve(rhs, u, rtol=1e-10, maxit=10)
+    assert res["status"] == 0 and res["iters"] == 1
+    assert abs(res["lam_min"] - 1.0) < 1e-8
+
+
+def test_preconditioner_matches_oracle(pkg):
+    import torch
+    cfg, g, rhs, S, F = _setup(pkg, "tri6_k2")
+    bd = pkg.Bddc(g, cfg["part"])
+    ob = BDDC(S, cfg["part"], scaling="deluxe")
+    x0 = ob.initial_guess(F)
+    r = F - ob.K @ x0
+    zo = ob.apply(r)
+    z = bd.apply(torch.tensor(r, device="cuda")).cpu().numpy()
+    nvf = len(S.dm.free)
+    assert np.abs(z[:nvf] - zo[:nvf]).max() <= 1e-11 * np.abs(zo[:nvf]).max()
+    assert np.abs(z[nvf:] - zo[nvf:]).max() <= 1e-10 * np.abs(zo[nvf:]).max()
+
+
+def test_full_size_benchmark_case_properties(pkg):
+    """32^3 perturbed mesh, 64 subdomains (the benchmark workload): converges,
+    lambda_min >= 1, the residual of the full saddle system is at the CG
+    tolerance and the discrete velocity is divergence-free elementwise."""
+    import torch
+    cfg = make_config("tri32_k2")
+    deg = 11
+    g = pkg.VemSystem(cfg["mesh"], 2, cfg["nu"])
+    rhs = g.load(deg, cfg["f"](g.quad_points(deg)))
+    bd = pkg.Bddc(g, cfg["part"])
+    u = torch.zeros_like(rhs)
+    res = bd.solve(rhs, u, rtol=1e-8, maxit=500)
+    assert res["status"] == 0
+    assert res["lam_min"] > 1.0 - 1e-8
+    r = rhs - g.apply(u)
+    assert torch.linalg.norm(r).item() <= 1e-7 * torch.linalg.norm(rhs).item()
+    div = r[g.n_vel_free:]            # pressure rows of the residual = -B u
+    assert torch.abs(div).max().item() <= 1e-7 * torch.abs(rhs).max().item()
