@@ -55,13 +55,29 @@ class _UF:
             self.p[max(ra, rb)] = min(ra, rb)
 
 
+class _BorderedSolver:
+    """Exact solves with [K  [0;w]; [0 w^T]  0] (w acts on the trailing
+    pressure block): sparse LU plus two steps of iterative refinement, so
+    that the local problems are solved to working accuracy also when the
+    viscosity jumps by orders of magnitude (pivoted LU alone loses digits)."""
+
+    def __init__(self, K, w):
+        n = K.shape[0]
+        col = np.zeros(n)
+        col[n - len(w):] = w
+        self.Kb = sp.bmat([[K, sp.csr_matrix(col[:, None])], [sp.csr_matrix(col[None, :]), None]],
+                          format="csc")
+        self.lu = spla.splu(self.Kb)
+
+    def solve(self, b):
+        x = self.lu.solve(b)
+        for _ in range(2):
+            x = x + self.lu.solve(b - self.Kb @ x)
+        return x
+
+
 def _bordered_lu(K, w):
-    """LU of [K  [0;w]; [0 w^T]  0] (w acts on the trailing pressure block)."""
-    n = K.shape[0]
-    col = np.zeros(n)
-    col[n - len(w):] = w
-    Kb = sp.bmat([[K, sp.csr_matrix(col[:, None])], [sp.csr_matrix(col[None, :]), None]], format="csc")
-    return spla.splu(Kb)
+    return _BorderedSolver(K, w)
 
 
 def _bsolve(lu, rhs):
