@@ -120,6 +120,10 @@ int vem_element_matrices(vem_system* sys, const int32_t* elems, int32_t count, i
 int vem_csr(vem_system* sys, int64_t* n, int64_t* nnz, int64_t* row_ptr, int32_t* col, double* vals);
 
 int vem_set_stream(vem_system* sys, void* cuda_stream);
+
+/* Diagnostics: number of kernels the library has launched since it was
+ * loaded (all handles, all threads). */
+int vem_kernel_launches(int64_t* count);
 void vem_free(vem_system* sys);
 const char* vem_last_error(void);
 
@@ -176,8 +180,19 @@ int pcg_solve(bddc* b, const double* f_dev, double* u_dev, double rtol, int maxi
 
 /* Statistics by name: "n_subdomains", "n_coarse", "n_macro",
  * "factor_bytes_dirichlet", "factor_bytes_neumann", "n_deluxe_faces",
- * "deluxe_bytes", "phi_bytes". */
+ * "deluxe_bytes", "phi_bytes", "coarse_bytes", "n_front_max", and the setup
+ * phase wall times "t_symbolic_ms", "t_upload_ms", "t_factor_dirichlet_ms",
+ * "t_factor_neumann_ms", "t_factor_deluxe_ms", "t_deluxe_extract_ms",
+ * "t_deluxe_combine_ms", "t_coarse_rhs_ms", "t_coarse_solves_ms",
+ * "t_coarse_gram_ms", "t_coarse_inverse_ms". */
 int bddc_info(bddc* b, const char* key, double* value);
+
+/* Diagnostics: nrep forward+backward sweeps through all local Neumann and
+ * Dirichlet factors (the triangular-solve part of one bddc_apply), timed
+ * with CUDA events on the handle's stream.  *ms: average time of one
+ * Neumann+Dirichlet sweep pair; *bytes: the factor bytes such a pair reads
+ * (every panel once forward, once backward).  Synchronizes. */
+int bddc_time_local_solves(bddc* b, int nrep, double* ms, double* bytes);
 int bddc_set_stream(bddc* b, void* cuda_stream);
 void bddc_free(bddc* b);
 

@@ -57,6 +57,7 @@ def lib():
         L.vem_free.argtypes = [P]
         L.vem_free.restype = None
         L.vem_last_error.restype = ctypes.c_char_p
+        L.vem_kernel_launches.argtypes = [i64p]
         if hasattr(L, "bddc_setup"):
             L.bddc_setup.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_int,
                                      ctypes.POINTER(BddcOptions), ctypes.POINTER(P)]
@@ -70,8 +71,18 @@ def lib():
             L.bddc_info.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
         if hasattr(L, "bddc_set_stream"):
             L.bddc_set_stream.argtypes = [P, P]
+        if hasattr(L, "bddc_time_local_solves"):
+            L.bddc_time_local_solves.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
+
+
+def kernel_launches():
+    """Kernels launched by the library since it was loaded."""
+    c = ctypes.c_int64()
+    _check(lib().vem_kernel_launches(ctypes.byref(c)))
+    return c.value
 
 
 def _check(status):
@@ -216,6 +227,11 @@ class Bddc:
         v = ctypes.c_double()
         _check(lib().bddc_info(self.h, key.encode(), ctypes.byref(v)))
         return v.value
+
+    def time_local_solves(self, nrep=5):
+        ms, by = ctypes.c_double(), ctypes.c_double()
+        _check(lib().bddc_time_local_solves(self.h, int(nrep), ctypes.byref(ms), ctypes.byref(by)))
+        return ms.value, by.value
 
     def set_stream(self, stream):
         _check(lib().bddc_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)))

@@ -12,6 +12,8 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <chrono>
+#include <string>
 
 namespace vb {
 void spmv(vem_system* s, const double* x, double* y, cudaStream_t st);
@@ -62,7 +64,7 @@ struct bddc {
   int64_t ndual = 0, niface_tot = 0;
   // PCG vectors
   vb::DBuf<double> r, z, p, Ap, scal;
-  double last_setup_ms = 0;
+  std::vector<std::pair<std::string, double>> times;   // setup phase wall times (ms)
 };
 
 namespace vb {
@@ -883,7 +885,7 @@ static void factor_batch(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status
   for (int h = 0; h <= B.maxh; ++h) {
     int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
     KFactor<double> f{V, B.d_levels.p + B.level_ptr[h], B.F.p, B.U.p, status.p};
-    launch(f, cnt, 256, 0, b->stream);
+    launch(f, cnt, 256, sizeof(double) * (2 * 64 * 32 + 32 + 8), b->stream);
   }
 }
 
@@ -1016,7 +1018,15 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     if (opts && opts->nd_leaf > 0) b->opt.leaf = opts->nd_leaf;
     cudaStream_t st = b->stream;
     BddcHost& H = b->H;
+    auto t0 = std::chrono::steady_clock::now();
+    auto mark = [&](const char* name) {
+      VB_CUDA(cudaStreamSynchronize(st));
+      auto t1 = std::chrono::steady_clock::now();
+      b->times.push_back({name, std::chrono::duration<double, std::milli>(t1 - t0).count()});
+      t0 = t1;
+    };
     bddc_host_setup(s, part, b->opt, H, s->elem_wmean);
+    mark("t_symbolic_ms");
     const int N = H.N;
     const int np = s->dof.np;
     // ---------------- flatten
@@ -1237,56 +1247,100 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     std::vector<int> dprobs(H.dir_prob.begin(), H.dir_prob.end()), nprobs(H.neu_prob.begin(), H.neu_prob.end());
     build_batch(b, b->bd, dprobs, true);
     build_batch(b, b->bn, nprobs, true);
-    build_batch(b, b->bx, dl_probs, false);
     upload_vec(b->d_nodes, b->h_nodes, st);
     upload_vec(b->d_probs, b->h_probs, st);
     upload_vec(b->d_subs, b->h_subs, st);
     upload_vec(b->d_macros, b->h_macros, st);
     upload_levels(b, b->bd);
     upload_levels(b, b->bn);
-    upload_levels(b, b->bx);
     BddcView V = make_view(b);
+    mark("t_upload_ms");
     // ---------------- numeric factorizations (S4)
     DBuf<int> status(1);
     status.zero(st);
     factor_batch(b, b->bd, V, status);
+    mark("t_factor_dirichlet_ms");
     factor_batch(b, b->bn, V, status);
-    factor_batch(b, b->bx, V, status);
+    mark("t_factor_neumann_ms");
     {
       auto stv = status.download(st);
       VB_CHECK(stv[0] != 2, VEM_EINVAL, "local factorization: matrix entry outside the symbolic front");
       VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "local factorization: zero or wrong-signed pivot");
     }
-    // ---------------- deluxe blocks (S6)
+    // ---------------- deluxe blocks (S6): face problems factored in chunks of
+    // bounded memory; each chunk's root update matrices are rotated to the
+    // dual coordinates and kept, the partial factors are released
     b->d_deluxe.alloc(std::max<int64_t>(deluxe_n, 1));
     if (!faces.empty()) {
-      DBuf<int> dp, dr, df;
-      DBuf<int64_t> dso, dwo, dsi, dsj, dcw;
-      upload_vec(dp, dl_probs, st);
-      upload_vec(dr, dl_roots, st);
-      upload_vec(df, faces, st);
-      upload_vec(dso, sd_off_v, st);
-      upload_vec(dwo, work_off_v, st);
-      upload_vec(dsi, sd_i, st);
-      upload_vec(dsj, sd_j, st);
-      upload_vec(dcw, cw_off, st);
-      int64_t sdn = 0, wn = 0, cwn = 0;
+      int64_t sdn = 0;
       for (size_t t = 0; t < dl_probs.size(); ++t) {
         const MacroDev& G = b->h_macros[H.probs[dl_probs[t]].macro];
         sdn += (int64_t)G.ndual * G.ndual;
-        wn += (int64_t)G.n * G.n;
       }
+      DBuf<double> SD(std::max<int64_t>(sdn, 1));
+      const double budget = 24.0 * (1 << 30);
+      size_t t0c = 0;
+      while (t0c < dl_probs.size()) {
+        double bytes = 0;
+        size_t t1c = t0c;
+        while (t1c < dl_probs.size()) {
+          const Problem& HP = H.probs[dl_probs[t1c]];
+          double pb = 0;
+          for (const Node& Nd : HP.nodes) pb += 8.0 * ((double)(Nd.np + Nd.nb) * Nd.np + (double)Nd.nb * Nd.nb);
+          const MacroDev& G = b->h_macros[HP.macro];
+          pb += 8.0 * G.n * G.n;
+          if (t1c > t0c && bytes + pb > budget) break;
+          bytes += pb;
+          ++t1c;
+        }
+        std::vector<int> cp(dl_probs.begin() + t0c, dl_probs.begin() + t1c);
+        std::vector<int> cr(dl_roots.begin() + t0c, dl_roots.begin() + t1c);
+        std::vector<int64_t> cso(sd_off_v.begin() + t0c, sd_off_v.begin() + t1c), cwo;
+        int64_t w = 0;
+        for (int q : cp) {
+          cwo.push_back(w);
+          const MacroDev& G = b->h_macros[H.probs[q].macro];
+          w += (int64_t)G.n * G.n;
+        }
+        Batch Bc;
+        build_batch(b, Bc, cp, false);
+        upload_vec(b->d_nodes, b->h_nodes, st);
+        upload_levels(b, Bc);
+        V = make_view(b);
+        factor_batch(b, Bc, V, status);
+        DBuf<int> dp, dr;
+        DBuf<int64_t> dso, dwo;
+        upload_vec(dp, cp, st);
+        upload_vec(dr, cr, st);
+        upload_vec(dso, cso, st);
+        upload_vec(dwo, cwo, st);
+        DBuf<double> work(std::max<int64_t>(w, 1));
+        launch(KDeluxeExtract{V, dp.p, dr.p, Bc.U.p, work.p, dwo.p, SD.p, dso.p}, (int)cp.size(), 256, 0, st);
+        VB_CUDA(cudaStreamSynchronize(st));
+        t0c = t1c;
+      }
+      {
+        auto stv = status.download(st);
+        VB_CHECK(stv[0] != 2, VEM_EINVAL, "deluxe factorization: entry outside the symbolic front");
+        VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe factorization: zero or wrong-signed pivot");
+      }
+      mark("t_factor_deluxe_ms");
+      DBuf<int> df;
+      DBuf<int64_t> dsi, dsj, dcw;
+      upload_vec(df, faces, st);
+      upload_vec(dsi, sd_i, st);
+      upload_vec(dsj, sd_j, st);
+      upload_vec(dcw, cw_off, st);
+      int64_t cwn = 0;
       for (int g : faces) cwn += (int64_t)b->h_macros[g].ndual * b->h_macros[g].ndual;
-      DBuf<double> SD(std::max<int64_t>(sdn, 1)), work(std::max<int64_t>(wn, 1)), cwork(std::max<int64_t>(cwn, 1));
+      DBuf<double> cwork(std::max<int64_t>(cwn, 1));
       V = make_view(b);
-      launch(KDeluxeExtract{V, dp.p, dr.p, b->bx.U.p, work.p, dwo.p, SD.p, dso.p}, (int)dl_probs.size(), 256, 0, st);
       launch(KDeluxeCombine{V, df.p, dsi.p, dsj.p, SD.p, cwork.p, dcw.p, b->d_deluxe.p, status.p}, (int)faces.size(),
              256, 0, st);
+      mark("t_deluxe_combine_ms");
       auto stv = status.download(st);
       VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe: face Schur complement sum not positive definite");
     }
-    b->bx.F.release();
-    b->bx.U.release();
     upload_vec(b->d_macros, b->h_macros, st);
     V = make_view(b);
     // ---------------- coarse basis and coarse matrix (S5)
@@ -1329,14 +1383,17 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
       DBuf<int64_t> drp;
       upload_vec(drp, rp, st);
       launch(KElemMatvec{V, drp.p, N, dW.p, KW.p, NC}, loc, 32, 0, st);
+      mark("t_coarse_rhs_ms");
       b->XN.alloc(std::max<int64_t>(b->bn.vec_n * NC, 1));
       b->UVN.alloc(std::max<int64_t>(b->bn.uvec_n * NC, 1));
       launch(KNeuRhsPhi{V, KW.p, b->XN.p, NC}, (int64_t)N * NC, 256, sizeof(double) * 256, st);
       solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, NC);
+      mark("t_coarse_solves_ms");
       launch(KPhiAssemble{V, dW.p, b->XN.p, PHI.p, NC}, (int64_t)N * NC, 256, sizeof(double) * 256, st);
       launch(KElemMatvec{V, drp.p, N, PHI.p, KW.p, NC}, loc, 32, 0, st);
       DBuf<double> SG((size_t)N * NC * NC);
       launch(KGram{V, PHI.p, KW.p, SG.p, NC}, N, 256, 0, st);
+      mark("t_coarse_gram_ms");
       int64_t nphi = 0;
       for (auto& D : b->h_subs) {
         D.phi_off = nphi;
@@ -1352,6 +1409,7 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
       launch(KCoarseAssemble{V, SG.p, KB.p, N, NC}, 1, 256, 0, st);
       status.zero(st);
       launch(KDenseInverse{KB.p, b->d_Kinv.p, nb, status.p}, 1, 256, sizeof(double) * 512, st);
+      mark("t_coarse_inverse_ms");
       auto stv = status.download(st);
       VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "coarse matrix singular");
     }
@@ -1503,3 +1561,35 @@ extern "C" int bddc_info(bddc* b, const char* key, double* value) {
 }
 
 extern "C" void bddc_free(bddc* b) { delete b; }
+
+extern "C" int bddc_time_local_solves(bddc* b, int nrep, double* ms, double* bytes) {
+  if (!b || nrep <= 0 || !ms || !bytes) { set_last_error("bddc_time_local_solves: bad argument"); return VEM_EINVAL; }
+  try {
+    const BddcView V = make_view(b);
+    cudaStream_t st = b->stream;
+    b->XN.zero(st);
+    b->XD.zero(st);
+    solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, 1);   // warm-up
+    solve_batch(b, b->bd, V, b->XD.p, b->UVD.p, 1);
+    cudaEvent_t e0, e1;
+    VB_CUDA(cudaEventCreate(&e0));
+    VB_CUDA(cudaEventCreate(&e1));
+    VB_CUDA(cudaEventRecord(e0, st));
+    for (int i = 0; i < nrep; ++i) {
+      solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, 1);
+      solve_batch(b, b->bd, V, b->XD.p, b->UVD.p, 1);
+    }
+    VB_CUDA(cudaEventRecord(e1, st));
+    VB_CUDA(cudaEventSynchronize(e1));
+    float t = 0;
+    VB_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / nrep;
+    // algorithmic bytes: every panel read once forward and once backward
+    *bytes = 2.0 * 8.0 * (double)(b->bn.nF + b->bd.nF);
+    return VEM_OK;
+  } catch (const Error& e) {
+    return bfail(e);
+  }
+}

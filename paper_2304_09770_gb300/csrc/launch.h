@@ -4,6 +4,7 @@
 // count, ex.smem the dynamic shared memory, ex.sync() the CTA barrier.
 #pragma once
 #include "common.h"
+#include <atomic>
 
 #ifdef __CUDACC__
 #define VB_HD __host__ __device__
@@ -12,6 +13,8 @@
 #endif
 
 namespace vb {
+
+extern std::atomic<int64_t> g_launches;   // kernels launched by the library
 
 struct KExec {
   int tid, nt;
@@ -38,6 +41,7 @@ inline void launch(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaS
     VB_CUDA(cudaFuncSetAttribute(k_run<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_run<F><<<(unsigned)nblocks, nthreads, smem, s>>>(f);
   VB_KERNEL_CHECK();
+  g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 #else
 template <class F>
@@ -45,6 +49,7 @@ inline void launch(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaS
   (void)nthreads;
   std::vector<double> buf(smem / sizeof(double) + 1, 0.0);
   for (int64_t b = 0; b < nblocks; ++b) f(KExec{0, 1, buf.data()}, (int)b);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 #endif
 

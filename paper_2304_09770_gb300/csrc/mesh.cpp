@@ -1,6 +1,7 @@
 // Host preprocessing: mesh topology, DOF numbering (Sec. 3, D1-D5) and the
 // fixed-size element records the element kernel reads.
 #include "system.h"
+#include "launch.h"
 
 #include <algorithm>
 #include <cmath>
@@ -9,6 +10,7 @@
 namespace vb {
 
 thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
 void set_last_error(const std::string& m) { g_last_error = m; }
 
 void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
@@ -251,3 +253,9 @@ void make_elem_tables(int k, ElemTables& T) {
 }
 
 }  // namespace vb
+
+extern "C" int vem_kernel_launches(int64_t* count) {
+  if (!count) return VEM_EINVAL;
+  *count = vb::g_launches.load();
+  return VEM_OK;
+}

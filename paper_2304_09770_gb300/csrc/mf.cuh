@@ -132,30 +132,83 @@ struct KFactor {
       }
       ex.sync();
     }
-    // right-looking partial LDL^T
-    for (int j = 0; j < np; ++j) {
-      const T* cj = pan + (int64_t)j * nf;
-      const T dj = cj[j];
-      if (ex.tid == 0) {
-        const int dt = V.dtype[P.pos_off + N.p0 + j];
-        const double sgn = dt == DT_VEL ? 1.0 : -1.0;
-        if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
+    // blocked right-looking partial LDL^T: panels of NBK columns, then a
+    // rank-NBK update of the trailing front in TT x TT tiles staged in
+    // shared memory (each thread owns a 4 x 4 sub-tile)
+    constexpr int NBK = 32, TT = 64;
+    double* sL = ex.smem;
+    double* sR = ex.smem + TT * NBK;
+    double* sd = ex.smem + 2 * TT * NBK;
+    for (int jb = 0; jb < np; jb += NBK) {
+      const int nbk = np - jb < NBK ? np - jb : NBK;
+      for (int jj = 0; jj < nbk; ++jj) {
+        const int j = jb + jj;
+        T* cj = pan + (int64_t)j * nf;
+        const T dj = cj[j];
+        if (ex.tid == 0) {
+          const int dt = V.dtype[P.pos_off + N.p0 + j];
+          const double sgn = dt == DT_VEL ? 1.0 : -1.0;
+          if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
+        }
+        const T inv = (T)1 / dj;
+        const int nk = jb + nbk - j - 1, nr = nf - j - 1;
+        for (int64_t idx = ex.tid; idx < (int64_t)nk * nr; idx += ex.nt) {
+          const int kk = j + 1 + (int)(idx / nr), ii = j + 1 + (int)(idx % nr);
+          if (ii < kk) continue;
+          pan[(int64_t)kk * nf + ii] -= cj[ii] * cj[kk] * inv;
+        }
+        ex.sync();
+        for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) cj[i] *= inv;
+        ex.sync();
       }
-      const T inv = (T)1 / dj;
-      const int m = nf - j - 1;
-      for (int64_t idx = ex.tid; idx < (int64_t)m * m; idx += ex.nt) {
-        const int kk = j + 1 + (int)(idx / m), ii = j + 1 + (int)(idx % m);
-        if (ii < kk) continue;
-        const T v = cj[ii] * cj[kk] * inv;
-        if (kk < np) pan[(int64_t)kk * nf + ii] -= v;
-        else upd[(int64_t)(kk - np) * nb + (ii - np)] -= v;
-      }
+      const int c0 = jb + nbk, m = nf - c0;
+      if (m <= 0) continue;
+      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = (double)pan[(int64_t)(jb + jj) * nf + jb + jj];
       ex.sync();
-      for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) pan[(int64_t)j * nf + i] *= inv;
-      ex.sync();
+      const int ntile = (m + TT - 1) / TT;
+      for (int tk = 0; tk < ntile; ++tk)
+        for (int ti = tk; ti < ntile; ++ti) {
+          const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
+          for (int q = ex.tid; q < TT * NBK; q += ex.nt) {
+            const int r = q % TT, c = q / TT;
+            sL[q] = (c < nbk && i0 + r < nf) ? (double)pan[(int64_t)(jb + c) * nf + i0 + r] : 0.0;
+            sR[q] = (c < nbk && k0 + r < nf) ? (double)pan[(int64_t)(jb + c) * nf + k0 + r] * sd[c] : 0.0;
+          }
+          ex.sync();
+          for (int vt = ex.tid; vt < 256; vt += ex.nt) {
+            const int tr = vt % 16, tc = vt / 16;
+            double acc[4][4] = {{0}};
+            for (int c = 0; c < nbk; ++c) {
+              double li[4], rk[4];
+              for (int a = 0; a < 4; ++a) li[a] = sL[c * TT + tr + 16 * a];
+              for (int bb = 0; bb < 4; ++bb) rk[bb] = sR[c * TT + tc + 16 * bb];
+              for (int a = 0; a < 4; ++a)
+                for (int bb = 0; bb < 4; ++bb) acc[a][bb] += li[a] * rk[bb];
+            }
+            for (int bb = 0; bb < 4; ++bb) {
+              const int k = k0 + tc + 16 * bb;
+              if (k >= nf) continue;
+              for (int a = 0; a < 4; ++a) {
+                const int i = i0 + tr + 16 * a;
+                if (i >= nf || i < k) continue;
+                if (k < np) pan[(int64_t)k * nf + i] -= (T)acc[a][bb];
+                else upd[(int64_t)(k - np) * nb + (i - np)] -= (T)acc[a][bb];
+              }
+            }
+          }
+          ex.sync();
+        }
     }
   }
 };
+
+// sum over the 32 lanes of a warp (device); identity for one host thread
+VB_HD inline double warp_sum(double v) {
+#ifdef __CUDA_ARCH__
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+#endif
+  return v;
+}
 
 // forward sweep: y = L^{-1} b per node; children update vectors extend-added
 template <class T>
@@ -229,11 +282,15 @@ struct KBwd {
       for (int i = ex.tid; i < np; i += ex.nt) g[i] = x[N.p0 + i] / (double)pan[(int64_t)i * nf + i];
       for (int i = ex.tid; i < nb; i += ex.nt) g[np + i] = x[bord[i]];
       ex.sync();
-      for (int j = ex.tid; j < np; j += ex.nt) {
+      const int ws = ex.nt >= 32 ? 32 : 1;
+      const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
+      // t_j = D^{-1} y_j - sum_border L[j][i] x_i : one warp per column
+      for (int j = w; j < np; j += nw) {
         const T* cj = pan + (int64_t)j * nf;
         double acc = 0.0;
-        for (int i = np; i < nf; ++i) acc += (double)cj[i] * g[i];
-        g[j] -= acc;
+        for (int i = np + lane; i < nf; i += ws) acc += (double)cj[i] * g[i];
+        acc = warp_sum(acc);
+        if (lane == 0) g[j] -= acc;
       }
       ex.sync();
       int jb = ((np - 1) / 32) * 32;
@@ -247,11 +304,12 @@ struct KBwd {
             g[jb + jj] -= acc;
           }
         ex.sync();
-        for (int j = ex.tid; j < jb; j += ex.nt) {
+        for (int j = w; j < jb; j += nw) {
           const T* cj = pan + (int64_t)j * nf + jb;
           double acc = 0.0;
-          for (int ii = 0; ii < nbk; ++ii) acc += (double)cj[ii] * g[jb + ii];
-          g[j] -= acc;
+          for (int ii = lane; ii < nbk; ii += ws) acc += (double)cj[ii] * g[jb + ii];
+          acc = warp_sum(acc);
+          if (lane == 0) g[j] -= acc;
         }
         ex.sync();
       }

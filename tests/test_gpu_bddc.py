@@ -54,9 +54,13 @@ def test_pcg_matches_oracle(pkg, name, scaling):
     x = u.cpu().numpy()
     xo = ro["x"]
     nvf = len(S.dm.free)
-    assert np.linalg.norm(x[:nvf] - xo[:nvf]) <= 1e-10 * np.linalg.norm(xo[:nvf])
+    # constant viscosity: 1e-10.  Viscosity contrast 1e4: the local factors
+    # differ by rounding amplified by the contrast; both CG runs stop at
+    # rtol 1e-8, whose solution bound is kappa * rtol (1.3e-6 here); 1e-8 used.
+    tol = 1e-10 if np.ptp(cfg["nu"]) == 0 else 1e-8
+    assert np.linalg.norm(x[:nvf] - xo[:nvf]) <= tol * np.linalg.norm(xo[:nvf])
     pz = lambda p: p - (S.wmean @ p) / S.wmean.sum()
-    assert np.linalg.norm(pz(x[nvf:]) - pz(xo[nvf:])) <= 1e-8 * np.linalg.norm(pz(xo[nvf:]))
+    assert np.linalg.norm(pz(x[nvf:]) - pz(xo[nvf:])) <= 100 * tol * np.linalg.norm(pz(xo[nvf:]))
     # against the direct solve of the saddle system, within the CG tolerance
     ud, pd = S.solve_direct(F=S.F)
     assert np.linalg.norm(x[:nvf] - ud[S.dm.free]) <= 1e-6 * np.linalg.norm(ud[S.dm.free])
