@@ -202,7 +202,9 @@ def run_ours(args, rank, world, dist):
     info = {k2: bd.info(k2) for k2 in ("n_coarse", "factor_bytes_dirichlet", "factor_bytes_neumann",
                                        "deluxe_bytes", "t_symbolic_ms", "t_factor_dirichlet_ms",
                                        "t_factor_neumann_ms", "t_factor_deluxe_ms", "t_deluxe_combine_ms",
-                                       "t_coarse_solves_ms", "t_coarse_inverse_ms")}
+                                       "t_coarse_solves_ms", "t_coarse_inverse_ms",
+                                       "gflop_factor_dirichlet", "gflop_factor_neumann",
+                                       "gflop_factor_deluxe")}
     r = torch.randn(g.n, dtype=torch.float64, device="cuda")
     z = torch.empty_like(r)
     for _ in range(3):

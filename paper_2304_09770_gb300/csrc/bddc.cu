@@ -30,6 +30,12 @@ struct Batch {
   DBuf<double> F;                         // panels (FP64)
   DBuf<double> U;                         // update matrices
   int64_t nF = 0, nU = 0;
+  int64_t nfv = 0;                        // sum of front sizes (front-vector store per rhs)
+  std::vector<int> ptask_ptr, btask_ptr;  // per level: pivot / border task ranges
+  std::vector<SolveTask> h_ptask, h_btask;
+  DBuf<SolveTask> d_ptask, d_btask;
+  DBuf<double> FV;
+  int fv_nrhs = 0;
 };
 
 }  // namespace vb
@@ -46,7 +52,8 @@ struct bddc {
   vb::DBuf<vb::MacroDev> d_macros;
   vb::DBuf<int> d_border, d_children, d_rel, d_dtype, d_dsrc, d_elpos, d_elptr, d_pv, d_sub_elems, d_vadj_ptr,
       d_vadj, d_vcon_ptr, d_vcon_id, d_iface, d_elloc, d_elloc_ptr, d_share, d_gpos, d_gif;
-  vb::DBuf<int64_t> d_vdof, d_press, d_coarse, d_mdofs;
+  vb::DBuf<int64_t> d_vdof, d_press, d_coarse, d_mdofs, d_fvoff;
+  std::vector<int64_t> h_fvoff;
   vb::DBuf<double> d_vcon_coef, d_wmean, d_hv, d_tau, d_deluxe;
   std::vector<vb::NodeDev> h_nodes;
   std::vector<vb::ProbDev> h_probs;
@@ -333,66 +340,6 @@ struct KCoarseAssemble {
   }
 };
 
-// Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix
-// (one CTA).  M is destroyed.
-struct KDenseInverse {
-  double* M;
-  double* Inv;
-  int64_t n;
-  int* status;
-  VB_HD void operator()(const KExec& ex, int) const {
-    double* red = ex.smem;          // nt values
-    int* ired = reinterpret_cast<int*>(ex.smem + ex.nt);
-    for (int64_t q = ex.tid; q < n * n; q += ex.nt) Inv[q] = (q / n == q % n) ? 1.0 : 0.0;
-    ex.sync();
-    for (int64_t c = 0; c < n; ++c) {
-      double best = -1.0;
-      int bi = (int)c;
-      for (int64_t r = c + ex.tid; r < n; r += ex.nt) {
-        double v = fabs(M[r * n + c]);
-        if (v > best) { best = v; bi = (int)r; }
-      }
-      red[ex.tid] = best;
-      ired[ex.tid] = bi;
-      ex.sync();
-      if (ex.tid == 0) {
-        for (int t = 1; t < ex.nt; ++t)
-          if (red[t] > red[0]) { red[0] = red[t]; ired[0] = ired[t]; }
-        if (!(red[0] > 0.0)) flag_error(status, 4);
-      }
-      ex.sync();
-      const int64_t p = ired[0];
-      if (p != c)
-        for (int64_t j = ex.tid; j < n; j += ex.nt) {
-          double t = M[c * n + j]; M[c * n + j] = M[p * n + j]; M[p * n + j] = t;
-          t = Inv[c * n + j]; Inv[c * n + j] = Inv[p * n + j]; Inv[p * n + j] = t;
-        }
-      ex.sync();
-      const double d = 1.0 / M[c * n + c];
-      ex.sync();
-      for (int64_t j = ex.tid; j < n; j += ex.nt) { M[c * n + j] *= d; Inv[c * n + j] *= d; }
-      ex.sync();
-      for (int64_t idx = ex.tid; idx < n * n; idx += ex.nt) {
-        const int64_t r = idx / n, j = idx % n;
-        if (r == c) continue;
-        const double f = M[r * n + c];
-        if (f == 0.0) continue;
-        if (j == c) continue;
-        M[r * n + j] -= f * M[c * n + j];
-        Inv[r * n + j] -= f * Inv[c * n + j];
-      }
-      ex.sync();
-      for (int64_t r = ex.tid; r < n; r += ex.nt) {
-        if (r == c) continue;
-        const double f = M[r * n + c];
-        Inv[r * n + c] -= f * Inv[c * n + c];
-        M[r * n + c] = 0.0;
-      }
-      ex.sync();
-    }
-  }
-};
-
 // deluxe: S_FF of one side from the root update matrix, rotated to the dual
 // coordinates: Sd = (H^T S H)[r:, r:]
 struct KDeluxeExtract {
@@ -445,60 +392,169 @@ struct KDeluxeExtract {
   }
 };
 
-// deluxe: D^(i) = (S_i + S_j)^{-1} S_i for the first sharing subdomain i
-// (Cholesky of the SPD sum, then n right-hand sides)
-struct KDeluxeCombine {
+// deluxe via a dense front: partial LDL^T of [[S_i + S_j, .], [S_i, .]]
+// gives L21 = S_i L11^{-T} Dg^{-1}, hence D^T = S_i (S_i+S_j)^{-1} = L21 L11^{-1}
+struct KDeluxeFront {
   BddcView V;
   const int* faces;
   const int64_t* sd_i;
   const int64_t* sd_j;
   const double* SD;
-  double* work;
-  const int64_t* work_off;
-  double* DEL;
+  double* PAN;
+  double* UPD;
+  const int64_t* pan_off;
+  const int64_t* upd_off;
   int* status;
   VB_HD void operator()(const KExec& ex, int blk) const {
     const MacroDev F = V.macros[faces[blk]];
-    const int nd = F.ndual;
+    const int nd = F.ndual, nf = 2 * nd;
     const double* Si = SD + sd_i[blk];
     const double* Sj = SD + sd_j[blk];
-    double* L = work + work_off[blk];
-    for (int64_t idx = ex.tid; idx < (int64_t)nd * nd; idx += ex.nt) L[idx] = Si[idx] + Sj[idx];
+    double* pan = PAN + pan_off[blk];
+    double* upd = UPD + upd_off[blk];
+    for (int64_t idx = ex.tid; idx < (int64_t)nd * nf; idx += ex.nt) {
+      const int j = (int)(idx / nf), i = (int)(idx % nf);
+      pan[idx] = i < nd ? Si[(int64_t)j * nd + i] + Sj[(int64_t)j * nd + i] : Si[(int64_t)j * nd + (i - nd)];
+    }
+    for (int64_t idx = ex.tid; idx < (int64_t)nd * nd; idx += ex.nt) upd[idx] = 0.0;
     ex.sync();
-    // right-looking Cholesky, column-major lower
-    for (int j = 0; j < nd; ++j) {
-      if (ex.tid == 0) {
-        double d = L[(int64_t)j * nd + j];
-        if (!(d > 0.0)) { flag_error(status, 5); d = 1.0; }
-        L[(int64_t)j * nd + j] = sqrt(d);
+    front_ldlt<double>(ex, pan, upd, nd, nd, nullptr, status);
+  }
+};
+
+struct GemmTile {
+  int face, ti, tj;
+};
+
+// D (column-major) = (L21 L11^{-1})^T, 64 x 64 output tiles, k staged by 32
+struct KDeluxeGemm {
+  BddcView V;
+  const GemmTile* tiles;
+  const int* faces;
+  const double* PAN;
+  const int64_t* pan_off;
+  double* DEL;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const GemmTile gt = tiles[blk];
+    const MacroDev F = V.macros[faces[gt.face]];
+    const int nd = F.ndual, nf = 2 * nd;
+    const double* pan = PAN + pan_off[gt.face];
+    double* D = DEL + F.deluxe_off;
+    const int i0 = gt.ti * 64, j0 = gt.tj * 64;
+    double* sA = ex.smem;            // [32][64]  L21 rows i0.., columns k
+    double* sB = ex.smem + 32 * 64;  // [32][64]  Linv rows k, columns j0..
+    double acc[4][4];
+    for (int vt = ex.tid; vt < 256; vt += ex.nt)
+      for (int a = 0; a < 4; ++a)
+        for (int bb = 0; bb < 4; ++bb) acc[a][bb] = 0.0;
+    // only the host path (one thread) needs per-virtual-thread storage
+#ifndef __CUDA_ARCH__
+    static thread_local double hacc[256][4][4];
+    for (int vt = 0; vt < 256; ++vt)
+      for (int a = 0; a < 4; ++a)
+        for (int bb = 0; bb < 4; ++bb) hacc[vt][a][bb] = 0.0;
+#endif
+    for (int k0 = j0; k0 < nd; k0 += 32) {
+      for (int q = ex.tid; q < 32 * 64; q += ex.nt) {
+        const int kk = q / 64, r = q % 64;
+        const int k = k0 + kk, i = i0 + r, j = j0 + r;
+        sA[q] = (k < nd && i < nd) ? pan[(int64_t)k * nf + nd + i] : 0.0;
+        double xb = 0.0;
+        if (k < nd && j < nd) xb = k == j ? 1.0 : (k > j ? pan[(int64_t)j * nf + k] : 0.0);
+        sB[q] = xb;
       }
       ex.sync();
-      const double dj = L[(int64_t)j * nd + j];
-      for (int i = j + 1 + ex.tid; i < nd; i += ex.nt) L[(int64_t)j * nd + i] /= dj;
-      ex.sync();
-      const int m = nd - j - 1;
-      for (int64_t idx = ex.tid; idx < (int64_t)m * m; idx += ex.nt) {
-        const int k = j + 1 + (int)(idx / m), i = j + 1 + (int)(idx % m);
-        if (i < k) continue;
-        L[(int64_t)k * nd + i] -= L[(int64_t)j * nd + i] * L[(int64_t)j * nd + k];
+      for (int vt = ex.tid; vt < 256; vt += ex.nt) {
+        const int tr = vt % 16, tc = vt / 16;
+#ifdef __CUDA_ARCH__
+        double (*A)[4] = acc;
+#else
+        double (*A)[4] = hacc[vt];
+#endif
+        for (int kk = 0; kk < 32; ++kk) {
+          double li[4], rk[4];
+          for (int a = 0; a < 4; ++a) li[a] = sA[kk * 64 + tr + 16 * a];
+          for (int bb = 0; bb < 4; ++bb) rk[bb] = sB[kk * 64 + tc + 16 * bb];
+          for (int a = 0; a < 4; ++a)
+            for (int bb = 0; bb < 4; ++bb) A[a][bb] += li[a] * rk[bb];
+        }
       }
       ex.sync();
     }
-    // D = L^{-T} L^{-1} S_i, one column per thread
-    double* D = DEL + F.deluxe_off;
-    for (int c = ex.tid; c < nd; c += ex.nt) {
-      double* x = D + (int64_t)c * nd;
-      for (int i = 0; i < nd; ++i) x[i] = Si[(int64_t)c * nd + i];
-      for (int i = 0; i < nd; ++i) {
-        double v = x[i];
-        for (int k = 0; k < i; ++k) v -= L[(int64_t)k * nd + i] * x[k];
-        x[i] = v / L[(int64_t)i * nd + i];
+    for (int vt = ex.tid; vt < 256; vt += ex.nt) {
+      const int tr = vt % 16, tc = vt / 16;
+#ifdef __CUDA_ARCH__
+      double (*A)[4] = acc;
+#else
+      double (*A)[4] = hacc[vt];
+#endif
+      for (int a = 0; a < 4; ++a)
+        for (int bb = 0; bb < 4; ++bb) {
+          const int i = i0 + tr + 16 * a, j = j0 + tc + 16 * bb;
+          if (i < nd && j < nd) D[(int64_t)i * nd + j] = A[a][bb];   // D[j][i] = M[i][j]
+        }
+    }
+  }
+};
+
+// Gauss-Jordan with partial pivoting on a row-major n x n matrix, one pivot
+// column per pair of launches: (1) pivot search, row swap and scaling,
+// (2) elimination of every other row, rows spread over many CTAs
+struct KGJPivot {
+  double* M;
+  double* Inv;
+  int64_t n, c;
+  int* status;
+  VB_HD void operator()(const KExec& ex, int) const {
+    double* red = ex.smem;
+    int* ired = reinterpret_cast<int*>(ex.smem + ex.nt);
+    double best = -1.0;
+    int bi = (int)c;
+    for (int64_t r = c + ex.tid; r < n; r += ex.nt) {
+      const double v = fabs(M[r * n + c]);
+      if (v > best) { best = v; bi = (int)r; }
+    }
+    red[ex.tid] = best;
+    ired[ex.tid] = bi;
+    ex.sync();
+    if (ex.tid == 0) {
+      for (int t = 1; t < ex.nt; ++t)
+        if (red[t] > red[0] || (red[t] == red[0] && ired[t] < ired[0])) { red[0] = red[t]; ired[0] = ired[t]; }
+      if (!(red[0] > 0.0)) flag_error(status, 4);
+    }
+    ex.sync();
+    const int64_t p = ired[0];
+    if (p != c)
+      for (int64_t j = ex.tid; j < n; j += ex.nt) {
+        double t = M[c * n + j]; M[c * n + j] = M[p * n + j]; M[p * n + j] = t;
+        t = Inv[c * n + j]; Inv[c * n + j] = Inv[p * n + j]; Inv[p * n + j] = t;
       }
-      for (int i = nd - 1; i >= 0; --i) {
-        double v = x[i];
-        for (int k = i + 1; k < nd; ++k) v -= L[(int64_t)i * nd + k] * x[k];
-        x[i] = v / L[(int64_t)i * nd + i];
+    ex.sync();
+    const double d = M[c * n + c] != 0.0 ? 1.0 / M[c * n + c] : 0.0;
+    ex.sync();
+    for (int64_t j = ex.tid; j < n; j += ex.nt) {
+      if (j >= c) M[c * n + j] *= d;
+      Inv[c * n + j] *= d;
+    }
+  }
+};
+
+struct KGJElim {
+  double* M;
+  double* Inv;
+  int64_t n, c;
+  int rows;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    for (int64_t r = (int64_t)blk * rows; r < (int64_t)(blk + 1) * rows && r < n; ++r) {
+      if (r == c) continue;
+      const double f = M[r * n + c];
+      ex.sync();
+      if (f != 0.0) {
+        for (int64_t j = c + 1 + ex.tid; j < n; j += ex.nt) M[r * n + j] -= f * M[c * n + j];
+        for (int64_t j = ex.tid; j < n; j += ex.nt) Inv[r * n + j] -= f * Inv[c * n + j];
       }
+      ex.sync();
+      if (ex.tid == 0) M[r * n + c] = 0.0;
     }
   }
 };
@@ -870,6 +926,26 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
     B.h_levels.push_back(pr.second);
   }
   for (int h = 0; h <= B.maxh; ++h) B.level_ptr[h + 1] += B.level_ptr[h];
+  // front-vector offsets and solve tasks per level
+  if (b->h_fvoff.size() < b->h_nodes.size()) b->h_fvoff.resize(b->h_nodes.size(), 0);
+  int64_t fv = 0;
+  B.ptask_ptr.assign(B.maxh + 2, 0);
+  B.btask_ptr.assign(B.maxh + 2, 0);
+  B.h_ptask.clear();
+  B.h_btask.clear();
+  for (int h = 0; h <= B.maxh; ++h) {
+    for (int q = B.level_ptr[h]; q < B.level_ptr[h + 1]; ++q) {
+      const int t = B.h_levels[q];
+      const NodeDev& N = b->h_nodes[t];
+      b->h_fvoff[t] = fv;
+      fv += N.np + N.nb;
+      for (int s0 = 0; s0 < N.np; s0 += TASK) B.h_ptask.push_back({t, s0, std::min(TASK, N.np - s0)});
+      for (int s0 = 0; s0 < N.nb; s0 += TASK) B.h_btask.push_back({t, s0, std::min(TASK, N.nb - s0)});
+    }
+    B.ptask_ptr[h + 1] = (int)B.h_ptask.size();
+    B.btask_ptr[h + 1] = (int)B.h_btask.size();
+  }
+  B.nfv = fv;
   B.vec_n = vec;
   B.uvec_n = uv;
   B.nF = nF;
@@ -877,7 +953,22 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
   (void)with_vectors;
 }
 
-static void upload_levels(bddc* b, Batch& B) { upload_vec(B.d_levels, B.h_levels, b->stream); }
+// factorization flops of a batch (partial LDL^T plus the L11 inversion)
+static double batch_gflop(bddc* b, const std::vector<int>& probs) {
+  double f = 0;
+  for (int q : probs)
+    for (const Node& Nd : b->H.probs[q].nodes) {
+      const double np = Nd.np, nf = Nd.np + Nd.nb;
+      f += np * nf * nf - nf * np * np + np * np * np / 3.0 + np * np * np / 3.0;
+    }
+  return f * 1e-9;
+}
+
+static void upload_levels(bddc* b, Batch& B) {
+  upload_vec(B.d_levels, B.h_levels, b->stream);
+  upload_vec(B.d_ptask, B.h_ptask, b->stream);
+  upload_vec(B.d_btask, B.h_btask, b->stream);
+}
 
 static void factor_batch(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status) {
   B.F.alloc(std::max<int64_t>(B.nF, 1));
@@ -885,19 +976,30 @@ static void factor_batch(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status
   for (int h = 0; h <= B.maxh; ++h) {
     int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
     KFactor<double> f{V, B.d_levels.p + B.level_ptr[h], B.F.p, B.U.p, status.p};
-    launch(f, cnt, 256, sizeof(double) * (2 * 64 * 32 + 32 + 8), b->stream);
+    launch(f, cnt, 256, sizeof(double) * (std::max(2 * 64 * 32 + 32, B.maxnf) + 8), b->stream);
   }
 }
 
 static void solve_batch(bddc* b, Batch& B, const BddcView& V, double* X, double* UV, int nrhs) {
-  size_t sm = sizeof(double) * (B.maxnf + 8);
+  cudaStream_t st = b->stream;
+  if (B.fv_nrhs < nrhs) {
+    B.FV.alloc(std::max<int64_t>(B.nfv * nrhs, 1));
+    B.fv_nrhs = nrhs;
+  }
+  const size_t sm = sizeof(double) * (B.maxnf + 8);
+  const int64_t* fvo = b->d_fvoff.p;
   for (int h = 0; h <= B.maxh; ++h) {
-    int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
-    launch(KFwd<double>{V, B.d_levels.p + B.level_ptr[h], B.F.p, X, UV, nrhs}, cnt, 256, sm, b->stream);
+    const int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
+    const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
+    const int nb_t = B.btask_ptr[h + 1] - B.btask_ptr[h];
+    launch(KFwdGather{V, B.d_levels.p + B.level_ptr[h], X, UV, B.FV.p, fvo, nrhs}, cnt, 128, 0, st);
+    launch(KFwdPivots<double>{V, B.d_ptask.p + B.ptask_ptr[h], B.F.p, B.FV.p, fvo, X, nrhs}, np_t, 128, sm, st);
+    launch(KFwdBorder<double>{V, B.d_btask.p + B.btask_ptr[h], B.F.p, B.FV.p, fvo, X, UV, nrhs}, nb_t, 128, sm, st);
   }
   for (int h = B.maxh; h >= 0; --h) {
-    int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
-    launch(KBwd<double>{V, B.d_levels.p + B.level_ptr[h], B.F.p, X, nrhs}, cnt, 256, sm, b->stream);
+    const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
+    launch(KBwdBorder<double>{V, B.d_ptask.p + B.ptask_ptr[h], B.F.p, X, B.FV.p, fvo, nrhs}, np_t, 256, sm, st);
+    launch(KBwdPivots<double>{V, B.d_ptask.p + B.ptask_ptr[h], B.F.p, B.FV.p, fvo, X, nrhs}, np_t, 256, sm, st);
   }
 }
 
@@ -1247,6 +1349,10 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     std::vector<int> dprobs(H.dir_prob.begin(), H.dir_prob.end()), nprobs(H.neu_prob.begin(), H.neu_prob.end());
     build_batch(b, b->bd, dprobs, true);
     build_batch(b, b->bn, nprobs, true);
+    upload_vec(b->d_fvoff, b->h_fvoff, st);
+    b->times.push_back({"gflop_factor_dirichlet", batch_gflop(b, dprobs)});
+    b->times.push_back({"gflop_factor_neumann", batch_gflop(b, nprobs)});
+    b->times.push_back({"gflop_factor_deluxe", batch_gflop(b, dl_probs)});
     upload_vec(b->d_nodes, b->h_nodes, st);
     upload_vec(b->d_probs, b->h_probs, st);
     upload_vec(b->d_subs, b->h_subs, st);
@@ -1326,17 +1432,33 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
       }
       mark("t_factor_deluxe_ms");
       DBuf<int> df;
-      DBuf<int64_t> dsi, dsj, dcw;
+      DBuf<int64_t> dsi, dsj, dpo, duo;
+      std::vector<int64_t> po, uo;
+      std::vector<GemmTile> tiles;
+      int64_t pn = 0, un = 0;
+      for (size_t t = 0; t < faces.size(); ++t) {
+        const int nd = b->h_macros[faces[t]].ndual;
+        po.push_back(pn);
+        pn += (int64_t)2 * nd * nd;
+        uo.push_back(un);
+        un += (int64_t)nd * nd;
+        const int nt = (nd + 63) / 64;
+        for (int ti = 0; ti < nt; ++ti)
+          for (int tj = 0; tj < nt; ++tj) tiles.push_back({(int)t, ti, tj});
+      }
       upload_vec(df, faces, st);
       upload_vec(dsi, sd_i, st);
       upload_vec(dsj, sd_j, st);
-      upload_vec(dcw, cw_off, st);
-      int64_t cwn = 0;
-      for (int g : faces) cwn += (int64_t)b->h_macros[g].ndual * b->h_macros[g].ndual;
-      DBuf<double> cwork(std::max<int64_t>(cwn, 1));
+      upload_vec(dpo, po, st);
+      upload_vec(duo, uo, st);
+      DBuf<GemmTile> dtiles;
+      upload_vec(dtiles, tiles, st);
+      DBuf<double> PAN(std::max<int64_t>(pn, 1)), UPD(std::max<int64_t>(un, 1));
       V = make_view(b);
-      launch(KDeluxeCombine{V, df.p, dsi.p, dsj.p, SD.p, cwork.p, dcw.p, b->d_deluxe.p, status.p}, (int)faces.size(),
-             256, 0, st);
+      launch(KDeluxeFront{V, df.p, dsi.p, dsj.p, SD.p, PAN.p, UPD.p, dpo.p, duo.p, status.p}, (int)faces.size(), 256,
+             sizeof(double) * (2 * 64 * 32 + 32 + 8 + 2048), st);
+      launch(KDeluxeGemm{V, dtiles.p, df.p, PAN.p, dpo.p, b->d_deluxe.p}, (int64_t)tiles.size(), 256,
+             sizeof(double) * (2 * 32 * 64 + 8), st);
       mark("t_deluxe_combine_ms");
       auto stv = status.download(st);
       VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe: face Schur complement sum not positive definite");
@@ -1408,7 +1530,16 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
       b->d_Kinv.alloc(nb * nb);
       launch(KCoarseAssemble{V, SG.p, KB.p, N, NC}, 1, 256, 0, st);
       status.zero(st);
-      launch(KDenseInverse{KB.p, b->d_Kinv.p, nb, status.p}, 1, 256, sizeof(double) * 512, st);
+      {
+        std::vector<double> eye(nb * nb, 0.0);
+        for (int64_t q = 0; q < nb; ++q) eye[q * nb + q] = 1.0;
+        b->d_Kinv.upload(eye, st);
+        const int rows = 8;
+        for (int64_t c = 0; c < nb; ++c) {
+          launch(KGJPivot{KB.p, b->d_Kinv.p, nb, c, status.p}, 1, 256, sizeof(double) * 512, st);
+          launch(KGJElim{KB.p, b->d_Kinv.p, nb, c, rows}, (nb + rows - 1) / rows, 256, 0, st);
+        }
+      }
       mark("t_coarse_inverse_ms");
       auto stv = status.download(st);
       VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "coarse matrix singular");
@@ -1553,7 +1684,14 @@ extern "C" int bddc_info(bddc* b, const char* key, double* value) {
       if (G.deluxe_off >= 0) t += 8.0 * G.ndual * G.ndual;
     *value = t;
   } else if (k == "phi_bytes") *value = 8.0 * b->d_phi.n;
+  else if (k == "coarse_bytes") *value = 8.0 * b->d_Kinv.n;
+  else if (k == "n_front_max") *value = std::max(b->bd.maxnf, b->bn.maxnf);
   else {
+    for (auto& pr : b->times)
+      if (pr.first == k) {
+        *value = pr.second;
+        return VEM_OK;
+      }
     set_last_error("bddc_info: unknown key " + k);
     return VEM_EINVAL;
   }

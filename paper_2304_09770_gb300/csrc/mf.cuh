@@ -25,6 +25,96 @@ VB_HD inline int front_index(const NodeDev& N, const int* bord, int x) {
   return bord[lo] == x ? N.np + lo : -1;
 }
 
+// Blocked right-looking partial LDL^T of one dense front (panel nf x np and
+// update block nb x nb, column-major, lower triangles), followed by the
+// in-place inversion of the unit lower diagonal block L11.  piv_type (may be
+// null: all positive) gives the expected pivot sign per pivot (velocity
+// positive; pressure and multiplier negative); a violation sets status 3.
+template <class T>
+VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, const int* piv_type, int* status) {
+    const int nf = np + nb;
+    // blocked right-looking partial LDL^T: panels of NBK columns, then a
+    // rank-NBK update of the trailing front in TT x TT tiles staged in
+    // shared memory (each thread owns a 4 x 4 sub-tile)
+    constexpr int NBK = 32, TT = 64;
+    double* sL = ex.smem;
+    double* sR = ex.smem + TT * NBK;
+    double* sd = ex.smem + 2 * TT * NBK;
+    for (int jb = 0; jb < np; jb += NBK) {
+      const int nbk = np - jb < NBK ? np - jb : NBK;
+      for (int jj = 0; jj < nbk; ++jj) {
+        const int j = jb + jj;
+        T* cj = pan + (int64_t)j * nf;
+        const T dj = cj[j];
+        if (ex.tid == 0) {
+          const double sgn = (!piv_type || piv_type[j] == DT_VEL) ? 1.0 : -1.0;
+          if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
+        }
+        const T inv = (T)1 / dj;
+        const int nk = jb + nbk - j - 1, nr = nf - j - 1;
+        for (int64_t idx = ex.tid; idx < (int64_t)nk * nr; idx += ex.nt) {
+          const int kk = j + 1 + (int)(idx / nr), ii = j + 1 + (int)(idx % nr);
+          if (ii < kk) continue;
+          pan[(int64_t)kk * nf + ii] -= cj[ii] * cj[kk] * inv;
+        }
+        ex.sync();
+        for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) cj[i] *= inv;
+        ex.sync();
+      }
+      const int c0 = jb + nbk, m = nf - c0;
+      if (m <= 0) continue;
+      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = (double)pan[(int64_t)(jb + jj) * nf + jb + jj];
+      ex.sync();
+      const int ntile = (m + TT - 1) / TT;
+      for (int tk = 0; tk < ntile; ++tk)
+        for (int ti = tk; ti < ntile; ++ti) {
+          const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
+          for (int q = ex.tid; q < TT * NBK; q += ex.nt) {
+            const int r = q % TT, c = q / TT;
+            sL[q] = (c < nbk && i0 + r < nf) ? (double)pan[(int64_t)(jb + c) * nf + i0 + r] : 0.0;
+            sR[q] = (c < nbk && k0 + r < nf) ? (double)pan[(int64_t)(jb + c) * nf + k0 + r] * sd[c] : 0.0;
+          }
+          ex.sync();
+          for (int vt = ex.tid; vt < 256; vt += ex.nt) {
+            const int tr = vt % 16, tc = vt / 16;
+            double acc[4][4] = {{0}};
+            for (int c = 0; c < nbk; ++c) {
+              double li[4], rk[4];
+              for (int a = 0; a < 4; ++a) li[a] = sL[c * TT + tr + 16 * a];
+              for (int bb = 0; bb < 4; ++bb) rk[bb] = sR[c * TT + tc + 16 * bb];
+              for (int a = 0; a < 4; ++a)
+                for (int bb = 0; bb < 4; ++bb) acc[a][bb] += li[a] * rk[bb];
+            }
+            for (int bb = 0; bb < 4; ++bb) {
+              const int k = k0 + tc + 16 * bb;
+              if (k >= nf) continue;
+              for (int a = 0; a < 4; ++a) {
+                const int i = i0 + tr + 16 * a;
+                if (i >= nf || i < k) continue;
+                if (k < np) pan[(int64_t)k * nf + i] -= (T)acc[a][bb];
+                else upd[(int64_t)(k - np) * nb + (i - np)] -= (T)acc[a][bb];
+              }
+            }
+          }
+          ex.sync();
+        }
+    }
+    // selective inversion: overwrite the unit lower L11 by L11^{-1} (unit
+    // lower), column by column from the right, so that the triangular
+    // sweeps become matrix-vector products over independent rows/columns
+    double* tmp = ex.smem;
+    for (int j = np - 2; j >= 0; --j) {
+      for (int k = j + 1 + ex.tid; k < np; k += ex.nt) tmp[k] = (double)pan[(int64_t)j * nf + k];
+      ex.sync();
+      for (int i = j + 1 + ex.tid; i < np; i += ex.nt) {
+        double acc = tmp[i];
+        for (int k = j + 1; k < i; ++k) acc += (double)pan[(int64_t)k * nf + i] * tmp[k];
+        pan[(int64_t)j * nf + i] = (T)(-acc);
+      }
+      ex.sync();
+    }
+}
+
 template <class T>
 struct KFactor {
   BddcView V;
@@ -132,73 +222,7 @@ struct KFactor {
       }
       ex.sync();
     }
-    // blocked right-looking partial LDL^T: panels of NBK columns, then a
-    // rank-NBK update of the trailing front in TT x TT tiles staged in
-    // shared memory (each thread owns a 4 x 4 sub-tile)
-    constexpr int NBK = 32, TT = 64;
-    double* sL = ex.smem;
-    double* sR = ex.smem + TT * NBK;
-    double* sd = ex.smem + 2 * TT * NBK;
-    for (int jb = 0; jb < np; jb += NBK) {
-      const int nbk = np - jb < NBK ? np - jb : NBK;
-      for (int jj = 0; jj < nbk; ++jj) {
-        const int j = jb + jj;
-        T* cj = pan + (int64_t)j * nf;
-        const T dj = cj[j];
-        if (ex.tid == 0) {
-          const int dt = V.dtype[P.pos_off + N.p0 + j];
-          const double sgn = dt == DT_VEL ? 1.0 : -1.0;
-          if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
-        }
-        const T inv = (T)1 / dj;
-        const int nk = jb + nbk - j - 1, nr = nf - j - 1;
-        for (int64_t idx = ex.tid; idx < (int64_t)nk * nr; idx += ex.nt) {
-          const int kk = j + 1 + (int)(idx / nr), ii = j + 1 + (int)(idx % nr);
-          if (ii < kk) continue;
-          pan[(int64_t)kk * nf + ii] -= cj[ii] * cj[kk] * inv;
-        }
-        ex.sync();
-        for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) cj[i] *= inv;
-        ex.sync();
-      }
-      const int c0 = jb + nbk, m = nf - c0;
-      if (m <= 0) continue;
-      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = (double)pan[(int64_t)(jb + jj) * nf + jb + jj];
-      ex.sync();
-      const int ntile = (m + TT - 1) / TT;
-      for (int tk = 0; tk < ntile; ++tk)
-        for (int ti = tk; ti < ntile; ++ti) {
-          const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
-          for (int q = ex.tid; q < TT * NBK; q += ex.nt) {
-            const int r = q % TT, c = q / TT;
-            sL[q] = (c < nbk && i0 + r < nf) ? (double)pan[(int64_t)(jb + c) * nf + i0 + r] : 0.0;
-            sR[q] = (c < nbk && k0 + r < nf) ? (double)pan[(int64_t)(jb + c) * nf + k0 + r] * sd[c] : 0.0;
-          }
-          ex.sync();
-          for (int vt = ex.tid; vt < 256; vt += ex.nt) {
-            const int tr = vt % 16, tc = vt / 16;
-            double acc[4][4] = {{0}};
-            for (int c = 0; c < nbk; ++c) {
-              double li[4], rk[4];
-              for (int a = 0; a < 4; ++a) li[a] = sL[c * TT + tr + 16 * a];
-              for (int bb = 0; bb < 4; ++bb) rk[bb] = sR[c * TT + tc + 16 * bb];
-              for (int a = 0; a < 4; ++a)
-                for (int bb = 0; bb < 4; ++bb) acc[a][bb] += li[a] * rk[bb];
-            }
-            for (int bb = 0; bb < 4; ++bb) {
-              const int k = k0 + tc + 16 * bb;
-              if (k >= nf) continue;
-              for (int a = 0; a < 4; ++a) {
-                const int i = i0 + tr + 16 * a;
-                if (i >= nf || i < k) continue;
-                if (k < np) pan[(int64_t)k * nf + i] -= (T)acc[a][bb];
-                else upd[(int64_t)(k - np) * nb + (i - np)] -= (T)acc[a][bb];
-              }
-            }
-          }
-          ex.sync();
-        }
-    }
+    front_ldlt<T>(ex, pan, upd, np, nb, V.dtype + P.pos_off + N.p0, status);
   }
 };
 
@@ -210,24 +234,32 @@ VB_HD inline double warp_sum(double v) {
   return v;
 }
 
-// forward sweep: y = L^{-1} b per node; children update vectors extend-added
-template <class T>
-struct KFwd {
+// Triangular sweeps over one tree level, split into tasks of up to TASK
+// rows (or columns) of one front, so that large fronts spread over many CTAs.
+// A task record: node id, first row/column, count.
+struct SolveTask {
+  int node, start, count;
+};
+constexpr int TASK = 128;
+
+// forward (1): front vector of each node = its own right-hand side entries
+// plus the children's update vectors (extend-add), one CTA per node
+struct KFwdGather {
   BddcView V;
   const int* list;
-  const T* F;
-  double* X;      // problem vectors, [vec_off*nrhs + r*n + pos]
-  double* UV;     // update vectors, [uvec_off*nrhs + r*nb + i]
+  const double* X;   // [vec_off*nrhs + r*n + pos]
+  const double* UV;  // [uvec_off*nrhs + r*nb + i]
+  double* FV;        // [fv_off*nrhs + r*nf + i]
+  const int64_t* fv_off;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
     const int t = list[blk];
     const NodeDev N = V.nodes[t];
     const ProbDev P = V.probs[N.prob];
-    const int np = N.np, nb = N.nb, nf = np + nb;
-    const T* pan = F + N.panel_off;
-    double* f = ex.smem;
+    const int np = N.np, nf = N.np + N.nb;
     for (int r = 0; r < nrhs; ++r) {
-      double* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
+      const double* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
+      double* f = FV + fv_off[t] * nrhs + (int64_t)r * nf;
       for (int i = ex.tid; i < nf; i += ex.nt) f[i] = i < np ? x[N.p0 + i] : 0.0;
       ex.sync();
       for (int c = 0; c < N.nchild; ++c) {
@@ -237,83 +269,145 @@ struct KFwd {
         for (int i = ex.tid; i < C.nb; i += ex.nt) f[rel[i]] += uc[i];
         ex.sync();
       }
-      for (int jb = 0; jb < np; jb += 32) {
-        const int nbk = np - jb < 32 ? np - jb : 32;
-        if (ex.tid == 0)
-          for (int jj = 0; jj < nbk; ++jj) {
-            const double y = f[jb + jj];
-            const T* cj = pan + (int64_t)(jb + jj) * nf;
-            for (int ii = jj + 1; ii < nbk; ++ii) f[jb + ii] -= (double)cj[jb + ii] * y;
-          }
-        ex.sync();
-        for (int i = jb + nbk + ex.tid; i < nf; i += ex.nt) {
-          double acc = 0.0;
-          for (int jj = 0; jj < nbk; ++jj) acc += (double)pan[(int64_t)(jb + jj) * nf + i] * f[jb + jj];
-          f[i] -= acc;
-        }
-        ex.sync();
+    }
+  }
+};
+
+// forward (2): y_p = L11^{-1} f_p for a task of pivot rows (unit lower)
+template <class T>
+struct KFwdPivots {
+  BddcView V;
+  const SolveTask* tasks;
+  const T* F;
+  const double* FV;
+  const int64_t* fv_off;
+  double* X;
+  int nrhs;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const SolveTask tk = tasks[blk];
+    const NodeDev N = V.nodes[tk.node];
+    const ProbDev P = V.probs[N.prob];
+    const int np = N.np, nf = N.np + N.nb;
+    const T* pan = F + N.panel_off;
+    const int kmax = tk.start + tk.count;   // columns needed: k < kmax
+    double* fs = ex.smem;
+    for (int r = 0; r < nrhs; ++r) {
+      const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)r * nf;
+      for (int k = ex.tid; k < kmax; k += ex.nt) fs[k] = f[k];
+      ex.sync();
+      for (int i = tk.start + ex.tid; i < kmax; i += ex.nt) {
+        double acc = fs[i];
+        for (int k = 0; k < i; ++k) acc += (double)pan[(int64_t)k * nf + i] * fs[k];
+        X[P.vec_off * nrhs + (int64_t)r * P.n + N.p0 + i] = acc;
       }
-      for (int i = ex.tid; i < np; i += ex.nt) x[N.p0 + i] = f[i];
-      double* u = UV + N.uvec_off * nrhs + (int64_t)r * nb;
-      for (int i = ex.tid; i < nb; i += ex.nt) u[i] = f[np + i];
+      ex.sync();
+    }
+    (void)np;
+  }
+};
+
+// forward (3): update vector u = f_b - L21 y for a task of border rows
+template <class T>
+struct KFwdBorder {
+  BddcView V;
+  const SolveTask* tasks;
+  const T* F;
+  const double* FV;
+  const int64_t* fv_off;
+  const double* X;
+  double* UV;
+  int nrhs;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const SolveTask tk = tasks[blk];
+    const NodeDev N = V.nodes[tk.node];
+    const ProbDev P = V.probs[N.prob];
+    const int np = N.np, nf = N.np + N.nb;
+    const T* pan = F + N.panel_off;
+    double* ys = ex.smem;
+    for (int r = 0; r < nrhs; ++r) {
+      const double* x = X + P.vec_off * nrhs + (int64_t)r * P.n + N.p0;
+      const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)r * nf;
+      for (int k = ex.tid; k < np; k += ex.nt) ys[k] = x[k];
+      ex.sync();
+      double* u = UV + N.uvec_off * nrhs + (int64_t)r * N.nb;
+      for (int i = tk.start + ex.tid; i < tk.start + tk.count; i += ex.nt) {
+        double acc = f[np + i];
+        for (int k = 0; k < np; ++k) acc -= (double)pan[(int64_t)k * nf + np + i] * ys[k];
+        u[i] = acc;
+      }
       ex.sync();
     }
   }
 };
 
-// backward sweep: x_p = L11^{-T} (D^{-1} y_p - L21^T x_border)
+// backward (1): t_j = y_j / d_j - sum_border L21[i][j] x_i for a task of
+// pivot columns (one warp per column)
 template <class T>
-struct KBwd {
+struct KBwdBorder {
   BddcView V;
-  const int* list;
+  const SolveTask* tasks;
   const T* F;
-  double* X;
+  const double* X;
+  double* TV;        // [fv_off*nrhs + r*nf + j] (reuses the front-vector store)
+  const int64_t* fv_off;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
-    const int t = list[blk];
-    const NodeDev N = V.nodes[t];
+    const SolveTask tk = tasks[blk];
+    const NodeDev N = V.nodes[tk.node];
     const ProbDev P = V.probs[N.prob];
     const int np = N.np, nb = N.nb, nf = np + nb;
     const T* pan = F + N.panel_off;
     const int* bord = V.border + N.border_off;
-    double* g = ex.smem;
+    double* xb = ex.smem;
+    const int ws = ex.nt >= 32 ? 32 : 1;
+    const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
     for (int r = 0; r < nrhs; ++r) {
-      double* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
-      for (int i = ex.tid; i < np; i += ex.nt) g[i] = x[N.p0 + i] / (double)pan[(int64_t)i * nf + i];
-      for (int i = ex.tid; i < nb; i += ex.nt) g[np + i] = x[bord[i]];
+      const double* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
+      for (int i = ex.tid; i < nb; i += ex.nt) xb[i] = x[bord[i]];
       ex.sync();
-      const int ws = ex.nt >= 32 ? 32 : 1;
-      const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
-      // t_j = D^{-1} y_j - sum_border L[j][i] x_i : one warp per column
-      for (int j = w; j < np; j += nw) {
+      double* tv = TV + fv_off[tk.node] * nrhs + (int64_t)r * nf;
+      for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
+        const T* cj = pan + (int64_t)j * nf + np;
+        double acc = 0.0;
+        for (int i = lane; i < nb; i += ws) acc += (double)cj[i] * xb[i];
+        acc = warp_sum(acc);
+        if (lane == 0) tv[j] = x[N.p0 + j] / (double)pan[(int64_t)j * nf + j] - acc;
+      }
+      ex.sync();
+    }
+  }
+};
+
+// backward (2): x_p = L11^{-T} t for a task of pivot columns (warp per column)
+template <class T>
+struct KBwdPivots {
+  BddcView V;
+  const SolveTask* tasks;
+  const T* F;
+  const double* TV;
+  const int64_t* fv_off;
+  double* X;
+  int nrhs;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const SolveTask tk = tasks[blk];
+    const NodeDev N = V.nodes[tk.node];
+    const ProbDev P = V.probs[N.prob];
+    const int np = N.np, nf = N.np + N.nb;
+    const T* pan = F + N.panel_off;
+    double* ts = ex.smem;
+    const int ws = ex.nt >= 32 ? 32 : 1;
+    const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
+    for (int r = 0; r < nrhs; ++r) {
+      const double* tv = TV + fv_off[tk.node] * nrhs + (int64_t)r * nf;
+      for (int i = tk.start + ex.tid; i < np; i += ex.nt) ts[i] = tv[i];
+      ex.sync();
+      for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
         const T* cj = pan + (int64_t)j * nf;
         double acc = 0.0;
-        for (int i = np + lane; i < nf; i += ws) acc += (double)cj[i] * g[i];
+        for (int i = j + 1 + lane; i < np; i += ws) acc += (double)cj[i] * ts[i];
         acc = warp_sum(acc);
-        if (lane == 0) g[j] -= acc;
+        if (lane == 0) X[P.vec_off * nrhs + (int64_t)r * P.n + N.p0 + j] = ts[j] + acc;
       }
-      ex.sync();
-      int jb = ((np - 1) / 32) * 32;
-      for (; np > 0 && jb >= 0; jb -= 32) {
-        const int nbk = np - jb < 32 ? np - jb : 32;
-        if (ex.tid == 0)
-          for (int jj = nbk - 1; jj >= 0; --jj) {
-            const T* cj = pan + (int64_t)(jb + jj) * nf;
-            double acc = 0.0;
-            for (int ii = jj + 1; ii < nbk; ++ii) acc += (double)cj[jb + ii] * g[jb + ii];
-            g[jb + jj] -= acc;
-          }
-        ex.sync();
-        for (int j = w; j < jb; j += nw) {
-          const T* cj = pan + (int64_t)j * nf + jb;
-          double acc = 0.0;
-          for (int ii = lane; ii < nbk; ii += ws) acc += (double)cj[ii] * g[jb + ii];
-          acc = warp_sum(acc);
-          if (lane == 0) g[j] -= acc;
-        }
-        ex.sync();
-      }
-      for (int i = ex.tid; i < np; i += ex.nt) x[N.p0 + i] = g[i];
       ex.sync();
     }
   }
