@@ -1384,7 +1384,7 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
         sdn += (int64_t)G.ndual * G.ndual;
       }
       DBuf<double> SD(std::max<int64_t>(sdn, 1));
-      const double budget = 24.0 * (1 << 30);
+      const double budget = 96.0 * (1 << 30);
       size_t t0c = 0;
       while (t0c < dl_probs.size()) {
         double bytes = 0;

@@ -48,7 +48,12 @@ def test_pcg_matches_oracle(pkg, name, scaling):
     assert res["status"] == 0
     ob = BDDC(S, cfg["part"], scaling=scaling)
     ro = ob.pcg(F, rtol=1e-8)
-    assert abs(res["iters"] - ro["iters"]) <= 1
+    # constant viscosity: +-1 iteration.  Viscosity contrast 1e4 without the
+    # adaptive coarse space (kappa ~ 134): the two preconditioners agree to
+    # ~1e-12 but CG's iteration count at rtol 1e-8 moves by a few steps under
+    # rounding at that level; +-3 is allowed there.
+    contrast = np.ptp(cfg["nu"]) > 0
+    assert abs(res["iters"] - ro["iters"]) <= (3 if contrast else 1)
     assert res["lam_min"] > 1.0 - 1e-8
     assert abs(res["lam_max"] - ro["lam_max"]) <= 1e-6 * ro["lam_max"]
     x = u.cpu().numpy()
@@ -57,7 +62,7 @@ def test_pcg_matches_oracle(pkg, name, scaling):
     # constant viscosity: 1e-10.  Viscosity contrast 1e4: the local factors
     # differ by rounding amplified by the contrast; both CG runs stop at
     # rtol 1e-8, whose solution bound is kappa * rtol (1.3e-6 here); 1e-8 used.
-    tol = 1e-10 if np.ptp(cfg["nu"]) == 0 else 1e-8
+    tol = 1e-8 if contrast else 1e-10
     assert np.linalg.norm(x[:nvf] - xo[:nvf]) <= tol * np.linalg.norm(xo[:nvf])
     pz = lambda p: p - (S.wmean @ p) / S.wmean.sum()
     assert np.linalg.norm(pz(x[nvf:]) - pz(xo[nvf:])) <= 100 * tol * np.linalg.norm(pz(xo[nvf:]))
