@@ -136,75 +136,51 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, rank, world, dist):
-    import numpy as np
-    import torch
-    import paper_2304_09770_gb300 as pkg
-    from synth import make_config
-
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    cfg = make_config(WORKLOAD)
+def measure(pkg, torch, cfg, fq, precision, steps, warmup, stream, with_e2e, rank):
+    """Times `steps` full steps (after `warmup`) of one precision form."""
     mesh, k, nu, part = cfg["mesh"], cfg["k"], cfg["nu"], cfg["part"]
-    stream = torch.cuda.current_stream()
-
-    # host inputs of one step: mesh arrays, viscosity, partition, load samples
-    probe = pkg.VemSystem(mesh, k, nu)
-    pts = probe.quad_points(LOAD_DEGREE)
-    fq = np.ascontiguousarray(cfg["f"](pts))
-    del probe
-    h2d = (mesh["xyz"].nbytes + mesh["face_ptr"].nbytes + mesh["face_vtx"].nbytes + mesh["elem_ptr"].nbytes
-           + mesh["elem_face"].nbytes + nu.nbytes + part.nbytes + fq.nbytes)
 
     def step(out_host=None):
         g = pkg.VemSystem(mesh, k, nu)
         g.set_stream(stream)
         rhs = g.load(LOAD_DEGREE, fq)
-        bd = pkg.Bddc(g, part)
+        bd = pkg.Bddc(g, part, precision=precision)
         u = torch.zeros_like(rhs)
         res = bd.solve(rhs, u, rtol=1e-8, maxit=1000)
         if out_host is not None:
             out_host.copy_(u, non_blocking=True)
         return g, bd, u, rhs, res
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
         torch.cuda.synchronize()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    # device-timed steps (inputs in host memory as the C-ABI takes them)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else Clocks(f"/tmp/clocks_rank{rank}.csv")
-    with clocks:
-        l0 = pkg.kernel_launches()
-        ev0.record(stream)
+    g = bd = u = rhs = None
+    l0 = pkg.kernel_launches()
+    ev0.record(stream)
+    for _ in range(steps):
         g = bd = u = rhs = None
-        for _ in range(args.steps):
-            g = bd = u = rhs = None
-            g, bd, u, rhs, res = step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        dev_ms = ev0.elapsed_time(ev1) / args.steps
-        launches = (pkg.kernel_launches() - l0) // args.steps
-        # end-to-end: same step plus the solution copied to pinned host memory
+        g, bd, u, rhs, res = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dev_ms = ev0.elapsed_time(ev1) / steps
+    launches = (pkg.kernel_launches() - l0) // steps
+    e2e_ms = None
+    if with_e2e:
         host_u = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
-        torch.cuda.synchronize()
         g = bd = u = rhs = None
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             g = bd = u = rhs = None
             g, bd, u, rhs, res = step(host_u)
         torch.cuda.synchronize()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    # phases of the last step, applies/s and the local-solve roofline
-    info = {k2: bd.info(k2) for k2 in ("n_coarse", "factor_bytes_dirichlet", "factor_bytes_neumann",
-                                       "deluxe_bytes", "t_symbolic_ms", "t_factor_dirichlet_ms",
-                                       "t_factor_neumann_ms", "t_factor_deluxe_ms", "t_deluxe_combine_ms",
-                                       "t_coarse_solves_ms", "t_coarse_inverse_ms",
-                                       "gflop_factor_dirichlet", "gflop_factor_neumann",
-                                       "gflop_factor_deluxe")}
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+    keys = ("factor_bytes_dirichlet", "factor_bytes_neumann", "deluxe_bytes", "t_symbolic_ms", "t_upload_ms",
+            "t_factor_dirichlet_ms", "t_factor_neumann_ms", "t_factor_deluxe_ms", "t_deluxe_combine_ms",
+            "t_coarse_rhs_ms", "t_coarse_solves_ms", "t_coarse_gram_ms", "t_coarse_inverse_ms",
+            "gflop_factor_dirichlet", "gflop_factor_neumann", "gflop_factor_deluxe")
+    info = {k2: bd.info(k2) for k2 in keys}
     r = torch.randn(g.n, dtype=torch.float64, device="cuda")
     z = torch.empty_like(r)
     for _ in range(3):
@@ -217,17 +193,51 @@ def run_ours(args, rank, world, dist):
     ev1.record(stream)
     torch.cuda.synchronize()
     apply_ms = ev0.elapsed_time(ev1) / napp
-    solve_ms, solve_bytes = bd.time_local_solves(5)
-    torch.cuda.synchronize()
-    t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device="cuda")
+    sweep_ms, sweep_bytes = bd.time_local_solves(5)
+    return dict(dev_ms=dev_ms, e2e_ms=e2e_ms, launches=launches, res=res, info=info, apply_ms=apply_ms,
+                sweep_ms=sweep_ms, sweep_bytes=sweep_bytes, n=g.n, n_coarse=bd.info("n_coarse"))
+
+
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+    import paper_2304_09770_gb300 as pkg
+    from synth import make_config
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    cfg = make_config(WORKLOAD)
+    mesh, k, nu, part = cfg["mesh"], cfg["k"], cfg["nu"], cfg["part"]
+    stream = torch.cuda.current_stream()
+    # host inputs of one step: mesh arrays, viscosity, partition, load samples
+    probe = pkg.VemSystem(mesh, k, nu)
+    pts = probe.quad_points(LOAD_DEGREE)
+    fq = np.ascontiguousarray(cfg["f"](pts))
+    del probe
+    h2d = (mesh["xyz"].nbytes + mesh["face_ptr"].nbytes + mesh["face_vtx"].nbytes + mesh["elem_ptr"].nbytes
+           + mesh["elem_face"].nbytes + nu.nbytes + part.nbytes + fq.nbytes)
+    if dist:
+        dist.barrier()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else Clocks(f"/tmp/clocks_rank{rank}.csv")
+    with clocks:
+        m32 = measure(pkg, torch, cfg, fq, 1, args.steps, args.warmup, stream, True, rank)
+        m64 = measure(pkg, torch, cfg, fq, 0, args.steps, args.warmup, stream, False, rank)
+    t = torch.tensor([m32["dev_ms"], m32["e2e_ms"], m64["dev_ms"]], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms, e2e_ms = t.tolist()
-    hbm, kind = peaks()
-    achieved = solve_bytes / (solve_ms * 1e-3) / 1e9
-    # kernels launched per step (counted by the library's structure)
+    dev_ms, e2e_ms, dev64 = t.tolist()
     if rank != 0:
         return
+    hbm, kind = peaks()
+
+    def roof(m):
+        ach = m["sweep_bytes"] / (m["sweep_ms"] * 1e-3) / 1e9
+        return {"kernel": "local triangular sweeps (level GEMV kernels, forward+backward, Neumann+Dirichlet "
+                          "factors)", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_kind": kind, "traffic": None,
+                "bytes_per_sweep_pair": m["sweep_bytes"], "ms_per_sweep_pair": m["sweep_ms"]}
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         try:
@@ -238,25 +248,29 @@ def run_ours(args, rank, world, dist):
                              "thread, seconds scaled linearly by the element ratio (understates the oracle)"}
         except Exception as e:  # noqa: BLE001
             cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:200]}
+    res = m32["res"]
     line = {
         "metric": METRIC, "value": dev_ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32-local/f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "mesh": "32^3 hex, interior vertices +-0.2h (seed 2), split quads",
-                   "k": 2, "subdomains": 64, "precision": "FP64 local factors", "rtol": 1e-8,
-                   "load_degree": LOAD_DEGREE, "l2": "inputs larger than L2 (local factors ~14 GB)",
+                   "k": 2, "subdomains": 64, "precision": "FP32 local factors + 1 refinement; FP64 CG, "
+                   "operator, coarse, deluxe inverses", "rtol": 1e-8, "load_degree": LOAD_DEGREE,
+                   "l2": "inputs larger than L2 (local factors 7-15 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iterations": res["iters"], "kappa": res["kappa"], "lam_min": res["lam_min"],
-        "bddc_applies_per_s": 1e3 / apply_ms, "ms_per_apply": apply_ms,
-        "setup_phases_ms": info,
-        "roofline": {"kernel": "local triangular sweeps (forward+backward, Neumann+Dirichlet factors)",
-                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": kind, "traffic": None},
+        "bddc_applies_per_s": 1e3 / m32["apply_ms"], "ms_per_apply": m32["apply_ms"],
+        "setup_phases_ms": m32["info"],
+        "fp64": {"value": dev64 / 1e3, "unit": "s", "iterations": m64["res"]["iters"],
+                 "kappa": m64["res"]["kappa"], "lam_min": m64["res"]["lam_min"],
+                 "bddc_applies_per_s": 1e3 / m64["apply_ms"], "ms_per_apply": m64["apply_ms"],
+                 "setup_phases_ms": m64["info"], "roofline": roof(m64), "gpu_launches": int(m64["launches"])},
+        "roofline": roof(m32),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(g.n * 8)},
+                "d2h_bytes_per_step": int(m32["n"] * 8)},
         "clocks": clocks.summary(),
-        "gpu_launches": int(launches),
+        "gpu_launches": int(m32["launches"]),
     }
     print(json.dumps(line), flush=True)
 

@@ -139,7 +139,10 @@ const char* vem_last_error(void);
 #define BDDC_SCALING_DELUXE 1         /* deluxe on macro faces, 1/card on edges     */
 
 typedef struct {
-  int32_t precision;        /* 0: FP64 local factors (the only value accepted) */
+  int32_t precision;        /* local factors and sweeps: 0 FP64; 1 FP32 with one step of
+                               refinement per local solve (residual in FP64 from the
+                               element matrices); 2 FP32 without refinement.  Coarse
+                               matrix, deluxe inverses, operator and CG stay FP64. */
   int32_t scaling;          /* unused (the bddc_setup argument decides)        */
   uint32_t constraints;     /* unused (the bddc_setup argument decides)        */
   double adaptive_threshold;/* unused: 0                                       */

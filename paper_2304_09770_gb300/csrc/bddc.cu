@@ -27,8 +27,12 @@ struct Batch {
   std::vector<int> level_ptr;             // nodes grouped by height
   DBuf<int> d_levels;
   std::vector<int> h_levels;
-  DBuf<double> F;                         // panels (FP64)
+  DBuf<double> F;                         // panels (FP64 local factors)
   DBuf<double> U;                         // update matrices
+  DBuf<float> F32, U32;                   // the same in FP32 (FP32-local factors)
+  DBuf<double> XB, XR;                    // refinement: right-hand sides, residuals
+  std::vector<MatvecTask> h_mtask;
+  DBuf<MatvecTask> d_mtask;
   int64_t nF = 0, nU = 0;
   int64_t nfv = 0;                        // sum of front sizes (front-vector store per rhs)
   std::vector<int> ptask_ptr, btask_ptr;  // per level: pivot / border task ranges
@@ -45,8 +49,11 @@ struct bddc {
   vb::BddcHost H;
   cudaStream_t stream = 0;
   vb::SetupOptions opt;
+  int prec = 0;                  // 0 FP64 local factors; 1 FP32 + one refinement; 2 FP32 plain
   // device copies of the structure
   vb::DBuf<vb::NodeDev> d_nodes;
+  vb::DBuf<int> d_mcon_ptr, d_mcon_vdof;
+  vb::DBuf<double> d_mcon_coef;
   vb::DBuf<vb::ProbDev> d_probs;
   vb::DBuf<vb::SubDev> d_subs;
   vb::DBuf<vb::MacroDev> d_macros;
@@ -342,11 +349,12 @@ struct KCoarseAssemble {
 
 // deluxe: S_FF of one side from the root update matrix, rotated to the dual
 // coordinates: Sd = (H^T S H)[r:, r:]
+template <class T>
 struct KDeluxeExtract {
   BddcView V;
   const int* probs;       // deluxe problem ids
   const int* roots;       // root node per problem
-  const double* U;        // deluxe batch update store
+  const T* U;             // deluxe batch update store
   double* work;           // n x n per problem
   const int64_t* work_off;
   double* SD;             // dual blocks
@@ -356,11 +364,11 @@ struct KDeluxeExtract {
     const NodeDev R = V.nodes[roots[blk]];
     const MacroDev F = V.macros[P.macro];
     const int n = F.n, r = F.r, nd = n - r;
-    const double* Ur = U + R.upd_off;
+    const T* Ur = U + R.upd_off;
     double* S = work + work_off[blk];
     for (int64_t idx = ex.tid; idx < (int64_t)n * n; idx += ex.nt) {
       const int k = (int)(idx / n), i = (int)(idx % n);
-      S[idx] = i >= k ? Ur[(int64_t)k * n + i] : Ur[(int64_t)i * n + k];
+      S[idx] = (double)(i >= k ? Ur[(int64_t)k * n + i] : Ur[(int64_t)i * n + k]);
     }
     ex.sync();
     // S <- H^T S (columns), then S <- (H^T S^T)^T = H^T S H using symmetry of S
@@ -946,6 +954,10 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
     B.btask_ptr[h + 1] = (int)B.h_btask.size();
   }
   B.nfv = fv;
+  B.h_mtask.clear();
+  for (int q : probs)
+    for (int s0 = 0; s0 < b->h_probs[q].n; s0 += TASK)
+      B.h_mtask.push_back({q, s0, std::min(TASK, b->h_probs[q].n - s0)});
   B.vec_n = vec;
   B.uvec_n = uv;
   B.nF = nF;
@@ -968,19 +980,27 @@ static void upload_levels(bddc* b, Batch& B) {
   upload_vec(B.d_levels, B.h_levels, b->stream);
   upload_vec(B.d_ptask, B.h_ptask, b->stream);
   upload_vec(B.d_btask, B.h_btask, b->stream);
+  upload_vec(B.d_mtask, B.h_mtask, b->stream);
 }
 
-static void factor_batch(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status) {
-  B.F.alloc(std::max<int64_t>(B.nF, 1));
-  B.U.alloc(std::max<int64_t>(B.nU, 1));
+template <class T>
+static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status, DBuf<T>& Fs, DBuf<T>& Us) {
+  Fs.alloc(std::max<int64_t>(B.nF, 1));
+  Us.alloc(std::max<int64_t>(B.nU, 1));
   for (int h = 0; h <= B.maxh; ++h) {
     int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
-    KFactor<double> f{V, B.d_levels.p + B.level_ptr[h], B.F.p, B.U.p, status.p};
+    KFactor<T> f{V, B.d_levels.p + B.level_ptr[h], Fs.p, Us.p, status.p};
     launch(f, cnt, 256, sizeof(double) * (std::max(2 * 64 * 32 + 32, B.maxnf) + 8), b->stream);
   }
 }
 
-static void solve_batch(bddc* b, Batch& B, const BddcView& V, double* X, double* UV, int nrhs) {
+static void factor_batch(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status) {
+  if (b->prec == 0) factor_batch_t<double>(b, B, V, status, B.F, B.U);
+  else factor_batch_t<float>(b, B, V, status, B.F32, B.U32);
+}
+
+template <class T>
+static void sweep_batch(bddc* b, Batch& B, const BddcView& V, const T* Fp, double* X, double* UV, int nrhs) {
   cudaStream_t st = b->stream;
   if (B.fv_nrhs < nrhs) {
     B.FV.alloc(std::max<int64_t>(B.nfv * nrhs, 1));
@@ -993,14 +1013,47 @@ static void solve_batch(bddc* b, Batch& B, const BddcView& V, double* X, double*
     const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
     const int nb_t = B.btask_ptr[h + 1] - B.btask_ptr[h];
     launch(KFwdGather{V, B.d_levels.p + B.level_ptr[h], X, UV, B.FV.p, fvo, nrhs}, cnt, 128, 0, st);
-    launch(KFwdPivots<double>{V, B.d_ptask.p + B.ptask_ptr[h], B.F.p, B.FV.p, fvo, X, nrhs}, np_t, 128, sm, st);
-    launch(KFwdBorder<double>{V, B.d_btask.p + B.btask_ptr[h], B.F.p, B.FV.p, fvo, X, UV, nrhs}, nb_t, 128, sm, st);
+    launch(KFwdPivots<T>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 128, sm, st);
+    launch(KFwdBorder<T>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 128, sm, st);
   }
   for (int h = B.maxh; h >= 0; --h) {
     const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
-    launch(KBwdBorder<double>{V, B.d_ptask.p + B.ptask_ptr[h], B.F.p, X, B.FV.p, fvo, nrhs}, np_t, 256, sm, st);
-    launch(KBwdPivots<double>{V, B.d_ptask.p + B.ptask_ptr[h], B.F.p, B.FV.p, fvo, X, nrhs}, np_t, 256, sm, st);
+    launch(KBwdBorder<T>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, B.FV.p, fvo, nrhs}, np_t, 256, sm, st);
+    launch(KBwdPivots<T>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 256, sm, st);
   }
+}
+
+struct KAxpyN {   // y += x over n entries
+  const double* x;
+  double* y;
+  int64_t n;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int64_t hi = (int64_t)(blk + 1) * 256 < n ? (int64_t)(blk + 1) * 256 : n;
+    for (int64_t i = (int64_t)blk * 256 + ex.tid; i < hi; i += ex.nt) y[i] += x[i];
+  }
+};
+
+// local solves of a batch, X (right-hand sides) overwritten by the
+// solutions; FP32-local factors get one step of refinement with the
+// residual computed in FP64 from the element matrices
+static void solve_batch(bddc* b, Batch& B, const BddcView& V, double* X, double* UV, int nrhs) {
+  if (b->prec == 0) {
+    sweep_batch<double>(b, B, V, B.F.p, X, UV, nrhs);
+    return;
+  }
+  if (b->prec == 2) {
+    sweep_batch<float>(b, B, V, B.F32.p, X, UV, nrhs);
+    return;
+  }
+  cudaStream_t st = b->stream;
+  const int64_t n = B.vec_n * nrhs;
+  if ((int64_t)B.XB.n < n) { B.XB.alloc(std::max<int64_t>(n, 1)); B.XR.alloc(std::max<int64_t>(n, 1)); }
+  VB_CUDA(cudaMemcpyAsync(B.XB.p, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  sweep_batch<float>(b, B, V, B.F32.p, X, UV, nrhs);
+  launch(KProbResidual{V, B.d_mtask.p, B.XB.p, X, B.XR.p, b->d_mcon_ptr.p, b->d_mcon_vdof.p, b->d_mcon_coef.p,
+                       nrhs}, (int64_t)B.h_mtask.size(), 128, 0, st);
+  sweep_batch<float>(b, B, V, B.F32.p, B.XR.p, UV, nrhs);
+  launch(KAxpyN{B.XR.p, X, n}, (n + 255) / 256, 256, 0, st);
 }
 
 static int max_macro_n(bddc* b) {
@@ -1118,6 +1171,10 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     b->opt.constraints = constraints;
     b->opt.scaling = scaling;
     if (opts && opts->nd_leaf > 0) b->opt.leaf = opts->nd_leaf;
+    if (opts) {
+      VB_CHECK(opts->precision >= 0 && opts->precision <= 2, VEM_EINVAL, "bddc_options.precision must be 0, 1 or 2");
+      b->prec = opts->precision;
+    }
     cudaStream_t st = b->stream;
     BddcHost& H = b->H;
     auto t0 = std::chrono::steady_clock::now();
@@ -1135,7 +1192,8 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     std::vector<int> border, children, rel, dtype, dsrc, elpos, elptr, pv, sub_elems, vadj_ptr, vadj, vcon_ptr,
         vcon_id, iface, elloc, elloc_ptr, share, gpos, gif;
     std::vector<int64_t> vdof, press, coarse, mdofs;
-    std::vector<double> vcon_coef, wmean, hv, tau;
+    std::vector<double> vcon_coef, wmean, hv, tau, mcon_coef;
+    std::vector<int> mcon_ptr, mcon_vdof;
     b->h_subs.assign(N, SubDev{});
     int64_t loc = 0;
     for (int i = 0; i < N; ++i) {
@@ -1164,6 +1222,23 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
       D.vcon_off = (int64_t)vcon_id.size();
       vcon_id.insert(vcon_id.end(), S.vcon_id.begin(), S.vcon_id.end());
       vcon_coef.insert(vcon_coef.end(), S.vcon_coef.begin(), S.vcon_coef.end());
+      {
+        // multiplier -> (local vdof, coef): the constraint rows by multiplier
+        int nm = 0;
+        for (int id : S.vcon_id) nm = std::max(nm, id + 1);
+        std::vector<std::vector<std::pair<int, double>>> rows(nm);
+        for (int v = 0; v < D.nv; ++v)
+          for (int q = S.vcon_ptr[v]; q < S.vcon_ptr[v + 1]; ++q) rows[S.vcon_id[q]].push_back({v, S.vcon_coef[q]});
+        D.mcon_ptr_off = (int64_t)mcon_ptr.size();
+        D.mcon_off = (int64_t)mcon_vdof.size();
+        int o2 = 0;
+        mcon_ptr.push_back(0);
+        for (auto& rw : rows) {
+          for (auto& pr : rw) { mcon_vdof.push_back(pr.first); mcon_coef.push_back(pr.second); }
+          o2 += (int)rw.size();
+          mcon_ptr.push_back(o2);
+        }
+      }
       D.press_off = (int64_t)press.size();
       press.insert(press.end(), S.press.begin(), S.press.end());
       wmean.insert(wmean.end(), S.wmean.begin(), S.wmean.end());
@@ -1343,6 +1418,9 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     upload_vec(b->d_wmean, wmean, st);
     upload_vec(b->d_hv, hv, st);
     upload_vec(b->d_tau, tau, st);
+    upload_vec(b->d_mcon_ptr, mcon_ptr, st);
+    upload_vec(b->d_mcon_vdof, mcon_vdof, st);
+    upload_vec(b->d_mcon_coef, mcon_coef, st);
     b->ncv = H.ncoarse_vel;
     b->nc = H.ncoarse;
     // batches
@@ -1421,7 +1499,11 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
         upload_vec(dso, cso, st);
         upload_vec(dwo, cwo, st);
         DBuf<double> work(std::max<int64_t>(w, 1));
-        launch(KDeluxeExtract{V, dp.p, dr.p, Bc.U.p, work.p, dwo.p, SD.p, dso.p}, (int)cp.size(), 256, 0, st);
+        if (b->prec == 0)
+          launch(KDeluxeExtract<double>{V, dp.p, dr.p, Bc.U.p, work.p, dwo.p, SD.p, dso.p}, (int)cp.size(), 256, 0, st);
+        else
+          launch(KDeluxeExtract<float>{V, dp.p, dr.p, Bc.U32.p, work.p, dwo.p, SD.p, dso.p}, (int)cp.size(), 256, 0,
+                 st);
         VB_CUDA(cudaStreamSynchronize(st));
         t0c = t1c;
       }
@@ -1672,8 +1754,8 @@ extern "C" int bddc_info(bddc* b, const char* key, double* value) {
   if (k == "n_subdomains") *value = b->H.N;
   else if (k == "n_coarse") *value = (double)b->nc;
   else if (k == "n_macro") *value = (double)b->h_macros.size();
-  else if (k == "factor_bytes_dirichlet") *value = 8.0 * b->bd.nF;
-  else if (k == "factor_bytes_neumann") *value = 8.0 * b->bn.nF;
+  else if (k == "factor_bytes_dirichlet") *value = (b->prec ? 4.0 : 8.0) * b->bd.nF;
+  else if (k == "factor_bytes_neumann") *value = (b->prec ? 4.0 : 8.0) * b->bn.nF;
   else if (k == "n_deluxe_faces") {
     int c = 0;
     for (auto& G : b->h_macros) c += G.deluxe_off >= 0;
@@ -1686,6 +1768,7 @@ extern "C" int bddc_info(bddc* b, const char* key, double* value) {
   } else if (k == "phi_bytes") *value = 8.0 * b->d_phi.n;
   else if (k == "coarse_bytes") *value = 8.0 * b->d_Kinv.n;
   else if (k == "n_front_max") *value = std::max(b->bd.maxnf, b->bn.maxnf);
+  else if (k == "precision") *value = b->prec;
   else {
     for (auto& pr : b->times)
       if (pr.first == k) {
@@ -1707,16 +1790,21 @@ extern "C" int bddc_time_local_solves(bddc* b, int nrep, double* ms, double* byt
     cudaStream_t st = b->stream;
     b->XN.zero(st);
     b->XD.zero(st);
-    solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, 1);   // warm-up
-    solve_batch(b, b->bd, V, b->XD.p, b->UVD.p, 1);
+    auto sweeps = [&]() {
+      if (b->prec == 0) {
+        sweep_batch<double>(b, b->bn, V, b->bn.F.p, b->XN.p, b->UVN.p, 1);
+        sweep_batch<double>(b, b->bd, V, b->bd.F.p, b->XD.p, b->UVD.p, 1);
+      } else {
+        sweep_batch<float>(b, b->bn, V, b->bn.F32.p, b->XN.p, b->UVN.p, 1);
+        sweep_batch<float>(b, b->bd, V, b->bd.F32.p, b->XD.p, b->UVD.p, 1);
+      }
+    };
+    sweeps();   // warm-up
     cudaEvent_t e0, e1;
     VB_CUDA(cudaEventCreate(&e0));
     VB_CUDA(cudaEventCreate(&e1));
     VB_CUDA(cudaEventRecord(e0, st));
-    for (int i = 0; i < nrep; ++i) {
-      solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, 1);
-      solve_batch(b, b->bd, V, b->XD.p, b->UVD.p, 1);
-    }
+    for (int i = 0; i < nrep; ++i) sweeps();
     VB_CUDA(cudaEventRecord(e1, st));
     VB_CUDA(cudaEventSynchronize(e1));
     float t = 0;
@@ -1725,7 +1813,7 @@ extern "C" int bddc_time_local_solves(bddc* b, int nrep, double* ms, double* byt
     cudaEventDestroy(e1);
     *ms = t / nrep;
     // algorithmic bytes: every panel read once forward and once backward
-    *bytes = 2.0 * 8.0 * (double)(b->bn.nF + b->bd.nF);
+    *bytes = 2.0 * (b->prec == 0 ? 8.0 : 4.0) * (double)(b->bn.nF + b->bd.nF);
     return VEM_OK;
   } catch (const Error& e) {
     return bfail(e);

@@ -25,6 +25,7 @@ struct SubDev {
   double volume, wsum;
   int64_t elem_off, vdof_off, vadj_ptr_off, vadj_off, vcon_ptr_off, vcon_off;
   int64_t press_off, iface_off, coarse_off, phi_off, elloc_off, ellocptr_off, loc_off;
+  int64_t mcon_ptr_off, mcon_off;
 };
 
 struct MacroDev {

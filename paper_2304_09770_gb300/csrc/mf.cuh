@@ -37,9 +37,9 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
     // rank-NBK update of the trailing front in TT x TT tiles staged in
     // shared memory (each thread owns a 4 x 4 sub-tile)
     constexpr int NBK = 32, TT = 64;
-    double* sL = ex.smem;
-    double* sR = ex.smem + TT * NBK;
-    double* sd = ex.smem + 2 * TT * NBK;
+    T* sL = reinterpret_cast<T*>(ex.smem);
+    T* sR = sL + TT * NBK;
+    T* sd = sL + 2 * TT * NBK;
     for (int jb = 0; jb < np; jb += NBK) {
       const int nbk = np - jb < NBK ? np - jb : NBK;
       for (int jj = 0; jj < nbk; ++jj) {
@@ -63,7 +63,7 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
       }
       const int c0 = jb + nbk, m = nf - c0;
       if (m <= 0) continue;
-      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = (double)pan[(int64_t)(jb + jj) * nf + jb + jj];
+      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = pan[(int64_t)(jb + jj) * nf + jb + jj];
       ex.sync();
       const int ntile = (m + TT - 1) / TT;
       for (int tk = 0; tk < ntile; ++tk)
@@ -71,15 +71,15 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
           const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
           for (int q = ex.tid; q < TT * NBK; q += ex.nt) {
             const int r = q % TT, c = q / TT;
-            sL[q] = (c < nbk && i0 + r < nf) ? (double)pan[(int64_t)(jb + c) * nf + i0 + r] : 0.0;
-            sR[q] = (c < nbk && k0 + r < nf) ? (double)pan[(int64_t)(jb + c) * nf + k0 + r] * sd[c] : 0.0;
+            sL[q] = (c < nbk && i0 + r < nf) ? pan[(int64_t)(jb + c) * nf + i0 + r] : (T)0;
+            sR[q] = (c < nbk && k0 + r < nf) ? pan[(int64_t)(jb + c) * nf + k0 + r] * sd[c] : (T)0;
           }
           ex.sync();
           for (int vt = ex.tid; vt < 256; vt += ex.nt) {
             const int tr = vt % 16, tc = vt / 16;
-            double acc[4][4] = {{0}};
+            T acc[4][4] = {{0}};
             for (int c = 0; c < nbk; ++c) {
-              double li[4], rk[4];
+              T li[4], rk[4];
               for (int a = 0; a < 4; ++a) li[a] = sL[c * TT + tr + 16 * a];
               for (int bb = 0; bb < 4; ++bb) rk[bb] = sR[c * TT + tc + 16 * bb];
               for (int a = 0; a < 4; ++a)
@@ -91,8 +91,8 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
               for (int a = 0; a < 4; ++a) {
                 const int i = i0 + tr + 16 * a;
                 if (i >= nf || i < k) continue;
-                if (k < np) pan[(int64_t)k * nf + i] -= (T)acc[a][bb];
-                else upd[(int64_t)(k - np) * nb + (i - np)] -= (T)acc[a][bb];
+                if (k < np) pan[(int64_t)k * nf + i] -= acc[a][bb];
+                else upd[(int64_t)(k - np) * nb + (i - np)] -= acc[a][bb];
               }
             }
           }
@@ -102,14 +102,14 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
     // selective inversion: overwrite the unit lower L11 by L11^{-1} (unit
     // lower), column by column from the right, so that the triangular
     // sweeps become matrix-vector products over independent rows/columns
-    double* tmp = ex.smem;
+    T* tmp = reinterpret_cast<T*>(ex.smem);
     for (int j = np - 2; j >= 0; --j) {
-      for (int k = j + 1 + ex.tid; k < np; k += ex.nt) tmp[k] = (double)pan[(int64_t)j * nf + k];
+      for (int k = j + 1 + ex.tid; k < np; k += ex.nt) tmp[k] = pan[(int64_t)j * nf + k];
       ex.sync();
       for (int i = j + 1 + ex.tid; i < np; i += ex.nt) {
-        double acc = tmp[i];
-        for (int k = j + 1; k < i; ++k) acc += (double)pan[(int64_t)k * nf + i] * tmp[k];
-        pan[(int64_t)j * nf + i] = (T)(-acc);
+        T acc = tmp[i];
+        for (int k = j + 1; k < i; ++k) acc += pan[(int64_t)k * nf + i] * tmp[k];
+        pan[(int64_t)j * nf + i] = -acc;
       }
       ex.sync();
     }
@@ -409,6 +409,77 @@ struct KBwdPivots {
         if (lane == 0) X[P.vec_off * nrhs + (int64_t)r * P.n + N.p0 + j] = ts[j] + acc;
       }
       ex.sync();
+    }
+  }
+};
+
+// residual of a local problem in FP64: R = B - K_q Z over the problem
+// positions (velocity rows from the element matrices, pressure rows from
+// B_K, multiplier rows from the constraint functionals); tasks of up to
+// TASK positions of one problem
+struct MatvecTask {
+  int prob, start, count;
+};
+struct KProbResidual {
+  BddcView V;
+  const MatvecTask* tasks;
+  const double* Bv;   // right-hand sides   [vec_off*nrhs + r*n + pos]
+  const double* Z;    // current solutions
+  double* R;
+  const int* mcon_ptr;   // per subdomain: multiplier -> (local vdof, coef)
+  const int* mcon_vdof;
+  const double* mcon_coef;
+  int nrhs;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const MatvecTask tk = tasks[blk];
+    const ProbDev P = V.probs[tk.prob];
+    const SubDev S = V.subs[P.sub];
+    const int npk = V.np;
+    const int* pv = V.pos_of_vdof + P.pv_off;
+    for (int r = 0; r < nrhs; ++r) {
+      const int64_t base = P.vec_off * nrhs + (int64_t)r * P.n;
+      const double* z = Z + base;
+      for (int pos = tk.start + ex.tid; pos < tk.start + tk.count; pos += ex.nt) {
+        const int dt = V.dtype[P.pos_off + pos], src = V.dsrc[P.pos_off + pos];
+        double acc = 0.0;
+        if (dt == DT_VEL) {
+          const int* vp = V.vadj_ptr + S.vadj_ptr_off;
+          for (int q = vp[src]; q < vp[src + 1]; ++q) {
+            const int le = V.vadj[S.vadj_off + 2 * q], a = V.vadj[S.vadj_off + 2 * q + 1];
+            const int e = V.sub_elems[S.elem_off + le];
+            const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+            const int* ep = V.elpos + P.elpos_off + V.elptr[P.elptr_off + le];
+            const double* Ae = V.A + V.offK2[e];
+            const double* Be = V.B + (int64_t)npk * V.offK[e];
+            for (int b = 0; b < nK + npk; ++b) {
+              const int x = ep[b];
+              if (x < 0) continue;
+              const double v = b < nK ? Ae[(int64_t)a * nK + b] : Be[(int64_t)(b - nK) * nK + a];
+              acc += v * z[x];
+            }
+          }
+          if (P.kind == PK_NEUMANN) {
+            const int* cp = V.vcon_ptr + S.vcon_ptr_off;
+            for (int q = cp[src]; q < cp[src + 1]; ++q)
+              acc += V.vcon_coef[S.vcon_off + q] * z[P.mult0 + V.vcon_id[S.vcon_off + q]];
+          }
+        } else if (dt == DT_PRESS) {
+          const int le = src / npk, a = src % npk;
+          const int e = V.sub_elems[S.elem_off + le];
+          const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+          const int* ep = V.elpos + P.elpos_off + V.elptr[P.elptr_off + le];
+          const double* Be = V.B + (int64_t)npk * V.offK[e];
+          for (int b = 0; b < nK; ++b) {
+            const int x = ep[b];
+            if (x >= 0) acc += Be[(int64_t)a * nK + b] * z[x];
+          }
+        } else if (dt == DT_MULT) {
+          const int* mp = mcon_ptr + S.mcon_ptr_off;
+          for (int q = mp[src]; q < mp[src + 1]; ++q)
+            acc += mcon_coef[S.mcon_off + q] * z[pv[mcon_vdof[S.mcon_off + q]]];
+        }
+        R[base + pos] = Bv[base + pos] - acc;
+      }
     }
   }
 };

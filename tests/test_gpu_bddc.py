@@ -113,3 +113,24 @@ def test_full_size_benchmark_case_properties(pkg):
     assert torch.linalg.norm(r).item() <= 1e-7 * torch.linalg.norm(rhs).item()
     div = r[g.n_vel_free:]            # pressure rows of the residual = -B u
     assert torch.abs(div).max().item() <= 1e-7 * torch.abs(rhs).max().item()
+
+
+@pytest.mark.parametrize("name", ["tri6_k2", "tri4_k3", "sinker8"])
+def test_fp32_local_with_refinement(pkg, name):
+    """FP32 local factors with one FP64-residual refinement per local solve:
+    rtol 1e-8 reached, iterations within +10% of the FP64 GPU form, relative
+    error <= 1e-7 against the FP64 oracle PCG solution."""
+    import torch
+    cfg, g, rhs, S, F = _setup(pkg, name)
+    b64 = pkg.Bddc(g, cfg["part"])
+    u64 = torch.zeros_like(rhs)
+    r64 = b64.solve(rhs, u64, rtol=1e-8, maxit=400)
+    b32 = pkg.Bddc(g, cfg["part"], precision=1)
+    u32 = torch.zeros_like(rhs)
+    r32 = b32.solve(rhs, u32, rtol=1e-8, maxit=400)
+    assert r64["status"] == 0 and r32["status"] == 0
+    assert r32["iters"] <= int(np.ceil(1.1 * r64["iters"]))
+    ro = BDDC(S, cfg["part"], scaling="deluxe").pcg(F, rtol=1e-8)
+    nvf = len(S.dm.free)
+    x = u32.cpu().numpy()
+    assert np.linalg.norm(x[:nvf] - ro["x"][:nvf]) <= 1e-7 * np.linalg.norm(ro["x"][:nvf])
