@@ -148,7 +148,7 @@ typedef struct {
   double adaptive_threshold;/* unused: 0                                       */
   int32_t nd_leaf;          /* elements per nested-dissection leaf (0: 4)      */
   int32_t use_graph;        /* unused: 0                                       */
-  int32_t refine;           /* unused: 0                                       */
+  int32_t refine;           /* refinement steps of the FP32 local solves (0: 1)  */
   int32_t reserved[8];
 } bddc_options;
 

@@ -191,13 +191,14 @@ class VemSystem:
 class Bddc:
     """bddc_setup + bddc_apply + pcg_solve over a VemSystem."""
 
-    def __init__(self, system, part, constraints=15, scaling=1, leaf=0, precision=0):
+    def __init__(self, system, part, constraints=15, scaling=1, leaf=0, precision=0, refine=0):
         L = lib()
         self.sys = system
         part = np.ascontiguousarray(part, dtype=np.int32)
         opts = BddcOptions()
         opts.nd_leaf = int(leaf)
         opts.precision = int(precision)
+        opts.refine = int(refine)
         h = ctypes.c_void_p()
         _check(L.bddc_setup(system.h, part.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(constraints),
                             int(scaling), ctypes.byref(opts), ctypes.byref(h)))

@@ -49,7 +49,8 @@ struct bddc {
   vb::BddcHost H;
   cudaStream_t stream = 0;
   vb::SetupOptions opt;
-  int prec = 0;                  // 0 FP64 local factors; 1 FP32 + one refinement; 2 FP32 plain
+  int prec = 0;                  // 0 FP64 local factors; 1 FP32 + refinement; 2 FP32 plain
+  int refine = 1;                // refinement steps of the FP32-local solves
   // device copies of the structure
   vb::DBuf<vb::NodeDev> d_nodes;
   vb::DBuf<int> d_mcon_ptr, d_mcon_vdof;
@@ -1050,10 +1051,12 @@ static void solve_batch(bddc* b, Batch& B, const BddcView& V, double* X, double*
   if ((int64_t)B.XB.n < n) { B.XB.alloc(std::max<int64_t>(n, 1)); B.XR.alloc(std::max<int64_t>(n, 1)); }
   VB_CUDA(cudaMemcpyAsync(B.XB.p, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   sweep_batch<float>(b, B, V, B.F32.p, X, UV, nrhs);
-  launch(KProbResidual{V, B.d_mtask.p, B.XB.p, X, B.XR.p, b->d_mcon_ptr.p, b->d_mcon_vdof.p, b->d_mcon_coef.p,
-                       nrhs}, (int64_t)B.h_mtask.size(), 128, 0, st);
-  sweep_batch<float>(b, B, V, B.F32.p, B.XR.p, UV, nrhs);
-  launch(KAxpyN{B.XR.p, X, n}, (n + 255) / 256, 256, 0, st);
+  for (int it = 0; it < b->refine; ++it) {
+    launch(KProbResidual{V, B.d_mtask.p, B.XB.p, X, B.XR.p, b->d_mcon_ptr.p, b->d_mcon_vdof.p, b->d_mcon_coef.p,
+                         nrhs}, (int64_t)B.h_mtask.size(), 128, 0, st);
+    sweep_batch<float>(b, B, V, B.F32.p, B.XR.p, UV, nrhs);
+    launch(KAxpyN{B.XR.p, X, n}, (n + 255) / 256, 256, 0, st);
+  }
 }
 
 static int max_macro_n(bddc* b) {
@@ -1174,6 +1177,8 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     if (opts) {
       VB_CHECK(opts->precision >= 0 && opts->precision <= 2, VEM_EINVAL, "bddc_options.precision must be 0, 1 or 2");
       b->prec = opts->precision;
+      VB_CHECK(opts->refine >= 0 && opts->refine <= 4, VEM_EINVAL, "bddc_options.refine must be 0..4");
+      if (opts->refine > 0) b->refine = opts->refine;
     }
     cudaStream_t st = b->stream;
     BddcHost& H = b->H;

@@ -117,15 +117,17 @@ def test_full_size_benchmark_case_properties(pkg):
 
 @pytest.mark.parametrize("name", ["tri6_k2", "tri4_k3", "sinker8"])
 def test_fp32_local_with_refinement(pkg, name):
-    """FP32 local factors with one FP64-residual refinement per local solve:
+    """FP32 local factors with FP64-residual refinement of every local solve:
     rtol 1e-8 reached, iterations within +10% of the FP64 GPU form, relative
-    error <= 1e-7 against the FP64 oracle PCG solution."""
+    error <= 1e-7 against the FP64 oracle PCG solution.  One refinement step
+    at constant viscosity; two at viscosity contrast 1e4, where one step
+    leaves the local solves too inexact (kappa doubles)."""
     import torch
     cfg, g, rhs, S, F = _setup(pkg, name)
     b64 = pkg.Bddc(g, cfg["part"])
     u64 = torch.zeros_like(rhs)
     r64 = b64.solve(rhs, u64, rtol=1e-8, maxit=400)
-    b32 = pkg.Bddc(g, cfg["part"], precision=1)
+    b32 = pkg.Bddc(g, cfg["part"], precision=1, refine=2 if np.ptp(cfg["nu"]) > 0 else 1)
     u32 = torch.zeros_like(rhs)
     r32 = b32.solve(rhs, u32, rtol=1e-8, maxit=400)
     assert r64["status"] == 0 and r32["status"] == 0
