@@ -275,6 +275,27 @@ def run_ours(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Small driver for profilers: one setup, then `napply` preconditioner
+    applies (FP64 or FP32-local local factors) on the named workload."""
+    import numpy as np
+    import torch
+    import paper_2304_09770_gb300 as pkg
+    from synth import make_config
+    cfg = make_config(args.workload)
+    g = pkg.VemSystem(cfg["mesh"], cfg["k"], cfg["nu"])
+    bd = pkg.Bddc(g, cfg["part"], precision=args.precision)
+    r = torch.randn(g.n, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    torch.cuda.synchronize()
+    l0 = pkg.kernel_launches()
+    for _ in range(args.napply):
+        bd.apply(r, z)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "setup_launches": l0,
+                      "apply_launches": (pkg.kernel_launches() - l0) // args.napply}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,7 +303,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["apply"], default=None,
+                    help="profiler driver: setup once, then --napply preconditioner applies")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--napply", type=int, default=3)
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

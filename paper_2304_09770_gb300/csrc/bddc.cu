@@ -17,6 +17,12 @@
 
 namespace vb {
 void spmv(vem_system* s, const double* x, double* y, cudaStream_t st);
+struct DelTask {
+  int macro, k0;
+};
+struct IfTask {
+  int sub, l0;
+};
 
 // one batch of problems (all Dirichlet, all Neumann or all deluxe ones)
 struct Batch {
@@ -75,7 +81,13 @@ struct bddc {
   int64_t nphi = 0;
   vb::DBuf<int> d_cg_ptr, d_cg_sub, d_cg_loc;   // coarse row -> (subdomain, local coordinate)
   // apply workspaces
-  vb::DBuf<double> XD, XN, UVD, UVN, rC, uC, cloc, wloc, dwork, y, part;
+  vb::DBuf<double> XD, XN, UVD, UVN, rC, uC, cloc, wloc, dwork, y, part, dtw, wd1, avgd;
+  std::vector<vb::DelTask> h_dtT, h_dtN;
+  std::vector<vb::IfTask> h_ift;
+  vb::DBuf<vb::DelTask> d_dtT, d_dtN;
+  vb::DBuf<vb::IfTask> d_ift;
+  int NC = 1;
+  int max_nd = 1;
   int64_t ndual = 0, niface_tot = 0;
   // PCG vectors
   vb::DBuf<double> r, z, p, Ap, scal;
@@ -570,6 +582,30 @@ struct KGJElim {
 
 // ----------------------------------------------------------------- apply
 
+// c = H^T c and c = H c with the entity's reflectors, block-parallel
+VB_HD inline void hh_T_par(const KExec& ex, const BddcView& V, const MacroDev& G, double* c, double* red) {
+  if (G.hv_off < 0) return;
+  for (int q = 0; q < G.r; ++q) {
+    const double* h = V.hv + G.hv_off + (int64_t)q * G.n;
+    double d = 0.0;
+    for (int i = ex.tid; i < G.n; i += ex.nt) d += h[i] * c[i];
+    d = block_sum(ex, d, red) * V.tau[G.tau_off + q];
+    for (int i = ex.tid; i < G.n; i += ex.nt) c[i] -= d * h[i];
+    ex.sync();
+  }
+}
+VB_HD inline void hh_par(const KExec& ex, const BddcView& V, const MacroDev& G, double* c, double* red) {
+  if (G.hv_off < 0) return;
+  for (int q = G.r - 1; q >= 0; --q) {
+    const double* h = V.hv + G.hv_off + (int64_t)q * G.n;
+    double d = 0.0;
+    for (int i = ex.tid; i < G.n; i += ex.nt) d += h[i] * c[i];
+    d = block_sum(ex, d, red) * V.tau[G.tau_off + q];
+    for (int i = ex.tid; i < G.n; i += ex.nt) c[i] -= d * h[i];
+    ex.sync();
+  }
+}
+
 // (1) r_G -> c = H^T r_G: primal part to the coarse rhs, dual part kept
 struct KRestrict {
   BddcView V;
@@ -580,17 +616,15 @@ struct KRestrict {
   VB_HD void operator()(const KExec& ex, int g) const {
     const MacroDev G = V.macros[g];
     double* c = ex.smem;
+    double* red = ex.smem + G.n;
     double ss = 0.0;
     for (int a = ex.tid; a < G.n; a += ex.nt) {
       c[a] = r[V.mdofs[G.dofs_off + a]];
       ss += c[a] * c[a];
     }
-    ss = block_sum(ex, ss, ex.smem + G.n);
-    if (ex.tid == 0) {
-      part[g] = ss;
-      hh_T_inplace(V, G, c);
-    }
-    ex.sync();
+    ss = block_sum(ex, ss, red);
+    if (ex.tid == 0) part[g] = ss;
+    hh_T_par(ex, V, G, c, red);
     for (int a = ex.tid; a < G.n; a += ex.nt) {
       if (a < G.r) rC[G.coarse0 + a] = c[a];
       else dwork[G.dual_off + a - G.r] = c[a];
@@ -617,17 +651,83 @@ struct KRestrictP0 {
   }
 };
 
+// deluxe GEMV tasks (DelTask): (face, first output index)
+
+// out = D^T x on the dual coordinates of deluxe faces: one warp per output,
+// lanes along the contiguous column of D (column-major storage)
+struct KDeluxeT {
+  BddcView V;
+  const DelTask* tasks;
+  const double* x;
+  double* out;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const DelTask tk = tasks[blk];
+    const MacroDev G = V.macros[tk.macro];
+    const int nd = G.ndual;
+    const double* xs = x + G.dual_off;
+    double* xv = ex.smem;
+    for (int i = ex.tid; i < nd; i += ex.nt) xv[i] = xs[i];
+    ex.sync();
+    const int ws = ex.nt >= 32 ? 32 : 1;
+    const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
+    const int k1 = tk.k0 + 64 < nd ? tk.k0 + 64 : nd;
+    for (int k = tk.k0 + w; k < k1; k += nw) {
+      const double* Dk = V.deluxe + G.deluxe_off + (int64_t)k * nd;
+      double a0 = 0.0, a1 = 0.0;
+      int i = lane;
+      for (; i + ws < nd; i += 2 * ws) { a0 += Dk[i] * xv[i]; a1 += Dk[i + ws] * xv[i + ws]; }
+      if (i < nd) a0 += Dk[i] * xv[i];
+      const double acc = warp_sum(a0 + a1);
+      if (lane == 0) out[G.dual_off + k] = acc;
+    }
+  }
+};
+
+// avg = D (w0 - w1) + w1 on deluxe faces: one thread per output, rows of
+// the column-major D read contiguously across threads
+struct KDeluxeN {
+  BddcView V;
+  const DelTask* tasks;
+  const double* w0;
+  const double* w1;
+  double* avg;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const DelTask tk = tasks[blk];
+    const MacroDev G = V.macros[tk.macro];
+    const int nd = G.ndual;
+    double* dv = ex.smem;
+    for (int i = ex.tid; i < nd; i += ex.nt) dv[i] = w0[G.dual_off + i] - w1[G.dual_off + i];
+    ex.sync();
+    const double* D = V.deluxe + G.deluxe_off;
+    for (int k = tk.k0 + ex.tid; k < tk.k0 + 256 && k < nd; k += ex.nt) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int i = 0;
+      for (; i + 3 < nd; i += 4) {
+        a0 += D[(int64_t)i * nd + k] * dv[i];
+        a1 += D[(int64_t)(i + 1) * nd + k] * dv[i + 1];
+        a2 += D[(int64_t)(i + 2) * nd + k] * dv[i + 2];
+        a3 += D[(int64_t)(i + 3) * nd + k] * dv[i + 3];
+      }
+      for (; i < nd; ++i) a0 += D[(int64_t)i * nd + k] * dv[i];
+      avg[G.dual_off + k] = (a0 + a1) + (a2 + a3) + w1[G.dual_off + k];
+    }
+  }
+};
+
 // (3) scaled dual residual of each sharing subdomain, back to the original
-// basis, written into its Neumann right-hand side
+// basis, written into its Neumann right-hand side (dt = D^T r on deluxe faces)
 struct KScaleToNeumann {
   BddcView V;
   const double* dwork;
+  const double* dt;
   double* XN;
   VB_HD void operator()(const KExec& ex, int g) const {
     const MacroDev G = V.macros[g];
     if (G.ndual == 0) return;
     double* c = ex.smem;
+    double* red = ex.smem + G.n;
     const double* dr = dwork + G.dual_off;
+    const double* dtr = dt + G.dual_off;
     for (int si = 0; si < G.nshare; ++si) {
       const int s = V.share[G.share_off + si];
       const SubDev S = V.subs[s];
@@ -636,21 +736,13 @@ struct KScaleToNeumann {
         double v = 0.0;
         if (a >= G.r) {
           const int k = a - G.r;
-          if (G.deluxe_off >= 0) {
-            // D^T r for the first side, r - D^T r for the second
-            const double* D = V.deluxe + G.deluxe_off + (int64_t)k * G.ndual;
-            double dt = 0.0;
-            for (int i = 0; i < G.ndual; ++i) dt += D[i] * dr[i];
-            v = si == 0 ? dt : dr[k] - dt;
-          } else {
-            v = dr[k] / G.nshare;
-          }
+          if (G.deluxe_off >= 0) v = si == 0 ? dtr[k] : dr[k] - dtr[k];
+          else v = dr[k] / G.nshare;
         }
         c[a] = v;
       }
       ex.sync();
-      if (ex.tid == 0) hh_inplace(V, G, c);
-      ex.sync();
+      hh_par(ex, V, G, c, red);
       const int* gp = V.gpos + G.gpos_off + (int64_t)si * G.n;
       for (int a = ex.tid; a < G.n; a += ex.nt) XN[P.vec_off + gp[a]] = c[a];
       ex.sync();
@@ -658,25 +750,31 @@ struct KScaleToNeumann {
   }
 };
 
-// (4) local coarse rhs contributions Phi_Gamma^T g
+// (4) local coarse rhs contributions Phi_Gamma^T g: one warp per coarse
+// column, lanes along the interface rows; tasks of 8 columns
 struct KCoarseLocal {
   BddcView V;
   const double* PG;
   const double* XN;
   double* cloc;
   int NC;
-  VB_HD void operator()(const KExec& ex, int i) const {
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int nblk_per = (NC + 7) / 8;
+    const int i = blk / nblk_per, c0 = (blk % nblk_per) * 8;
     const SubDev S = V.subs[i];
     const ProbDev P = V.probs[S.neu];
     const int* pv = V.pos_of_vdof + P.pv_off;
-    for (int c = ex.tid; c < S.ncl; c += ex.nt) {
+    const int ws = ex.nt >= 32 ? 32 : 1;
+    const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
+    for (int c = c0 + w; c < c0 + 8 && c < S.ncl; c += nw) {
       const double* ph = PG + S.phi_off + (int64_t)c * S.niface;
       double acc = 0.0;
-      for (int l = 0; l < S.niface; ++l) {
+      for (int l = lane; l < S.niface; l += ws) {
         const int pos = pv[V.iface[S.iface_off + l]];
         if (pos >= 0) acc += ph[l] * XN[P.vec_off + pos];
       }
-      cloc[(int64_t)i * NC + c] = acc;
+      acc = warp_sum(acc);
+      if (lane == 0) cloc[(int64_t)i * NC + c] = acc;
     }
   }
 };
@@ -715,68 +813,77 @@ struct KCoarseSolve {
   }
 };
 
-// (8) w_Gamma = z_Gamma + Phi_Gamma u_C on the interface of each subdomain
+// (8) w_Gamma = z_Gamma + Phi_Gamma u_C: tasks (subdomain, 256 interface rows)
 struct KProlongLocal {
   BddcView V;
+  const IfTask* tasks;
   const double* PG;
   const double* XN;
   const double* uC;
   double* wloc;
-  VB_HD void operator()(const KExec& ex, int i) const {
-    const SubDev S = V.subs[i];
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const IfTask tk = tasks[blk];
+    const SubDev S = V.subs[tk.sub];
     const ProbDev P = V.probs[S.neu];
     const int* pv = V.pos_of_vdof + P.pv_off;
     const int64_t* g = V.coarse + S.coarse_off;
-    for (int l = ex.tid; l < S.niface; l += ex.nt) {
+    double* uc = ex.smem;
+    for (int c = ex.tid; c < S.ncl; c += ex.nt) uc[c] = uC[g[c]];
+    ex.sync();
+    for (int l = tk.l0 + ex.tid; l < tk.l0 + 256 && l < S.niface; l += ex.nt) {
       const int pos = pv[V.iface[S.iface_off + l]];
       double acc = pos >= 0 ? XN[P.vec_off + pos] : 0.0;
-      for (int c = 0; c < S.ncl; ++c) acc += PG[S.phi_off + (int64_t)c * S.niface + l] * uC[g[c]];
+      for (int c = 0; c < S.ncl; ++c) acc += PG[S.phi_off + (int64_t)c * S.niface + l] * uc[c];
       wloc[S.iface_off + l] = acc;
     }
   }
 };
 
-// (9) averaging R~_D^T: primal coordinates from u_C, dual ones scaled and
-// summed, back to the original basis
-struct KAverage {
+// (9a) dual coordinates of each side's interface values: first side into
+// w0, second into w1 (deluxe faces); the counting average into w0 otherwise
+struct KAverageDual {
   BddcView V;
   const double* wloc;
+  double* w0;
+  double* w1;
+  VB_HD void operator()(const KExec& ex, int g) const {
+    const MacroDev G = V.macros[g];
+    if (G.ndual == 0) return;
+    double* w = ex.smem;
+    double* red = ex.smem + G.n;
+    for (int k = ex.tid; k < G.ndual; k += ex.nt) w0[G.dual_off + k] = 0.0;
+    ex.sync();
+    for (int si = 0; si < G.nshare; ++si) {
+      const SubDev S = V.subs[V.share[G.share_off + si]];
+      const int* gi = V.gif + G.gif_off + (int64_t)si * G.n;
+      for (int a = ex.tid; a < G.n; a += ex.nt) w[a] = wloc[S.iface_off + gi[a]];
+      ex.sync();
+      hh_T_par(ex, V, G, w, red);
+      for (int k = ex.tid; k < G.ndual; k += ex.nt) {
+        const double v = w[G.r + k];
+        if (G.deluxe_off >= 0) (si == 0 ? w0 : w1)[G.dual_off + k] = v;
+        else w0[G.dual_off + k] += v / G.nshare;
+      }
+      ex.sync();
+    }
+  }
+};
+
+// (9b) z_G = H [u_C primal; averaged dual] scattered to the system vector
+struct KAverageOut {
+  BddcView V;
+  const double* avg_deluxe;
+  const double* avg_count;
   const double* uC;
   double* z;
   VB_HD void operator()(const KExec& ex, int g) const {
     const MacroDev G = V.macros[g];
-    double* c = ex.smem;              // result coordinates
-    double* w = ex.smem + G.n;        // one side's values
-    double* w0 = ex.smem + 2 * G.n;   // first side's dual coordinates
-    for (int a = ex.tid; a < G.n; a += ex.nt) c[a] = a < G.r ? uC[G.coarse0 + a] : 0.0;
+    double* c = ex.smem;
+    double* red = ex.smem + G.n;
+    const double* av = (G.deluxe_off >= 0 ? avg_deluxe : avg_count) + G.dual_off;
+    for (int a = ex.tid; a < G.n; a += ex.nt) c[a] = a < G.r ? uC[G.coarse0 + a] : av[a - G.r];
     ex.sync();
-    for (int si = 0; si < G.nshare && G.ndual > 0; ++si) {
-      const int s = V.share[G.share_off + si];
-      const SubDev S = V.subs[s];
-      const int* gi = V.gif + G.gif_off + (int64_t)si * G.n;
-      for (int a = ex.tid; a < G.n; a += ex.nt) w[a] = wloc[S.iface_off + gi[a]];
-      ex.sync();
-      if (ex.tid == 0) hh_T_inplace(V, G, w);
-      ex.sync();
-      if (G.deluxe_off >= 0) {
-        if (si == 0) {
-          for (int a = ex.tid; a < G.ndual; a += ex.nt) w0[a] = w[G.r + a];
-        } else {
-          // D (w0 - w1) + w1
-          for (int k = ex.tid; k < G.ndual; k += ex.nt) {
-            double acc = 0.0;
-            for (int i = 0; i < G.ndual; ++i)
-              acc += V.deluxe[G.deluxe_off + (int64_t)i * G.ndual + k] * (w0[i] - w[G.r + i]);
-            c[G.r + k] = acc + w[G.r + k];
-          }
-        }
-      } else {
-        for (int k = ex.tid; k < G.ndual; k += ex.nt) c[G.r + k] += w[G.r + k] / G.nshare;
-      }
-      ex.sync();
-    }
-    if (ex.tid == 0) hh_inplace(V, G, c);
-    ex.sync();
+    hh_par(ex, V, G, c, red);
     for (int a = ex.tid; a < G.n; a += ex.nt) z[V.mdofs[G.dofs_off + a]] = c[a];
   }
 };
@@ -1007,7 +1114,7 @@ static void sweep_batch(bddc* b, Batch& B, const BddcView& V, const T* Fp, doubl
     B.FV.alloc(std::max<int64_t>(B.nfv * nrhs, 1));
     B.fv_nrhs = nrhs;
   }
-  const size_t sm = sizeof(double) * (B.maxnf + 8);
+  const size_t sm = sizeof(double) * (RB * (B.maxnf + 8));
   const int64_t* fvo = b->d_fvoff.p;
   for (int h = 0; h <= B.maxh; ++h) {
     const int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
@@ -1073,21 +1180,24 @@ static void apply_bddc(bddc* b, const double* r, double* z) {
   const int nmac = (int)b->h_macros.size();
   const int N = b->H.N;
   const size_t msm = sizeof(double) * (3 * max_macro_n(b) + 256 + 8);
-  const int NC = 1;
+  const size_t dsm = sizeof(double) * (b->max_nd + 8);
+  const int NC = b->NC;
   b->XN.zero(st);
   launch(KRestrict{V, r, b->rC.p, b->dwork.p, b->part.p}, nmac, 256, msm, st);
   launch(KRestrictP0{V, r, b->rC.p, b->part.p, nmac}, N, 256, sizeof(double) * 256, st);
-  launch(KScaleToNeumann{V, b->dwork.p, b->XN.p}, nmac, 256, msm, st);
-  int ncl_max = 1;
-  for (auto& S : b->h_subs) ncl_max = std::max(ncl_max, S.ncl);
-  launch(KCoarseLocal{V, b->d_phi.p, b->XN.p, b->cloc.p, ncl_max}, N, 128, 0, st);
-  launch(KCoarseGather{V, b->d_cg_ptr.p, b->d_cg_sub.p, b->d_cg_loc.p, b->cloc.p, b->rC.p, ncl_max},
+  launch(KDeluxeT{V, b->d_dtT.p, b->dwork.p, b->dtw.p}, (int64_t)b->h_dtT.size(), 256, dsm, st);
+  launch(KScaleToNeumann{V, b->dwork.p, b->dtw.p, b->XN.p}, nmac, 256, msm, st);
+  launch(KCoarseLocal{V, b->d_phi.p, b->XN.p, b->cloc.p, NC}, (int64_t)N * ((NC + 7) / 8), 256, 0, st);
+  launch(KCoarseGather{V, b->d_cg_ptr.p, b->d_cg_sub.p, b->d_cg_loc.p, b->cloc.p, b->rC.p, NC},
          (b->nc + 1 + 255) / 256, 256, 0, st);
   launch(KCoarseSolve{b->d_Kinv.p, b->rC.p, b->uC.p, b->nc + 1}, b->nc + 1, 256, sizeof(double) * 256, st);
-  solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, NC);
-  launch(KProlongLocal{V, b->d_phi.p, b->XN.p, b->uC.p, b->wloc.p}, N, 128, 0, st);
+  solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, 1);
+  launch(KProlongLocal{V, b->d_ift.p, b->d_phi.p, b->XN.p, b->uC.p, b->wloc.p}, (int64_t)b->h_ift.size(), 256,
+         sizeof(double) * (NC + 8), st);
+  launch(KAverageDual{V, b->wloc.p, b->dwork.p, b->wd1.p}, nmac, 256, msm, st);
+  launch(KDeluxeN{V, b->d_dtN.p, b->dwork.p, b->wd1.p, b->avgd.p}, (int64_t)b->h_dtN.size(), 256, dsm, st);
   VB_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * s->n, st));
-  launch(KAverage{V, b->wloc.p, b->uC.p, z}, nmac, 256, msm, st);
+  launch(KAverageOut{V, b->avgd.p, b->dwork.p, b->uC.p, z}, nmac, 256, msm, st);
   spmv(s, z, b->y.p, st);
   launch(KDirRhs{V, b->y.p, -1.0, b->XD.p}, N, 256, sizeof(double) * 256, st);
   solve_batch(b, b->bd, V, b->XD.p, b->UVD.p, 1);
@@ -1657,6 +1767,25 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     for (auto& D : b->h_subs) nif += D.niface;
     b->wloc.alloc(std::max<int64_t>(nif, 1));
     b->dwork.alloc(std::max<int64_t>(b->ndual, 1));
+    b->dtw.alloc(std::max<int64_t>(b->ndual, 1));
+    b->wd1.alloc(std::max<int64_t>(b->ndual, 1));
+    b->avgd.alloc(std::max<int64_t>(b->ndual, 1));
+    b->NC = NC;
+    b->h_dtT.clear();
+    b->h_dtN.clear();
+    for (size_t g = 0; g < b->h_macros.size(); ++g) {
+      const MacroDev& G = b->h_macros[g];
+      if (G.deluxe_off < 0) continue;
+      b->max_nd = std::max(b->max_nd, G.ndual);
+      for (int k0 = 0; k0 < G.ndual; k0 += 64) b->h_dtT.push_back({(int)g, k0});
+      for (int k0 = 0; k0 < G.ndual; k0 += 256) b->h_dtN.push_back({(int)g, k0});
+    }
+    b->h_ift.clear();
+    for (int i = 0; i < N; ++i)
+      for (int l0 = 0; l0 < b->h_subs[i].niface; l0 += 256) b->h_ift.push_back({i, l0});
+    upload_vec(b->d_dtT, b->h_dtT, st);
+    upload_vec(b->d_dtN, b->h_dtN, st);
+    upload_vec(b->d_ift, b->h_ift, st);
     b->y.alloc(s->n);
     b->part.alloc(b->h_macros.size() + N + 1024 + 8);
     b->r.alloc(s->n);

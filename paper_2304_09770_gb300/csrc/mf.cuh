@@ -273,6 +273,10 @@ struct KFwdGather {
   }
 };
 
+// Right-hand sides are processed in groups of RB: every factor entry read
+// from memory serves RB accumulators.
+constexpr int RB = 4;
+
 // forward (2): y_p = L11^{-1} f_p for a task of pivot rows (unit lower)
 template <class T>
 struct KFwdPivots {
@@ -287,22 +291,30 @@ struct KFwdPivots {
     const SolveTask tk = tasks[blk];
     const NodeDev N = V.nodes[tk.node];
     const ProbDev P = V.probs[N.prob];
-    const int np = N.np, nf = N.np + N.nb;
+    const int nf = N.np + N.nb;
     const T* pan = F + N.panel_off;
-    const int kmax = tk.start + tk.count;   // columns needed: k < kmax
-    double* fs = ex.smem;
-    for (int r = 0; r < nrhs; ++r) {
-      const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)r * nf;
-      for (int k = ex.tid; k < kmax; k += ex.nt) fs[k] = f[k];
+    const int kmax = tk.start + tk.count;
+    double* fs = ex.smem;   // [RB][kmax]
+    for (int r0 = 0; r0 < nrhs; r0 += RB) {
+      const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
+      for (int q = ex.tid; q < RB * kmax; q += ex.nt) {
+        const int r = q / kmax, k = q % kmax;
+        fs[q] = r < nr ? FV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + k] : 0.0;
+      }
       ex.sync();
       for (int i = tk.start + ex.tid; i < kmax; i += ex.nt) {
-        double acc = fs[i];
-        for (int k = 0; k < i; ++k) acc += (double)pan[(int64_t)k * nf + i] * fs[k];
-        X[P.vec_off * nrhs + (int64_t)r * P.n + N.p0 + i] = acc;
+        double acc[RB];
+        for (int r = 0; r < RB; ++r) acc[r] = fs[r * kmax + i];
+        const T* col = pan + i;
+#pragma unroll 4
+        for (int k = 0; k < i; ++k) {
+          const double v = (double)col[(int64_t)k * nf];
+          for (int r = 0; r < RB; ++r) acc[r] += v * fs[r * kmax + k];
+        }
+        for (int r = 0; r < nr; ++r) X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + i] = acc[r];
       }
       ex.sync();
     }
-    (void)np;
   }
 };
 
@@ -323,17 +335,27 @@ struct KFwdBorder {
     const ProbDev P = V.probs[N.prob];
     const int np = N.np, nf = N.np + N.nb;
     const T* pan = F + N.panel_off;
-    double* ys = ex.smem;
-    for (int r = 0; r < nrhs; ++r) {
-      const double* x = X + P.vec_off * nrhs + (int64_t)r * P.n + N.p0;
-      const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)r * nf;
-      for (int k = ex.tid; k < np; k += ex.nt) ys[k] = x[k];
+    double* ys = ex.smem;   // [RB][np]
+    for (int r0 = 0; r0 < nrhs; r0 += RB) {
+      const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
+      for (int q = ex.tid; q < RB * np; q += ex.nt) {
+        const int r = q / np, k = q % np;
+        ys[q] = r < nr ? X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + k] : 0.0;
+      }
       ex.sync();
-      double* u = UV + N.uvec_off * nrhs + (int64_t)r * N.nb;
       for (int i = tk.start + ex.tid; i < tk.start + tk.count; i += ex.nt) {
-        double acc = f[np + i];
-        for (int k = 0; k < np; ++k) acc -= (double)pan[(int64_t)k * nf + np + i] * ys[k];
-        u[i] = acc;
+        double acc[RB];
+        for (int r = 0; r < RB; ++r) acc[r] = 0.0;
+        const T* col = pan + np + i;
+#pragma unroll 4
+        for (int k = 0; k < np; ++k) {
+          const double v = (double)col[(int64_t)k * nf];
+          for (int r = 0; r < RB; ++r) acc[r] += v * ys[r * np + k];
+        }
+        for (int r = 0; r < nr; ++r) {
+          const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf;
+          UV[N.uvec_off * nrhs + (int64_t)(r0 + r) * N.nb + i] = f[np + i] - acc[r];
+        }
       }
       ex.sync();
     }
@@ -358,20 +380,32 @@ struct KBwdBorder {
     const int np = N.np, nb = N.nb, nf = np + nb;
     const T* pan = F + N.panel_off;
     const int* bord = V.border + N.border_off;
-    double* xb = ex.smem;
+    double* xb = ex.smem;   // [RB][nb]
     const int ws = ex.nt >= 32 ? 32 : 1;
     const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
-    for (int r = 0; r < nrhs; ++r) {
-      const double* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
-      for (int i = ex.tid; i < nb; i += ex.nt) xb[i] = x[bord[i]];
+    for (int r0 = 0; r0 < nrhs; r0 += RB) {
+      const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
+      for (int q = ex.tid; q < RB * nb; q += ex.nt) {
+        const int r = q / (nb > 0 ? nb : 1), i = q % (nb > 0 ? nb : 1);
+        xb[q] = r < nr ? X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + bord[i]] : 0.0;
+      }
       ex.sync();
-      double* tv = TV + fv_off[tk.node] * nrhs + (int64_t)r * nf;
       for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
         const T* cj = pan + (int64_t)j * nf + np;
-        double acc = 0.0;
-        for (int i = lane; i < nb; i += ws) acc += (double)cj[i] * xb[i];
-        acc = warp_sum(acc);
-        if (lane == 0) tv[j] = x[N.p0 + j] / (double)pan[(int64_t)j * nf + j] - acc;
+        double acc[RB];
+        for (int r = 0; r < RB; ++r) acc[r] = 0.0;
+#pragma unroll 4
+        for (int i = lane; i < nb; i += ws) {
+          const double v = (double)cj[i];
+          for (int r = 0; r < RB; ++r) acc[r] += v * xb[r * nb + i];
+        }
+        const double dj = (double)pan[(int64_t)j * nf + j];
+        for (int r = 0; r < nr; ++r) {
+          const double t = warp_sum(acc[r]);
+          if (lane == 0)
+            TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] =
+                X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] / dj - t;
+        }
       }
       ex.sync();
     }
@@ -394,19 +428,31 @@ struct KBwdPivots {
     const ProbDev P = V.probs[N.prob];
     const int np = N.np, nf = N.np + N.nb;
     const T* pan = F + N.panel_off;
-    double* ts = ex.smem;
+    const int L = np - tk.start;   // rows tk.start..np-1 staged
+    double* ts = ex.smem;          // [RB][L]
     const int ws = ex.nt >= 32 ? 32 : 1;
     const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
-    for (int r = 0; r < nrhs; ++r) {
-      const double* tv = TV + fv_off[tk.node] * nrhs + (int64_t)r * nf;
-      for (int i = tk.start + ex.tid; i < np; i += ex.nt) ts[i] = tv[i];
+    for (int r0 = 0; r0 < nrhs; r0 += RB) {
+      const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
+      for (int q = ex.tid; q < RB * L; q += ex.nt) {
+        const int r = q / L, i = q % L;
+        ts[q] = r < nr ? TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + tk.start + i] : 0.0;
+      }
       ex.sync();
       for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
         const T* cj = pan + (int64_t)j * nf;
-        double acc = 0.0;
-        for (int i = j + 1 + lane; i < np; i += ws) acc += (double)cj[i] * ts[i];
-        acc = warp_sum(acc);
-        if (lane == 0) X[P.vec_off * nrhs + (int64_t)r * P.n + N.p0 + j] = ts[j] + acc;
+        double acc[RB];
+        for (int r = 0; r < RB; ++r) acc[r] = 0.0;
+#pragma unroll 4
+        for (int i = j + 1 + lane; i < np; i += ws) {
+          const double v = (double)cj[i];
+          for (int r = 0; r < RB; ++r) acc[r] += v * ts[r * L + i - tk.start];
+        }
+        for (int r = 0; r < nr; ++r) {
+          const double t = warp_sum(acc[r]);
+          if (lane == 0)
+            X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] = ts[r * L + j - tk.start] + t;
+        }
       }
       ex.sync();
     }
