@@ -1107,8 +1107,8 @@ static void factor_batch(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status
   else factor_batch_t<float>(b, B, V, status, B.F32, B.U32);
 }
 
-template <class T>
-static void sweep_batch(bddc* b, Batch& B, const BddcView& V, const T* Fp, double* X, double* UV, int nrhs) {
+template <class T, int RB>
+static void sweep_batch_rb(bddc* b, Batch& B, const BddcView& V, const T* Fp, double* X, double* UV, int nrhs) {
   cudaStream_t st = b->stream;
   if (B.fv_nrhs < nrhs) {
     B.FV.alloc(std::max<int64_t>(B.nfv * nrhs, 1));
@@ -1121,14 +1121,20 @@ static void sweep_batch(bddc* b, Batch& B, const BddcView& V, const T* Fp, doubl
     const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
     const int nb_t = B.btask_ptr[h + 1] - B.btask_ptr[h];
     launch(KFwdGather{V, B.d_levels.p + B.level_ptr[h], X, UV, B.FV.p, fvo, nrhs}, cnt, 128, 0, st);
-    launch(KFwdPivots<T>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 128, sm, st);
-    launch(KFwdBorder<T>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 128, sm, st);
+    launch(KFwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 128, sm, st);
+    launch(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 128, sm, st);
   }
   for (int h = B.maxh; h >= 0; --h) {
     const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
-    launch(KBwdBorder<T>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, B.FV.p, fvo, nrhs}, np_t, 256, sm, st);
-    launch(KBwdPivots<T>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 256, sm, st);
+    launch(KBwdBorder<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, B.FV.p, fvo, nrhs}, np_t, 256, sm, st);
+    launch(KBwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 256, sm, st);
   }
+}
+
+template <class T>
+static void sweep_batch(bddc* b, Batch& B, const BddcView& V, const T* Fp, double* X, double* UV, int nrhs) {
+  if (nrhs >= 4) sweep_batch_rb<T, 4>(b, B, V, Fp, X, UV, nrhs);
+  else sweep_batch_rb<T, 1>(b, B, V, Fp, X, UV, nrhs);
 }
 
 struct KAxpyN {   // y += x over n entries

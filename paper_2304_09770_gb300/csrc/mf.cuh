@@ -273,12 +273,12 @@ struct KFwdGather {
   }
 };
 
-// Right-hand sides are processed in groups of RB: every factor entry read
-// from memory serves RB accumulators.
-constexpr int RB = 4;
+// Right-hand sides are processed in groups of RB (template argument): every
+// factor entry read from memory serves RB accumulators (RB = 1 for the
+// single right-hand side of the CG iteration, 4 for the coarse basis).
 
 // forward (2): y_p = L11^{-1} f_p for a task of pivot rows (unit lower)
-template <class T>
+template <class T, int RB>
 struct KFwdPivots {
   BddcView V;
   const SolveTask* tasks;
@@ -319,7 +319,7 @@ struct KFwdPivots {
 };
 
 // forward (3): update vector u = f_b - L21 y for a task of border rows
-template <class T>
+template <class T, int RB>
 struct KFwdBorder {
   BddcView V;
   const SolveTask* tasks;
@@ -364,7 +364,7 @@ struct KFwdBorder {
 
 // backward (1): t_j = y_j / d_j - sum_border L21[i][j] x_i for a task of
 // pivot columns (one warp per column)
-template <class T>
+template <class T, int RB>
 struct KBwdBorder {
   BddcView V;
   const SolveTask* tasks;
@@ -413,7 +413,7 @@ struct KBwdBorder {
 };
 
 // backward (2): x_p = L11^{-T} t for a task of pivot columns (warp per column)
-template <class T>
+template <class T, int RB>
 struct KBwdPivots {
   BddcView V;
   const SolveTask* tasks;
