@@ -41,9 +41,9 @@ struct Batch {
   DBuf<MatvecTask> d_mtask;
   int64_t nF = 0, nU = 0;
   int64_t nfv = 0;                        // sum of front sizes (front-vector store per rhs)
-  std::vector<int> ptask_ptr, btask_ptr;  // per level: pivot / border task ranges
-  std::vector<SolveTask> h_ptask, h_btask;
-  DBuf<SolveTask> d_ptask, d_btask;
+  std::vector<int> ptask_ptr, btask_ptr, fptask_ptr;   // per level: task ranges
+  std::vector<SolveTask> h_ptask, h_btask, h_fptask;  // pivot columns, border vectors, pivot-row vectors
+  DBuf<SolveTask> d_ptask, d_btask, d_fptask;
   DBuf<double> FV;
   int fv_nrhs = 0;
 };
@@ -439,7 +439,7 @@ struct KDeluxeFront {
     }
     for (int64_t idx = ex.tid; idx < (int64_t)nd * nd; idx += ex.nt) upd[idx] = 0.0;
     ex.sync();
-    front_ldlt<double>(ex, pan, upd, nd, nd, nullptr, status);
+    front_ldlt<double>(ex, pan, upd, nd, nd, nf, nullptr, status);
   }
 };
 
@@ -1023,8 +1023,12 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
     for (size_t k = 0; k < HP.nodes.size(); ++k) {
       int gid = b->h_probs[q].root - (int)HP.nodes.size() + 1 + (int)k;
       NodeDev& N = b->h_nodes[gid];
+      // panels 4-element aligned with a leading dimension that is a
+      // multiple of 4, so that 16-byte vector loads of columns are aligned
+      N.ld = ((N.np + N.nb + 3) / 4) * 4;
+      nF = ((nF + 3) / 4) * 4;
       N.panel_off = nF;
-      nF += (int64_t)(N.np + N.nb) * N.np;
+      nF += (int64_t)N.ld * N.np;
       N.upd_off = nU;
       nU += (int64_t)N.nb * N.nb;
       N.uvec_off = uv;
@@ -1047,8 +1051,11 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
   int64_t fv = 0;
   B.ptask_ptr.assign(B.maxh + 2, 0);
   B.btask_ptr.assign(B.maxh + 2, 0);
+  B.fptask_ptr.assign(B.maxh + 2, 0);
   B.h_ptask.clear();
   B.h_btask.clear();
+  B.h_fptask.clear();
+  const int W = b->prec == 0 ? 2 : 4;   // rows per 16-byte vector load
   for (int h = 0; h <= B.maxh; ++h) {
     for (int q = B.level_ptr[h]; q < B.level_ptr[h + 1]; ++q) {
       const int t = B.h_levels[q];
@@ -1056,10 +1063,15 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
       b->h_fvoff[t] = fv;
       fv += N.np + N.nb;
       for (int s0 = 0; s0 < N.np; s0 += TASK) B.h_ptask.push_back({t, s0, std::min(TASK, N.np - s0)});
-      for (int s0 = 0; s0 < N.nb; s0 += TASK) B.h_btask.push_back({t, s0, std::min(TASK, N.nb - s0)});
+      const int nvp = (N.np + W - 1) / W;
+      for (int s0 = 0; s0 < nvp; s0 += TASK) B.h_fptask.push_back({t, s0, std::min(TASK, nvp - s0)});
+      const int a0 = (N.np / W) * W;
+      const int nvb = N.nb > 0 ? (N.np + N.nb - a0 + W - 1) / W : 0;
+      for (int s0 = 0; s0 < nvb; s0 += TASK) B.h_btask.push_back({t, s0, std::min(TASK, nvb - s0)});
     }
     B.ptask_ptr[h + 1] = (int)B.h_ptask.size();
     B.btask_ptr[h + 1] = (int)B.h_btask.size();
+    B.fptask_ptr[h + 1] = (int)B.h_fptask.size();
   }
   B.nfv = fv;
   B.h_mtask.clear();
@@ -1088,6 +1100,7 @@ static void upload_levels(bddc* b, Batch& B) {
   upload_vec(B.d_levels, B.h_levels, b->stream);
   upload_vec(B.d_ptask, B.h_ptask, b->stream);
   upload_vec(B.d_btask, B.h_btask, b->stream);
+  upload_vec(B.d_fptask, B.h_fptask, b->stream);
   upload_vec(B.d_mtask, B.h_mtask, b->stream);
 }
 
@@ -1118,10 +1131,10 @@ static void sweep_batch_rb(bddc* b, Batch& B, const BddcView& V, const T* Fp, do
   const int64_t* fvo = b->d_fvoff.p;
   for (int h = 0; h <= B.maxh; ++h) {
     const int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
-    const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
+    const int fp_t = B.fptask_ptr[h + 1] - B.fptask_ptr[h];
     const int nb_t = B.btask_ptr[h + 1] - B.btask_ptr[h];
     launch(KFwdGather{V, B.d_levels.p + B.level_ptr[h], X, UV, B.FV.p, fvo, nrhs}, cnt, 128, 0, st);
-    launch(KFwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 128, sm, st);
+    launch(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, fp_t, 128, sm, st);
     launch(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 128, sm, st);
   }
   for (int h = B.maxh; h >= 0; --h) {

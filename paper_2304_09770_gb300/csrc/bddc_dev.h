@@ -6,7 +6,7 @@
 namespace vb {
 
 struct NodeDev {
-  int prob, p0, np, nb, parent, height, first_child, nchild, flags;
+  int prob, p0, np, nb, parent, height, first_child, nchild, flags, ld;
   int64_t border_off, panel_off, upd_off, rel_off, uvec_off;
 };
 

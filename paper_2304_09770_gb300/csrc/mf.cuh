@@ -31,7 +31,8 @@ VB_HD inline int front_index(const NodeDev& N, const int* bord, int x) {
 // null: all positive) gives the expected pivot sign per pivot (velocity
 // positive; pressure and multiplier negative); a violation sets status 3.
 template <class T>
-VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, const int* piv_type, int* status) {
+VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, int ld, const int* piv_type,
+                             int* status) {
     const int nf = np + nb;
     // blocked right-looking partial LDL^T: panels of NBK columns, then a
     // rank-NBK update of the trailing front in TT x TT tiles staged in
@@ -44,7 +45,7 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
       const int nbk = np - jb < NBK ? np - jb : NBK;
       for (int jj = 0; jj < nbk; ++jj) {
         const int j = jb + jj;
-        T* cj = pan + (int64_t)j * nf;
+        T* cj = pan + (int64_t)j * ld;
         const T dj = cj[j];
         if (ex.tid == 0) {
           const double sgn = (!piv_type || piv_type[j] == DT_VEL) ? 1.0 : -1.0;
@@ -55,7 +56,7 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
         for (int64_t idx = ex.tid; idx < (int64_t)nk * nr; idx += ex.nt) {
           const int kk = j + 1 + (int)(idx / nr), ii = j + 1 + (int)(idx % nr);
           if (ii < kk) continue;
-          pan[(int64_t)kk * nf + ii] -= cj[ii] * cj[kk] * inv;
+          pan[(int64_t)kk * ld + ii] -= cj[ii] * cj[kk] * inv;
         }
         ex.sync();
         for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) cj[i] *= inv;
@@ -63,7 +64,7 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
       }
       const int c0 = jb + nbk, m = nf - c0;
       if (m <= 0) continue;
-      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = pan[(int64_t)(jb + jj) * nf + jb + jj];
+      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = pan[(int64_t)(jb + jj) * ld + jb + jj];
       ex.sync();
       const int ntile = (m + TT - 1) / TT;
       for (int tk = 0; tk < ntile; ++tk)
@@ -71,8 +72,8 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
           const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
           for (int q = ex.tid; q < TT * NBK; q += ex.nt) {
             const int r = q % TT, c = q / TT;
-            sL[q] = (c < nbk && i0 + r < nf) ? pan[(int64_t)(jb + c) * nf + i0 + r] : (T)0;
-            sR[q] = (c < nbk && k0 + r < nf) ? pan[(int64_t)(jb + c) * nf + k0 + r] * sd[c] : (T)0;
+            sL[q] = (c < nbk && i0 + r < nf) ? pan[(int64_t)(jb + c) * ld + i0 + r] : (T)0;
+            sR[q] = (c < nbk && k0 + r < nf) ? pan[(int64_t)(jb + c) * ld + k0 + r] * sd[c] : (T)0;
           }
           ex.sync();
           for (int vt = ex.tid; vt < 256; vt += ex.nt) {
@@ -91,7 +92,7 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
               for (int a = 0; a < 4; ++a) {
                 const int i = i0 + tr + 16 * a;
                 if (i >= nf || i < k) continue;
-                if (k < np) pan[(int64_t)k * nf + i] -= acc[a][bb];
+                if (k < np) pan[(int64_t)k * ld + i] -= acc[a][bb];
                 else upd[(int64_t)(k - np) * nb + (i - np)] -= acc[a][bb];
               }
             }
@@ -104,12 +105,12 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, co
     // sweeps become matrix-vector products over independent rows/columns
     T* tmp = reinterpret_cast<T*>(ex.smem);
     for (int j = np - 2; j >= 0; --j) {
-      for (int k = j + 1 + ex.tid; k < np; k += ex.nt) tmp[k] = pan[(int64_t)j * nf + k];
+      for (int k = j + 1 + ex.tid; k < np; k += ex.nt) tmp[k] = pan[(int64_t)j * ld + k];
       ex.sync();
       for (int i = j + 1 + ex.tid; i < np; i += ex.nt) {
         T acc = tmp[i];
-        for (int k = j + 1; k < i; ++k) acc += pan[(int64_t)k * nf + i] * tmp[k];
-        pan[(int64_t)j * nf + i] = -acc;
+        for (int k = j + 1; k < i; ++k) acc += pan[(int64_t)k * ld + i] * tmp[k];
+        pan[(int64_t)j * ld + i] = -acc;
       }
       ex.sync();
     }
@@ -127,12 +128,12 @@ struct KFactor {
     const NodeDev N = V.nodes[t];
     const ProbDev P = V.probs[N.prob];
     const SubDev S = V.subs[P.sub];
-    const int np = N.np, nb = N.nb, nf = np + nb;
+    const int np = N.np, nb = N.nb, ld = N.ld;
     const int npk = V.np;
     T* pan = F + N.panel_off;
     T* upd = U + N.upd_off;
     const int* bord = V.border + N.border_off;
-    for (int64_t i = ex.tid; i < (int64_t)nf * np; i += ex.nt) pan[i] = (T)0;
+    for (int64_t i = ex.tid; i < (int64_t)ld * np; i += ex.nt) pan[i] = (T)0;
     for (int64_t i = ex.tid; i < (int64_t)nb * nb; i += ex.nt) upd[i] = (T)0;
     ex.sync();
     // original matrix entries of the pivot columns (one thread per column)
@@ -140,7 +141,7 @@ struct KFactor {
       const int pos = N.p0 + j;
       const int dt = V.dtype[P.pos_off + pos];
       const int src = V.dsrc[P.pos_off + pos];
-      T* colp = pan + (int64_t)j * nf;
+      T* colp = pan + (int64_t)j * ld;
       if (dt == DT_VEL) {
         const int* vp = V.vadj_ptr + S.vadj_ptr_off;
         for (int q = vp[src]; q < vp[src + 1]; ++q) {
@@ -217,12 +218,12 @@ struct KFactor {
         if (ii < kk) continue;
         const int rc = rel[kk], rr = rel[ii];
         const T v = Uc[idx];
-        if (rc < np) pan[(int64_t)rc * nf + rr] += v;
+        if (rc < np) pan[(int64_t)rc * ld + rr] += v;
         else upd[(int64_t)(rc - np) * nb + (rr - np)] += v;
       }
       ex.sync();
     }
-    front_ldlt<T>(ex, pan, upd, np, nb, V.dtype + P.pos_off + N.p0, status);
+    front_ldlt<T>(ex, pan, upd, np, nb, ld, V.dtype + P.pos_off + N.p0, status);
   }
 };
 
@@ -277,23 +278,51 @@ struct KFwdGather {
 // factor entry read from memory serves RB accumulators (RB = 1 for the
 // single right-hand side of the CG iteration, 4 for the coarse basis).
 
-// forward (2): y_p = L11^{-1} f_p for a task of pivot rows (unit lower)
+// 16-byte vector loads of factor columns: W consecutive rows per load (the
+// panels are 4-element aligned with a leading dimension divisible by 4)
+template <class T>
+struct VecW;
+template <>
+struct VecW<double> {
+  static constexpr int W = 2;
+};
+template <>
+struct VecW<float> {
+  static constexpr int W = 4;
+};
+VB_HD inline void vload(const double* p, double* o) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+}
+VB_HD inline void vload(const float* p, double* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+
+// forward (2): y_p = L11^{-1} f_p; a task is a range of W-row vectors of
+// the pivot rows, one vector per thread
 template <class T, int RB>
 struct KFwdPivots {
   BddcView V;
-  const SolveTask* tasks;
+  const SolveTask* tasks;   // {node, first vector, vectors}
   const T* F;
   const double* FV;
   const int64_t* fv_off;
   double* X;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
+    constexpr int W = VecW<T>::W;
     const SolveTask tk = tasks[blk];
     const NodeDev N = V.nodes[tk.node];
     const ProbDev P = V.probs[N.prob];
-    const int nf = N.np + N.nb;
+    const int np = N.np, nf = N.np + N.nb, ld = N.ld;
     const T* pan = F + N.panel_off;
-    const int kmax = tk.start + tk.count;
+    const int rend = W * (tk.start + tk.count);
+    const int kmax = rend < np ? rend : np;
     double* fs = ex.smem;   // [RB][kmax]
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
@@ -302,23 +331,40 @@ struct KFwdPivots {
         fs[q] = r < nr ? FV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + k] : 0.0;
       }
       ex.sync();
-      for (int i = tk.start + ex.tid; i < kmax; i += ex.nt) {
-        double acc[RB];
-        for (int r = 0; r < RB; ++r) acc[r] = fs[r * kmax + i];
-        const T* col = pan + i;
-#pragma unroll 4
-        for (int k = 0; k < i; ++k) {
-          const double v = (double)col[(int64_t)k * nf];
-          for (int r = 0; r < RB; ++r) acc[r] += v * fs[r * kmax + k];
+      for (int v = tk.start + ex.tid; v < tk.start + tk.count; v += ex.nt) {
+        const int i0 = W * v;
+        double acc[W][RB];
+        for (int j = 0; j < W; ++j)
+          for (int r = 0; r < RB; ++r) acc[j][r] = i0 + j < kmax ? fs[r * kmax + i0 + j] : 0.0;
+        const T* base = pan + i0;
+        double val[W];
+        for (int k = 0; k < i0; ++k) {
+          vload(base + (int64_t)k * ld, val);
+          for (int r = 0; r < RB; ++r) {
+            const double x = fs[r * kmax + k];
+            for (int j = 0; j < W; ++j) acc[j][r] += val[j] * x;
+          }
         }
-        for (int r = 0; r < nr; ++r) X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + i] = acc[r];
+        const int kt = i0 + W - 1 < kmax ? i0 + W - 1 : kmax;
+        for (int k = i0; k < kt; ++k) {
+          vload(base + (int64_t)k * ld, val);
+          for (int r = 0; r < RB; ++r) {
+            const double x = fs[r * kmax + k];
+            for (int j = 0; j < W; ++j)
+              if (i0 + j > k) acc[j][r] += val[j] * x;
+          }
+        }
+        for (int j = 0; j < W; ++j)
+          if (i0 + j < np)
+            for (int r = 0; r < nr; ++r) X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + i0 + j] = acc[j][r];
       }
       ex.sync();
     }
   }
 };
 
-// forward (3): update vector u = f_b - L21 y for a task of border rows
+// forward (3): update vector u = f_b - L21 y; a task is a range of W-row
+// vectors of the border rows (aligned base floor(np/W)*W), one per thread
 template <class T, int RB>
 struct KFwdBorder {
   BddcView V;
@@ -330,10 +376,12 @@ struct KFwdBorder {
   double* UV;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
+    constexpr int W = VecW<T>::W;
     const SolveTask tk = tasks[blk];
     const NodeDev N = V.nodes[tk.node];
     const ProbDev P = V.probs[N.prob];
-    const int np = N.np, nf = N.np + N.nb;
+    const int np = N.np, nf = N.np + N.nb, ld = N.ld;
+    const int a0 = (np / W) * W;
     const T* pan = F + N.panel_off;
     double* ys = ex.smem;   // [RB][np]
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
@@ -343,18 +391,28 @@ struct KFwdBorder {
         ys[q] = r < nr ? X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + k] : 0.0;
       }
       ex.sync();
-      for (int i = tk.start + ex.tid; i < tk.start + tk.count; i += ex.nt) {
-        double acc[RB];
-        for (int r = 0; r < RB; ++r) acc[r] = 0.0;
-        const T* col = pan + np + i;
-#pragma unroll 4
+      for (int v = tk.start + ex.tid; v < tk.start + tk.count; v += ex.nt) {
+        const int i0 = a0 + W * v;
+        double acc[W][RB];
+        for (int j = 0; j < W; ++j)
+          for (int r = 0; r < RB; ++r) acc[j][r] = 0.0;
+        const T* base = pan + i0;
+        double val[W];
+#pragma unroll 2
         for (int k = 0; k < np; ++k) {
-          const double v = (double)col[(int64_t)k * nf];
-          for (int r = 0; r < RB; ++r) acc[r] += v * ys[r * np + k];
+          vload(base + (int64_t)k * ld, val);
+          for (int r = 0; r < RB; ++r) {
+            const double x = ys[r * np + k];
+            for (int j = 0; j < W; ++j) acc[j][r] += val[j] * x;
+          }
         }
-        for (int r = 0; r < nr; ++r) {
-          const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf;
-          UV[N.uvec_off * nrhs + (int64_t)(r0 + r) * N.nb + i] = f[np + i] - acc[r];
+        for (int j = 0; j < W; ++j) {
+          const int row = i0 + j;
+          if (row < np || row >= nf) continue;
+          for (int r = 0; r < nr; ++r) {
+            const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf;
+            UV[N.uvec_off * nrhs + (int64_t)(r0 + r) * N.nb + (row - np)] = f[row] - acc[j][r];
+          }
         }
       }
       ex.sync();
@@ -363,7 +421,7 @@ struct KFwdBorder {
 };
 
 // backward (1): t_j = y_j / d_j - sum_border L21[i][j] x_i for a task of
-// pivot columns (one warp per column)
+// pivot columns (one warp per column, lanes along W-row vectors)
 template <class T, int RB>
 struct KBwdBorder {
   BddcView V;
@@ -374,10 +432,13 @@ struct KBwdBorder {
   const int64_t* fv_off;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
+    constexpr int W = VecW<T>::W;
     const SolveTask tk = tasks[blk];
     const NodeDev N = V.nodes[tk.node];
     const ProbDev P = V.probs[N.prob];
-    const int np = N.np, nb = N.nb, nf = np + nb;
+    const int np = N.np, nb = N.nb, nf = np + nb, ld = N.ld;
+    const int a0 = (np / W) * W;
+    const int nvec = (nf - a0 + W - 1) / W;
     const T* pan = F + N.panel_off;
     const int* bord = V.border + N.border_off;
     double* xb = ex.smem;   // [RB][nb]
@@ -386,20 +447,24 @@ struct KBwdBorder {
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
       for (int q = ex.tid; q < RB * nb; q += ex.nt) {
-        const int r = q / (nb > 0 ? nb : 1), i = q % (nb > 0 ? nb : 1);
+        const int r = q / nb, i = q % nb;
         xb[q] = r < nr ? X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + bord[i]] : 0.0;
       }
       ex.sync();
       for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
-        const T* cj = pan + (int64_t)j * nf + np;
+        const T* cj = pan + (int64_t)j * ld + a0;
         double acc[RB];
         for (int r = 0; r < RB; ++r) acc[r] = 0.0;
-#pragma unroll 4
-        for (int i = lane; i < nb; i += ws) {
-          const double v = (double)cj[i];
-          for (int r = 0; r < RB; ++r) acc[r] += v * xb[r * nb + i];
+        double val[W];
+        for (int q = lane; q < nvec; q += ws) {
+          vload(cj + W * q, val);
+          for (int jj = 0; jj < W; ++jj) {
+            const int row = a0 + W * q + jj;
+            if (row < np || row >= nf) continue;
+            for (int r = 0; r < RB; ++r) acc[r] += val[jj] * xb[r * nb + row - np];
+          }
         }
-        const double dj = (double)pan[(int64_t)j * nf + j];
+        const double dj = (double)pan[(int64_t)j * ld + j];
         for (int r = 0; r < nr; ++r) {
           const double t = warp_sum(acc[r]);
           if (lane == 0)
@@ -412,7 +477,8 @@ struct KBwdBorder {
   }
 };
 
-// backward (2): x_p = L11^{-T} t for a task of pivot columns (warp per column)
+// backward (2): x_p = L11^{-T} t for a task of pivot columns (warp per
+// column, lanes along W-row vectors of the column below the diagonal)
 template <class T, int RB>
 struct KBwdPivots {
   BddcView V;
@@ -423,10 +489,11 @@ struct KBwdPivots {
   double* X;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
+    constexpr int W = VecW<T>::W;
     const SolveTask tk = tasks[blk];
     const NodeDev N = V.nodes[tk.node];
     const ProbDev P = V.probs[N.prob];
-    const int np = N.np, nf = N.np + N.nb;
+    const int np = N.np, nf = N.np + N.nb, ld = N.ld;
     const T* pan = F + N.panel_off;
     const int L = np - tk.start;   // rows tk.start..np-1 staged
     double* ts = ex.smem;          // [RB][L]
@@ -440,13 +507,19 @@ struct KBwdPivots {
       }
       ex.sync();
       for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
-        const T* cj = pan + (int64_t)j * nf;
+        const int b0 = ((j + 1) / W) * W;
+        const int nvec = (np - b0 + W - 1) / W;
+        const T* cj = pan + (int64_t)j * ld + b0;
         double acc[RB];
         for (int r = 0; r < RB; ++r) acc[r] = 0.0;
-#pragma unroll 4
-        for (int i = j + 1 + lane; i < np; i += ws) {
-          const double v = (double)cj[i];
-          for (int r = 0; r < RB; ++r) acc[r] += v * ts[r * L + i - tk.start];
+        double val[W];
+        for (int q = lane; q < nvec; q += ws) {
+          vload(cj + W * q, val);
+          for (int jj = 0; jj < W; ++jj) {
+            const int row = b0 + W * q + jj;
+            if (row <= j || row >= np) continue;
+            for (int r = 0; r < RB; ++r) acc[r] += val[jj] * ts[r * L + row - tk.start];
+          }
         }
         for (int r = 0; r < nr; ++r) {
           const double t = warp_sum(acc[r]);
