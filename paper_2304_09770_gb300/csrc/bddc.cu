@@ -1062,12 +1062,12 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
       const NodeDev& N = b->h_nodes[t];
       b->h_fvoff[t] = fv;
       fv += N.np + N.nb;
-      for (int s0 = 0; s0 < N.np; s0 += TASK) B.h_ptask.push_back({t, s0, std::min(TASK, N.np - s0)});
+      for (int s0 = 0; s0 < N.np; s0 += BCOLS) B.h_ptask.push_back({t, s0, std::min(BCOLS, N.np - s0)});
       const int nvp = (N.np + W - 1) / W;
-      for (int s0 = 0; s0 < nvp; s0 += TASK) B.h_fptask.push_back({t, s0, std::min(TASK, nvp - s0)});
+      for (int s0 = 0; s0 < nvp; s0 += FVEC) B.h_fptask.push_back({t, s0, std::min(FVEC, nvp - s0)});
       const int a0 = (N.np / W) * W;
       const int nvb = N.nb > 0 ? (N.np + N.nb - a0 + W - 1) / W : 0;
-      for (int s0 = 0; s0 < nvb; s0 += TASK) B.h_btask.push_back({t, s0, std::min(TASK, nvb - s0)});
+      for (int s0 = 0; s0 < nvb; s0 += FVEC) B.h_btask.push_back({t, s0, std::min(FVEC, nvb - s0)});
     }
     B.ptask_ptr[h + 1] = (int)B.h_ptask.size();
     B.btask_ptr[h + 1] = (int)B.h_btask.size();
@@ -1128,14 +1128,18 @@ static void sweep_batch_rb(bddc* b, Batch& B, const BddcView& V, const T* Fp, do
     B.fv_nrhs = nrhs;
   }
   const size_t sm = sizeof(double) * (RB * (B.maxnf + 8));
+  const size_t smf = sm + sizeof(double) * FWARPS * FVEC * 4 * RB;   // + partial sums of the warps
+  VB_CHECK(smf <= 227 * 1024, VEM_EINVAL, "front too large for the sweep kernels' shared memory");
   const int64_t* fvo = b->d_fvoff.p;
   for (int h = 0; h <= B.maxh; ++h) {
     const int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
     const int fp_t = B.fptask_ptr[h + 1] - B.fptask_ptr[h];
     const int nb_t = B.btask_ptr[h + 1] - B.btask_ptr[h];
     launch(KFwdGather{V, B.d_levels.p + B.level_ptr[h], X, UV, B.FV.p, fvo, nrhs}, cnt, 128, 0, st);
-    launch(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, fp_t, 128, sm, st);
-    launch(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 128, sm, st);
+    launch(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, fp_t, 32 * FWARPS, smf,
+           st);
+    launch(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 32 * FWARPS, smf,
+           st);
   }
   for (int h = B.maxh; h >= 0; --h) {
     const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];

@@ -234,6 +234,12 @@ VB_HD inline double warp_sum(double v) {
 #endif
   return v;
 }
+VB_HD inline float warp_sum(float v) {
+#ifdef __CUDA_ARCH__
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+#endif
+  return v;
+}
 
 // Triangular sweeps over one tree level, split into tasks of up to TASK
 // rows (or columns) of one front, so that large fronts spread over many CTAs.
@@ -242,6 +248,7 @@ struct SolveTask {
   int node, start, count;
 };
 constexpr int TASK = 128;
+constexpr int BCOLS = 32;   // pivot columns per backward-sweep task (4 per warp)
 
 // forward (1): front vector of each node = its own right-hand side entries
 // plus the children's update vectors (extend-add), one CTA per node
@@ -295,7 +302,7 @@ VB_HD inline void vload(const double* p, double* o) {
   o[0] = v.x;
   o[1] = v.y;
 }
-VB_HD inline void vload(const float* p, double* o) {
+VB_HD inline void vload(const float* p, float* o) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   o[0] = v.x;
   o[1] = v.y;
@@ -303,8 +310,57 @@ VB_HD inline void vload(const float* p, double* o) {
   o[3] = v.w;
 }
 
-// forward (2): y_p = L11^{-1} f_p; a task is a range of W-row vectors of
-// the pivot rows, one vector per thread
+// The sweeps accumulate in the factor's precision: FP64 arithmetic runs at
+// a small fraction of the FP32 rate on this GPU, and an FP32-local solve
+// is followed by refinement with an FP64 residual anyway.  Right-hand sides
+// are staged in shared memory in that precision too.
+
+// Forward tasks cover up to FVEC W-row vectors (one per lane); the warps of
+// the CTA split the column range and their partial sums are added in a
+// fixed order through shared memory.  Loads are issued in groups of 4
+// columns so that each lane keeps several 16-byte loads in flight.
+constexpr int FVEC = 32;
+constexpr int FWARPS = 8;
+
+// rows [i0, i0+W) of L[.][k] * x_k accumulated for k in [ka, kb); entries
+// with row <= k (diagonal block of the unit lower inverse) skipped when
+// `tri` is set
+template <class T, int RB>
+VB_HD inline void fwd_accum(const T* base, int ld, const T* xs, int xld, int ka, int kb, int i0, bool tri,
+                            T (*acc)[RB]) {
+  constexpr int W = VecW<T>::W;
+  const int kfull = tri ? (kb < i0 ? kb : i0) : kb;
+  int k = ka;
+  for (; k + 4 <= kfull; k += 4) {
+    T v0[W], v1[W], v2[W], v3[W];
+    vload(base + (int64_t)k * ld, v0);
+    vload(base + (int64_t)(k + 1) * ld, v1);
+    vload(base + (int64_t)(k + 2) * ld, v2);
+    vload(base + (int64_t)(k + 3) * ld, v3);
+    for (int r = 0; r < RB; ++r) {
+      const T* x = xs + r * xld + k;
+      for (int j = 0; j < W; ++j) acc[j][r] += v0[j] * x[0] + v1[j] * x[1] + v2[j] * x[2] + v3[j] * x[3];
+    }
+  }
+  for (; k < kfull; ++k) {
+    T v[W];
+    vload(base + (int64_t)k * ld, v);
+    for (int r = 0; r < RB; ++r)
+      for (int j = 0; j < W; ++j) acc[j][r] += v[j] * xs[r * xld + k];
+  }
+  if (!tri) return;
+  const int kt = kb < i0 + W - 1 ? kb : i0 + W - 1;
+  for (k = ka > i0 ? ka : i0; k < kt; ++k) {
+    T v[W];
+    vload(base + (int64_t)k * ld, v);
+    for (int r = 0; r < RB; ++r)
+      for (int j = 0; j < W; ++j)
+        if (i0 + j > k) acc[j][r] += v[j] * xs[r * xld + k];
+  }
+}
+
+// forward (2): y_p = L11^{-1} f_p (L11^{-1} unit lower, stored in place);
+// a task is up to FVEC W-row vectors of the pivot rows
 template <class T, int RB>
 struct KFwdPivots {
   BddcView V;
@@ -323,48 +379,44 @@ struct KFwdPivots {
     const T* pan = F + N.panel_off;
     const int rend = W * (tk.start + tk.count);
     const int kmax = rend < np ? rend : np;
-    double* fs = ex.smem;   // [RB][kmax]
+    const int ws = ex.nt >= 32 ? 32 : 1;
+    const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
+    const int kc = (kmax + nw - 1) / nw, ka = w * kc, kb = ka + kc < kmax ? ka + kc : kmax;
+    T* fs = reinterpret_cast<T*>(ex.smem);        // [RB][kmax]
+    T* red = fs + ((RB * kmax + 3) & ~3);         // [nw][FVEC][W][RB]
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
       for (int q = ex.tid; q < RB * kmax; q += ex.nt) {
         const int r = q / kmax, k = q % kmax;
-        fs[q] = r < nr ? FV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + k] : 0.0;
+        fs[q] = r < nr ? (T)FV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + k] : (T)0;
       }
       ex.sync();
-      for (int v = tk.start + ex.tid; v < tk.start + tk.count; v += ex.nt) {
-        const int i0 = W * v;
-        double acc[W][RB];
+      for (int v = lane; v < tk.count; v += ws) {
+        const int i0 = W * (tk.start + v);
+        T acc[W][RB];
         for (int j = 0; j < W; ++j)
-          for (int r = 0; r < RB; ++r) acc[j][r] = i0 + j < kmax ? fs[r * kmax + i0 + j] : 0.0;
-        const T* base = pan + i0;
-        double val[W];
-        for (int k = 0; k < i0; ++k) {
-          vload(base + (int64_t)k * ld, val);
-          for (int r = 0; r < RB; ++r) {
-            const double x = fs[r * kmax + k];
-            for (int j = 0; j < W; ++j) acc[j][r] += val[j] * x;
-          }
-        }
-        const int kt = i0 + W - 1 < kmax ? i0 + W - 1 : kmax;
-        for (int k = i0; k < kt; ++k) {
-          vload(base + (int64_t)k * ld, val);
-          for (int r = 0; r < RB; ++r) {
-            const double x = fs[r * kmax + k];
-            for (int j = 0; j < W; ++j)
-              if (i0 + j > k) acc[j][r] += val[j] * x;
-          }
-        }
+          for (int r = 0; r < RB; ++r) acc[j][r] = (T)0;
+        fwd_accum<T, RB>(pan + i0, ld, fs, kmax, ka, kb, i0, true, acc);
         for (int j = 0; j < W; ++j)
-          if (i0 + j < np)
-            for (int r = 0; r < nr; ++r) X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + i0 + j] = acc[j][r];
+          for (int r = 0; r < RB; ++r) red[((w * FVEC + v) * W + j) * RB + r] = acc[j][r];
+      }
+      ex.sync();
+      for (int q = ex.tid; q < tk.count * W; q += ex.nt) {
+        const int v = q / W, j = q % W, row = W * (tk.start + v) + j;
+        if (row >= np) continue;
+        for (int r = 0; r < nr; ++r) {
+          T y = fs[r * kmax + row];
+          for (int u = 0; u < nw; ++u) y += red[((u * FVEC + v) * W + j) * RB + r];
+          X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + row] = y;
+        }
       }
       ex.sync();
     }
   }
 };
 
-// forward (3): update vector u = f_b - L21 y; a task is a range of W-row
-// vectors of the border rows (aligned base floor(np/W)*W), one per thread
+// forward (3): update vector u = f_b - L21 y; a task is up to FVEC W-row
+// vectors of the border rows (aligned base floor(np/W)*W)
 template <class T, int RB>
 struct KFwdBorder {
   BddcView V;
@@ -383,42 +435,71 @@ struct KFwdBorder {
     const int np = N.np, nf = N.np + N.nb, ld = N.ld;
     const int a0 = (np / W) * W;
     const T* pan = F + N.panel_off;
-    double* ys = ex.smem;   // [RB][np]
+    const int ws = ex.nt >= 32 ? 32 : 1;
+    const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
+    const int kc = (np + nw - 1) / nw, ka = w * kc, kb = ka + kc < np ? ka + kc : np;
+    T* ys = reinterpret_cast<T*>(ex.smem);      // [RB][np]
+    T* red = ys + ((RB * np + 3) & ~3);         // [nw][FVEC][W][RB]
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
       for (int q = ex.tid; q < RB * np; q += ex.nt) {
         const int r = q / np, k = q % np;
-        ys[q] = r < nr ? X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + k] : 0.0;
+        ys[q] = r < nr ? (T)X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + k] : (T)0;
       }
       ex.sync();
-      for (int v = tk.start + ex.tid; v < tk.start + tk.count; v += ex.nt) {
-        const int i0 = a0 + W * v;
-        double acc[W][RB];
+      for (int v = lane; v < tk.count; v += ws) {
+        const int i0 = a0 + W * (tk.start + v);
+        T acc[W][RB];
         for (int j = 0; j < W; ++j)
-          for (int r = 0; r < RB; ++r) acc[j][r] = 0.0;
-        const T* base = pan + i0;
-        double val[W];
-#pragma unroll 2
-        for (int k = 0; k < np; ++k) {
-          vload(base + (int64_t)k * ld, val);
-          for (int r = 0; r < RB; ++r) {
-            const double x = ys[r * np + k];
-            for (int j = 0; j < W; ++j) acc[j][r] += val[j] * x;
-          }
-        }
-        for (int j = 0; j < W; ++j) {
-          const int row = i0 + j;
-          if (row < np || row >= nf) continue;
-          for (int r = 0; r < nr; ++r) {
-            const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf;
-            UV[N.uvec_off * nrhs + (int64_t)(r0 + r) * N.nb + (row - np)] = f[row] - acc[j][r];
-          }
+          for (int r = 0; r < RB; ++r) acc[j][r] = (T)0;
+        fwd_accum<T, RB>(pan + i0, ld, ys, np, ka, kb, i0, false, acc);
+        for (int j = 0; j < W; ++j)
+          for (int r = 0; r < RB; ++r) red[((w * FVEC + v) * W + j) * RB + r] = acc[j][r];
+      }
+      ex.sync();
+      for (int q = ex.tid; q < tk.count * W; q += ex.nt) {
+        const int v = q / W, j = q % W, row = a0 + W * (tk.start + v) + j;
+        if (row < np || row >= nf) continue;
+        for (int r = 0; r < nr; ++r) {
+          T s = (T)0;
+          for (int u = 0; u < nw; ++u) s += red[((u * FVEC + v) * W + j) * RB + r];
+          const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf;
+          UV[N.uvec_off * nrhs + (int64_t)(r0 + r) * N.nb + (row - np)] = f[row] - (double)s;
         }
       }
       ex.sync();
     }
   }
 };
+
+// sum over rows [lo, hi) of column segment c (vectors from aligned row b0)
+// of c[row] * xs[r*xld + row - xoff], lanes striding over W-row vectors
+template <class T, int RB>
+VB_HD inline void col_dot(const T* c, int b0, int lo, int hi, const T* xs, int xld, int xoff, int lane, int ws,
+                          T* acc) {
+  constexpr int W = VecW<T>::W;
+  const int nvec = hi > b0 ? (hi - b0 + W - 1) / W : 0;
+  int q = lane;
+  for (; q + 3 * ws < nvec; q += 4 * ws) {
+    T v[4][W];
+    for (int u = 0; u < 4; ++u) vload(c + W * (q + u * ws), v[u]);
+    for (int u = 0; u < 4; ++u)
+      for (int jj = 0; jj < W; ++jj) {
+        const int row = b0 + W * (q + u * ws) + jj;
+        if (row < lo || row >= hi) continue;
+        for (int r = 0; r < RB; ++r) acc[r] += v[u][jj] * xs[r * xld + row - xoff];
+      }
+  }
+  for (; q < nvec; q += ws) {
+    T v[W];
+    vload(c + W * q, v);
+    for (int jj = 0; jj < W; ++jj) {
+      const int row = b0 + W * q + jj;
+      if (row < lo || row >= hi) continue;
+      for (int r = 0; r < RB; ++r) acc[r] += v[jj] * xs[r * xld + row - xoff];
+    }
+  }
+}
 
 // backward (1): t_j = y_j / d_j - sum_border L21[i][j] x_i for a task of
 // pivot columns (one warp per column, lanes along W-row vectors)
@@ -438,35 +519,25 @@ struct KBwdBorder {
     const ProbDev P = V.probs[N.prob];
     const int np = N.np, nb = N.nb, nf = np + nb, ld = N.ld;
     const int a0 = (np / W) * W;
-    const int nvec = (nf - a0 + W - 1) / W;
     const T* pan = F + N.panel_off;
     const int* bord = V.border + N.border_off;
-    double* xb = ex.smem;   // [RB][nb]
+    T* xb = reinterpret_cast<T*>(ex.smem);   // [RB][nb]
     const int ws = ex.nt >= 32 ? 32 : 1;
     const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
       for (int q = ex.tid; q < RB * nb; q += ex.nt) {
         const int r = q / nb, i = q % nb;
-        xb[q] = r < nr ? X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + bord[i]] : 0.0;
+        xb[q] = r < nr ? (T)X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + bord[i]] : (T)0;
       }
       ex.sync();
       for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
-        const T* cj = pan + (int64_t)j * ld + a0;
-        double acc[RB];
-        for (int r = 0; r < RB; ++r) acc[r] = 0.0;
-        double val[W];
-        for (int q = lane; q < nvec; q += ws) {
-          vload(cj + W * q, val);
-          for (int jj = 0; jj < W; ++jj) {
-            const int row = a0 + W * q + jj;
-            if (row < np || row >= nf) continue;
-            for (int r = 0; r < RB; ++r) acc[r] += val[jj] * xb[r * nb + row - np];
-          }
-        }
+        T acc[RB];
+        for (int r = 0; r < RB; ++r) acc[r] = (T)0;
+        col_dot<T, RB>(pan + (int64_t)j * ld + a0, a0, np, nf, xb, nb, np, lane, ws, acc);
         const double dj = (double)pan[(int64_t)j * ld + j];
         for (int r = 0; r < nr; ++r) {
-          const double t = warp_sum(acc[r]);
+          const double t = (double)warp_sum(acc[r]);
           if (lane == 0)
             TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] =
                 X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] / dj - t;
@@ -496,35 +567,26 @@ struct KBwdPivots {
     const int np = N.np, nf = N.np + N.nb, ld = N.ld;
     const T* pan = F + N.panel_off;
     const int L = np - tk.start;   // rows tk.start..np-1 staged
-    double* ts = ex.smem;          // [RB][L]
+    T* ts = reinterpret_cast<T*>(ex.smem);   // [RB][L]
     const int ws = ex.nt >= 32 ? 32 : 1;
     const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
       for (int q = ex.tid; q < RB * L; q += ex.nt) {
         const int r = q / L, i = q % L;
-        ts[q] = r < nr ? TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + tk.start + i] : 0.0;
+        ts[q] = r < nr ? (T)TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + tk.start + i] : (T)0;
       }
       ex.sync();
       for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
         const int b0 = ((j + 1) / W) * W;
-        const int nvec = (np - b0 + W - 1) / W;
-        const T* cj = pan + (int64_t)j * ld + b0;
-        double acc[RB];
-        for (int r = 0; r < RB; ++r) acc[r] = 0.0;
-        double val[W];
-        for (int q = lane; q < nvec; q += ws) {
-          vload(cj + W * q, val);
-          for (int jj = 0; jj < W; ++jj) {
-            const int row = b0 + W * q + jj;
-            if (row <= j || row >= np) continue;
-            for (int r = 0; r < RB; ++r) acc[r] += val[jj] * ts[r * L + row - tk.start];
-          }
-        }
+        T acc[RB];
+        for (int r = 0; r < RB; ++r) acc[r] = (T)0;
+        col_dot<T, RB>(pan + (int64_t)j * ld + b0, b0, j + 1, np, ts, L, tk.start, lane, ws, acc);
         for (int r = 0; r < nr; ++r) {
-          const double t = warp_sum(acc[r]);
+          const double t = (double)warp_sum(acc[r]);
           if (lane == 0)
-            X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] = ts[r * L + j - tk.start] + t;
+            X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] =
+                TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] + t;
         }
       }
       ex.sync();
