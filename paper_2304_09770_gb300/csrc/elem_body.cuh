@@ -3,9 +3,8 @@
 // Pi^0_{k-1} grad, Pi^0_k (Eq. velSpace), the local stiffness
 // a_h^K = consistency + stabilization (Eq. discreteA) and B_K.
 //
-// One cooperating group of `nt` threads (a CTA) builds one element.  The
-// body is written against a tiny execution interface (thread id, count,
-// barrier) so that it also runs with a single host thread.
+// One cooperating group of `nt` threads (a CTA) builds one element, written
+// against a tiny execution interface (thread id, count, barrier).
 //
 // Polynomial facts used (all in scaled monomials xi = (x - x_K)/h_K):
 //  * any homogeneous w in [P_d]^3 splits as

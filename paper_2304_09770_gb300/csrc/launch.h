@@ -43,14 +43,6 @@ inline void launch(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaS
   VB_KERNEL_CHECK();
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
-#else
-template <class F>
-inline void launch(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaStream_t) {
-  (void)nthreads;
-  std::vector<double> buf(smem / sizeof(double) + 1, 0.0);
-  for (int64_t b = 0; b < nblocks; ++b) f(KExec{0, 1, buf.data()}, (int)b);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-}
 #endif
 
 VB_HD inline void flag_error(int* p, int v) {

@@ -227,7 +227,7 @@ struct KFactor {
   }
 };
 
-// sum over the 32 lanes of a warp (device); identity for one host thread
+// sum over the 32 lanes of a warp
 VB_HD inline double warp_sum(double v) {
 #ifdef __CUDA_ARCH__
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
