@@ -105,6 +105,33 @@ int vem_quad_points(vem_system* sys, int degree, int64_t* n, double* xyz_out);
  * the same degree.  f_at_quad: host [n*3]; rhs_dev: device [n_free+n_press]. */
 int vem_load(vem_system* sys, int degree, const double* f_at_quad, double* rhs_dev);
 
+/* Load vector without device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * themselves or through the library, for example code running under a
+ * memory budget fixed in advance, or inside a framework that owns every
+ * device allocation through its own pool.
+ *
+ * Computes the same vector as vem_load, but f is given on the device:
+ * f_at_quad_dev: device [n*3], the load f sampled at the points of
+ * vem_quad_points(sys, degree, ...) in that order; rhs_dev: device
+ * [n_free+n_press], overwritten.  Neither is kept after the call.
+ * Its only scratch is one fixed array of 16 MiB compiled into the library:
+ * every GPU that loads the library holds it until the process exits.  It
+ * holds the quadrature offsets ((nE+1) int64 values, padded to 256 bytes)
+ * and the element load vectors (8 bytes per element velocity DOF);
+ * a mesh that needs more returns VEM_EINVAL with the required size in
+ * vem_last_error() and writes nothing (use vem_load there).
+ * Calls no cudaMalloc, cudaFree or other allocating routine.  The work is
+ * enqueued on the system's stream and the call returns without waiting.
+ * Every call uses the same scratch array and every call rewrites what it
+ * reads, so calls that run one after another on the GPU give independent
+ * results; calls whose GPU work overlaps (other streams, other threads,
+ * other handles on the same device) race on the array.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Call it with the system's device current. */
+int vem_load_noalloc(vem_system* sys, int degree, const double* f_at_quad_dev, double* rhs_dev);
+
 /* y = K x over the system vector layout (Eq. MatrixForm).  Device arrays. */
 int vem_apply(vem_system* sys, const double* x_dev, double* y_dev);
 

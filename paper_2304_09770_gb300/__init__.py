@@ -50,6 +50,7 @@ def lib():
         L.vem_free_dofs.argtypes = [P, i64p]
         L.vem_quad_points.argtypes = [P, ctypes.c_int, i64p, P]
         L.vem_load.argtypes = [P, ctypes.c_int, P, P]
+        L.vem_load_noalloc.argtypes = [P, ctypes.c_int, P, P]
         L.vem_apply.argtypes = [P, P, P]
         L.vem_element_matrices.argtypes = [P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), P, P, P]
         L.vem_csr.argtypes = [P, i64p, i64p, P, P, P]
@@ -151,6 +152,13 @@ class VemSystem:
         if out is None:
             out = torch.empty(self.n, dtype=torch.float64, device="cuda")
         _check(lib().vem_load(self.h, degree, _ptr(f_values), _dptr(out)))
+        return out
+
+    def load_noalloc(self, degree, f_dev, out):
+        """vem_load_noalloc: the load vector from f already on the device
+        (float64 cuda tensor [n, 3] at the vem_quad_points rule), written
+        into the caller's tensor `out`; the library allocates nothing."""
+        _check(lib().vem_load_noalloc(self.h, int(degree), _dptr(f_dev), _dptr(out)))
         return out
 
     def apply(self, x, y=None):

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 namespace vb {
 
@@ -575,3 +576,152 @@ extern "C" int vem_set_stream(vem_system* s, void* st) {
 }
 
 extern "C" void vem_free(vem_system* s) { delete s; }
+
+// ------------------------------------------------ load without device allocation
+//
+// vem_load_noalloc: the load vector of vem_load for callers that may not
+// allocate device memory.  Its only scratch is the fixed array below; the
+// kernels are the ones vem_load launches (element load vectors, then the
+// deterministic gather), preceded by one kernel that writes the quadrature
+// point offsets into the same array.
+
+namespace vb {
+
+constexpr int64_t kLoadScratchBytes = 16ll << 20;   // 16 MiB per device
+constexpr int kLoadScratchDevices = 64;
+static __device__ __align__(256) unsigned char g_load_scratch[kLoadScratchBytes];
+
+// Device address of g_load_scratch on the current device, looked up once
+// per device (in host code the symbol is only a host-side stand-in).
+static unsigned char* load_scratch_address() {
+  static std::mutex mu;
+  static void* addr[kLoadScratchDevices] = {};
+  int dev = -1;
+  VB_CUDA(cudaGetDevice(&dev));
+  VB_CHECK(dev >= 0 && dev < kLoadScratchDevices, VEM_EINVAL, "vem_load_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_load_scratch);
+    if (e != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      throw Error(VEM_ECUDA, std::string("vem_load_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    }
+    addr[dev] = p;
+  }
+  return static_cast<unsigned char*>(addr[dev]);
+}
+
+// Gauss-Legendre rule on [0,1] with n <= 16 points into fixed arrays, in
+// increasing node order; the same Newton iteration and arithmetic as
+// gauss01, so the nodes and weights agree bit for bit.
+static void gauss01_fixed(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double pp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 2; j <= n; ++j) {
+        double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      pp = n * (z * p1 - p0) / (z * z - 1.0);
+      double z1 = z;
+      z = z1 - p1 / pp;
+      if (std::fabs(z - z1) < 1e-15) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int j = 2; j <= n; ++j) {
+      double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+      p0 = p1;
+      p1 = p2;
+    }
+    pp = n * (z * p1 - p0) / (z * z - 1.0);
+    // the Newton roots decrease with i: store them in reverse for increasing nodes
+    x[n - 1 - i] = 0.5 * (z + 1.0);
+    w[n - 1 - i] = 0.5 * (2.0 / ((1.0 - z * z) * pp * pp));
+  }
+}
+
+// qoff[e] = first load-rule point of element e, qoff[nE] = total: one CTA,
+// each thread owns a contiguous run of elements; exclusive scan of the run
+// totals in shared memory
+struct KLoadOffsets {
+  const ElemRec* rec;
+  int nE;
+  int64_t pts_per_tet;
+  int64_t* qoff;
+  __device__ int64_t count(int e) const {
+    const ElemRec& R = rec[e];
+    int nt = 0;
+    for (int f = 0; f < R.nf; ++f) nt += R.fnv[f] - 2;
+    return (int64_t)nt * pts_per_tet;
+  }
+  __device__ void operator()(const KExec& ex, int) const {
+    int64_t* run = reinterpret_cast<int64_t*>(ex.smem);
+    const int per = (nE + ex.nt - 1) / ex.nt;
+    const int lo = min(nE, ex.tid * per), hi = min(nE, lo + per);
+    int64_t s = 0;
+    for (int e = lo; e < hi; ++e) s += count(e);
+    run[ex.tid] = s;
+    ex.sync();
+    if (ex.tid == 0) {
+      int64_t acc = 0;
+      for (int t = 0; t < ex.nt; ++t) {
+        const int64_t v = run[t];
+        run[t] = acc;
+        acc += v;
+      }
+      qoff[nE] = acc;
+    }
+    ex.sync();
+    int64_t acc = run[ex.tid];
+    for (int e = lo; e < hi; ++e) {
+      qoff[e] = acc;
+      acc += count(e);
+    }
+  }
+};
+
+}  // namespace vb
+
+extern "C" int vem_load_noalloc(vem_system* s, int degree, const double* fq, double* rhs) {
+  if (!s || !fq || !rhs) { set_last_error("vem_load_noalloc: null argument"); return VEM_EINVAL; }
+  try {
+    VB_CHECK(degree >= 0 && degree <= 24, VEM_EINVAL, "vem_load_noalloc: load degree out of range");
+    const int nE = s->topo.nE;
+    const int64_t nloc = s->h_eoff.back();   // sum of the element DOF counts
+    const int64_t off_bytes = ((int64_t)(nE + 1) * 8 + 255) / 256 * 256;
+    const int64_t need = off_bytes + nloc * 8;
+    if (need > kLoadScratchBytes) {
+      char msg[200];
+      std::snprintf(msg, sizeof msg,
+                    "vem_load_noalloc: this mesh needs %lld bytes of scratch, above the fixed %lld; use vem_load",
+                    (long long)need, (long long)kLoadScratchBytes);
+      set_last_error(msg);
+      return VEM_EINVAL;
+    }
+    unsigned char* base = load_scratch_address();
+    int64_t* qoff = reinterpret_cast<int64_t*>(base);
+    double* rloc = reinterpret_cast<double*>(base + off_bytes);
+    LoadRule L;
+    L.nq = (degree + 3) / 2 + 1;
+    gauss01_fixed(L.nq, L.x, L.w);
+    const int64_t nq3 = (int64_t)L.nq * L.nq * L.nq;
+    launch(KLoadOffsets{s->d_rec.p, nE, nq3, qoff}, 1, 1024, sizeof(int64_t) * 1024, s->stream);
+    const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4);
+    if (s->dof.k == 2)
+      launch(KLoadLocal<2>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE, 128, lsm, s->stream);
+    else if (s->dof.k == 3)
+      launch(KLoadLocal<3>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE, 128, lsm, s->stream);
+    else
+      launch(KLoadLocal<4>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE, 128, lsm, s->stream);
+    launch(KGatherRhs{s->n, s->dof.nvf, s->d_adj_ptr.p, s->d_adj_elem.p, s->d_adj_loc.p, s->d_eoff.p, rloc, rhs},
+           (s->n + 255) / 256, 256, 0, s->stream);
+    return VEM_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
