@@ -140,15 +140,25 @@ def measure(pkg, torch, cfg, fq, precision, steps, warmup, stream, with_e2e, ran
     """Times `steps` full steps (after `warmup`) of one precision form."""
     mesh, k, nu, part = cfg["mesh"], cfg["k"], cfg["nu"], cfg["part"]
 
+    phases = {}
+
     def step(out_host=None):
+        # every library call below synchronizes, so host clocks split the step
+        t0 = time.perf_counter()
         g = pkg.VemSystem(mesh, k, nu)
         g.set_stream(stream)
+        t1 = time.perf_counter()
         rhs = g.load(LOAD_DEGREE, fq)
+        t2 = time.perf_counter()
         bd = pkg.Bddc(g, part, precision=precision)
+        t3 = time.perf_counter()
         u = torch.zeros_like(rhs)
         res = bd.solve(rhs, u, rtol=1e-8, maxit=1000)
+        t4 = time.perf_counter()
         if out_host is not None:
             out_host.copy_(u, non_blocking=True)
+        phases.update(vem_assemble=(t1 - t0) * 1e3, vem_load=(t2 - t1) * 1e3, bddc_setup=(t3 - t2) * 1e3,
+                      pcg_solve=(t4 - t3) * 1e3)
         return g, bd, u, rhs, res
 
     for _ in range(warmup):
@@ -181,6 +191,8 @@ def measure(pkg, torch, cfg, fq, precision, steps, warmup, stream, with_e2e, ran
             "t_coarse_rhs_ms", "t_coarse_solves_ms", "t_coarse_gram_ms", "t_coarse_inverse_ms",
             "gflop_factor_dirichlet", "gflop_factor_neumann", "gflop_factor_deluxe")
     info = {k2: bd.info(k2) for k2 in keys}
+    vkeys = ("t_topology_ms", "t_element_launch_ms", "t_pattern_ms", "t_pattern_upload_ms", "t_gpu_finish_ms")
+    vinfo = {k2: g.info(k2) for k2 in vkeys}
     r = torch.randn(g.n, dtype=torch.float64, device="cuda")
     z = torch.empty_like(r)
     for _ in range(3):
@@ -194,7 +206,8 @@ def measure(pkg, torch, cfg, fq, precision, steps, warmup, stream, with_e2e, ran
     torch.cuda.synchronize()
     apply_ms = ev0.elapsed_time(ev1) / napp
     sweep_ms, sweep_bytes = bd.time_local_solves(5)
-    return dict(dev_ms=dev_ms, e2e_ms=e2e_ms, launches=launches, res=res, info=info, apply_ms=apply_ms,
+    return dict(dev_ms=dev_ms, e2e_ms=e2e_ms, launches=launches, res=res, info=info, vinfo=vinfo,
+                phases=dict(phases), apply_ms=apply_ms,
                 sweep_ms=sweep_ms, sweep_bytes=sweep_bytes, n=g.n, n_coarse=bd.info("n_coarse"))
 
 
@@ -260,11 +273,11 @@ def run_ours(args, rank, world, dist):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iterations": res["iters"], "kappa": res["kappa"], "lam_min": res["lam_min"],
         "bddc_applies_per_s": 1e3 / m32["apply_ms"], "ms_per_apply": m32["apply_ms"],
-        "setup_phases_ms": m32["info"],
+        "setup_phases_ms": m32["info"], "step_phases_ms": m32["phases"], "assemble_phases_ms": m32["vinfo"],
         "fp64": {"value": dev64 / 1e3, "unit": "s", "iterations": m64["res"]["iters"],
                  "kappa": m64["res"]["kappa"], "lam_min": m64["res"]["lam_min"],
                  "bddc_applies_per_s": 1e3 / m64["apply_ms"], "ms_per_apply": m64["apply_ms"],
-                 "setup_phases_ms": m64["info"], "roofline": roof(m64), "gpu_launches": int(m64["launches"])},
+                 "setup_phases_ms": m64["info"], "step_phases_ms": m64["phases"], "roofline": roof(m64), "gpu_launches": int(m64["launches"])},
         "roofline": roof(m32),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
@@ -296,6 +309,75 @@ def run_profile(args):
                       "apply_launches": (pkg.kernel_launches() - l0) // args.napply}))
 
 
+CONFIG_RUNS = [
+    # (workload, precision, adaptive theta): the five configurations of the
+    # benchmark family; sinker meshes also with the adaptive coarse space
+    ("cube4_k2", 0, 0.0), ("cube4_k2", 1, 0.0),
+    ("tri32_k2", 0, 0.0), ("tri32_k2", 1, 0.0),
+    ("tri48_greedy", 0, 0.0), ("tri48_greedy", 1, 0.0),
+    ("tri16_k2", 0, 0.0), ("tri16_k2", 1, 0.0),
+    ("tri16_k3", 0, 0.0), ("tri16_k3", 1, 0.0),
+    ("tri16_k4", 0, 0.0), ("tri16_k4", 1, 0.0),
+    ("sinker32_dr1e4", 0, 0.0), ("sinker32_dr1e4", 1, 0.0), ("sinker32_dr1e4", 0, 10.0), ("sinker32_dr1e4", 1, 10.0),
+    ("sinker32_dr1e6", 0, 0.0), ("sinker32_dr1e6", 0, 10.0), ("sinker32_dr1e6", 1, 10.0),
+]
+
+
+def run_configs(args):
+    """One solve per configuration and form: times of each library call,
+    CG iterations, Lanczos estimates, and properties of the computed
+    solution (saddle-system residual, elementwise divergence), one JSON line
+    each."""
+    import numpy as np
+    import torch
+    import paper_2304_09770_gb300 as pkg
+    from synth import make_config
+    only = set(args.only.split(",")) if args.only else None
+    cache = {}
+    for name, prec, theta in CONFIG_RUNS:
+        if only and name not in only:
+            continue
+        cfg = cache.get(name) or make_config(name)
+        cache.clear()
+        cache[name] = cfg
+        k = cfg["k"]
+        deg = 2 * k - 2   # load rule: enough for the solver study, small host arrays at 48^3
+        line = {"workload": name, "precision": prec, "adaptive": theta, "k": k,
+                "elements": int(cfg["mesh"]["elem_ptr"].shape[0] - 1), "subdomains": int(cfg["part"].max() + 1)}
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = pkg.VemSystem(cfg["mesh"], k, cfg["nu"])
+            t1 = time.perf_counter()
+            fq = cfg["f"](g.quad_points(deg))
+            t2 = time.perf_counter()
+            rhs = g.load(deg, fq)
+            t3 = time.perf_counter()
+            # FP32-local: two refinement steps where one leaves the local
+            # solves too inexact (viscosity contrast, degree 4)
+            refine = 2 if prec and (np.ptp(cfg["nu"]) > 0 or k >= 4) else 0
+            line["refine"] = refine if prec else None
+            bd = pkg.Bddc(g, cfg["part"], precision=prec, refine=refine, adaptive=theta)
+            t4 = time.perf_counter()
+            u = torch.zeros_like(rhs)
+            res = bd.solve(rhs, u, rtol=1e-8, maxit=2000)
+            t5 = time.perf_counter()
+            r = rhs - g.apply(u)
+            line.update(n_dofs=int(g.n), nnz=g.info("nnz"), status=res["status"], iterations=res["iters"],
+                        kappa=res["kappa"], lam_min=res["lam_min"], n_coarse=bd.info("n_coarse"),
+                        n_adaptive=bd.info("n_adaptive"),
+                        rel_residual=torch.linalg.norm(r).item() / torch.linalg.norm(rhs).item(),
+                        max_div=torch.abs(r[g.n_vel_free:]).max().item() / torch.abs(rhs).max().item(),
+                        t_assemble_s=t1 - t0, t_load_s=t3 - t2, t_setup_s=t4 - t3, t_solve_s=t5 - t4,
+                        time_to_solution_s=(t1 - t0) + (t3 - t2) + (t4 - t3) + (t5 - t4),
+                        factor_bytes=bd.info("factor_bytes_dirichlet") + bd.info("factor_bytes_neumann"))
+            del bd, g, u, rhs, r
+        except Exception as e:  # noqa: BLE001
+            line.update(error=str(e)[:300])
+        torch.cuda.empty_cache()
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,9 +390,15 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--napply", type=int, default=3)
+    ap.add_argument("--configs", action="store_true",
+                    help="one solve per benchmark configuration and form (JSON line each)")
+    ap.add_argument("--only", default="", help="with --configs: comma-separated workload names")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+        return
+    if args.configs:
+        run_configs(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

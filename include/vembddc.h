@@ -87,6 +87,14 @@ typedef struct bddc bddc;
  * pressures (Eq. MatrixForm).  nu_per_element: host [nE].  Synchronizes. */
 int vem_assemble(const vem_mesh* mesh, int k, const double* nu_per_element, vem_system** out);
 
+/* Statistics by name: "nnz" (nonzeros of K), "n_elements", and the
+ * vem_assemble phase wall times (host clock) "t_topology_ms" (topology, DOF
+ * numbering, element records), "t_element_launch_ms" (uploads and the
+ * element kernel launch), "t_pattern_ms" (CSR pattern on the host while the
+ * element kernel runs), "t_pattern_upload_ms" (pattern upload, assembly
+ * launch), "t_gpu_finish_ms" (waiting for the GPU). */
+int vem_info(const vem_system* sys, const char* key, double* value);
+
 /* Sizes: free velocity DOFs, element pressures, all velocity DOFs. */
 int vem_dof_layout(const vem_system* sys, int64_t* n_vel_free, int64_t* n_press, int64_t* n_vel_all);
 
@@ -172,11 +180,29 @@ typedef struct {
                                matrix, deluxe inverses, operator and CG stay FP64. */
   int32_t scaling;          /* unused (the bddc_setup argument decides)        */
   uint32_t constraints;     /* unused (the bddc_setup argument decides)        */
-  double adaptive_threshold;/* unused: 0                                       */
+  double adaptive_threshold;/* theta > 0 (deluxe scaling only): adaptive coarse
+                               space of Sec. 6.  Per macro face, the generalized
+                               eigenproblem (S~_i : S~_j) psi = lambda (S_i : S_j) psi
+                               on the face's dual coordinates (S_s the face block of
+                               the subdomain Schur complement, S~_s the Schur
+                               complement of the constrained Neumann matrix onto
+                               the face, A : B = (A^-1 + B^-1)^-1); every eigenvector
+                               with lambda < 1/theta adds the primal functional
+                               (S_i : S_j) psi, and the setup is run again with the
+                               enlarged primal space (at most 64 per face).  0: off */
   int32_t nd_leaf;          /* elements per nested-dissection leaf (0: 4)      */
-  int32_t use_graph;        /* unused: 0                                       */
+  int32_t use_graph;        /* 0 or 1: pcg_solve runs its whole loop as one CUDA
+                               graph launch (a conditional while node whose body is
+                               one iteration, scalars and stop rule on the device)
+                               and bddc_apply replays a captured graph (captured
+                               again when r or z change); -1: host-driven loop and
+                               direct launches                                  */
   int32_t refine;           /* refinement steps of the FP32 local solves (0: 1)  */
-  int32_t reserved[8];
+  int32_t tc_update;        /* FP32 factorizations: 0 or 1 trailing updates of
+                               fronts beyond 96 rows on the tensor cores (tcgen05,
+                               operands split into TF32 high and low parts, FP32
+                               accumulation in tensor memory); -1: FP32 FMA units */
+  int32_t reserved[7];
 } bddc_options;
 
 /* BDDC setup (Sec. 4-6) for the partition elem_to_subdomain (host [nE],
@@ -210,6 +236,7 @@ int pcg_solve(bddc* b, const double* f_dev, double* u_dev, double rtol, int maxi
 
 /* Statistics by name: "n_subdomains", "n_coarse", "n_macro",
  * "factor_bytes_dirichlet", "factor_bytes_neumann", "n_deluxe_faces",
+ * "n_adaptive" (primal functionals added by the adaptive coarse space), "t_adaptive_eig_ms",
  * "deluxe_bytes", "phi_bytes", "coarse_bytes", "n_front_max", and the setup
  * phase wall times "t_symbolic_ms", "t_upload_ms", "t_factor_dirichlet_ms",
  * "t_factor_neumann_ms", "t_factor_deluxe_ms", "t_deluxe_extract_ms",
@@ -223,6 +250,14 @@ int bddc_info(bddc* b, const char* key, double* value);
  * Neumann+Dirichlet sweep pair; *bytes: the factor bytes such a pair reads
  * (every panel once forward, once backward).  Synchronizes. */
 int bddc_time_local_solves(bddc* b, int nrep, double* ms, double* bytes);
+/* Diagnostics: one 128 x 128 x 32 tile product of the tensor-core front
+ * update (tcgen05, TF32 high/low operand split, FP32 accumulation in
+ * tensor memory, Sec. 4 local factorizations in FP32) on deterministic
+ * data in [-1, 1), against an FP64 product.  *max_err: max |D - D_fp64|;
+ * *max_ref: max |D_fp64|.  Returns VEM_ETIMEOUT if the bounded wait for the
+ * product gave up.  Uses the current device; synchronizes it. */
+int vem_tc_selftest(double* max_err, double* max_ref);
+
 int bddc_set_stream(bddc* b, void* cuda_stream);
 void bddc_free(bddc* b);
 

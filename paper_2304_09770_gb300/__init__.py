@@ -32,7 +32,8 @@ class _Mesh(ctypes.Structure):
 class BddcOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("scaling", ctypes.c_int32), ("constraints", ctypes.c_uint32),
                 ("adaptive_threshold", ctypes.c_double), ("nd_leaf", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("refine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("use_graph", ctypes.c_int32), ("refine", ctypes.c_int32), ("tc_update", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 def lib():
@@ -59,6 +60,7 @@ def lib():
         L.vem_free.restype = None
         L.vem_last_error.restype = ctypes.c_char_p
         L.vem_kernel_launches.argtypes = [i64p]
+        L.vem_info.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
         if hasattr(L, "bddc_setup"):
             L.bddc_setup.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_uint32, ctypes.c_int,
                                      ctypes.POINTER(BddcOptions), ctypes.POINTER(P)]
@@ -192,6 +194,11 @@ class VemSystem:
         _check(lib().vem_csr(self.h, ctypes.byref(n), ctypes.byref(nnz), _ptr(rp), _ptr(col), _ptr(val)))
         return sp.csr_matrix((val, col, rp), shape=(n.value, n.value))
 
+    def info(self, key):
+        v = ctypes.c_double()
+        _check(lib().vem_info(self.h, key.encode(), ctypes.byref(v)))
+        return v.value
+
     def set_stream(self, stream):
         _check(lib().vem_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)))
 
@@ -199,7 +206,8 @@ class VemSystem:
 class Bddc:
     """bddc_setup + bddc_apply + pcg_solve over a VemSystem."""
 
-    def __init__(self, system, part, constraints=15, scaling=1, leaf=0, precision=0, refine=0):
+    def __init__(self, system, part, constraints=15, scaling=1, leaf=0, precision=0, refine=0, use_graph=0,
+                 adaptive=0.0, tc_update=0):
         L = lib()
         self.sys = system
         part = np.ascontiguousarray(part, dtype=np.int32)
@@ -207,6 +215,9 @@ class Bddc:
         opts.nd_leaf = int(leaf)
         opts.precision = int(precision)
         opts.refine = int(refine)
+        opts.use_graph = int(use_graph)
+        opts.adaptive_threshold = float(adaptive)
+        opts.tc_update = int(tc_update)
         h = ctypes.c_void_p()
         _check(L.bddc_setup(system.h, part.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(constraints),
                             int(scaling), ctypes.byref(opts), ctypes.byref(h)))

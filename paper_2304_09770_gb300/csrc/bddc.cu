@@ -7,6 +7,7 @@
 #include "bddc_setup.h"
 #include "bddc_dev.h"
 #include "mf.cuh"
+#include "dense.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -14,6 +15,7 @@
 #include <numeric>
 #include <chrono>
 #include <string>
+#include <type_traits>
 
 namespace vb {
 void spmv(vem_system* s, const double* x, double* y, cudaStream_t st);
@@ -39,6 +41,10 @@ struct Batch {
   DBuf<double> XB, XR;                    // refinement: right-hand sides, residuals
   std::vector<MatvecTask> h_mtask;
   DBuf<MatvecTask> d_mtask;
+  std::vector<ElemTask> h_etask;          // (problem, local element) of every problem
+  DBuf<ElemTask> d_etask;
+  DBuf<double> YE;                        // element shares of the residual
+  int64_t ye_n = 0;                       // per right-hand side
   int64_t nF = 0, nU = 0;
   int64_t nfv = 0;                        // sum of front sizes (front-vector store per rhs)
   std::vector<int> ptask_ptr, btask_ptr, fptask_ptr;   // per level: task ranges
@@ -92,6 +98,33 @@ struct bddc {
   // PCG vectors
   vb::DBuf<double> r, z, p, Ap, scal;
   std::vector<std::pair<std::string, double>> times;   // setup phase wall times (ms)
+  // CUDA graphs: the PCG loop (one conditional while node whose body is one
+  // iteration) and bddc_apply; captured on a private stream, replayed on
+  // `stream`
+  bool use_graph = true;
+  bool use_tc = true;            // FP32 front updates on the tensor cores (tcgen05, 3xTF32)
+  // adaptive coarse space (Sec. 6): threshold, rows added, and the face
+  // Schur complements S_F kept from the first setup
+  double adapt_theta = 0.0;
+  int n_adaptive = 0;
+  bool keep_sf = false;
+  vb::DBuf<double> d_sf;
+  std::vector<int> sf_faces;
+  std::vector<int64_t> sf_i, sf_j;
+  cudaStream_t cap_stream = nullptr;
+  vb::DBuf<double> xg, pcg_s, pcg_al, pcg_be;   // iterate, scalars, Lanczos records
+  int pcg_cap = 0;                              // records allocated (>= maxit)
+  cudaGraphExec_t pcg_exec = nullptr;
+  int64_t pcg_body_launches = 0;
+  cudaGraphExec_t app_exec = nullptr;
+  const double* app_r = nullptr;
+  double* app_z = nullptr;
+  int64_t app_launches = 0;
+  ~bddc() {
+    if (pcg_exec) cudaGraphExecDestroy(pcg_exec);
+    if (app_exec) cudaGraphExecDestroy(app_exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 
 namespace vb {
@@ -228,18 +261,19 @@ struct KElemMatvec {
 
 // Neumann right-hand sides of the coarse basis: -K W at the problem
 // positions, pressure part projected onto sum-zero data (zero-mean Q_I)
+// (columns c0 .. c0+ch-1 of the NC coarse columns; XN holds ch columns)
 struct KNeuRhsPhi {
   BddcView V;
   const double* KW;
   double* XN;
-  int NC;
+  int NC, c0, ch;
   VB_HD void operator()(const KExec& ex, int blk) const {
-    const int i = blk / NC, c = blk % NC;
+    const int i = blk / ch, c = blk % ch;
     const SubDev S = V.subs[i];
     const ProbDev P = V.probs[S.neu];
     const int nloc = S.nv + S.npress;
-    const double* kw = KW + S.loc_off * NC + (int64_t)c * nloc;
-    double* x = XN + P.vec_off * NC + (int64_t)c * P.n;
+    const double* kw = KW + S.loc_off * NC + (int64_t)(c0 + c) * nloc;
+    double* x = XN + P.vec_off * ch + (int64_t)c * P.n;
     // compatibility with the subdomain-constant pressure: shift the pressure
     // data by (sum of its constant-coefficient entries)/|Omega_i| times w
     double sg = 0.0;
@@ -263,15 +297,15 @@ struct KPhiAssemble {
   const double* W;
   const double* XN;
   double* PHI;
-  int NC;
+  int NC, c0, ch;
   VB_HD void operator()(const KExec& ex, int blk) const {
-    const int i = blk / NC, c = blk % NC;
+    const int i = blk / ch, c = blk % ch;
     const SubDev S = V.subs[i];
     const ProbDev P = V.probs[S.neu];
     const int nloc = S.nv + S.npress;
-    const double* w = W + S.loc_off * NC + (int64_t)c * nloc;
-    double* phi = PHI + S.loc_off * NC + (int64_t)c * nloc;
-    const double* x = XN + P.vec_off * NC + (int64_t)c * P.n;
+    const double* w = W + S.loc_off * NC + (int64_t)(c0 + c) * nloc;
+    double* phi = PHI + S.loc_off * NC + (int64_t)(c0 + c) * nloc;
+    const double* x = XN + P.vec_off * ch + (int64_t)c * P.n;
     const int* pv = V.pos_of_vdof + P.pv_off;
     for (int v = ex.tid; v < S.nv; v += ex.nt) {
       const int pos = pv[v];
@@ -1075,9 +1109,15 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
   }
   B.nfv = fv;
   B.h_mtask.clear();
-  for (int q : probs)
+  B.h_etask.clear();
+  for (int q : probs) {
     for (int s0 = 0; s0 < b->h_probs[q].n; s0 += TASK)
       B.h_mtask.push_back({q, s0, std::min(TASK, b->h_probs[q].n - s0)});
+    for (int le = 0; le < (int)b->H.subs[b->H.probs[q].sub].elems.size(); ++le) B.h_etask.push_back({q, le});
+  }
+  // the element-share store spans every element of the mesh (each element
+  // belongs to one subdomain, hence to one problem of the batch)
+  B.ye_n = b->sys->h_eoff.back() + (int64_t)b->sys->dof.np * b->sys->topo.nE;
   B.vec_n = vec;
   B.uvec_n = uv;
   B.nF = nF;
@@ -1102,16 +1142,31 @@ static void upload_levels(bddc* b, Batch& B) {
   upload_vec(B.d_btask, B.h_btask, b->stream);
   upload_vec(B.d_fptask, B.h_fptask, b->stream);
   upload_vec(B.d_mtask, B.h_mtask, b->stream);
+  upload_vec(B.d_etask, B.h_etask, b->stream);
 }
 
 template <class T>
 static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status, DBuf<T>& Fs, DBuf<T>& Us) {
   Fs.alloc(std::max<int64_t>(B.nF, 1));
   Us.alloc(std::max<int64_t>(B.nU, 1));
+  const size_t base = sizeof(double) * (std::max(2 * 64 * 32 + 32, B.maxnf) + 8);
   for (int h = 0; h <= B.maxh; ++h) {
     int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
-    KFactor<T> f{V, B.d_levels.p + B.level_ptr[h], Fs.p, Us.p, status.p};
-    launch(f, cnt, 256, sizeof(double) * (std::max(2 * 64 * 32 + 32, B.maxnf) + 8), b->stream);
+    int nfmax = 0;
+    for (int q = B.level_ptr[h]; q < B.level_ptr[h + 1]; ++q) {
+      const NodeDev& Nd = b->h_nodes[B.h_levels[q]];
+      nfmax = std::max(nfmax, Nd.np + Nd.nb);
+    }
+    // FP32 fronts with trailing blocks beyond 64 rows: tensor-core updates
+    if (std::is_same<T, float>::value && b->use_tc && nfmax > 96) {
+      const size_t off = (base + 127) / 128 * 128;
+      KFactor<float, true> f{V, B.d_levels.p + B.level_ptr[h], reinterpret_cast<float*>(Fs.p),
+                             reinterpret_cast<float*>(Us.p), status.p, off};
+      launch(f, cnt, 256, off + TC_SMEM_BYTES, b->stream);
+    } else {
+      KFactor<T> f{V, B.d_levels.p + B.level_ptr[h], Fs.p, Us.p, status.p};
+      launch(f, cnt, 256, base, b->stream);
+    }
   }
 }
 
@@ -1120,10 +1175,19 @@ static void factor_batch(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status
   else factor_batch_t<float>(b, B, V, status, B.F32, B.U32);
 }
 
+// captured graphs hold workspace addresses: drop them before a workspace
+// is reallocated (they are captured again on next use; a graph being
+// captured is not affected)
+static void invalidate_graphs(bddc* b) {
+  if (b->pcg_exec) { cudaGraphExecDestroy(b->pcg_exec); b->pcg_exec = nullptr; }
+  if (b->app_exec) { cudaGraphExecDestroy(b->app_exec); b->app_exec = nullptr; }
+}
+
 template <class T, int RB>
 static void sweep_batch_rb(bddc* b, Batch& B, const BddcView& V, const T* Fp, double* X, double* UV, int nrhs) {
   cudaStream_t st = b->stream;
   if (B.fv_nrhs < nrhs) {
+    invalidate_graphs(b);
     B.FV.alloc(std::max<int64_t>(B.nfv * nrhs, 1));
     B.fv_nrhs = nrhs;
   }
@@ -1178,12 +1242,29 @@ static void solve_batch(bddc* b, Batch& B, const BddcView& V, double* X, double*
   }
   cudaStream_t st = b->stream;
   const int64_t n = B.vec_n * nrhs;
-  if ((int64_t)B.XB.n < n) { B.XB.alloc(std::max<int64_t>(n, 1)); B.XR.alloc(std::max<int64_t>(n, 1)); }
+  if ((int64_t)B.XB.n < n) {
+    invalidate_graphs(b);
+    B.XB.alloc(std::max<int64_t>(n, 1));
+    B.XR.alloc(std::max<int64_t>(n, 1));
+  }
   VB_CUDA(cudaMemcpyAsync(B.XB.p, X, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   sweep_batch<float>(b, B, V, B.F32.p, X, UV, nrhs);
+  const int chunk = std::min(nrhs, 16);
+  if ((int64_t)B.YE.n < B.ye_n * chunk) {
+    invalidate_graphs(b);
+    B.YE.alloc(B.ye_n * chunk);
+  }
+  const size_t esm = sizeof(double) * 4 * (b->sys->nKmax + b->sys->dof.np);
   for (int it = 0; it < b->refine; ++it) {
-    launch(KProbResidual{V, B.d_mtask.p, B.XB.p, X, B.XR.p, b->d_mcon_ptr.p, b->d_mcon_vdof.p, b->d_mcon_coef.p,
-                         nrhs}, (int64_t)B.h_mtask.size(), 128, 0, st);
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+      const int nr = std::min(chunk, nrhs - r0);
+      if (nr >= 4)
+        launch(KElemProduct<4>{V, B.d_etask.p, X, B.YE.p, nrhs, r0, nr}, (int64_t)B.h_etask.size(), 128, esm, st);
+      else
+        launch(KElemProduct<1>{V, B.d_etask.p, X, B.YE.p, nrhs, r0, nr}, (int64_t)B.h_etask.size(), 128, esm, st);
+      launch(KGatherResidual{V, B.d_mtask.p, B.XB.p, X, B.YE.p, B.XR.p, b->d_mcon_ptr.p, b->d_mcon_vdof.p,
+                             b->d_mcon_coef.p, nrhs, r0, nr}, (int64_t)B.h_mtask.size(), 128, 0, st);
+    }
     sweep_batch<float>(b, B, V, B.F32.p, B.XR.p, UV, nrhs);
     launch(KAxpyN{B.XR.p, X, n}, (n + 255) / 256, 256, 0, st);
   }
@@ -1287,6 +1368,412 @@ static void lanczos(const std::vector<double>& al, const std::vector<double>& be
   lmax = kth(m - 1);
 }
 
+// ------------------------------------------------------- graph-captured PCG
+// Device scalars of the PCG loop
+enum { PS_RZ = 0, PS_RZN, PS_PAP, PS_ALPHA, PS_BETA, PS_NR2, PS_TOL, PS_IT, PS_MAXIT, PS_STATUS, PS_COUNT };
+// PS_STATUS: 0 running, 1 converged, 2 breakdown, 3 maxit reached
+
+// beta_{j-1} = (r_j, z_j) / (r_{j-1}, z_{j-1}) (0 at j = 0), recorded for Lanczos
+struct KPcgBeta {
+  double* s;
+  double* be;
+  __device__ void operator()(const KExec& ex, int) const {
+    if (ex.tid != 0) return;
+    const int it = (int)s[PS_IT];
+    const double rzn = s[PS_RZN];
+    double beta = 0.0;
+    if (it > 0) {
+      beta = rzn / s[PS_RZ];
+      be[it - 1] = beta;
+    }
+    s[PS_BETA] = beta;
+    s[PS_RZ] = rzn;
+  }
+};
+// p = z + beta p
+struct KPcgDirection {
+  const double* z;
+  double* p;
+  const double* s;
+  int64_t n;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    const double beta = s[PS_BETA];
+    const int64_t hi = (int64_t)(blk + 1) * 256 < n ? (int64_t)(blk + 1) * 256 : n;
+    for (int64_t i = (int64_t)blk * 256 + ex.tid; i < hi; i += ex.nt) p[i] = z[i] + beta * p[i];
+  }
+};
+// alpha = (r, z) / (p, K p), or breakdown when p^T K p <= 0 or non-finite
+struct KPcgAlpha {
+  double* s;
+  double* al;
+  __device__ void operator()(const KExec& ex, int) const {
+    if (ex.tid != 0) return;
+    const double pAp = s[PS_PAP], rz = s[PS_RZ];
+    if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(rz)) {
+      s[PS_STATUS] = 2.0;
+      s[PS_ALPHA] = 0.0;
+      return;
+    }
+    const double alpha = rz / pAp;
+    s[PS_ALPHA] = alpha;
+    al[(int)s[PS_IT]] = alpha;
+  }
+};
+// x += alpha p, r -= alpha K p (skipped after a breakdown)
+struct KPcgUpdate {
+  const double* p;
+  const double* Ap;
+  double* x;
+  double* r;
+  const double* s;
+  int64_t n;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    if (s[PS_STATUS] != 0.0) return;
+    const double alpha = s[PS_ALPHA];
+    const int64_t hi = (int64_t)(blk + 1) * 256 < n ? (int64_t)(blk + 1) * 256 : n;
+    for (int64_t i = (int64_t)blk * 256 + ex.tid; i < hi; i += ex.nt) {
+      x[i] = alpha * p[i] + x[i];
+      r[i] = -alpha * Ap[i] + r[i];
+    }
+  }
+};
+// iteration count, stop rule ||r_Gamma|| <= rtol ||r_Gamma,0|| (tolerance
+// pre-multiplied), maxit; sets the loop condition
+struct KPcgCheck {
+  double* s;
+  cudaGraphConditionalHandle h;
+  __device__ void operator()(const KExec& ex, int) const {
+    if (ex.tid != 0) return;
+    unsigned int more = 0;
+    if (s[PS_STATUS] == 0.0) {
+      const double it = s[PS_IT] + 1.0;
+      s[PS_IT] = it;
+      if (sqrt(s[PS_NR2]) <= s[PS_TOL]) s[PS_STATUS] = 1.0;
+      else if (it >= s[PS_MAXIT]) s[PS_STATUS] = 3.0;
+      else more = 1;
+    }
+    cudaGraphSetConditional(h, more);
+  }
+};
+
+static cudaStream_t capture_stream(bddc* b) {
+  if (!b->cap_stream) VB_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  return b->cap_stream;
+}
+
+// (a, b) -> s[slot], deterministic two-pass sum
+static void dot_to(bddc* b, const double* x, const double* y, int64_t n, double* out) {
+  launch(KDotPartial{x, y, n, b->part.p + b->part.n - 1024 - 1}, 1024, 256, sizeof(double) * 256, b->stream);
+  launch(KSumPartial{b->part.p + b->part.n - 1024 - 1, 1024, out}, 1, 256, sizeof(double) * 256, b->stream);
+}
+
+// ||r_Gamma||^2 (interface velocity and p_0 parts) -> out
+static void iface_norm2_to(bddc* b, const double* r, double* out) {
+  const BddcView V = make_view(b);
+  const int nmac = (int)b->h_macros.size();
+  const size_t msm = sizeof(double) * (3 * max_macro_n(b) + 256 + 8);
+  launch(KRestrict{V, r, b->rC.p, b->dwork.p, b->part.p}, nmac, 256, msm, b->stream);
+  launch(KRestrictP0{V, r, b->rC.p, b->part.p, nmac}, b->H.N, 256, sizeof(double) * 256, b->stream);
+  launch(KSumPartial{b->part.p, nmac + b->H.N, out}, 1, 256, sizeof(double) * 256, b->stream);
+}
+
+// one PCG iteration on (x, r, p) with the device scalars; same operations
+// and order as the host-driven loop
+static void pcg_body(bddc* b, cudaGraphConditionalHandle h) {
+  const int64_t n = b->sys->n;
+  const int nblk = (int)((n + 255) / 256);
+  double* s = b->pcg_s.p;
+  apply_bddc(b, b->r.p, b->z.p);
+  dot_to(b, b->r.p, b->z.p, n, s + PS_RZN);
+  launch(KPcgBeta{s, b->pcg_be.p}, 1, 32, 0, b->stream);
+  launch(KPcgDirection{b->z.p, b->p.p, s, n}, nblk, 256, 0, b->stream);
+  spmv(b->sys, b->p.p, b->Ap.p, b->stream);
+  dot_to(b, b->p.p, b->Ap.p, n, s + PS_PAP);
+  launch(KPcgAlpha{s, b->pcg_al.p}, 1, 32, 0, b->stream);
+  launch(KPcgUpdate{b->p.p, b->Ap.p, b->xg.p, b->r.p, s, n}, nblk, 256, 0, b->stream);
+  iface_norm2_to(b, b->r.p, s + PS_NR2);
+  launch(KPcgCheck{s, h}, 1, 32, 0, b->stream);
+}
+
+// Captures the PCG loop: a graph with one conditional while node whose body
+// is pcg_body (the condition starts at 1 on every launch)
+static void pcg_capture(bddc* b) {
+  if (b->pcg_exec) { VB_CUDA(cudaGraphExecDestroy(b->pcg_exec)); b->pcg_exec = nullptr; }
+  cudaGraph_t g = nullptr;
+  VB_CUDA(cudaGraphCreate(&g, 0));
+  cudaStream_t cs = capture_stream(b);
+  cudaStream_t saved = b->stream;
+  try {
+    cudaGraphConditionalHandle h;
+    VB_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    VB_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const int64_t l0 = g_launches.load();
+    VB_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    b->stream = cs;
+    try {
+      pcg_body(b, h);
+    } catch (...) {
+      cudaGraph_t tmp = nullptr;
+      cudaStreamEndCapture(cs, &tmp);
+      (void)cudaGetLastError();
+      throw;
+    }
+    b->stream = saved;
+    VB_CUDA(cudaStreamEndCapture(cs, &body));
+    b->pcg_body_launches = g_launches.load() - l0;
+    g_launches.fetch_sub(b->pcg_body_launches);   // counted when the graph runs
+    VB_CUDA(cudaGraphInstantiate(&b->pcg_exec, g, 0));
+  } catch (...) {
+    b->stream = saved;
+    cudaGraphDestroy(g);
+    throw;
+  }
+  cudaGraphDestroy(g);
+}
+
+// z = M^{-1} r through a captured graph (re-captured when r or z change)
+static void apply_graph(bddc* b, const double* r, double* z) {
+  if (!b->app_exec || b->app_r != r || b->app_z != z) {
+    if (b->app_exec) { VB_CUDA(cudaGraphExecDestroy(b->app_exec)); b->app_exec = nullptr; }
+    cudaStream_t cs = capture_stream(b);
+    cudaStream_t saved = b->stream;
+    cudaGraph_t g = nullptr;
+    const int64_t l0 = g_launches.load();
+    VB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    b->stream = cs;
+    try {
+      apply_bddc(b, r, z);
+    } catch (...) {
+      b->stream = saved;
+      cudaStreamEndCapture(cs, &g);
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      throw;
+    }
+    b->stream = saved;
+    VB_CUDA(cudaStreamEndCapture(cs, &g));
+    b->app_launches = g_launches.load() - l0;
+    g_launches.fetch_sub(b->app_launches);
+    cudaError_t e = cudaGraphInstantiate(&b->app_exec, g, 0);
+    cudaGraphDestroy(g);
+    VB_CUDA(e);
+    b->app_r = r;
+    b->app_z = z;
+  }
+  VB_CUDA(cudaGraphLaunch(b->app_exec, b->stream));
+  g_launches.fetch_add(b->app_launches);
+}
+
+// ------------------------------------------------ adaptive coarse space (S7)
+// Sec. 6.  For every macro face F with sides i, j and dual coordinates F_D:
+//   S~_s = (E^T K_rr^(s)-1 E)^-1 = M_s^-1 (E: the dual basis columns H e_c,
+//   K_rr the constrained Neumann matrix), so A = S~_i : S~_j = (M_i + M_j)^-1;
+//   B = S_i : S_j = S_j (S_i + S_j)^-1 S_i = S_j D_i (D_i the deluxe block).
+// A psi = lambda B psi is solved as G^T B G y = mu y with M_i + M_j = G G^T,
+// psi = G y and lambda = 1/mu; eigenvalues lambda < 1/theta (mu > theta) give
+// the new primal functionals B psi on F_D, which are mapped back to the
+// face's DOFs with H.  The eigenvector scaling differs from a B-normalised
+// one by a factor per vector, which leaves the primal space unchanged.
+struct AdaptTask {
+  int sub, macro, si, c0, ncol;
+  int64_t moff;
+};
+
+// column c of a task: H e_{r+c0+c} on the macro's DOFs, written at their
+// positions in the subdomain's Neumann problem (the rest of X is zero)
+struct KAdaptRhs {
+  BddcView V;
+  const AdaptTask* tasks;
+  double* X;
+  int nrhs;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    const AdaptTask tk = tasks[blk / nrhs];
+    const int c = blk % nrhs;
+    if (c >= tk.ncol) return;
+    const MacroDev G = V.macros[tk.macro];
+    const ProbDev P = V.probs[V.subs[tk.sub].neu];
+    double* v = ex.smem;
+    double* red = ex.smem + G.n;
+    for (int a = ex.tid; a < G.n; a += ex.nt) v[a] = a == G.r + tk.c0 + c ? 1.0 : 0.0;
+    ex.sync();
+    hh_par(ex, V, G, v, red);
+    const int* gp = V.gpos + G.gpos_off + (int64_t)tk.si * G.n;
+    for (int a = ex.tid; a < G.n; a += ex.nt) X[P.vec_off * nrhs + (int64_t)c * P.n + gp[a]] = v[a];
+  }
+};
+
+// column c0+c of M_s: the dual coordinates (H^T x)[r:] of the solution
+struct KAdaptGather {
+  BddcView V;
+  const AdaptTask* tasks;
+  const double* X;
+  double* M;
+  int nrhs;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    const AdaptTask tk = tasks[blk / nrhs];
+    const int c = blk % nrhs;
+    if (c >= tk.ncol) return;
+    const MacroDev G = V.macros[tk.macro];
+    const ProbDev P = V.probs[V.subs[tk.sub].neu];
+    double* v = ex.smem;
+    double* red = ex.smem + G.n;
+    const int* gp = V.gpos + G.gpos_off + (int64_t)tk.si * G.n;
+    for (int a = ex.tid; a < G.n; a += ex.nt) v[a] = X[P.vec_off * nrhs + (int64_t)c * P.n + gp[a]];
+    ex.sync();
+    hh_T_par(ex, V, G, v, red);
+    const int nd = G.n - G.r;
+    for (int k = ex.tid; k < nd; k += ex.nt) M[tk.moff + (int64_t)(tk.c0 + c) * nd + k] = v[G.r + k];
+  }
+};
+
+// N = M_i + M_j per face (items: a = M_i, b = M_j, c = N offsets)
+struct KAddPair {
+  const double* M;
+  double* Nout;
+  const DenseItem* items;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    const DenseItem it = items[blk];
+    const int64_t nn = (int64_t)it.n * it.n;
+    for (int64_t q = ex.tid; q < nn; q += ex.nt) Nout[it.c + q] = M[it.a + q] + M[it.b + q];
+  }
+};
+
+// Adaptive primal rows of every macro face (in the face's DOF order, one
+// functional of length n per row) into extra[macro]; returns the count
+static int adaptive_rows(bddc* b, std::vector<std::vector<double>>& extra) {
+  cudaStream_t st = b->stream;
+  const BddcView V = make_view(b);
+  const int nfc = (int)b->sf_faces.size();
+  extra.assign(b->h_macros.size(), {});
+  if (nfc == 0) return 0;
+  const int N = b->H.N;
+  constexpr int MAXSEL = 64;
+  std::vector<int> nd(nfc);
+  std::vector<int64_t> mi(nfc), mj(nfc), fo(nfc), yo(nfc);
+  int64_t mtot = 0, ftot = 0, ytot = 0;
+  int nmax = 1;
+  for (int t = 0; t < nfc; ++t) {
+    nd[t] = b->h_macros[b->sf_faces[t]].ndual;
+    const int64_t q = (int64_t)nd[t] * nd[t];
+    mi[t] = mtot;
+    mj[t] = mtot + q;
+    mtot += 2 * q;
+    fo[t] = ftot;
+    ftot += q;
+    yo[t] = ytot;
+    ytot += (int64_t)MAXSEL * nd[t];
+    nmax = std::max(nmax, b->h_macros[b->sf_faces[t]].n);
+  }
+  // ---- M_s = E^T K_rr^-1 E: multi-RHS Neumann solves, one face per
+  // subdomain at a time ("slots"), NCc dual columns per solve
+  DBuf<double> M(std::max<int64_t>(mtot, 1));
+  std::vector<std::vector<std::pair<int, int>>> sub_faces(N);
+  for (int t = 0; t < nfc; ++t) {
+    const Macro& G = b->H.macros[b->sf_faces[t]];
+    sub_faces[G.share[0]].push_back({t, 0});
+    sub_faces[G.share[1]].push_back({t, 1});
+  }
+  size_t nslot = 0;
+  for (auto& v : sub_faces) nslot = std::max(nslot, v.size());
+  constexpr int NCc = 32;
+  DBuf<double> X(std::max<int64_t>(b->bn.vec_n * NCc, 1)), UV(std::max<int64_t>(b->bn.uvec_n * NCc, 1));
+  DBuf<AdaptTask> dtasks;
+  const size_t asm_ = sizeof(double) * (nmax + 256);
+  for (size_t slot = 0; slot < nslot; ++slot) {
+    int maxnd = 0;
+    for (int i = 0; i < N; ++i)
+      if (slot < sub_faces[i].size()) maxnd = std::max(maxnd, nd[sub_faces[i][slot].first]);
+    for (int c0 = 0; c0 < maxnd; c0 += NCc) {
+      std::vector<AdaptTask> tasks;
+      for (int i = 0; i < N; ++i) {
+        if (slot >= sub_faces[i].size()) continue;
+        const auto [t, si] = sub_faces[i][slot];
+        if (c0 >= nd[t]) continue;
+        tasks.push_back({i, b->sf_faces[t], si, c0, std::min(NCc, nd[t] - c0), si == 0 ? mi[t] : mj[t]});
+      }
+      if (tasks.empty()) continue;
+      upload_vec(dtasks, tasks, st);
+      X.zero(st);
+      launch(KAdaptRhs{V, dtasks.p, X.p, NCc}, (int64_t)tasks.size() * NCc, 256, asm_, st);
+      solve_batch(b, b->bn, V, X.p, UV.p, NCc);
+      launch(KAdaptGather{V, dtasks.p, X.p, M.p, NCc}, (int64_t)tasks.size() * NCc, 256, asm_, st);
+    }
+  }
+  // ---- dense per-face steps
+  std::vector<DenseItem> it_add(nfc), it_b(nfc), it_f(nfc), it_t1(nfc), it_c(nfc), it_tri(nfc), it_rows(nfc);
+  std::vector<GemmTask> gt;
+  for (int t = 0; t < nfc; ++t) {
+    const MacroDev& G = b->h_macros[b->sf_faces[t]];
+    it_add[t] = {nd[t], mi[t], mj[t], fo[t]};                 // Nf = M_i + M_j
+    it_b[t] = {nd[t], b->sf_j[t], G.deluxe_off, fo[t]};       // Bf = S_j D_i
+    it_f[t] = {nd[t], fo[t], 0, 0};                           // in-place on one matrix
+    it_t1[t] = {nd[t], fo[t], fo[t], fo[t]};                  // T1 = Bf G ; Cf = G^T T1
+    it_tri[t] = {nd[t], fo[t], 2 * fo[t], fo[t]};             // Cf ; d/e (2n per face) ; tau
+    it_rows[t] = {nd[t], fo[t], fo[t], 0};                    // G (in Nf) ; Bf
+    const int ntl = (nd[t] + 63) / 64;
+    for (int ti = 0; ti < ntl; ++ti)
+      for (int tj = 0; tj < ntl; ++tj) gt.push_back({t, ti, tj});
+  }
+  DBuf<DenseItem> d_add, d_b, d_f, d_t1, d_tri, d_rows;
+  DBuf<GemmTask> d_gt;
+  upload_vec(d_add, it_add, st);
+  upload_vec(d_b, it_b, st);
+  upload_vec(d_f, it_f, st);
+  upload_vec(d_t1, it_t1, st);
+  upload_vec(d_tri, it_tri, st);
+  upload_vec(d_rows, it_rows, st);
+  upload_vec(d_gt, gt, st);
+  const int64_t ft = std::max<int64_t>(ftot, 1);
+  DBuf<double> Nf(ft), Bf(ft), T1(ft), Cf(ft), DE(2 * ft), TAU(ft), Y(std::max<int64_t>(ytot, 1)),
+      LAM((int64_t)nfc * MAXSEL);
+  DBuf<int> cnt(nfc), status(1);
+  status.zero(st);
+  const size_t gsm = sizeof(double) * 2 * 16 * 65;
+  launch(KAddPair{M.p, Nf.p, d_add.p}, nfc, 256, 0, st);
+  launch(KSymmetrize{Nf.p, d_f.p}, nfc, 256, 0, st);
+  launch(KBatchGemm{b->d_sf.p, b->d_deluxe.p, Bf.p, d_b.p, d_gt.p, 0, 1.0, 0.0}, (int64_t)gt.size(), 256, gsm, st);
+  launch(KSymmetrize{Bf.p, d_f.p}, nfc, 256, 0, st);
+  launch(KCholesky{Nf.p, d_f.p, status.p}, nfc, 256, 0, st);
+  launch(KBatchGemm{Bf.p, Nf.p, T1.p, d_t1.p, d_gt.p, 0, 1.0, 0.0}, (int64_t)gt.size(), 256, gsm, st);
+  launch(KBatchGemm{Nf.p, T1.p, Cf.p, d_t1.p, d_gt.p, 1, 1.0, 0.0}, (int64_t)gt.size(), 256, gsm, st);
+  launch(KSymmetrize{Cf.p, d_f.p}, nfc, 256, 0, st);
+  int ndmax = 1;
+  for (int t = 0; t < nfc; ++t) ndmax = std::max(ndmax, nd[t]);
+  launch(KTridiag{Cf.p, DE.p, TAU.p, d_tri.p}, nfc, 256, sizeof(double) * (2 * ndmax + 256), st);
+  DBuf<int64_t> d_yo;
+  upload_vec(d_yo, yo, st);
+  launch(KTridiagEig{Cf.p, DE.p, TAU.p, d_tri.p, b->adapt_theta, MAXSEL, cnt.p, LAM.p, Y.p, d_yo.p}, nfc, 256,
+         sizeof(double) * (4 * ndmax + 256 + MAXSEL), st);
+  launch(KConstraintRows{Nf.p, Bf.p, Y.p, d_yo.p, d_rows.p, cnt.p, MAXSEL}, nfc, 256, sizeof(double) * ndmax, st);
+  const auto stv = status.download(st);
+  VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "adaptive: sum of the face Neumann Schur complement inverses not SPD");
+  const auto hc = cnt.download(st);
+  const auto hy = Y.download(st);
+  int added = 0;
+  for (int t = 0; t < nfc; ++t) {
+    const int g = b->sf_faces[t];
+    const Macro& G = b->H.macros[g];
+    const int n = (int)G.dofs.size();
+    const int m = std::min(hc[t], MAXSEL);
+    std::vector<double> c(n), v(n);
+    for (int s2 = 0; s2 < m; ++s2) {
+      std::fill(c.begin(), c.end(), 0.0);
+      for (int k = 0; k < nd[t]; ++k) c[G.r + k] = hy[yo[t] + (int64_t)s2 * nd[t] + k];
+      hh_apply(G, c.data(), v.data());
+      extra[g].insert(extra[g].end(), v.begin(), v.end());
+      ++added;
+    }
+  }
+  return added;
+}
+
 }  // namespace vb
 
 using namespace vb;
@@ -1296,23 +1783,9 @@ static int bfail(const Error& e) {
   return e.status;
 }
 
-extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constraints, int scaling,
-                          const bddc_options* opts, bddc** out) {
-  if (!s || !part || !out) { set_last_error("bddc_setup: null argument"); return VEM_EINVAL; }
-  *out = nullptr;
-  bddc* b = new bddc();
-  try {
-    b->sys = s;
-    b->stream = s->stream;
-    b->opt.constraints = constraints;
-    b->opt.scaling = scaling;
-    if (opts && opts->nd_leaf > 0) b->opt.leaf = opts->nd_leaf;
-    if (opts) {
-      VB_CHECK(opts->precision >= 0 && opts->precision <= 2, VEM_EINVAL, "bddc_options.precision must be 0, 1 or 2");
-      b->prec = opts->precision;
-      VB_CHECK(opts->refine >= 0 && opts->refine <= 4, VEM_EINVAL, "bddc_options.refine must be 0..4");
-      if (opts->refine > 0) b->refine = opts->refine;
-    }
+// the whole numeric and symbolic setup of one handle (options already set)
+static void setup_core(bddc* b, const int32_t* part) {
+    vem_system* s = b->sys;
     cudaStream_t st = b->stream;
     BddcHost& H = b->H;
     auto t0 = std::chrono::steady_clock::now();
@@ -1682,6 +2155,12 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
       mark("t_deluxe_combine_ms");
       auto stv = status.download(st);
       VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe: face Schur complement sum not positive definite");
+      if (b->keep_sf) {
+        b->d_sf = std::move(SD);
+        b->sf_faces = faces;
+        b->sf_i = sd_i;
+        b->sf_j = sd_j;
+      }
     }
     upload_vec(b->d_macros, b->h_macros, st);
     V = make_view(b);
@@ -1726,12 +2205,18 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
       upload_vec(drp, rp, st);
       launch(KElemMatvec{V, drp.p, N, dW.p, KW.p, NC}, loc, 32, 0, st);
       mark("t_coarse_rhs_ms");
-      b->XN.alloc(std::max<int64_t>(b->bn.vec_n * NC, 1));
-      b->UVN.alloc(std::max<int64_t>(b->bn.uvec_n * NC, 1));
-      launch(KNeuRhsPhi{V, KW.p, b->XN.p, NC}, (int64_t)N * NC, 256, sizeof(double) * 256, st);
-      solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, NC);
+      // constrained Neumann solves for the coarse basis, CH columns at a time
+      // (the right-hand-side, front-vector and refinement stores scale with CH)
+      const int CH = std::min(NC, 64);
+      b->XN.alloc(std::max<int64_t>(b->bn.vec_n * CH, 1));
+      b->UVN.alloc(std::max<int64_t>(b->bn.uvec_n * CH, 1));
+      for (int c0 = 0; c0 < NC; c0 += CH) {
+        const int ch = std::min(CH, NC - c0);
+        launch(KNeuRhsPhi{V, KW.p, b->XN.p, NC, c0, ch}, (int64_t)N * ch, 256, sizeof(double) * 256, st);
+        solve_batch(b, b->bn, V, b->XN.p, b->UVN.p, ch);
+        launch(KPhiAssemble{V, dW.p, b->XN.p, PHI.p, NC, c0, ch}, (int64_t)N * ch, 256, sizeof(double) * 256, st);
+      }
       mark("t_coarse_solves_ms");
-      launch(KPhiAssemble{V, dW.p, b->XN.p, PHI.p, NC}, (int64_t)N * NC, 256, sizeof(double) * 256, st);
       launch(KElemMatvec{V, drp.p, N, PHI.p, KW.p, NC}, loc, 32, 0, st);
       DBuf<double> SG((size_t)N * NC * NC);
       launch(KGram{V, PHI.p, KW.p, SG.p, NC}, N, 256, 0, st);
@@ -1817,6 +2302,58 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
     b->Ap.alloc(s->n);
     b->scal.alloc(4);
     VB_CUDA(cudaStreamSynchronize(st));
+}
+
+// options of bddc_setup into a fresh handle
+static void configure(bddc* b, vem_system* s, uint32_t constraints, int scaling, const bddc_options* opts) {
+  b->sys = s;
+  b->stream = s->stream;
+  b->opt.constraints = constraints;
+  b->opt.scaling = scaling;
+  if (!opts) return;
+  if (opts->nd_leaf > 0) b->opt.leaf = opts->nd_leaf;
+  VB_CHECK(opts->use_graph >= -1 && opts->use_graph <= 1, VEM_EINVAL, "bddc_options.use_graph must be -1, 0 or 1");
+  b->use_graph = opts->use_graph >= 0;
+  VB_CHECK(opts->precision >= 0 && opts->precision <= 2, VEM_EINVAL, "bddc_options.precision must be 0, 1 or 2");
+  b->prec = opts->precision;
+  VB_CHECK(opts->refine >= 0 && opts->refine <= 4, VEM_EINVAL, "bddc_options.refine must be 0..4");
+  if (opts->refine > 0) b->refine = opts->refine;
+  VB_CHECK(opts->tc_update >= -1 && opts->tc_update <= 1, VEM_EINVAL, "bddc_options.tc_update must be -1, 0 or 1");
+  b->use_tc = opts->tc_update >= 0;
+  VB_CHECK(opts->adaptive_threshold >= 0.0, VEM_EINVAL, "bddc_options.adaptive_threshold must be >= 0");
+  b->adapt_theta = opts->adaptive_threshold;
+}
+
+extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constraints, int scaling,
+                          const bddc_options* opts, bddc** out) {
+  if (!s || !part || !out) { set_last_error("bddc_setup: null argument"); return VEM_EINVAL; }
+  *out = nullptr;
+  bddc* b = new bddc();
+  try {
+    configure(b, s, constraints, scaling, opts);
+    const bool adaptive = b->adapt_theta > 0.0 && scaling == BDDC_SCALING_DELUXE && !(constraints & BDDC_ALL);
+    b->keep_sf = adaptive;
+    setup_core(b, part);
+    if (adaptive) {
+      // Sec. 6: eigenvector-based primal rows per macro face, then the whole
+      // setup again with the enlarged primal space
+      auto t0 = std::chrono::steady_clock::now();
+      std::vector<std::vector<double>> extra;
+      const int added = adaptive_rows(b, extra);
+      const double t_eig = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      std::vector<std::pair<std::string, double>> t1 = b->times;
+      if (added > 0) {
+        delete b;
+        b = nullptr;
+        b = new bddc();
+        configure(b, s, constraints, scaling, opts);
+        b->opt.extra = std::move(extra);
+        setup_core(b, part);
+        for (auto& pr : t1) b->times.push_back({"first_" + pr.first, pr.second});
+      }
+      b->times.push_back({"t_adaptive_eig_ms", t_eig});
+      b->n_adaptive = added;
+    }
     *out = b;
     return VEM_OK;
   } catch (const Error& e) {
@@ -1832,7 +2369,8 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
 extern "C" int bddc_apply(bddc* b, const double* r, double* z) {
   if (!b || !r || !z) { set_last_error("bddc_apply: null argument"); return VEM_EINVAL; }
   try {
-    apply_bddc(b, r, z);
+    if (b->use_graph) apply_graph(b, r, z);
+    else apply_bddc(b, r, z);
     return VEM_OK;
   } catch (const Error& e) {
     return bfail(e);
@@ -1842,6 +2380,7 @@ extern "C" int bddc_apply(bddc* b, const double* r, double* z) {
 extern "C" int pcg_solve(bddc* b, const double* f, double* u, double rtol, int maxit, int* iters, double* kappa,
                          double* lam_min, double* lam_max) {
   if (!b || !f || !u) { set_last_error("pcg_solve: null argument"); return VEM_EINVAL; }
+  if (maxit < 0) { set_last_error("pcg_solve: maxit < 0"); return VEM_EINVAL; }
   try {
     vem_system* s = b->sys;
     const int64_t n = s->n;
@@ -1849,19 +2388,56 @@ extern "C" int pcg_solve(bddc* b, const double* f, double* u, double rtol, int m
     const BddcView V = make_view(b);
     const int N = b->H.N;
     const int nblk = (int)((n + 255) / 256);
+    // the graph form iterates on a private copy of u (its addresses are
+    // captured once per handle)
+    if (b->use_graph && (int64_t)b->xg.n != n) { invalidate_graphs(b); b->xg.alloc(n); }
+    double* x = b->use_graph ? b->xg.p : u;
     // x0: interior Dirichlet solves, zero interface data
-    VB_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, st));
+    VB_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
     launch(KDirRhs{V, f, 1.0, b->XD.p}, N, 256, sizeof(double) * 256, st);
     solve_batch(b, b->bd, V, b->XD.p, b->UVD.p, 1);
-    launch(KDirOut{V, b->XD.p, nullptr, u}, N, 256, sizeof(double) * 256, st);
-    spmv(s, u, b->Ap.p, st);
+    launch(KDirOut{V, b->XD.p, nullptr, x}, N, 256, sizeof(double) * 256, st);
+    spmv(s, x, b->Ap.p, st);
     launch(KSub{f, b->Ap.p, b->r.p, n}, nblk, 256, 0, st);
     const double n0 = iface_norm(b, b->r.p);
     const double nf = std::sqrt(dot(b, f, f, n));
     std::vector<double> al, be;
     int it = 0;
     int status = VEM_OK;
-    if (n0 > 1e-14 * nf) {
+    if (n0 > 1e-14 * nf && maxit == 0) {
+      status = VEM_ENOTCONV;
+    } else if (n0 > 1e-14 * nf && b->use_graph) {
+      // the whole loop as one graph launch: a conditional while node runs
+      // one iteration per pass until the device-side stop rule clears it
+      if (b->pcg_cap < maxit || !b->pcg_exec) {
+        if (b->pcg_cap < maxit || !b->pcg_s.p) {
+          invalidate_graphs(b);
+          b->pcg_cap = std::max(maxit, 64);
+          b->pcg_al.alloc(b->pcg_cap);
+          b->pcg_be.alloc(b->pcg_cap);
+          b->pcg_s.alloc(PS_COUNT);
+        }
+        pcg_capture(b);
+      }
+      double hs[PS_COUNT] = {};
+      hs[PS_TOL] = rtol * n0;
+      hs[PS_MAXIT] = maxit;
+      VB_CUDA(cudaMemcpyAsync(b->pcg_s.p, hs, sizeof hs, cudaMemcpyHostToDevice, st));
+      VB_CUDA(cudaMemsetAsync(b->p.p, 0, sizeof(double) * n, st));
+      VB_CUDA(cudaGraphLaunch(b->pcg_exec, st));
+      VB_CUDA(cudaMemcpyAsync(hs, b->pcg_s.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+      VB_CUDA(cudaStreamSynchronize(st));
+      it = (int)hs[PS_IT];
+      const int ps = (int)hs[PS_STATUS];
+      status = ps == 1 ? VEM_OK : (ps == 2 ? VEM_EBREAKDOWN : VEM_ENOTCONV);
+      g_launches.fetch_add(b->pcg_body_launches * (it + (ps == 2 ? 1 : 0)));
+      al.resize(it);
+      be.resize(it > 0 ? it - 1 : 0);
+      if (it > 0) VB_CUDA(cudaMemcpyAsync(al.data(), b->pcg_al.p, sizeof(double) * it, cudaMemcpyDeviceToHost, st));
+      if (it > 1) VB_CUDA(cudaMemcpyAsync(be.data(), b->pcg_be.p, sizeof(double) * (it - 1), cudaMemcpyDeviceToHost, st));
+      VB_CUDA(cudaStreamSynchronize(st));
+    } else if (n0 > 1e-14 * nf) {
+      // host-driven loop: the scalars come back to the host every iteration
       apply_bddc(b, b->r.p, b->z.p);
       VB_CUDA(cudaMemcpyAsync(b->p.p, b->z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
       double rz = dot(b, b->r.p, b->z.p, n);
@@ -1871,7 +2447,7 @@ extern "C" int pcg_solve(bddc* b, const double* f, double* u, double rtol, int m
         const double pAp = dot(b, b->p.p, b->Ap.p, n);
         if (!(pAp > 0.0) || !std::isfinite(pAp) || !std::isfinite(rz)) { status = VEM_EBREAKDOWN; break; }
         const double alpha = rz / pAp;
-        launch(KAxpby{b->p.p, u, alpha, 1.0, n}, nblk, 256, 0, st);
+        launch(KAxpby{b->p.p, x, alpha, 1.0, n}, nblk, 256, 0, st);
         launch(KAxpby{b->Ap.p, b->r.p, -alpha, 1.0, n}, nblk, 256, 0, st);
         ++it;
         al.push_back(alpha);
@@ -1885,6 +2461,7 @@ extern "C" int pcg_solve(bddc* b, const double* f, double* u, double rtol, int m
         launch(KAxpby{b->z.p, b->p.p, 1.0, beta, n}, nblk, 256, 0, st);
       }
     }
+    if (x != u) VB_CUDA(cudaMemcpyAsync(u, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     double lmin = 1.0, lmax = 1.0;
     lanczos(al, be, lmin, lmax);
     if (iters) *iters = it;
@@ -1926,6 +2503,7 @@ extern "C" int bddc_info(bddc* b, const char* key, double* value) {
   else if (k == "coarse_bytes") *value = 8.0 * b->d_Kinv.n;
   else if (k == "n_front_max") *value = std::max(b->bd.maxnf, b->bn.maxnf);
   else if (k == "precision") *value = b->prec;
+  else if (k == "n_adaptive") *value = b->n_adaptive;
   else {
     for (auto& pr : b->times)
       if (pr.first == k) {

@@ -349,6 +349,12 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
       if (o.constraints & 4)
         for (int c = 0; c < 3; ++c) { A.insert(A.end(), comp[c].begin(), comp[c].end()); m++; }
       if (o.constraints & 8) { A.insert(A.end(), flux.begin(), flux.end()); m++; }
+      const size_t gi = H.macros.size();
+      if (gi < o.extra.size() && !o.extra[gi].empty()) {
+        VB_CHECK(o.extra[gi].size() % (size_t)n == 0, VEM_EINVAL, "adaptive rows do not match the macro face");
+        A.insert(A.end(), o.extra[gi].begin(), o.extra[gi].end());
+        m += (int)(o.extra[gi].size() / n);
+      }
       householder(n, m, A, G, 1e-10);
     }
     H.macros.push_back(std::move(G));

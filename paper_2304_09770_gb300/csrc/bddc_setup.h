@@ -81,6 +81,9 @@ struct SetupOptions {
   uint32_t constraints = 0xF;    // 1 vertex, 2 edge, 4 face, 8 flux; 16 all-interface-primal
   int scaling = 1;               // 0 multiplicity, 1 deluxe on faces
   int leaf = 4;                  // elements per nested-dissection leaf
+  // adaptive primal rows (Sec. 6) per macro index: concatenated functionals
+  // over the macro's DOFs (its dofs order), appended to the face constraints
+  std::vector<std::vector<double>> extra;
 };
 
 void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOptions& o, BddcHost& H,

@@ -782,23 +782,46 @@ struct ElemBuilder {
       }
     }
     ex.sync();
-    // (8) P = I - Dm PiN
-    for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
-      int r = idx / nK, c = idx % nK;
-      double acc = (r == c) ? 1.0 : 0.0;
-      for (int q = 0; q < nb; ++q) acc -= Dm[(size_t)r * nb + q] * PiN[(size_t)q * nK + c];
-      Pm[idx] = acc;
+    // (8)-(9) A = nu (Ac + P^T diag(s) P), s_i = max(Ac_ii, h_K), with
+    // P = I - X, X = Dm PiN of rank nb, through the low-rank expansion
+    //   P^T S P = S - F PiN - (F PiN)^T + PiN^T W PiN,  F = S Dm, W = Dm^T F
+    // (F: nK x nb and G = W PiN: nb x nK, row-major, in the Pm scratch)
+    double* F = Pm;
+    double* W = Pm + (size_t)nK * nb;
+    double* G = W + (size_t)nb * nb;
+    for (int idx = ex.tid; idx < nK * nb; idx += ex.nt) {
+      const int r = idx / nb;
+      const double sr = Ac[(size_t)r * nK + r];
+      F[idx] = (sr > hK ? sr : hK) * Dm[idx];
     }
     ex.sync();
-    // (9) A = nu (Ac + P^T diag(s) P), s_i = max(Ac_ii, h_K)
+    for (int idx = ex.tid; idx < nb * nb; idx += ex.nt) {
+      const int a = idx / nb, bq = idx % nb;
+      double acc = 0.0;
+      for (int q = 0; q < nK; ++q) acc += Dm[(size_t)q * nb + a] * F[(size_t)q * nb + bq];
+      W[idx] = acc;
+    }
+    ex.sync();
+    for (int idx = ex.tid; idx < nb * nK; idx += ex.nt) {
+      const int a = idx / nK, c = idx % nK;
+      double acc = 0.0;
+      for (int bq = 0; bq < nb; ++bq) acc += W[(size_t)a * nb + bq] * PiN[(size_t)bq * nK + c];
+      G[idx] = acc;
+    }
+    ex.sync();
     for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
-      int r = idx / nK, c = idx % nK;
+      const int r = idx / nK, c = idx % nK;
       if (r > c) continue;
       double acc = 0.0;
-      for (int q = 0; q < nK; ++q) {
-        double s = Ac[(size_t)q * nK + q];
-        s = s > hK ? s : hK;
-        acc += Pm[(size_t)q * nK + r] * s * Pm[(size_t)q * nK + c];
+      if (r == c) {
+        const double sr = Ac[(size_t)r * nK + r];
+        acc = sr > hK ? sr : hK;
+      }
+      const double* fr = F + (size_t)r * nb;
+      const double* fc = F + (size_t)c * nb;
+      for (int q = 0; q < nb; ++q) {
+        const double pr = PiN[(size_t)q * nK + r], pc = PiN[(size_t)q * nK + c];
+        acc += pr * G[(size_t)q * nK + c] - fr[q] * pc - fc[q] * pr;
       }
       double v = nu * (Ac[idx] + acc);
       Aout[(size_t)r * nK + c] = v;

@@ -29,7 +29,7 @@ struct KExec {
 #ifdef __CUDACC__
 template <class F>
 __global__ void k_run(const F f) {
-  extern __shared__ double vb_smem[];
+  extern __shared__ __align__(16) double vb_smem[];
   f(KExec{(int)threadIdx.x, (int)blockDim.x, vb_smem}, (int)blockIdx.x);
 }
 

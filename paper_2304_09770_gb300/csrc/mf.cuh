@@ -11,6 +11,9 @@
 #include "launch.h"
 #include "bddc_dev.h"
 #include "bddc_setup.h"
+#include "tc.cuh"
+
+#include <type_traits>
 
 namespace vb {
 
@@ -25,6 +28,56 @@ VB_HD inline int front_index(const NodeDev& N, const int* bord, int x) {
   return bord[lo] == x ? N.np + lo : -1;
 }
 
+// Trailing update of one panel (columns jb .. jb+nbk-1, rows and columns from
+// c0 on, m of them) on the tensor cores: lower tiles (ti >= tk) of 128 x 128;
+// each tile stages L (rows of the tile) and L D (its columns) as TF32 pairs,
+// runs the 3xTF32 product into TMEM and subtracts it from the front
+// (pivot columns in the panel, the rest in the update matrix).
+__device__ inline bool tc_trailing_update(const KExec& ex, TcCtx& c, float* pan, float* upd, int np, int nb, int ld,
+                                          int nf, int jb, int nbk, int c0, int m, const float* sd) {
+  float* Ahi = c.tiles;
+  float* Alo = c.tiles + TC_TILE_FLOATS;
+  float* Bhi = c.tiles + 2 * TC_TILE_FLOATS;
+  float* Blo = c.tiles + 3 * TC_TILE_FLOATS;
+  const int nt = (m + TC_M - 1) / TC_M;
+  const int w = ex.tid >> 5, lane = ex.tid & 31;
+  const int rowblk = w & 3, colhalf = w >> 2;   // 8 warps: 4 lane groups x 2 column halves
+  for (int tk = 0; tk < nt; ++tk)
+    for (int ti = tk; ti < nt; ++ti) {
+      const int k0 = c0 + tk * TC_N, i0 = c0 + ti * TC_M;
+      for (int q = ex.tid; q < TC_M * TC_K; q += ex.nt) {
+        const int col = q / TC_M, mm = q % TC_M;
+        const int o = tc_off(mm, col);
+        const float x = (col < nbk && i0 + mm < nf) ? pan[(int64_t)(jb + col) * ld + i0 + mm] : 0.0f;
+        const float xh = tc_tf32(x);
+        Ahi[o] = xh;
+        Alo[o] = x - xh;
+        const float y = (col < nbk && k0 + mm < nf) ? pan[(int64_t)(jb + col) * ld + k0 + mm] * sd[col] : 0.0f;
+        const float yh = tc_tf32(y);
+        Bhi[o] = yh;
+        Blo[o] = y - yh;
+      }
+      if (!tc_product(ex, c)) return false;
+      const int i = i0 + rowblk * 32 + lane;
+      for (int cc = 0; cc < 2; ++cc) {
+        float v[32];
+        tc_ld32(c.taddr + ((uint32_t)(rowblk * 32) << 16) + (uint32_t)(colhalf * 64 + cc * 32), v);
+        const int kb = k0 + colhalf * 64 + cc * 32;
+        if (i < nf)
+          for (int q = 0; q < 32; ++q) {
+            const int k = kb + q;
+            if (k >= nf || i < k) continue;
+            if (k < np) pan[(int64_t)k * ld + i] -= v[q];
+            else upd[(int64_t)(k - np) * nb + (i - np)] -= v[q];
+          }
+      }
+      tc_fence_before();
+      ex.sync();
+      tc_fence_after();
+    }
+  return true;
+}
+
 // Blocked right-looking partial LDL^T of one dense front (panel nf x np and
 // update block nb x nb, column-major, lower triangles), followed by the
 // in-place inversion of the unit lower diagonal block L11.  piv_type (may be
@@ -32,7 +85,7 @@ VB_HD inline int front_index(const NodeDev& N, const int* bord, int x) {
 // positive; pressure and multiplier negative); a violation sets status 3.
 template <class T>
 VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, int ld, const int* piv_type,
-                             int* status) {
+                             int* status, TcCtx* tc = nullptr) {
     const int nf = np + nb;
     // blocked right-looking partial LDL^T: panels of NBK columns, then a
     // rank-NBK update of the trailing front in TT x TT tiles staged in
@@ -66,6 +119,15 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, in
       if (m <= 0) continue;
       for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = pan[(int64_t)(jb + jj) * ld + jb + jj];
       ex.sync();
+#ifdef __CUDA_ARCH__
+      if constexpr (std::is_same<T, float>::value) {
+        if (tc && m > TT) {
+          // tensor-core tiles (3xTF32, 128 x 128, accumulators in TMEM)
+          if (!tc_trailing_update(ex, *tc, pan, upd, np, nb, ld, nf, jb, nbk, c0, m, sd)) return;
+          continue;
+        }
+      }
+#endif
       const int ntile = (m + TT - 1) / TT;
       for (int tk = 0; tk < ntile; ++tk)
         for (int ti = tk; ti < ntile; ++ti) {
@@ -116,14 +178,29 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, in
     }
 }
 
-template <class T>
+template <class T, bool UseTC = false>
 struct KFactor {
   BddcView V;
   const int* list;
   T* F;
   T* U;
   int* status;
-  VB_HD void operator()(const KExec& ex, int blk) const {
+  size_t tc_smem_off = 0;   // UseTC: byte offset of the tensor-core tiles in shared memory
+  __device__ void operator()(const KExec& ex, int blk) const {
+    if constexpr (UseTC) {
+      TcCtx c;
+      c.tiles = reinterpret_cast<float*>(reinterpret_cast<char*>(ex.smem) + tc_smem_off);
+      c.mbar = reinterpret_cast<uint64_t*>(c.tiles + 4 * TC_TILE_FLOATS);
+      c.taddr_slot = reinterpret_cast<uint32_t*>(c.mbar + 1);
+      c.status = status;
+      tc_init(ex, c);
+      body(ex, blk, &c);
+      tc_release(ex, c);
+      return;
+    }
+    body(ex, blk, nullptr);
+  }
+  __device__ void body(const KExec& ex, int blk, TcCtx* tc) const {
     const int t = list[blk];
     const NodeDev N = V.nodes[t];
     const ProbDev P = V.probs[N.prob];
@@ -223,7 +300,7 @@ struct KFactor {
       }
       ex.sync();
     }
-    front_ldlt<T>(ex, pan, upd, np, nb, ld, V.dtype + P.pos_off + N.p0, status);
+    front_ldlt<T>(ex, pan, upd, np, nb, ld, V.dtype + P.pos_off + N.p0, status, tc);
   }
 };
 
@@ -321,6 +398,8 @@ VB_HD inline void vload(const float* p, float* o) {
 // columns so that each lane keeps several 16-byte loads in flight.
 constexpr int FVEC = 32;
 constexpr int FWARPS = 8;
+// backward tasks: each warp takes BCOL adjacent columns at a time
+constexpr int BCOL = 4;
 
 // rows [i0, i0+W) of L[.][k] * x_k accumulated for k in [ka, kb); entries
 // with row <= k (diagonal block of the unit lower inverse) skipped when
@@ -501,6 +580,47 @@ VB_HD inline void col_dot(const T* c, int b0, int lo, int hi, const T* xs, int x
   }
 }
 
+// NC adjacent columns at once (column u at c + u*ld, u < ncol): per column
+// the sum over rows [lo[u], hi) of c_u[row] * x[row], lanes striding over
+// W-row vectors from the aligned row b0.  x is staged in shared memory from
+// row b0 on (xs[r*xld + row - b0], zero past hi), so each factor vector meets
+// one aligned shared-memory vector load per right-hand side; rows below
+// lo[u] are masked only in the vectors that reach below lo_max = max lo[u].
+template <class T, int RB, int NC>
+__device__ inline void col_dot_n(const T* c, int64_t ld, int ncol, int b0, int lo_max, const int* lo, int hi,
+                                 const T* xs, int xld, int lane, T (*acc)[RB]) {
+  constexpr int W = VecW<T>::W;
+  const int nvec = hi > b0 ? (hi - b0 + W - 1) / W : 0;
+#pragma unroll 2
+  for (int q = lane; q < nvec; q += 32) {
+    T v[NC][W];
+#pragma unroll
+    for (int u = 0; u < NC; ++u)
+      if (u < ncol) vload(c + u * ld + W * q, v[u]);
+    T xv[RB][W];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) vload(xs + r * xld + W * q, xv[r]);
+    const int rb = b0 + W * q;
+    if (rb < lo_max) {
+#pragma unroll
+      for (int u = 0; u < NC; ++u)
+#pragma unroll
+        for (int jj = 0; jj < W; ++jj)
+          if (u < ncol && rb + jj >= lo[u])
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[u][r] += v[u][jj] * xv[r][jj];
+    } else {
+#pragma unroll
+      for (int u = 0; u < NC; ++u)
+        if (u < ncol)
+#pragma unroll
+          for (int jj = 0; jj < W; ++jj)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[u][r] += v[u][jj] * xv[r][jj];
+    }
+  }
+}
+
 // backward (1): t_j = y_j / d_j - sum_border L21[i][j] x_i for a task of
 // pivot columns (one warp per column, lanes along W-row vectors)
 template <class T, int RB>
@@ -521,26 +641,39 @@ struct KBwdBorder {
     const int a0 = (np / W) * W;
     const T* pan = F + N.panel_off;
     const int* bord = V.border + N.border_off;
-    T* xb = reinterpret_cast<T*>(ex.smem);   // [RB][nb]
+    // border values staged from the aligned row a0: xb[r*xld + row - a0],
+    // zero for the pivot rows below np and past nf
+    const int xld = ((nf - a0 + W - 1) / W) * W;
+    T* xb = reinterpret_cast<T*>(ex.smem);   // [RB][xld]
     const int ws = ex.nt >= 32 ? 32 : 1;
     const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
-      for (int q = ex.tid; q < RB * nb; q += ex.nt) {
-        const int r = q / nb, i = q % nb;
-        xb[q] = r < nr ? (T)X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + bord[i]] : (T)0;
+      for (int q = ex.tid; q < RB * xld; q += ex.nt) {
+        const int r = q / xld, row = a0 + q % xld;
+        xb[q] = (r < nr && row >= np && row < nf)
+                    ? (T)X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + bord[row - np]] : (T)0;
       }
       ex.sync();
-      for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
-        T acc[RB];
-        for (int r = 0; r < RB; ++r) acc[r] = (T)0;
-        col_dot<T, RB>(pan + (int64_t)j * ld + a0, a0, np, nf, xb, nb, np, lane, ws, acc);
-        const double dj = (double)pan[(int64_t)j * ld + j];
-        for (int r = 0; r < nr; ++r) {
-          const double t = (double)warp_sum(acc[r]);
-          if (lane == 0)
-            TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] =
-                X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] / dj - t;
+      const int jend = tk.start + tk.count;
+      for (int j0 = tk.start + BCOL * w; j0 < jend; j0 += BCOL * nw) {
+        const int ncol = jend - j0 < BCOL ? jend - j0 : BCOL;
+        T acc[BCOL][RB];
+        int lo[BCOL];
+        for (int u = 0; u < BCOL; ++u) {
+          lo[u] = np;
+          for (int r = 0; r < RB; ++r) acc[u][r] = (T)0;
+        }
+        col_dot_n<T, RB, BCOL>(pan + (int64_t)j0 * ld + a0, ld, ncol, a0, a0, lo, nf, xb, xld, lane, acc);
+        for (int u = 0; u < ncol; ++u) {
+          const int j = j0 + u;
+          const double dj = (double)pan[(int64_t)j * ld + j];
+          for (int r = 0; r < nr; ++r) {
+            const double t = (double)warp_sum(acc[u][r]);
+            if (lane == 0)
+              TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] =
+                  X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] / dj - t;
+          }
         }
       }
       ex.sync();
@@ -566,27 +699,41 @@ struct KBwdPivots {
     const ProbDev P = V.probs[N.prob];
     const int np = N.np, nf = N.np + N.nb, ld = N.ld;
     const T* pan = F + N.panel_off;
-    const int L = np - tk.start;   // rows tk.start..np-1 staged
+    // rows tk.start..np-1 staged from the aligned row bs: ts[r*L + row - bs],
+    // zero below tk.start and past np
+    const int bs = (tk.start / W) * W;
+    const int L = ((np - bs + W - 1) / W) * W;
     T* ts = reinterpret_cast<T*>(ex.smem);   // [RB][L]
     const int ws = ex.nt >= 32 ? 32 : 1;
     const int nw = ex.nt / ws, w = ex.tid / ws, lane = ex.tid % ws;
     for (int r0 = 0; r0 < nrhs; r0 += RB) {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
       for (int q = ex.tid; q < RB * L; q += ex.nt) {
-        const int r = q / L, i = q % L;
-        ts[q] = r < nr ? (T)TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + tk.start + i] : (T)0;
+        const int r = q / L, row = bs + q % L;
+        ts[q] = (r < nr && row >= tk.start && row < np)
+                    ? (T)TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + row] : (T)0;
       }
       ex.sync();
-      for (int j = tk.start + w; j < tk.start + tk.count; j += nw) {
-        const int b0 = ((j + 1) / W) * W;
-        T acc[RB];
-        for (int r = 0; r < RB; ++r) acc[r] = (T)0;
-        col_dot<T, RB>(pan + (int64_t)j * ld + b0, b0, j + 1, np, ts, L, tk.start, lane, ws, acc);
-        for (int r = 0; r < nr; ++r) {
-          const double t = (double)warp_sum(acc[r]);
-          if (lane == 0)
-            X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] =
-                TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] + t;
+      const int jend = tk.start + tk.count;
+      for (int j0 = tk.start + BCOL * w; j0 < jend; j0 += BCOL * nw) {
+        const int ncol = jend - j0 < BCOL ? jend - j0 : BCOL;
+        const int b0 = ((j0 + 1) / W) * W;
+        T acc[BCOL][RB];
+        int lo[BCOL];
+        for (int u = 0; u < BCOL; ++u) {
+          lo[u] = j0 + u + 1;
+          for (int r = 0; r < RB; ++r) acc[u][r] = (T)0;
+        }
+        col_dot_n<T, RB, BCOL>(pan + (int64_t)j0 * ld + b0, ld, ncol, b0, j0 + ncol, lo, np, ts + (b0 - bs), L,
+                               lane, acc);
+        for (int u = 0; u < ncol; ++u) {
+          const int j = j0 + u;
+          for (int r = 0; r < nr; ++r) {
+            const double t = (double)warp_sum(acc[u][r]);
+            if (lane == 0)
+              X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] =
+                  TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] + t;
+          }
         }
       }
       ex.sync();
@@ -594,31 +741,102 @@ struct KBwdPivots {
   }
 };
 
-// residual of a local problem in FP64: R = B - K_q Z over the problem
-// positions (velocity rows from the element matrices, pressure rows from
-// B_K, multiplier rows from the constraint functionals); tasks of up to
-// TASK positions of one problem
+// Residual of a local problem in FP64, R = B - K_q Z over the problem
+// positions, in two deterministic steps.
+//
+// (1) KElemProduct: for each element of each problem of the batch, the
+// element's share y_e = [A_e B_e^T; B_e 0] z_e of the product, with z_e
+// gathered through the element's position map (entries outside the problem
+// are zero).  One CTA per element: warps over the element's rows, lanes
+// along the contiguous row of A_e (coalesced), RB right-hand sides per pass
+// so every matrix entry read serves RB of them.  Output YE: per element
+// (nK + np) rows for each right-hand side of the chunk.
+//
+// (2) KGatherResidual: per position, the sum of the element shares of its
+// row in a fixed order (the subdomain's adjacency lists), the constraint
+// terms of the constrained Neumann problem (multiplier columns and rows),
+// and R = B - sum.
 struct MatvecTask {
   int prob, start, count;
 };
-struct KProbResidual {
+struct ElemTask {
+  int prob, le;
+};
+
+// YE offset of element e's block for right-hand side r of a chunk of nr
+VB_HD inline int64_t ye_off(const BddcView& V, int e, int nr, int r, int nKp) {
+  return (V.offK[e] + (int64_t)V.np * e) * nr + (int64_t)r * nKp;
+}
+
+template <int RB>
+struct KElemProduct {
+  BddcView V;
+  const ElemTask* tasks;
+  const double* Z;
+  double* YE;
+  int nrhs, r0, nr;   // chunk [r0, r0 + nr) of the nrhs right-hand sides
+  __device__ void operator()(const KExec& ex, int blk) const {
+    const ElemTask tk = tasks[blk];
+    const ProbDev P = V.probs[tk.prob];
+    const SubDev S = V.subs[P.sub];
+    const int npk = V.np;
+    const int e = V.sub_elems[S.elem_off + tk.le];
+    const int nK = (int)(V.offK[e + 1] - V.offK[e]), nKp = nK + npk;
+    const int* ep = V.elpos + P.elpos_off + V.elptr[P.elptr_off + tk.le];
+    const double* Ae = V.A + V.offK2[e];
+    const double* Be = V.B + (int64_t)npk * V.offK[e];
+    double* zs = ex.smem;   // [RB][nKp]
+    const int nw = ex.nt >> 5, w = ex.tid >> 5, lane = ex.tid & 31;
+    for (int c0 = 0; c0 < nr; c0 += RB) {
+      const int nc = nr - c0 < RB ? nr - c0 : RB;
+      for (int q = ex.tid; q < RB * nKp; q += ex.nt) {
+        const int r = q / nKp, b = q % nKp, x = ep[b];
+        zs[q] = (r < nc && x >= 0) ? Z[P.vec_off * nrhs + (int64_t)(r0 + c0 + r) * P.n + x] : 0.0;
+      }
+      ex.sync();
+      for (int a = w; a < nKp; a += nw) {
+        if (ep[a] < 0) continue;   // not a row of this problem
+        double acc[RB];
+        for (int r = 0; r < RB; ++r) acc[r] = 0.0;
+        const double* row = a < nK ? Ae + (int64_t)a * nK : Be + (int64_t)(a - nK) * nK;
+        for (int b = lane; b < nK; b += 32) {
+          const double v = row[b];
+          for (int r = 0; r < RB; ++r) acc[r] += v * zs[r * nKp + b];
+        }
+        if (a < nK)
+          for (int al = lane; al < npk; al += 32) {
+            const double v = Be[(int64_t)al * nK + a];
+            for (int r = 0; r < RB; ++r) acc[r] += v * zs[r * nKp + nK + al];
+          }
+        for (int r = 0; r < RB; ++r) {
+          const double t = warp_sum(acc[r]);
+          if (lane == 0 && r < nc) YE[ye_off(V, e, nr, c0 + r, nKp) + a] = t;
+        }
+      }
+      ex.sync();
+    }
+  }
+};
+
+struct KGatherResidual {
   BddcView V;
   const MatvecTask* tasks;
   const double* Bv;   // right-hand sides   [vec_off*nrhs + r*n + pos]
   const double* Z;    // current solutions
+  const double* YE;   // element shares of the chunk
   double* R;
   const int* mcon_ptr;   // per subdomain: multiplier -> (local vdof, coef)
   const int* mcon_vdof;
   const double* mcon_coef;
-  int nrhs;
-  VB_HD void operator()(const KExec& ex, int blk) const {
+  int nrhs, r0, nr;
+  __device__ void operator()(const KExec& ex, int blk) const {
     const MatvecTask tk = tasks[blk];
     const ProbDev P = V.probs[tk.prob];
     const SubDev S = V.subs[P.sub];
     const int npk = V.np;
     const int* pv = V.pos_of_vdof + P.pv_off;
-    for (int r = 0; r < nrhs; ++r) {
-      const int64_t base = P.vec_off * nrhs + (int64_t)r * P.n;
+    for (int r = 0; r < nr; ++r) {
+      const int64_t base = P.vec_off * nrhs + (int64_t)(r0 + r) * P.n;
       const double* z = Z + base;
       for (int pos = tk.start + ex.tid; pos < tk.start + tk.count; pos += ex.nt) {
         const int dt = V.dtype[P.pos_off + pos], src = V.dsrc[P.pos_off + pos];
@@ -628,16 +846,8 @@ struct KProbResidual {
           for (int q = vp[src]; q < vp[src + 1]; ++q) {
             const int le = V.vadj[S.vadj_off + 2 * q], a = V.vadj[S.vadj_off + 2 * q + 1];
             const int e = V.sub_elems[S.elem_off + le];
-            const int nK = (int)(V.offK[e + 1] - V.offK[e]);
-            const int* ep = V.elpos + P.elpos_off + V.elptr[P.elptr_off + le];
-            const double* Ae = V.A + V.offK2[e];
-            const double* Be = V.B + (int64_t)npk * V.offK[e];
-            for (int b = 0; b < nK + npk; ++b) {
-              const int x = ep[b];
-              if (x < 0) continue;
-              const double v = b < nK ? Ae[(int64_t)a * nK + b] : Be[(int64_t)(b - nK) * nK + a];
-              acc += v * z[x];
-            }
+            const int nKp = (int)(V.offK[e + 1] - V.offK[e]) + npk;
+            acc += YE[ye_off(V, e, nr, r, nKp) + a];
           }
           if (P.kind == PK_NEUMANN) {
             const int* cp = V.vcon_ptr + S.vcon_ptr_off;
@@ -648,12 +858,7 @@ struct KProbResidual {
           const int le = src / npk, a = src % npk;
           const int e = V.sub_elems[S.elem_off + le];
           const int nK = (int)(V.offK[e + 1] - V.offK[e]);
-          const int* ep = V.elpos + P.elpos_off + V.elptr[P.elptr_off + le];
-          const double* Be = V.B + (int64_t)npk * V.offK[e];
-          for (int b = 0; b < nK; ++b) {
-            const int x = ep[b];
-            if (x >= 0) acc += Be[(int64_t)a * nK + b] * z[x];
-          }
+          acc = YE[ye_off(V, e, nr, r, nK + npk) + nK + a];
         } else if (dt == DT_MULT) {
           const int* mp = mcon_ptr + S.mcon_ptr_off;
           for (int q = mp[src]; q < mp[src + 1]; ++q)

@@ -56,6 +56,7 @@ struct vem_system {
   vb::Topo topo;
   vb::DofNumbering dof;
   cudaStream_t stream = 0;
+  std::vector<std::pair<std::string, double>> times;   // vem_assemble phase wall times (ms)
   int nKmax = 0;
   // element tables and outputs on the device
   vb::DBuf<vb::ElemRec> d_rec;

@@ -5,6 +5,7 @@
 #include "elem_body.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 
@@ -294,6 +295,12 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
   *out = nullptr;
   vem_system* s = new vem_system();
   try {
+    auto t0 = std::chrono::steady_clock::now();
+    auto mark = [&](const char* name) {
+      auto t1 = std::chrono::steady_clock::now();
+      s->times.push_back({name, std::chrono::duration<double, std::milli>(t1 - t0).count()});
+      t0 = t1;
+    };
     build_topology(mesh, s->topo);
     number_dofs(s->topo, k, s->dof);
     const Topo& t = s->topo;
@@ -315,6 +322,7 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
       VB_CHECK((int)g.size() == recs[e].nK, VEM_EINVAL, "element DOF count mismatch");
       for (size_t i = 0; i < g.size(); ++i) s->h_sysdof[offK[e] + i] = d.free_index[g[i]];
     }
+    mark("t_topology_ms");
     // upload element data, build element matrices
     s->d_rec.alloc(t.nE);
     VB_CUDA(cudaMemcpyAsync(s->d_rec.p, recs.data(), recs.size() * sizeof(ElemRec), cudaMemcpyHostToDevice, s->stream));
@@ -331,7 +339,8 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
     if (k == 2) launch_elements<2>(s, dK, dK2);
     else if (k == 3) launch_elements<3>(s, dK, dK2);
     else launch_elements<4>(s, dK, dK2);
-    // CSR pattern and row adjacency (host)
+    mark("t_element_launch_ms");
+    // CSR pattern and row adjacency (host, overlapping the element kernel)
     const int64_t nvf = d.nvf, np = d.np;
     s->n = nvf + d.npress;
     std::vector<int64_t> cnt(s->n + 1, 0);
@@ -398,6 +407,7 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
         std::vector<int>().swap(ccols[c]);
       }
     }
+    mark("t_pattern_ms");
     VB_CHECK(s->n < (int64_t)INT32_MAX, VEM_EINVAL, "system too large for 32-bit column indices");
     s->nnz = rowptr[s->n];
     s->d_rowptr.upload(rowptr, s->stream);
@@ -412,7 +422,9 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
     launch(fa, s->n, 32, 0, s->stream);
 
     s->d_eoffK2 = std::move(dK2);
+    mark("t_pattern_upload_ms");
     VB_CUDA(cudaStreamSynchronize(s->stream));
+    mark("t_gpu_finish_ms");
     *out = s;
     return VEM_OK;
   } catch (const Error& e) {
@@ -423,6 +435,17 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
     set_last_error(e.what());
     return VEM_ENOMEM;
   }
+}
+
+extern "C" int vem_info(const vem_system* s, const char* key, double* value) {
+  if (!s || !key || !value) { set_last_error("vem_info: null argument"); return VEM_EINVAL; }
+  const std::string k(key);
+  if (k == "nnz") { *value = (double)s->nnz; return VEM_OK; }
+  if (k == "n_elements") { *value = s->topo.nE; return VEM_OK; }
+  for (auto& pr : s->times)
+    if (pr.first == k) { *value = pr.second; return VEM_OK; }
+  set_last_error("vem_info: unknown key " + k);
+  return VEM_EINVAL;
 }
 
 extern "C" int vem_dof_layout(const vem_system* s, int64_t* nvf, int64_t* np, int64_t* nvel) {

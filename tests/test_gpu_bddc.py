@@ -136,3 +136,100 @@ def test_fp32_local_with_refinement(pkg, name):
     nvf = len(S.dm.free)
     x = u32.cpu().numpy()
     assert np.linalg.norm(x[:nvf] - ro["x"][:nvf]) <= 1e-7 * np.linalg.norm(ro["x"][:nvf])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_loop_matches_host_loop(pkg, precision):
+    """The PCG loop as one CUDA graph (conditional while node, scalars on
+    the device) against the host-driven loop: same iteration count, the same
+    solution to rounding, the same Lanczos estimates; a second solve through
+    the same captured graph repeats the first; maxit stops both forms at the
+    same place; the captured bddc_apply equals the direct one."""
+    import torch
+    cfg, g, rhs, S, F = _setup(pkg, "tri6_k2")
+    out = {}
+    for ug in (-1, 0):
+        bd = pkg.Bddc(g, cfg["part"], precision=precision, use_graph=ug)
+        u = torch.zeros_like(rhs)
+        res = bd.solve(rhs, u, rtol=1e-8, maxit=300)
+        assert res["status"] == 0
+        u2 = torch.full_like(rhs, 3.0)
+        res2 = bd.solve(rhs, u2, rtol=1e-8, maxit=300)
+        assert res2["iters"] == res["iters"] and torch.equal(u, u2)
+        short = bd.solve(rhs, torch.zeros_like(rhs), rtol=1e-8, maxit=3)
+        assert short["status"] == -6 and short["iters"] == 3
+        z = bd.apply(rhs)
+        z2 = bd.apply(rhs)
+        assert torch.equal(z, z2)
+        out[ug] = (res, u.cpu().numpy(), z.cpu().numpy())
+    (rh, uh, zh), (rg, ug_, zg) = out[-1], out[0]
+    # the two loops round differently (fused updates on the device); the
+    # FP32-local preconditioner (with refinement) passes such differences on
+    assert rg["iters"] == rh["iters"]
+    assert abs(rg["lam_max"] - rh["lam_max"]) <= 1e-8 * rh["lam_max"]
+    assert abs(rg["lam_min"] - rh["lam_min"]) <= 1e-8
+    assert np.linalg.norm(ug_ - uh) <= 1e-10 * np.linalg.norm(uh)
+    assert np.abs(zg - zh).max() <= 1e-13 * np.abs(zh).max()
+
+
+@pytest.mark.parametrize("theta", [10.0, 2.0])
+def test_adaptive_coarse_space_matches_oracle(pkg, theta):
+    """Adaptive primal enrichment (Sec. 6) at viscosity contrast 1e4: the
+    same number of added functionals as the oracle's eigenproblems, the same
+    CG behaviour (iterations, Lanczos estimates) and solution, and a better
+    conditioned preconditioner than without enrichment at theta = 2."""
+    import torch
+    cfg, g, rhs, S, F = _setup(pkg, "sinker8")
+    bd = pkg.Bddc(g, cfg["part"], adaptive=theta)
+    u = torch.zeros_like(rhs)
+    res = bd.solve(rhs, u, rtol=1e-8, maxit=300)
+    assert res["status"] == 0
+    ob = BDDC(S, cfg["part"], scaling="deluxe", adaptive=theta)
+    ro = ob.pcg(F, rtol=1e-8)
+    assert int(bd.info("n_adaptive")) == ob.n_adaptive
+    assert abs(res["iters"] - ro["iters"]) <= 3
+    assert res["lam_min"] > 1.0 - 1e-8
+    assert abs(res["lam_max"] - ro["lam_max"]) <= 1e-4 * ro["lam_max"]
+    nvf = len(S.dm.free)
+    x = u.cpu().numpy()
+    assert np.linalg.norm(x[:nvf] - ro["x"][:nvf]) <= 1e-8 * np.linalg.norm(ro["x"][:nvf])
+    if theta == 2.0:
+        base = pkg.Bddc(g, cfg["part"]).solve(rhs, torch.zeros_like(rhs), rtol=1e-8, maxit=300)
+        assert res["kappa"] < 0.5 * base["kappa"] and res["iters"] < base["iters"]
+
+
+def test_tensor_core_tile_product(pkg):
+    """One 128 x 128 x 32 tile of the tensor-core front update (tcgen05,
+    TF32 high/low split, FP32 accumulation) against FP64: FP32-level error,
+    well below what a single TF32 product (about 1e-3 relative) would give."""
+    import ctypes
+    L = pkg.lib()
+    L.vem_tc_selftest.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    err, ref = ctypes.c_double(), ctypes.c_double()
+    assert L.vem_tc_selftest(ctypes.byref(err), ctypes.byref(ref)) == 0, L.vem_last_error()
+    assert ref.value > 1.0
+    assert err.value <= 2e-5 * ref.value
+
+
+def test_tensor_core_factorization_matches_fma_path(pkg):
+    """16^3 perturbed mesh, 64 subdomains (fronts of several hundred rows, so
+    the tensor-core path runs): FP32-local BDDC-PCG with tensor-core front
+    updates against the same form on the FP32 FMA units and against the FP64
+    form: iterations within +10% of FP64, solutions within 1e-7."""
+    import torch
+    cfg = make_config("tri16_k2")
+    g = pkg.VemSystem(cfg["mesh"], 2, cfg["nu"])
+    rhs = g.load(4, cfg["f"](g.quad_points(4)))
+    out = {}
+    for name, kw in (("fp64", dict(precision=0)), ("tc", dict(precision=1, tc_update=0)),
+                     ("fma", dict(precision=1, tc_update=-1))):
+        bd = pkg.Bddc(g, cfg["part"], **kw)
+        u = torch.zeros_like(rhs)
+        res = bd.solve(rhs, u, rtol=1e-8, maxit=500)
+        assert res["status"] == 0
+        out[name] = (res, u.cpu().numpy())
+    (r64, u64), (rtc, utc), (rf, uf) = out["fp64"], out["tc"], out["fma"]
+    assert rtc["iters"] <= int(np.ceil(1.1 * r64["iters"]))
+    assert abs(rtc["iters"] - rf["iters"]) <= 1
+    assert np.linalg.norm(utc - u64) <= 1e-7 * np.linalg.norm(u64)
+    assert np.linalg.norm(utc - uf) <= 1e-7 * np.linalg.norm(uf)
