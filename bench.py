@@ -289,13 +289,28 @@ def run_ours(args, rank, world, dist):
 
 
 def run_profile(args):
-    """Small driver for profilers: one setup, then `napply` preconditioner
-    applies (FP64 or FP32-local local factors) on the named workload."""
+    """Small driver for profilers.  apply: one setup, then `napply`
+    preconditioner applies (FP64 or FP32-local local factors) on the named
+    workload.  step: one whole step (assembly, load, setup, PCG solve)."""
     import numpy as np
     import torch
     import paper_2304_09770_gb300 as pkg
     from synth import make_config
     cfg = make_config(args.workload)
+    if args.profile == "step":
+        g = pkg.VemSystem(cfg["mesh"], cfg["k"], cfg["nu"])
+        fq = cfg["f"](g.quad_points(LOAD_DEGREE))
+        l0 = pkg.kernel_launches()
+        rhs = g.load(LOAD_DEGREE, fq)
+        bd = pkg.Bddc(g, cfg["part"], precision=args.precision)
+        l1 = pkg.kernel_launches()
+        u = torch.zeros_like(rhs)
+        res = bd.solve(rhs, u, rtol=1e-8, maxit=1000)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": args.workload, "precision": args.precision, "assemble_launches": l0,
+                          "setup_launches": l1 - l0, "solve_launches": pkg.kernel_launches() - l1,
+                          "iterations": res["iters"]}))
+        return
     g = pkg.VemSystem(cfg["mesh"], cfg["k"], cfg["nu"])
     bd = pkg.Bddc(g, cfg["part"], precision=args.precision)
     r = torch.randn(g.n, dtype=torch.float64, device="cuda")
@@ -373,7 +388,7 @@ def run_configs(args):
                         factor_bytes=bd.info("factor_bytes_dirichlet") + bd.info("factor_bytes_neumann"))
             del bd, g, u, rhs, r
         except Exception as e:  # noqa: BLE001
-            line.update(error=str(e)[:300])
+            line.update(error=str(e)[:300], gib_free=torch.cuda.mem_get_info()[0] / 2**30)
         torch.cuda.empty_cache()
         print(json.dumps(line), flush=True)
 
@@ -385,8 +400,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["apply"], default=None,
-                    help="profiler driver: setup once, then --napply preconditioner applies")
+    ap.add_argument("--profile", choices=["apply", "step"], default=None,
+                    help="profiler driver: setup once then --napply preconditioner applies, or one whole step")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--napply", type=int, default=3)

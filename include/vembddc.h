@@ -198,10 +198,11 @@ typedef struct {
                                again when r or z change); -1: host-driven loop and
                                direct launches                                  */
   int32_t refine;           /* refinement steps of the FP32 local solves (0: 1)  */
-  int32_t tc_update;        /* FP32 factorizations: 0 or 1 trailing updates of
-                               fronts beyond 96 rows on the tensor cores (tcgen05,
-                               operands split into TF32 high and low parts, FP32
-                               accumulation in tensor memory); -1: FP32 FMA units */
+  int32_t tc_update;        /* FP32 factorizations: 1 trailing updates of fronts
+                               beyond 96 rows on the tensor cores (tcgen05, operands
+                               split into three TF32 parts, FP32 accumulation in
+                               tensor memory); 0 or -1 (default): FP32 FMA units,
+                               which are faster and more accurate in this release */
   int32_t reserved[7];
 } bddc_options;
 
@@ -251,7 +252,7 @@ int bddc_info(bddc* b, const char* key, double* value);
  * (every panel once forward, once backward).  Synchronizes. */
 int bddc_time_local_solves(bddc* b, int nrep, double* ms, double* bytes);
 /* Diagnostics: one 128 x 128 x 32 tile product of the tensor-core front
- * update (tcgen05, TF32 high/low operand split, FP32 accumulation in
+ * update (tcgen05, three-part TF32 operand split, FP32 accumulation in
  * tensor memory, Sec. 4 local factorizations in FP32) on deterministic
  * data in [-1, 1), against an FP64 product.  *max_err: max |D - D_fp64|;
  * *max_ref: max |D_fp64|.  Returns VEM_ETIMEOUT if the bounded wait for the

@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
+#include <cstdio>
 #include <numeric>
 #include <chrono>
 #include <string>
@@ -102,7 +104,8 @@ struct bddc {
   // iteration) and bddc_apply; captured on a private stream, replayed on
   // `stream`
   bool use_graph = true;
-  bool use_tc = true;            // FP32 front updates on the tensor cores (tcgen05, 3xTF32)
+  vb::DBuf<float2> d_A2;         // element matrices as FP32 pairs (FP32-local refinement residual)
+  bool use_tc = false;           // FP32 front updates on the tensor cores (tcgen05, split TF32)
   // adaptive coarse space (Sec. 6): threshold, rows added, and the face
   // Schur complements S_F kept from the first setup
   double adapt_theta = 0.0;
@@ -139,6 +142,7 @@ static BddcView make_view(bddc* b) {
   V.offK = s->d_eoff.p;
   V.offK2 = s->d_eoffK2.p;
   V.A = s->d_A.p;
+  V.A2 = b->d_A2.p;
   V.B = s->d_B.p;
   V.nodes = b->d_nodes.p;
   V.probs = b->d_probs.p;
@@ -1157,6 +1161,9 @@ static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& stat
       const NodeDev& Nd = b->h_nodes[B.h_levels[q]];
       nfmax = std::max(nfmax, Nd.np + Nd.nb);
     }
+    // large fronts: 2 or 4 groups of 256 threads, each on its own trailing tile
+    const int nthr = 256;
+    const size_t gbase = sizeof(double) * (std::max((nthr / 256) * 2 * 64 * 32 + 32, B.maxnf) + 8);
     // FP32 fronts with trailing blocks beyond 64 rows: tensor-core updates
     if (std::is_same<T, float>::value && b->use_tc && nfmax > 96) {
       const size_t off = (base + 127) / 128 * 128;
@@ -1165,7 +1172,7 @@ static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& stat
       launch(f, cnt, 256, off + TC_SMEM_BYTES, b->stream);
     } else {
       KFactor<T> f{V, B.d_levels.p + B.level_ptr[h], Fs.p, Us.p, status.p};
-      launch(f, cnt, 256, base, b->stream);
+      launch(f, cnt, nthr, gbase, b->stream);
     }
   }
 }
@@ -1258,10 +1265,15 @@ static void solve_batch(bddc* b, Batch& B, const BddcView& V, double* X, double*
   for (int it = 0; it < b->refine; ++it) {
     for (int r0 = 0; r0 < nrhs; r0 += chunk) {
       const int nr = std::min(chunk, nrhs - r0);
-      if (nr >= 4)
-        launch(KElemProduct<4>{V, B.d_etask.p, X, B.YE.p, nrhs, r0, nr}, (int64_t)B.h_etask.size(), 128, esm, st);
+      const int64_t ne = (int64_t)B.h_etask.size();
+      if (V.A2 && nr >= 4)
+        launch(KElemProduct<4, true>{V, B.d_etask.p, X, B.YE.p, nrhs, r0, nr}, ne, 128, 2 * esm, st);
+      else if (V.A2)
+        launch(KElemProduct<1, true>{V, B.d_etask.p, X, B.YE.p, nrhs, r0, nr}, ne, 128, 2 * esm, st);
+      else if (nr >= 4)
+        launch(KElemProduct<4>{V, B.d_etask.p, X, B.YE.p, nrhs, r0, nr}, ne, 128, esm, st);
       else
-        launch(KElemProduct<1>{V, B.d_etask.p, X, B.YE.p, nrhs, r0, nr}, (int64_t)B.h_etask.size(), 128, esm, st);
+        launch(KElemProduct<1>{V, B.d_etask.p, X, B.YE.p, nrhs, r0, nr}, ne, 128, esm, st);
       launch(KGatherResidual{V, B.d_mtask.p, B.XB.p, X, B.YE.p, B.XR.p, b->d_mcon_ptr.p, b->d_mcon_vdof.p,
                              b->d_mcon_coef.p, nrhs, r0, nr}, (int64_t)B.h_mtask.size(), 128, 0, st);
     }
@@ -1793,7 +1805,14 @@ static void setup_core(bddc* b, const int32_t* part) {
       VB_CUDA(cudaStreamSynchronize(st));
       auto t1 = std::chrono::steady_clock::now();
       b->times.push_back({name, std::chrono::duration<double, std::milli>(t1 - t0).count()});
-      t0 = t1;
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+        b->times.push_back({std::string("gib_free_after_") + name, (double)fr / (1 << 30)});
+      static const bool log = std::getenv("VEMBDDC_SETUP_LOG") != nullptr;
+      if (log)
+        std::fprintf(stderr, "bddc_setup: %s %.1f ms, %.1f GiB free\n", name, b->times[b->times.size() - 2].second,
+                     (double)fr / (1 << 30));
+      t0 = std::chrono::steady_clock::now();
     };
     bddc_host_setup(s, part, b->opt, H, s->elem_wmean);
     mark("t_symbolic_ms");
@@ -2048,14 +2067,28 @@ static void setup_core(bddc* b, const int32_t* part) {
     upload_vec(b->d_macros, b->h_macros, st);
     upload_levels(b, b->bd);
     upload_levels(b, b->bn);
+    if (b->prec == 1) {
+      // element matrices as FP32 (high, low) pairs for the refinement residual
+      const int64_t na = (int64_t)s->d_A.n;
+      b->d_A2.alloc(na);
+      launch(KSplitPairs{s->d_A.p, b->d_A2.p, na}, (na + 255) / 256, 256, 0, st);
+    }
     BddcView V = make_view(b);
     mark("t_upload_ms");
     // ---------------- numeric factorizations (S4)
     DBuf<int> status(1);
     status.zero(st);
+    // the update matrices are consumed by the parents during the
+    // factorization and not needed afterwards: released batch by batch
     factor_batch(b, b->bd, V, status);
+    VB_CUDA(cudaStreamSynchronize(st));
+    b->bd.U.release();
+    b->bd.U32.release();
     mark("t_factor_dirichlet_ms");
     factor_batch(b, b->bn, V, status);
+    VB_CUDA(cudaStreamSynchronize(st));
+    b->bn.U.release();
+    b->bn.U32.release();
     mark("t_factor_neumann_ms");
     {
       auto stv = status.download(st);
@@ -2319,7 +2352,7 @@ static void configure(bddc* b, vem_system* s, uint32_t constraints, int scaling,
   VB_CHECK(opts->refine >= 0 && opts->refine <= 4, VEM_EINVAL, "bddc_options.refine must be 0..4");
   if (opts->refine > 0) b->refine = opts->refine;
   VB_CHECK(opts->tc_update >= -1 && opts->tc_update <= 1, VEM_EINVAL, "bddc_options.tc_update must be -1, 0 or 1");
-  b->use_tc = opts->tc_update >= 0;
+  b->use_tc = opts->tc_update > 0;
   VB_CHECK(opts->adaptive_threshold >= 0.0, VEM_EINVAL, "bddc_options.adaptive_threshold must be >= 0");
   b->adapt_theta = opts->adaptive_threshold;
 }

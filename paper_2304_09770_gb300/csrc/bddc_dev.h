@@ -40,6 +40,7 @@ struct BddcView {
   int64_t nvf, n;
   const int64_t *offK, *offK2;
   const double *A, *B;
+  const float2* A2;    // A as FP32 (high, low) pairs for the refinement residual, or null
   // structure
   const NodeDev* nodes;
   const ProbDev* probs;

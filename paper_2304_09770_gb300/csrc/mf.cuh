@@ -30,32 +30,31 @@ VB_HD inline int front_index(const NodeDev& N, const int* bord, int x) {
 
 // Trailing update of one panel (columns jb .. jb+nbk-1, rows and columns from
 // c0 on, m of them) on the tensor cores: lower tiles (ti >= tk) of 128 x 128;
-// each tile stages L (rows of the tile) and L D (its columns) as TF32 pairs,
-// runs the 3xTF32 product into TMEM and subtracts it from the front
+// each tile stages L (rows of the tile) and L D (its columns, once per tile
+// column) as three TF32 parts, runs the split product into TMEM and
+// subtracts it from the front
 // (pivot columns in the panel, the rest in the update matrix).
 __device__ inline bool tc_trailing_update(const KExec& ex, TcCtx& c, float* pan, float* upd, int np, int nb, int ld,
                                           int nf, int jb, int nbk, int c0, int m, const float* sd) {
-  float* Ahi = c.tiles;
-  float* Alo = c.tiles + TC_TILE_FLOATS;
-  float* Bhi = c.tiles + 2 * TC_TILE_FLOATS;
-  float* Blo = c.tiles + 3 * TC_TILE_FLOATS;
+  float* A = c.tiles;                                // TF32 parts of the tile rows
+  float* B = c.tiles + TC_PARTS * TC_TILE_FLOATS;    // TF32 parts of the tile columns
   const int nt = (m + TC_M - 1) / TC_M;
   const int w = ex.tid >> 5, lane = ex.tid & 31;
   const int rowblk = w & 3, colhalf = w >> 2;   // 8 warps: 4 lane groups x 2 column halves
-  for (int tk = 0; tk < nt; ++tk)
+  for (int tk = 0; tk < nt; ++tk) {
+    const int k0 = c0 + tk * TC_N;
+    // columns of the tile row: L D (scaled by the pivots), staged once per tk
+    for (int q = ex.tid; q < TC_N * TC_K; q += ex.nt) {
+      const int col = q / TC_N, mm = q % TC_N;
+      const float y = (col < nbk && k0 + mm < nf) ? pan[(int64_t)(jb + col) * ld + k0 + mm] * sd[col] : 0.0f;
+      tc_split3(y, B, tc_off(mm, col));
+    }
     for (int ti = tk; ti < nt; ++ti) {
-      const int k0 = c0 + tk * TC_N, i0 = c0 + ti * TC_M;
+      const int i0 = c0 + ti * TC_M;
       for (int q = ex.tid; q < TC_M * TC_K; q += ex.nt) {
         const int col = q / TC_M, mm = q % TC_M;
-        const int o = tc_off(mm, col);
         const float x = (col < nbk && i0 + mm < nf) ? pan[(int64_t)(jb + col) * ld + i0 + mm] : 0.0f;
-        const float xh = tc_tf32(x);
-        Ahi[o] = xh;
-        Alo[o] = x - xh;
-        const float y = (col < nbk && k0 + mm < nf) ? pan[(int64_t)(jb + col) * ld + k0 + mm] * sd[col] : 0.0f;
-        const float yh = tc_tf32(y);
-        Bhi[o] = yh;
-        Blo[o] = y - yh;
+        tc_split3(x, A, tc_off(mm, col));
       }
       if (!tc_product(ex, c)) return false;
       const int i = i0 + rowblk * 32 + lane;
@@ -75,7 +74,21 @@ __device__ inline bool tc_trailing_update(const KExec& ex, TcCtx& c, float* pan,
       ex.sync();
       tc_fence_after();
     }
+  }
   return true;
+}
+
+// barrier of one group of 256 threads (named barrier 1 + grp), or of the
+// whole CTA when it works as a single group
+VB_HD inline void group_sync(const KExec& ex, int ngrp, int grp) {
+#ifdef __CUDA_ARCH__
+  if (ngrp > 1) {
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(256) : "memory");
+    return;
+  }
+#endif
+  (void)grp;
+  ex.sync();
 }
 
 // Blocked right-looking partial LDL^T of one dense front (panel nf x np and
@@ -90,10 +103,16 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, in
     // blocked right-looking partial LDL^T: panels of NBK columns, then a
     // rank-NBK update of the trailing front in TT x TT tiles staged in
     // shared memory (each thread owns a 4 x 4 sub-tile)
+    // With more than 256 threads the CTA works as groups of 256, each on its
+    // own trailing tile (named barriers per group), so that large fronts keep
+    // several tiles in flight.
     constexpr int NBK = 32, TT = 64;
-    T* sL = reinterpret_cast<T*>(ex.smem);
+    const int ngrp = ex.nt >= 512 ? ex.nt / 256 : 1;
+    const int grp = ngrp > 1 ? ex.tid / 256 : 0;
+    const int gt = ngrp > 1 ? ex.tid % 256 : ex.tid, gnt = ngrp > 1 ? 256 : ex.nt;
+    T* sL = reinterpret_cast<T*>(ex.smem) + (int64_t)grp * 2 * TT * NBK;
     T* sR = sL + TT * NBK;
-    T* sd = sL + 2 * TT * NBK;
+    T* sd = reinterpret_cast<T*>(ex.smem) + (int64_t)ngrp * 2 * TT * NBK;
     for (int jb = 0; jb < np; jb += NBK) {
       const int nbk = np - jb < NBK ? np - jb : NBK;
       for (int jj = 0; jj < nbk; ++jj) {
@@ -122,23 +141,33 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, in
 #ifdef __CUDA_ARCH__
       if constexpr (std::is_same<T, float>::value) {
         if (tc && m > TT) {
-          // tensor-core tiles (3xTF32, 128 x 128, accumulators in TMEM)
+          // tensor-core tiles (split TF32, 128 x 128, accumulators in TMEM)
           if (!tc_trailing_update(ex, *tc, pan, upd, np, nb, ld, nf, jb, nbk, c0, m, sd)) return;
           continue;
         }
       }
 #endif
       const int ntile = (m + TT - 1) / TT;
-      for (int tk = 0; tk < ntile; ++tk)
-        for (int ti = tk; ti < ntile; ++ti) {
-          const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
-          for (int q = ex.tid; q < TT * NBK; q += ex.nt) {
-            const int r = q % TT, c = q / TT;
-            sL[q] = (c < nbk && i0 + r < nf) ? pan[(int64_t)(jb + c) * ld + i0 + r] : (T)0;
-            sR[q] = (c < nbk && k0 + r < nf) ? pan[(int64_t)(jb + c) * ld + k0 + r] * sd[c] : (T)0;
+      const int ntot = ntile * (ntile + 1) / 2;          // lower tiles, tk-major
+      const int rounds = (ntot + ngrp - 1) / ngrp;
+      for (int rr = 0; rr < rounds; ++rr) {
+          const int tt = rr * ngrp + grp;
+          const bool act = tt < ntot;
+          int tk = 0, ti = 0;
+          if (act) {
+            int rem = tt;
+            while (rem >= ntile - tk) { rem -= ntile - tk; ++tk; }
+            ti = tk + rem;
           }
-          ex.sync();
-          for (int vt = ex.tid; vt < 256; vt += ex.nt) {
+          const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
+          if (act)
+            for (int q = gt; q < TT * NBK; q += gnt) {
+              const int r = q % TT, c = q / TT;
+              sL[q] = (c < nbk && i0 + r < nf) ? pan[(int64_t)(jb + c) * ld + i0 + r] : (T)0;
+              sR[q] = (c < nbk && k0 + r < nf) ? pan[(int64_t)(jb + c) * ld + k0 + r] * sd[c] : (T)0;
+            }
+          group_sync(ex, ngrp, grp);
+          for (int vt = gt; act && vt < 256; vt += gnt) {
             const int tr = vt % 16, tc = vt / 16;
             T acc[4][4] = {{0}};
             for (int c = 0; c < nbk; ++c) {
@@ -159,8 +188,9 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, in
               }
             }
           }
-          ex.sync();
-        }
+          group_sync(ex, ngrp, grp);
+      }
+      ex.sync();
     }
     // selective inversion: overwrite the unit lower L11 by L11^{-1} (unit
     // lower), column by column from the right, so that the triangular
@@ -190,7 +220,7 @@ struct KFactor {
     if constexpr (UseTC) {
       TcCtx c;
       c.tiles = reinterpret_cast<float*>(reinterpret_cast<char*>(ex.smem) + tc_smem_off);
-      c.mbar = reinterpret_cast<uint64_t*>(c.tiles + 4 * TC_TILE_FLOATS);
+      c.mbar = reinterpret_cast<uint64_t*>(c.tiles + 2 * TC_PARTS * TC_TILE_FLOATS);
       c.taddr_slot = reinterpret_cast<uint32_t*>(c.mbar + 1);
       c.status = status;
       tc_init(ex, c);
@@ -768,7 +798,46 @@ VB_HD inline int64_t ye_off(const BddcView& V, int e, int nr, int r, int nKp) {
   return (V.offK[e] + (int64_t)V.np * e) * nr + (int64_t)r * nKp;
 }
 
-template <int RB>
+// x = hi + lo with hi = fl32(x), lo = fl32(x - hi): 48 significant bits
+struct KSplitPairs {
+  const double* x;
+  float2* out;
+  int64_t n;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    const int64_t i = (int64_t)blk * ex.nt + ex.tid;
+    if (i >= n) return;
+    const double v = x[i];
+    const float h = (float)v;
+    out[i] = make_float2(h, (float)(v - (double)h));
+  }
+};
+
+// double-float accumulation: (s, c) holds s + c with |c| << |s|;
+// add a*b (a, b FP32) exactly up to the rounding of c (TwoProd with an FMA,
+// TwoSum), plus the first-order low-part terms
+// (the _rn intrinsics keep the compiler from contracting the error-free
+// steps into FMAs)
+__device__ inline void df_fma(float& s, float& c, float ah, float al, float zh, float zl) {
+  const float p = __fmul_rn(ah, zh);
+  const float e = fmaf(ah, zh, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c += err + e + fmaf(ah, zl, al * zh);
+}
+__device__ inline void df_add(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+  s = t;
+  c += c2 + err;
+}
+
+// DF = true: the A_e part in double-float arithmetic on the FP32 units from
+// the (high, low) copy V.A2 (FP64 units run at a small fraction of the FP32
+// rate here); the B_e parts stay FP64
+template <int RB, bool DF = false>
 struct KElemProduct {
   BddcView V;
   const ElemTask* tasks;
@@ -786,12 +855,19 @@ struct KElemProduct {
     const double* Ae = V.A + V.offK2[e];
     const double* Be = V.B + (int64_t)npk * V.offK[e];
     double* zs = ex.smem;   // [RB][nKp]
+    float* zf = reinterpret_cast<float*>(ex.smem + RB * nKp);   // DF: [RB][nKp] high, then low parts
     const int nw = ex.nt >> 5, w = ex.tid >> 5, lane = ex.tid & 31;
     for (int c0 = 0; c0 < nr; c0 += RB) {
       const int nc = nr - c0 < RB ? nr - c0 : RB;
       for (int q = ex.tid; q < RB * nKp; q += ex.nt) {
         const int r = q / nKp, b = q % nKp, x = ep[b];
-        zs[q] = (r < nc && x >= 0) ? Z[P.vec_off * nrhs + (int64_t)(r0 + c0 + r) * P.n + x] : 0.0;
+        const double z = (r < nc && x >= 0) ? Z[P.vec_off * nrhs + (int64_t)(r0 + c0 + r) * P.n + x] : 0.0;
+        zs[q] = z;
+        if (DF) {
+          const float h = (float)z;
+          zf[q] = h;
+          zf[RB * nKp + q] = (float)(z - (double)h);
+        }
       }
       ex.sync();
       for (int a = w; a < nKp; a += nw) {
@@ -799,9 +875,27 @@ struct KElemProduct {
         double acc[RB];
         for (int r = 0; r < RB; ++r) acc[r] = 0.0;
         const double* row = a < nK ? Ae + (int64_t)a * nK : Be + (int64_t)(a - nK) * nK;
-        for (int b = lane; b < nK; b += 32) {
-          const double v = row[b];
-          for (int r = 0; r < RB; ++r) acc[r] += v * zs[r * nKp + b];
+        if (DF && a < nK) {
+          const float2* row2 = V.A2 + V.offK2[e] + (int64_t)a * nK;
+          float sh[RB], sl[RB];
+          for (int r = 0; r < RB; ++r) sh[r] = sl[r] = 0.0f;
+          for (int b = lane; b < nK; b += 32) {
+            const float2 v = row2[b];
+            for (int r = 0; r < RB; ++r) df_fma(sh[r], sl[r], v.x, v.y, zf[r * nKp + b], zf[RB * nKp + r * nKp + b]);
+          }
+          for (int r = 0; r < RB; ++r) {
+            for (int o = 16; o > 0; o >>= 1) {
+              const float s2 = __shfl_xor_sync(0xffffffffu, sh[r], o), c2 = __shfl_xor_sync(0xffffffffu, sl[r], o);
+              df_add(sh[r], sl[r], s2, c2);
+            }
+            // every lane holds the sum; lane 0 adds it once below
+            if (lane == 0) acc[r] = (double)sh[r] + (double)sl[r];
+          }
+        } else {
+          for (int b = lane; b < nK; b += 32) {
+            const double v = row[b];
+            for (int r = 0; r < RB; ++r) acc[r] += v * zs[r * nKp + b];
+          }
         }
         if (a < nK)
           for (int al = lane; al < npk; al += 32) {

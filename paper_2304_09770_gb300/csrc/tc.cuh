@@ -1,9 +1,12 @@
 // Fifth-generation tensor cores (tcgen05) for the FP32 front factorization:
 // the rank-32 trailing update of a dense front, C -= L (D L^T), in 128 x 128
 // output tiles accumulated in tensor memory (TMEM).  FP32 operands are split
-// into TF32 high and low parts (hi = round(x), lo = x - hi) and each tile is
-// Ahi*Bhi + Ahi*Blo + Alo*Bhi with FP32 accumulation, which keeps the update
-// at FP32 accuracy (the dropped Alo*Blo term is of relative size 2^-22).
+// into three TF32 parts, x = x0 + x1 + x2 (x0 = round(x), x1 = round(x - x0),
+// x2 = x - x0 - x1, each exact in TF32), and each tile is the sum of the six
+// products x_a y_b with a + b <= 2, accumulated in FP32: the dropped terms
+// are of relative size 2^-33, so the update carries FP32 accuracy (a
+// two-part split, 2^-22, was not enough for the local problems at a
+// viscosity contrast of 1e4).
 //
 // Operand tiles are staged by the CTA's threads in shared memory in the
 // no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix;
@@ -18,13 +21,14 @@ namespace vb {
 
 constexpr int TC_M = 128, TC_N = 128, TC_K = 32;
 constexpr int TC_TILE_FLOATS = TC_M * TC_K;   // one operand tile
-// shared memory of the TC path: 4 operand tiles, then mbarrier + TMEM address
-constexpr size_t TC_SMEM_BYTES = 4 * TC_TILE_FLOATS * sizeof(float) + 16;
+constexpr int TC_PARTS = 3;                     // TF32 parts per operand
+// shared memory of the TC path: A parts, B parts, then mbarrier + TMEM address
+constexpr size_t TC_SMEM_BYTES = 2 * TC_PARTS * TC_TILE_FLOATS * sizeof(float) + 16;
 // mbarrier polls before a wait gives up (about a second)
 constexpr long long TC_WAIT_LIMIT = 1ll << 26;
 
 struct TcCtx {
-  float* tiles;        // [4][TC_TILE_FLOATS]: A hi, A lo, B hi, B lo
+  float* tiles;        // [2*TC_PARTS][TC_TILE_FLOATS]: A parts 0..2, B parts 0..2
   uint64_t* mbar;
   uint32_t* taddr_slot;
   uint32_t taddr;
@@ -57,6 +61,16 @@ __device__ inline float tc_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
+}
+
+// x into its three TF32 parts at offset o of the part tiles starting at t
+__device__ inline void tc_split3(float x, float* t, int o) {
+  const float x0 = tc_tf32(x);
+  const float r = x - x0;
+  const float x1 = tc_tf32(r);
+  t[o] = x0;
+  t[TC_TILE_FLOATS + o] = x1;
+  t[2 * TC_TILE_FLOATS + o] = r - x1;
 }
 
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -123,7 +137,7 @@ __device__ inline void tc_ld32(uint32_t taddr, float* v) {
 }
 
 // D = A B^T for the staged 128 x 32 tiles (A: rows of the output, B: its
-// columns), 3xTF32, into TMEM; thread 0 issues and waits (bounded), the
+// columns), split-TF32, into TMEM; thread 0 issues and waits (bounded), the
 // outcome is shared through the CTA.  Returns false after a failed wait.
 __device__ inline bool tc_product(const KExec& ex, TcCtx& c) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -133,16 +147,19 @@ __device__ inline bool tc_product(const KExec& ex, TcCtx& c) {
   __shared__ int tc_ok;
   if (ex.tid == 0) {
     const uint32_t base = tc_smem_addr(c.tiles);
-    const uint32_t a_hi = base, a_lo = base + TC_TILE_FLOATS * 4, b_hi = base + 2 * TC_TILE_FLOATS * 4,
-                   b_lo = base + 3 * TC_TILE_FLOATS * 4;
+    constexpr uint32_t TB = TC_TILE_FLOATS * 4;
+    const uint32_t a0 = base, b0 = base + TC_PARTS * TB;
+    // part pairs (a, b) with a + b <= 2, the small products first so that
+    // they are summed before the large ones join the accumulator
+    const int pa[6] = {1, 0, 2, 0, 1, 0}, pb[6] = {1, 2, 0, 1, 0, 0};
     // K = 8 per MMA: two core matrices (256 bytes) along K per step
-    for (int ks = 0; ks < TC_K / 8; ++ks) {
-      const uint32_t o = ks * 256;
-      tc_mma(c.taddr, tc_desc(a_hi + o, 128, 1024), tc_desc(b_hi + o, 128, 1024), ks > 0);
-      tc_mma(c.taddr, tc_desc(a_hi + o, 128, 1024), tc_desc(b_lo + o, 128, 1024), 1);
-      tc_mma(c.taddr, tc_desc(a_lo + o, 128, 1024), tc_desc(b_hi + o, 128, 1024), 1);
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+    for (int q = 0; q < 6; ++q)
+      for (int ks = 0; ks < TC_K / 8; ++ks) {
+        const uint32_t o = ks * 256;
+        tc_mma(c.taddr, tc_desc(a0 + pa[q] * TB + o, 128, 1024), tc_desc(b0 + pb[q] * TB + o, 128, 1024),
+               (ks > 0 || q > 0) ? 1u : 0u);
+      }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      tc_smem_addr(c.mbar))
                  : "memory");
     const uint32_t mb = tc_smem_addr(c.mbar);

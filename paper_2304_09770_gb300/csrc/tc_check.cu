@@ -1,5 +1,5 @@
 // Diagnostics of the tensor-core tile product used by the FP32 front
-// factorization (tcgen05, TF32 high/low split, FP32 accumulation in TMEM):
+// factorization (tcgen05, three-part TF32 split, FP32 accumulation in TMEM):
 // one 128 x 128 x 32 product on deterministic data against an FP64 product.
 #include "common.h"
 #include "launch.h"
@@ -22,18 +22,14 @@ struct KTcCheck {
   __device__ void operator()(const KExec& ex, int) const {
     TcCtx c;
     c.tiles = reinterpret_cast<float*>(ex.smem);
-    c.mbar = reinterpret_cast<uint64_t*>(c.tiles + 4 * TC_TILE_FLOATS);
+    c.mbar = reinterpret_cast<uint64_t*>(c.tiles + 2 * TC_PARTS * TC_TILE_FLOATS);
     c.taddr_slot = reinterpret_cast<uint32_t*>(c.mbar + 1);
     c.status = status;
     tc_init(ex, c);
     for (int q = ex.tid; q < TC_M * TC_K; q += ex.nt) {
       const int col = q / TC_M, mm = q % TC_M, o = tc_off(mm, col);
-      const float x = tc_check_val(mm, col, 0), y = tc_check_val(mm, col, 1);
-      const float xh = tc_tf32(x), yh = tc_tf32(y);
-      c.tiles[o] = xh;
-      c.tiles[TC_TILE_FLOATS + o] = x - xh;
-      c.tiles[2 * TC_TILE_FLOATS + o] = yh;
-      c.tiles[3 * TC_TILE_FLOATS + o] = y - yh;
+      tc_split3(tc_check_val(mm, col, 0), c.tiles, o);
+      tc_split3(tc_check_val(mm, col, 1), c.tiles + TC_PARTS * TC_TILE_FLOATS, o);
     }
     double err = 0.0, mx = 0.0;
     const bool ran = tc_product(ex, c);

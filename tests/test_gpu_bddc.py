@@ -200,7 +200,7 @@ def test_adaptive_coarse_space_matches_oracle(pkg, theta):
 
 def test_tensor_core_tile_product(pkg):
     """One 128 x 128 x 32 tile of the tensor-core front update (tcgen05,
-    TF32 high/low split, FP32 accumulation) against FP64: FP32-level error,
+    three-part TF32 split, FP32 accumulation) against FP64: FP32-level error,
     well below what a single TF32 product (about 1e-3 relative) would give."""
     import ctypes
     L = pkg.lib()
@@ -208,7 +208,7 @@ def test_tensor_core_tile_product(pkg):
     err, ref = ctypes.c_double(), ctypes.c_double()
     assert L.vem_tc_selftest(ctypes.byref(err), ctypes.byref(ref)) == 0, L.vem_last_error()
     assert ref.value > 1.0
-    assert err.value <= 2e-5 * ref.value
+    assert err.value <= 2e-6 * ref.value
 
 
 def test_tensor_core_factorization_matches_fma_path(pkg):
@@ -221,7 +221,7 @@ def test_tensor_core_factorization_matches_fma_path(pkg):
     g = pkg.VemSystem(cfg["mesh"], 2, cfg["nu"])
     rhs = g.load(4, cfg["f"](g.quad_points(4)))
     out = {}
-    for name, kw in (("fp64", dict(precision=0)), ("tc", dict(precision=1, tc_update=0)),
+    for name, kw in (("fp64", dict(precision=0)), ("tc", dict(precision=1, tc_update=1)),
                      ("fma", dict(precision=1, tc_update=-1))):
         bd = pkg.Bddc(g, cfg["part"], **kw)
         u = torch.zeros_like(rhs)
