@@ -1162,7 +1162,7 @@ static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& stat
       nfmax = std::max(nfmax, Nd.np + Nd.nb);
     }
     // large fronts: 2 or 4 groups of 256 threads, each on its own trailing tile
-    const int nthr = 256;
+    const int nthr = nfmax > 512 ? 1024 : (nfmax > 192 ? 512 : 256);
     const size_t gbase = sizeof(double) * (std::max((nthr / 256) * 2 * 64 * 32 + 32, B.maxnf) + 8);
     // FP32 fronts with trailing blocks beyond 64 rows: tensor-core updates
     if (std::is_same<T, float>::value && b->use_tc && nfmax > 96) {
@@ -1207,15 +1207,28 @@ static void sweep_batch_rb(bddc* b, Batch& B, const BddcView& V, const T* Fp, do
     const int fp_t = B.fptask_ptr[h + 1] - B.fptask_ptr[h];
     const int nb_t = B.btask_ptr[h + 1] - B.btask_ptr[h];
     launch(KFwdGather{V, B.d_levels.p + B.level_ptr[h], X, UV, B.FV.p, fvo, nrhs}, cnt, 128, 0, st);
-    launch(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, fp_t, 32 * FWARPS, smf,
-           st);
-    launch(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 32 * FWARPS, smf,
-           st);
+    // FP32, single right-hand side: registers capped for 6 (forward) or 5
+    // (backward) resident CTAs per SM
+    // (these kernels wait on memory; occupancy hides the latency)
+    if constexpr (RB == 1 && std::is_same<T, float>::value) {
+      launch_lb<6>(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, fp_t, smf, st);
+      launch_lb<6>(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, smf, st);
+    } else {
+      launch(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, fp_t, 32 * FWARPS, smf,
+             st);
+      launch(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 32 * FWARPS,
+             smf, st);
+    }
   }
   for (int h = B.maxh; h >= 0; --h) {
     const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
-    launch(KBwdBorder<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, B.FV.p, fvo, nrhs}, np_t, 256, sm, st);
-    launch(KBwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 256, sm, st);
+    if constexpr (RB == 1 && std::is_same<T, float>::value) {
+      launch_lb<5>(KBwdBorder<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, B.FV.p, fvo, nrhs}, np_t, sm, st);
+      launch_lb<5>(KBwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, sm, st);
+    } else {
+      launch(KBwdBorder<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, B.FV.p, fvo, nrhs}, np_t, 256, sm, st);
+      launch(KBwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 256, sm, st);
+    }
   }
 }
 
@@ -2181,8 +2194,11 @@ static void setup_core(bddc* b, const int32_t* part) {
       upload_vec(dtiles, tiles, st);
       DBuf<double> PAN(std::max<int64_t>(pn, 1)), UPD(std::max<int64_t>(un, 1));
       V = make_view(b);
-      launch(KDeluxeFront{V, df.p, dsi.p, dsj.p, SD.p, PAN.p, UPD.p, dpo.p, duo.p, status.p}, (int)faces.size(), 256,
-             sizeof(double) * (2 * 64 * 32 + 32 + 8 + 2048), st);
+      // one CTA per face, four groups of 256 threads on separate trailing tiles
+      int ndmax = 0;
+      for (int g : faces) ndmax = std::max(ndmax, b->h_macros[g].ndual);
+      launch(KDeluxeFront{V, df.p, dsi.p, dsj.p, SD.p, PAN.p, UPD.p, dpo.p, duo.p, status.p}, (int)faces.size(), 1024,
+             sizeof(double) * (std::max(4 * 2 * 64 * 32 + 32, ndmax) + 8), st);
       launch(KDeluxeGemm{V, dtiles.p, df.p, PAN.p, dpo.p, b->d_deluxe.p}, (int64_t)tiles.size(), 256,
              sizeof(double) * (2 * 32 * 64 + 8), st);
       mark("t_deluxe_combine_ms");

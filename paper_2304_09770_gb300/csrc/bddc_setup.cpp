@@ -533,6 +533,16 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
         for (int q = S.vadj_ptr[v]; q < S.vadj_ptr[v + 1]; ++q) els.push_back(S.vadj[2 * q]);
         vnode[v] = lca_of(T, pos_in_order, els);
       }
+      // element column -> local velocity DOF (-1: fixed), shared by the problems
+      std::vector<int> elv_off(ne + 1, 0), elv;
+      for (int le = 0; le < ne; ++le) {
+        const int e = S.elems[le];
+        for (int64_t q = s->h_eoff[e]; q < s->h_eoff[e + 1]; ++q) {
+          const int64_t g = s->h_sysdof[q];
+          elv.push_back(g >= 0 ? lv(g) : -1);
+        }
+        elv_off[le + 1] = (int)elv.size();
+      }
       // ---- problems
       std::vector<int> kinds = {PK_DIRICHLET, PK_NEUMANN};
       std::vector<int> dl_macro;
@@ -621,13 +631,10 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
         // element column -> position
         P.elpos_off.assign(ne + 1, 0);
         P.elpos.clear();
+        P.elpos.reserve(elv.size() + (size_t)ne * np);
         for (int le = 0; le < ne; ++le) {
-          int e = S.elems[le];
-          int nK = (int)(s->h_eoff[e + 1] - s->h_eoff[e]);
-          for (int b = 0; b < nK; ++b) {
-            int64_t g = s->h_sysdof[s->h_eoff[e] + b];
-            P.elpos.push_back(g >= 0 ? P.pos_of_vdof[lv(g)] : -1);
-          }
+          for (int q = elv_off[le]; q < elv_off[le + 1]; ++q)
+            P.elpos.push_back(elv[q] >= 0 ? P.pos_of_vdof[elv[q]] : -1);
           for (int a = 0; a < np; ++a) P.elpos.push_back(ppos[le * np + a]);
           P.elpos_off[le + 1] = (int)P.elpos.size();
         }
@@ -647,44 +654,53 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
             P.nodes[pn].nchild = 2;
           }
         }
-        // borders (postorder: children first)
+        // borders (postorder: children first): the positions beyond the
+        // node's pivots coupled to them, i.e. the children's borders plus the
+        // positions of every element touching a pivot (all of them through a
+        // velocity pivot, the velocity ones through a pressure pivot) and the
+        // constraint multipliers of the velocity pivots; elements and
+        // positions are de-duplicated with per-node stamps
         std::vector<std::vector<int>> bset(P.nodes.size());
+        std::vector<int> pstamp(P.n, -1), estamp(ne, -1), evstamp(ne, -1), elist, evlist;
         for (int pn = 0; pn < (int)P.nodes.size(); ++pn) {
           Node& Nd = P.nodes[pn];
           const int last = Nd.p0 + Nd.np;
           std::vector<int> cand;
-          for (int c = 0; c < Nd.nchild; ++c) {
-            auto& cb = bset[P.children[Nd.first_child + c]];
-            cand.insert(cand.end(), cb.begin(), cb.end());
-          }
+          auto add = [&](int x) {
+            if (x >= last && pstamp[x] != pn) {
+              pstamp[x] = pn;
+              cand.push_back(x);
+            }
+          };
+          for (int c = 0; c < Nd.nchild; ++c)
+            for (int x : bset[P.children[Nd.first_child + c]]) add(x);
+          elist.clear();
+          evlist.clear();
           for (int p = Nd.p0; p < last; ++p) {
             if (P.dtype[p] == DT_VEL) {
               int v = (int)P.dsrc[p];
               for (int q = S.vadj_ptr[v]; q < S.vadj_ptr[v + 1]; ++q) {
                 int le = S.vadj[2 * q];
-                for (int z = P.elpos_off[le]; z < P.elpos_off[le + 1]; ++z)
-                  if (P.elpos[z] >= last) cand.push_back(P.elpos[z]);
+                if (estamp[le] != pn) { estamp[le] = pn; elist.push_back(le); }
               }
               if (kind == PK_NEUMANN)
-                for (int q = S.vcon_ptr[v]; q < S.vcon_ptr[v + 1]; ++q) {
-                  int mp = P.mult0 + S.vcon_id[q];
-                  if (mp >= last) cand.push_back(mp);
-                }
+                for (int q = S.vcon_ptr[v]; q < S.vcon_ptr[v + 1]; ++q) add(P.mult0 + S.vcon_id[q]);
             } else if (P.dtype[p] == DT_PRESS) {
               int le = (int)P.dsrc[p] / np;
-              int e = S.elems[le];
-              int nK = (int)(s->h_eoff[e + 1] - s->h_eoff[e]);
-              for (int b = 0; b < nK; ++b) {
-                int z = P.elpos[P.elpos_off[le] + b];
-                if (z >= last) cand.push_back(z);
-              }
+              if (evstamp[le] != pn) { evstamp[le] = pn; evlist.push_back(le); }
             }
           }
+          for (int le : elist)
+            for (int z = P.elpos_off[le]; z < P.elpos_off[le + 1]; ++z) add(P.elpos[z]);
+          for (int le : evlist) {
+            if (estamp[le] == pn) continue;   // all its positions are in already
+            int e = S.elems[le];
+            int nK = (int)(s->h_eoff[e + 1] - s->h_eoff[e]);
+            for (int b = 0; b < nK; ++b) add(P.elpos[P.elpos_off[le] + b]);
+          }
           std::sort(cand.begin(), cand.end());
-          cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-          cand.erase(std::remove_if(cand.begin(), cand.end(), [&](int x) { return x < last; }), cand.end());
-          bset[pn] = cand;
-          Nd.nb = (int)cand.size();
+          bset[pn] = std::move(cand);
+          Nd.nb = (int)bset[pn].size();
         }
         // offsets, rel maps, heights
         int64_t panel = 0, upd = 0, uv = 0;
@@ -713,15 +729,17 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
           }
           const Node& Pa = P.nodes[Nd.parent];
           const int* pb = &P.border[Pa.border_off];
+          // both borders are sorted: one merge walk
+          int q = 0;
           for (int x : bset[pn]) {
             int fi;
             if (x < Pa.p0 + Pa.np) {
               VB_CHECK(x >= Pa.p0, VEM_EINVAL, "symbolic: border entry below the parent's pivots");
               fi = x - Pa.p0;
             } else {
-              const int* it = std::lower_bound(pb, pb + Pa.nb, x);
-              VB_CHECK(it != pb + Pa.nb && *it == x, VEM_EINVAL, "symbolic: child border not in parent front");
-              fi = Pa.np + (int)(it - pb);
+              while (q < Pa.nb && pb[q] < x) ++q;
+              VB_CHECK(q < Pa.nb && pb[q] == x, VEM_EINVAL, "symbolic: child border not in parent front");
+              fi = Pa.np + q;
             }
             P.rel.push_back(fi);
           }

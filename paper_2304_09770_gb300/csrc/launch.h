@@ -33,6 +33,25 @@ __global__ void k_run(const F f) {
   f(KExec{(int)threadIdx.x, (int)blockDim.x, vb_smem}, (int)blockIdx.x);
 }
 
+// the same with 256 threads and at least MINB resident CTAs per SM (the
+// compiler caps the registers accordingly)
+template <class F, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_run_lb(const F f) {
+  extern __shared__ __align__(16) double vb_smem[];
+  f(KExec{(int)threadIdx.x, (int)blockDim.x, vb_smem}, (int)blockIdx.x);
+}
+
+template <int MINB, class F>
+inline void launch_lb(const F& f, int64_t nblocks, size_t smem, cudaStream_t s) {
+  if (nblocks <= 0) return;
+  VB_CHECK(nblocks < (int64_t)INT32_MAX, VEM_EINVAL, "grid too large");
+  if (smem > 48 * 1024)
+    VB_CUDA(cudaFuncSetAttribute(k_run_lb<F, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_run_lb<F, MINB><<<(unsigned)nblocks, 256, smem, s>>>(f);
+  VB_KERNEL_CHECK();
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 template <class F>
 inline void launch(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaStream_t s) {
   if (nblocks <= 0) return;

@@ -31,6 +31,8 @@ CONFIGS = {
     "tri4_k3": dict(n=4, perturb=0.2, seed=9, k=3, parts=(2, 2, 2), load="manufactured"),
     "tri4_k4": dict(n=4, perturb=0.2, seed=10, k=4, parts=(2, 2, 1), load="manufactured"),
     "cube6_k2": dict(n=6, perturb=0.0, seed=None, k=2, parts=(3, 3, 3), load="manufactured"),
+    # 6^3 perturbed, 8 uneven greedy subdomains (the 48^3 / 512 case in small)
+    "tri6_greedy": dict(n=6, perturb=0.15, seed=11, k=2, greedy=(8, 31), load="manufactured"),
     "sinker8": dict(n=8, perturb=0.0, seed=None, k=2, parts=(2, 2, 2), load="sinker",
                     sinkers=(8, 5), dr=1e4),
 }

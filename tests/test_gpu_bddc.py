@@ -35,7 +35,7 @@ def _setup(pkg, name, deg=None):
 
 
 CASES = [("cube4_k2", "deluxe"), ("tri4_k2", "deluxe"), ("tri6_k2", "deluxe"), ("tri6_k2", "multiplicity"),
-         ("tri4_k3", "deluxe"), ("cube6_k2", "deluxe"), ("sinker8", "deluxe")]
+         ("tri4_k3", "deluxe"), ("cube6_k2", "deluxe"), ("sinker8", "deluxe"), ("tri6_greedy", "deluxe")]
 
 
 @pytest.mark.parametrize("name,scaling", CASES)
