@@ -502,17 +502,9 @@ struct KDeluxeGemm {
     const int i0 = gt.ti * 64, j0 = gt.tj * 64;
     double* sA = ex.smem;            // [32][64]  L21 rows i0.., columns k
     double* sB = ex.smem + 32 * 64;  // [32][64]  Linv rows k, columns j0..
-    double acc[4][4];
-    for (int vt = ex.tid; vt < 256; vt += ex.nt)
-      for (int a = 0; a < 4; ++a)
-        for (int bb = 0; bb < 4; ++bb) acc[a][bb] = 0.0;
-    // only the host path (one thread) needs per-virtual-thread storage
-#ifndef __CUDA_ARCH__
-    static thread_local double hacc[256][4][4];
-    for (int vt = 0; vt < 256; ++vt)
-      for (int a = 0; a < 4; ++a)
-        for (int bb = 0; bb < 4; ++bb) hacc[vt][a][bb] = 0.0;
-#endif
+    double acc[4][4];   // launched with 256 threads: one 4 x 4 sub-tile each
+    for (int a = 0; a < 4; ++a)
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] = 0.0;
     for (int k0 = j0; k0 < nd; k0 += 32) {
       for (int q = ex.tid; q < 32 * 64; q += ex.nt) {
         const int kk = q / 64, r = q % 64;
@@ -525,11 +517,7 @@ struct KDeluxeGemm {
       ex.sync();
       for (int vt = ex.tid; vt < 256; vt += ex.nt) {
         const int tr = vt % 16, tc = vt / 16;
-#ifdef __CUDA_ARCH__
         double (*A)[4] = acc;
-#else
-        double (*A)[4] = hacc[vt];
-#endif
         for (int kk = 0; kk < 32; ++kk) {
           double li[4], rk[4];
           for (int a = 0; a < 4; ++a) li[a] = sA[kk * 64 + tr + 16 * a];
@@ -542,11 +530,7 @@ struct KDeluxeGemm {
     }
     for (int vt = ex.tid; vt < 256; vt += ex.nt) {
       const int tr = vt % 16, tc = vt / 16;
-#ifdef __CUDA_ARCH__
       double (*A)[4] = acc;
-#else
-      double (*A)[4] = hacc[vt];
-#endif
       for (int a = 0; a < 4; ++a)
         for (int bb = 0; bb < 4; ++bb) {
           const int i = i0 + tr + 16 * a, j = j0 + tc + 16 * bb;

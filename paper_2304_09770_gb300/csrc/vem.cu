@@ -99,8 +99,7 @@ struct KSpmv {
   const double* val;
   const double* x;
   double* y;
-  VB_HD void operator()(const KExec& ex, int blk) const {
-#ifdef __CUDA_ARCH__
+  __device__ void operator()(const KExec& ex, int blk) const {
     int lane = ex.tid & 31;
     int64_t r = (int64_t)blk * (ex.nt >> 5) + (ex.tid >> 5);
     if (r >= nrows) return;
@@ -108,13 +107,6 @@ struct KSpmv {
     for (int64_t p = rowptr[r] + lane; p < rowptr[r + 1]; p += 32) acc += val[p] * __ldg(x + col[p]);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) y[r] = acc;
-#else
-    for (int64_t r = (int64_t)blk * 8; r < nrows && r < (int64_t)blk * 8 + 8; ++r) {
-      double acc = 0.0;
-      for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p) acc += val[p] * x[col[p]];
-      y[r] = acc;
-    }
-#endif
   }
 };
 
