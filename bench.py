@@ -12,8 +12,8 @@ load, 4 x 4 x 4 box subdomains.
 
 --impl reference times the CPU oracle (NumPy/SciPy) on a bounded sample of
 the same workload family and extrapolates to the full size.  With N > 1
-(torchrun) every rank solves its own replica (the method is not sharded
-across GPUs in this build).
+(torchrun) every rank solves its own replica (the solver runs on one GPU;
+ranks do not exchange data).
 """
 import argparse
 import json
@@ -231,8 +231,8 @@ def run_ours(args, rank, world, dist):
            + mesh["elem_face"].nbytes + nu.nbytes + part.nbytes + fq.nbytes)
     if dist:
         dist.barrier()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else Clocks(f"/tmp/clocks_rank{rank}.csv")
+    import tempfile
+    clocks = Clocks(os.path.join(tempfile.gettempdir(), f"vembddc_clocks_rank{rank}.csv"))
     with clocks:
         m32 = measure(pkg, torch, cfg, fq, 1, args.steps, args.warmup, stream, True, rank)
         m64 = measure(pkg, torch, cfg, fq, 0, args.steps, args.warmup, stream, False, rank)
