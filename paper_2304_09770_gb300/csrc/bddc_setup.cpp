@@ -230,6 +230,7 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
   // multiplicity and sharing sets of free velocity DOFs
   H.mult.assign(nvf, 0);
   std::vector<std::vector<int>> share(nvf);
+#pragma omp parallel for schedule(static, 4096)
   for (int64_t r = 0; r < nvf; ++r) {
     auto& sv = share[r];
     for (int64_t q = s->h_adj_ptr[r]; q < s->h_adj_ptr[r + 1]; ++q) sv.push_back(part[s->h_adj_elem[q]]);
@@ -238,7 +239,11 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
     H.mult[r] = (int)sv.size();
   }
   // ---- macro entities: interface mesh entities grouped by sharing set and connectivity
-  std::map<std::pair<int, int64_t>, int> ent_index;
+  // entity (type, id) -> interface entity number, through one flat table
+  // over vertices, edges, faces and elements
+  const int64_t ent_off[5] = {0, t.nV, (int64_t)t.nV + t.nEd, (int64_t)t.nV + t.nEd + t.nF,
+                              (int64_t)t.nV + t.nEd + t.nF + t.nE};
+  std::vector<int> ent_index(ent_off[4], -1);
   std::vector<std::pair<int, int64_t>> ents;
   std::vector<std::vector<int64_t>> ent_dofs;
   for (int64_t r = 0; r < nvf; ++r) {
@@ -246,26 +251,18 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
     int ty;
     int64_t id;
     dof_entity(d, d.free_to_global[r], ty, id);
-    auto key = std::make_pair(ty, id);
-    auto it = ent_index.find(key);
-    int ei;
-    if (it == ent_index.end()) {
-      ei = (int)ents.size();
-      ent_index.emplace(key, ei);
-      ents.push_back(key);
+    int& slot = ent_index[ent_off[ty] + id];
+    if (slot < 0) {
+      slot = (int)ents.size();
+      ents.push_back({ty, id});
       ent_dofs.push_back({});
-    } else {
-      ei = it->second;
     }
-    ent_dofs[ei].push_back(r);
+    ent_dofs[slot].push_back(r);
   }
   const int nent = (int)ents.size();
   UF uf(nent);
   auto same = [&](int a, int b) { return share[ent_dofs[a][0]] == share[ent_dofs[b][0]]; };
-  auto find_ent = [&](int ty, int64_t id) {
-    auto it = ent_index.find({ty, id});
-    return it == ent_index.end() ? -1 : it->second;
-  };
+  auto find_ent = [&](int ty, int64_t id) { return ent_index[ent_off[ty] + id]; };
   for (int ei = 0; ei < nent; ++ei) {
     auto [ty, id] = ents[ei];
     if (ty == 1) {

@@ -172,7 +172,10 @@ struct KQuadPoints {
   }
 };
 
-// per element: F[c][a] = sum_p w f_c m_a(xi); local rhs = P0^T F (Eq. discreteF)
+// per element: F[c][a] = sum_p w f_c m_a(xi); local rhs = P0^T F (Eq. discreteF).
+// The load-rule points are generated once each, in chunks staged in shared
+// memory (scaled coordinates and w f), and every (c, a) moment sums over the
+// chunk in point order.
 template <int K>
 struct KLoadLocal {
   const ElemRec* rec;
@@ -184,10 +187,13 @@ struct KLoadLocal {
   const ElemTables* tab;
   LoadRule L;
   double* rloc;
-  VB_HD void operator()(const KExec& ex, int e) const {
+  static constexpr int CH = 128;   // points per staged chunk
+  static size_t smem_bytes() { return sizeof(double) * (3 * pdim3(K) + 4 + 6 * CH); }
+  __device__ void operator()(const KExec& ex, int e) const {
     constexpr int NP1 = pdim3(K);
     double* Fm = ex.smem;
     double* geo = ex.smem + 3 * NP1;   // xK[3], hK
+    double* pt = geo + 4;              // [CH][6]: scaled x, y, z, then w f_c
     const ElemRec& R = rec[e];
     if (ex.tid == 0) {
       elem_centroid(R, xyz, geo);
@@ -204,26 +210,36 @@ struct KLoadLocal {
       geo[3] = sqrt(h2);
     }
     ex.sync();
-    int npts = (int)(qoff[e + 1] - qoff[e]);
-    for (int idx = ex.tid; idx < 3 * NP1; idx += ex.nt) {
-      int c = idx / NP1, a = idx % NP1;
-      const Exp3 ea = tab->e3[a];
-      double acc = 0.0;
-      for (int p = 0; p < npts; ++p) {
+    const int npts = (int)(qoff[e + 1] - qoff[e]);
+    const int c = ex.tid / NP1, a = ex.tid % NP1;
+    const bool mine = ex.tid < 3 * NP1;
+    const Exp3 ea = tab->e3[mine ? a : 0];
+    double acc = 0.0;
+    for (int p0 = 0; p0 < npts; p0 += CH) {
+      const int cnt = npts - p0 < CH ? npts - p0 : CH;
+      for (int q = ex.tid; q < cnt; q += ex.nt) {
         double x[3], w;
-        load_point(L, R, xyz, geo, p, x, &w);
-        double px = (x[0] - geo[0]) / geo[3], py = (x[1] - geo[1]) / geo[3], pz = (x[2] - geo[2]) / geo[3];
-        acc += w * fq[3 * (qoff[e] + p) + c] * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c);
+        load_point(L, R, xyz, geo, p0 + q, x, &w);
+        double* d = pt + 6 * q;
+        for (int k = 0; k < 3; ++k) d[k] = (x[k] - geo[k]) / geo[3];
+        for (int k = 0; k < 3; ++k) d[3 + k] = w * fq[3 * (qoff[e] + p0 + q) + k];
       }
-      Fm[idx] = acc;
+      ex.sync();
+      if (mine)
+        for (int q = 0; q < cnt; ++q) {
+          const double* d = pt + 6 * q;
+          acc += d[3 + c] * ipow(d[0], ea.a) * ipow(d[1], ea.b) * ipow(d[2], ea.c);
+        }
+      ex.sync();
     }
+    if (mine) Fm[ex.tid] = acc;
     ex.sync();
     int nK = (int)(offK[e + 1] - offK[e]);
     const double* P = P0 + (size_t)3 * NP1 * offK[e];
     for (int col = ex.tid; col < nK; col += ex.nt) {
-      double acc = 0.0;
-      for (int q = 0; q < 3 * NP1; ++q) acc += P[(size_t)q * nK + col] * Fm[q];
-      rloc[offK[e] + col] = acc;
+      double s = 0.0;
+      for (int q = 0; q < 3 * NP1; ++q) s += P[(size_t)q * nK + col] * Fm[q];
+      rloc[offK[e] + col] = s;
     }
   }
 };
@@ -506,7 +522,7 @@ extern "C" int vem_load(vem_system* s, int degree, const double* fq, double* rhs
     VB_CUDA(cudaMemcpyAsync(df.p, fq, df.n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     DBuf<double> rloc(s->h_eoff.back());
     const int nE = s->topo.nE;
-    const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4);
+    const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4 + 6 * KLoadLocal<2>::CH);
     if (s->dof.k == 2)
       launch(KLoadLocal<2>{s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE, 128, lsm, s->stream);
     else if (s->dof.k == 3)
@@ -726,7 +742,7 @@ extern "C" int vem_load_noalloc(vem_system* s, int degree, const double* fq, dou
     gauss01_fixed(L.nq, L.x, L.w);
     const int64_t nq3 = (int64_t)L.nq * L.nq * L.nq;
     launch(KLoadOffsets{s->d_rec.p, nE, nq3, qoff}, 1, 1024, sizeof(int64_t) * 1024, s->stream);
-    const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4);
+    const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4 + 6 * KLoadLocal<2>::CH);
     if (s->dof.k == 2)
       launch(KLoadLocal<2>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE, 128, lsm, s->stream);
     else if (s->dof.k == 3)
