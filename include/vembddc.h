@@ -92,7 +92,7 @@ int vem_assemble(const vem_mesh* mesh, int k, const double* nu_per_element, vem_
  * numbering, element records), "t_element_launch_ms" (uploads and the
  * element kernel launch), "t_pattern_ms" (CSR pattern on the host while the
  * element kernel runs), "t_pattern_upload_ms" (pattern upload, assembly
- * launch), "t_gpu_finish_ms" (waiting for the GPU). */
+ * launch), "t_gpu_finish_ms" (waiting for the GPU).  Unknown keys: VEM_EINVAL. */
 int vem_info(const vem_system* sys, const char* key, double* value);
 
 /* Sizes: free velocity DOFs, element pressures, all velocity DOFs. */
@@ -242,7 +242,12 @@ int pcg_solve(bddc* b, const double* f_dev, double* u_dev, double rtol, int maxi
  * phase wall times "t_symbolic_ms", "t_upload_ms", "t_factor_dirichlet_ms",
  * "t_factor_neumann_ms", "t_factor_deluxe_ms", "t_deluxe_extract_ms",
  * "t_deluxe_combine_ms", "t_coarse_rhs_ms", "t_coarse_solves_ms",
- * "t_coarse_gram_ms", "t_coarse_inverse_ms". */
+ * "t_coarse_gram_ms", "t_coarse_inverse_ms"; "gib_free_after_<phase>" (free
+ * device memory after each of those phases, GiB); "gflop_factor_dirichlet",
+ * "gflop_factor_neumann", "gflop_factor_deluxe"; with the adaptive coarse
+ * space the first setup's phases are kept as "first_<key>".  With the
+ * environment variable VEMBDDC_SETUP_LOG set, each phase is also printed to
+ * stderr as it ends. */
 int bddc_info(bddc* b, const char* key, double* value);
 
 /* Diagnostics: nrep forward+backward sweeps through all local Neumann and

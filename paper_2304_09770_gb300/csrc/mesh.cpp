@@ -220,6 +220,61 @@ void build_elem_records(const Topo& t, const DofNumbering& d, std::vector<ElemRe
 #include "elem_body.cuh"
 namespace vb {
 
+void build_csr_pattern(const std::vector<ElemRec>& recs, const std::vector<int64_t>& offK,
+                       const std::vector<int64_t>& sysdof, const std::vector<int64_t>& adj_ptr,
+                       const std::vector<int>& adj_elem, const std::vector<int>& adj_loc, int64_t nvf, int np,
+                       int64_t n, std::vector<int64_t>& rowptr, std::vector<int>& cols) {
+  // Two parallel passes over the rows: count the distinct columns of each
+  // row, then write them sorted into their final place.  Each thread marks
+  // the columns of its current row in a bitmap (de-duplication without
+  // sorting the repeats) and clears the marks afterwards.
+  rowptr.assign(n + 1, 0);
+  auto row_cols = [&](int64_t r, std::vector<uint64_t>& bits, std::vector<int>& buf) {
+    buf.clear();
+    for (int64_t q = adj_ptr[r]; q < adj_ptr[r + 1]; ++q) {
+      const int e = adj_elem[q], loc = adj_loc[q];
+      const int nK = recs[e].nK;
+      for (int bb = 0; bb < nK; ++bb) {
+        const int64_t cc = sysdof[offK[e] + bb];
+        if (cc < 0) continue;
+        uint64_t& w = bits[cc >> 6];
+        const uint64_t m = (uint64_t)1 << (cc & 63);
+        if (!(w & m)) {
+          w |= m;
+          buf.push_back((int)cc);
+        }
+      }
+      if (loc < nK)   // a velocity row: the element's pressures (distinct per element)
+        for (int a = 0; a < np; ++a) buf.push_back((int)(nvf + (int64_t)e * np + a));
+    }
+    for (int x : buf)
+      if (x < nvf) bits[x >> 6] = 0;   // every marked bit belongs to this row
+  };
+#pragma omp parallel
+  {
+    std::vector<uint64_t> bits((size_t)((n + 63) / 64), 0);
+    std::vector<int> buf;
+#pragma omp for schedule(dynamic, 1024)
+    for (int64_t r = 0; r < n; ++r) {
+      row_cols(r, bits, buf);
+      rowptr[r + 1] = (int64_t)buf.size();
+    }
+#pragma omp single
+    {
+      for (int64_t r = 0; r < n; ++r) rowptr[r + 1] += rowptr[r];
+      cols.resize(rowptr[n]);
+    }
+#pragma omp for schedule(dynamic, 1024)
+    for (int64_t r = 0; r < n; ++r) {
+      row_cols(r, bits, buf);
+      std::sort(buf.begin(), buf.end());
+      std::copy(buf.begin(), buf.end(), cols.begin() + rowptr[r]);
+    }
+  }
+}
+
+
+
 void make_elem_tables(int k, ElemTables& T) {
   T = ElemTables{};
   int i = 0;

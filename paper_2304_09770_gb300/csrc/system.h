@@ -48,6 +48,13 @@ void number_dofs(const Topo& t, int k, DofNumbering& d);
 // element-local velocity DOFs (global numbers) in the element-local order
 void element_global_dofs(const Topo& t, const DofNumbering& d, int e, std::vector<int64_t>& out);
 void build_elem_records(const Topo& t, const DofNumbering& d, std::vector<ElemRec>& recs);
+// CSR pattern of K = [A B^T; B 0] over the system layout (free velocity,
+// then element pressures): row r holds the columns of every element
+// adjacent to r (velocity rows also the element's pressures); sorted rows
+void build_csr_pattern(const std::vector<ElemRec>& recs, const std::vector<int64_t>& offK,
+                       const std::vector<int64_t>& sysdof, const std::vector<int64_t>& adj_ptr,
+                       const std::vector<int>& adj_elem, const std::vector<int>& adj_loc, int64_t nvf, int np,
+                       int64_t n, std::vector<int64_t>& rowptr, std::vector<int>& cols);
 
 }  // namespace vb
 

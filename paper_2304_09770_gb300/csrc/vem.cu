@@ -375,46 +375,10 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
         s->h_adj_loc[fill[r]] = recs[e].nK + a;
         fill[r]++;
       }
-    std::vector<int64_t> rowptr(s->n + 1, 0);
+    std::vector<int64_t> rowptr;
     std::vector<int> cols;
-    {
-      // rows in parallel chunks: column sets per row, then one concatenation
-      const int64_t nrow = s->n;
-      const int nchunk = 64;
-      std::vector<std::vector<int>> ccols(nchunk);
-      std::vector<std::vector<int64_t>> clen(nchunk);
-#pragma omp parallel for schedule(dynamic)
-      for (int c = 0; c < nchunk; ++c) {
-        const int64_t r0 = nrow * c / nchunk, r1 = nrow * (c + 1) / nchunk;
-        std::vector<int> buf;
-        for (int64_t r = r0; r < r1; ++r) {
-          buf.clear();
-          for (int64_t q = cnt[r]; q < cnt[r + 1]; ++q) {
-            int e = s->h_adj_elem[q], loc = s->h_adj_loc[q];
-            int nK = recs[e].nK;
-            for (int bb = 0; bb < nK; ++bb) {
-              int64_t cc = s->h_sysdof[offK[e] + bb];
-              if (cc >= 0) buf.push_back((int)cc);
-            }
-            if (loc < nK)
-              for (int a = 0; a < np; ++a) buf.push_back((int)(nvf + (int64_t)e * np + a));
-          }
-          std::sort(buf.begin(), buf.end());
-          buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-          ccols[c].insert(ccols[c].end(), buf.begin(), buf.end());
-          clen[c].push_back((int64_t)buf.size());
-        }
-      }
-      int64_t tot = 0;
-      for (int c = 0; c < nchunk; ++c) tot += (int64_t)ccols[c].size();
-      cols.reserve(tot);
-      int64_t r = 0;
-      for (int c = 0; c < nchunk; ++c) {
-        for (int64_t L : clen[c]) { rowptr[r + 1] = rowptr[r] + L; ++r; }
-        cols.insert(cols.end(), ccols[c].begin(), ccols[c].end());
-        std::vector<int>().swap(ccols[c]);
-      }
-    }
+    build_csr_pattern(recs, offK, s->h_sysdof, s->h_adj_ptr, s->h_adj_elem, s->h_adj_loc, nvf, (int)np, s->n,
+                      rowptr, cols);
     mark("t_pattern_ms");
     VB_CHECK(s->n < (int64_t)INT32_MAX, VEM_EINVAL, "system too large for 32-bit column indices");
     s->nnz = rowptr[s->n];
