@@ -301,6 +301,7 @@ extern "C" const char* vem_last_error(void) { return vb::g_last_error.c_str(); }
 extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_system** out) {
   if (!out || !nu) { set_last_error("vem_assemble: null argument"); return VEM_EINVAL; }
   *out = nullptr;
+  if (k < 2 || k > 4) { set_last_error("vem_assemble: degree k must be 2, 3 or 4"); return VEM_EINVAL; }
   vem_system* s = new vem_system();
   try {
     auto t0 = std::chrono::steady_clock::now();
