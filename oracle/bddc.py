@@ -413,8 +413,10 @@ class BDDC:
 
     # ------------------------------------------------------------- adaptive
     def _adapt(self, nu_tol, svd_tol):
-        """Adds eigenvector-based primal rows per macro face (Sec. 6)."""
+        """Adds eigenvector-based primal rows per macro face (Sec. 6); the
+        eigenvalues of every face are kept in self.adapt_eigs."""
         added = 0
+        self.adapt_eigs = {}
         for gi, G in enumerate(self.macro):
             if gi not in self.SF:
                 continue
@@ -440,6 +442,7 @@ class BDDC:
             A = 0.5 * (A + A.T)
             Bm = 0.5 * (Bm + Bm.T)
             lam, V = sla.eigh(A, Bm)
+            self.adapt_eigs[gi] = lam
             sel = lam < 1.0 / nu_tol
             if not sel.any():
                 continue

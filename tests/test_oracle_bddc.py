@@ -113,3 +113,27 @@ def test_flux_primal_gives_benign_dual_space(system):
         C = G["C"]
         Qd = G["T"][:, :G["ndual"]]
         assert np.abs(C @ Qd).max() < 1e-10
+
+
+def test_adaptive_eigenvalues_and_monotonicity():
+    """Adaptive coarse space (Sec. 6) on the 4^3 perturbed mesh: since the
+    Neumann Schur complement onto a face is below the principal minor of
+    the Dirichlet one (S~ <= S, more freedom lowers the energy) and parallel
+    sums are monotone, every eigenvalue of (S~_i : S~_j, S_i : S_j) lies in
+    (0, 1]; lowering theta (raising the cut 1/theta) adds functionals and
+    does not raise kappa; lambda_min stays 1 (Theorem on the benign space)."""
+    cfg = make_config("tri4_k2")
+    S = System(cfg["mesh"], cfg["k"], cfg["nu"], f=cfg["f"], load_deg=6)
+    F = np.concatenate([S.F[S.dm.free], np.zeros(S.dm.npress)])
+    added, kappas = [], []
+    for theta in (10.0, 2.0, 1.1):
+        b = BDDC(S, cfg["part"], adaptive=theta)
+        eigs = np.concatenate(list(b.adapt_eigs.values()))
+        assert eigs.min() > 0.0 and eigs.max() <= 1.0 + 1e-10
+        r = b.pcg(F, rtol=1e-8)
+        assert r["lam_min"] > 1.0 - 1e-8
+        added.append(b.n_adaptive)
+        kappas.append(r["lam_max"] / r["lam_min"])
+        assert b.n_adaptive == int((eigs < 1.0 / theta).sum())
+    assert added[0] <= added[1] <= added[2] and added[2] > added[0]
+    assert kappas[0] >= kappas[1] - 1e-8 >= kappas[2] - 2e-8
