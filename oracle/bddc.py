@@ -19,7 +19,7 @@ Paper, Sec. 4-6:
 * Deluxe scaling on macro faces, D_F^(k) = (S_F^(i) + S_F^(j))^{-1} S_F^(k)
   with S_F the principal minor of the subdomain Schur complement on the
   dual face coordinates (Sec. 6); counting scaling 1/card on macro edges
-  (Eq. pseudoinv).
+  (Eq. pseudoinv), or, as an option, the deluxe formula on edges too.
 * Adaptive primal enrichment (Sec. 6): generalized eigenproblems
   (S~_i : S~_j) psi = nu (S_i : S_j) psi per face, A:B = (A^-1 + B^-1)^-1;
   eigenvectors with nu < 1/nu_tol give extra primal rows (S_i : S_j) psi.
@@ -91,7 +91,8 @@ class BDDC:
 
     constraints: tuple from {'vertex','edge','face','flux'} or 'all'
     (every interface DOF primal).  scaling: 'deluxe' (faces; edges by
-    counting) or 'multiplicity'.  adaptive: None or nu_tol.
+    counting), 'deluxe_edges' (faces and edges deluxe) or 'multiplicity'.
+    adaptive: None or nu_tol.
     """
 
     def __init__(self, S, part, constraints=("vertex", "edge", "face", "flux"),
@@ -100,6 +101,8 @@ class BDDC:
         topo, dm = S.topo, S.dm
         self.part = np.asarray(part)
         self.N = int(self.part.max()) + 1
+        if scaling not in ("deluxe", "deluxe_edges", "multiplicity"):
+            raise ValueError("scaling must be 'deluxe', 'deluxe_edges' or 'multiplicity'")
         self.scaling = scaling
         self.nvf = len(dm.free)
         self.npr = dm.npress
@@ -189,7 +192,7 @@ class BDDC:
             G["C"] = self._constraints(G, constraints, topo, dm, gfree, ent_of, nint)
         self.adaptive = adaptive
         self._setup(svd_tol)
-        if adaptive is not None and scaling == "deluxe":
+        if adaptive is not None and scaling in ("deluxe", "deluxe_edges"):
             self._adapt(adaptive, svd_tol)
 
     # ------------------------------------------------------------- constraints
@@ -389,11 +392,17 @@ class BDDC:
         return At @ W + Bt.T @ P
 
     def _deluxe(self):
-        """Face deluxe blocks D_F^(k) = (S_F^(i)+S_F^(j))^{-1} S_F^(k)."""
+        """Deluxe blocks D_G^(k) = (sum_{j in N_G} S_G^(j))^{-1} S_G^(k), with
+        S_G^(k) the principal minor of the subdomain Schur complement on the
+        dual coordinates of the macro entity G: on every macro face (Sec. 6,
+        N_F = {i, j}), and with scaling 'deluxe_edges' also on every macro
+        edge, over the card(N_E) >= 3 subdomains sharing it (the same
+        formula; the paper's edges use 1/card, Eq. pseudoinv)."""
         self.SF = {}
         self.DF = {}
+        kinds = {"deluxe": ("face",), "deluxe_edges": ("face", "edge")}.get(self.scaling, ())
         for gi, G in enumerate(self.macro):
-            if G["kind"] != "face" or self.scaling != "deluxe" or G["ndual"] == 0:
+            if G["kind"] not in kinds or G["ndual"] == 0:
                 continue
             blocks = {}
             for i in G["share"]:
@@ -402,10 +411,9 @@ class BDDC:
                 R = self._schur_cols(sub, cols)
                 blocks[i] = R[cols]
                 blocks[i] = 0.5 * (blocks[i] + blocks[i].T)
-            i, j = G["share"]
-            Ssum = blocks[i] + blocks[j]
+            Ssum = sum(blocks[s] for s in G["share"])
             self.SF[gi] = blocks
-            self.DF[gi] = {s: np.linalg.solve(Ssum, blocks[s]) for s in (i, j)}
+            self.DF[gi] = {s: np.linalg.solve(Ssum, blocks[s]) for s in G["share"]}
 
     def _dual_cols(self, sub, gi):
         # local coordinate indices of the dual columns of macro entity gi
@@ -418,7 +426,7 @@ class BDDC:
         added = 0
         self.adapt_eigs = {}
         for gi, G in enumerate(self.macro):
-            if gi not in self.SF:
+            if gi not in self.SF or G["kind"] != "face":
                 continue
             i, j = G["share"]
             St = {}
@@ -523,13 +531,13 @@ class BDDC:
 
     def _scale(self, gi, i, w):
         G = self.macro[gi]
-        if self.scaling == "deluxe" and gi in self.DF:
+        if gi in self.DF:
             return self.DF[gi][i] @ w
         return w / len(G["share"])
 
     def _scale_T(self, gi, i, r):
         G = self.macro[gi]
-        if self.scaling == "deluxe" and gi in self.DF:
+        if gi in self.DF:
             return self.DF[gi][i].T @ r
         return r / len(G["share"])
 
