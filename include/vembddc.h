@@ -172,6 +172,11 @@ const char* vem_last_error(void);
 /* scaling: averaging of the dual interface values (Sec. 4.3, Sec. 6)       */
 #define BDDC_SCALING_MULTIPLICITY 0   /* 1/card on every dual DOF (Eq. pseudoinv)   */
 #define BDDC_SCALING_DELUXE 1         /* deluxe on macro faces, 1/card on edges     */
+#define BDDC_SCALING_DELUXE_EDGES 2   /* deluxe on macro faces and on macro edges:
+                                         D_E^(k) = (sum_j S_E^(j))^-1 S_E^(k) over the
+                                         subdomains j sharing the edge E (the face
+                                         formula of Sec. 6 taken over card(E) >= 3
+                                         subdomains instead of 1/card)              */
 
 typedef struct {
   int32_t precision;        /* local factors and sweeps: 0 FP64; 1 FP32 with one step of
@@ -180,7 +185,7 @@ typedef struct {
                                matrix, deluxe inverses, operator and CG stay FP64. */
   int32_t scaling;          /* unused (the bddc_setup argument decides)        */
   uint32_t constraints;     /* unused (the bddc_setup argument decides)        */
-  double adaptive_threshold;/* theta > 0 (deluxe scaling only): adaptive coarse
+  double adaptive_threshold;/* theta > 0 (deluxe scalings only): adaptive coarse
                                space of Sec. 6.  Per macro face, the generalized
                                eigenproblem (S~_i : S~_j) psi = lambda (S_i : S_j) psi
                                on the face's dual coordinates (S_s the face block of
@@ -212,9 +217,11 @@ typedef struct {
  * basis, nested-dissection multifrontal LDL^T factorizations of the
  * subdomain Dirichlet problems (Eq. uipi) and constrained Neumann problems
  * (zero-mean interior pressure, primal values fixed), the deluxe face
- * blocks (Sec. 6) and the coarse saddle matrix bordered by
- * sum_i |Omega_i| p_0,i = 0.  opts may be NULL.  The handle keeps a pointer
- * to sys, which must outlive it.  Synchronizes. */
+ * blocks (Sec. 6; with BDDC_SCALING_DELUXE_EDGES also the deluxe edge
+ * blocks) and the coarse saddle matrix bordered by
+ * sum_i |Omega_i| p_0,i = 0.  scaling: one of the BDDC_SCALING_* values,
+ * else VEM_EINVAL.  opts may be NULL.  The handle keeps a pointer to sys,
+ * which must outlive it.  Synchronizes. */
 int bddc_setup(vem_system* sys, const int32_t* elem_to_subdomain, uint32_t constraints, int scaling,
                const bddc_options* opts, bddc** out);
 
@@ -237,8 +244,8 @@ int pcg_solve(bddc* b, const double* f_dev, double* u_dev, double rtol, int maxi
 
 /* Statistics by name: "n_subdomains", "n_coarse", "n_macro",
  * "factor_bytes_dirichlet", "factor_bytes_neumann", "n_deluxe_faces",
- * "n_adaptive" (primal functionals added by the adaptive coarse space), "t_adaptive_eig_ms",
- * "deluxe_bytes", "phi_bytes", "coarse_bytes", "n_front_max", and the setup
+ * "n_deluxe_edges", "n_adaptive" (primal functionals added by the adaptive
+ * coarse space), "t_adaptive_eig_ms", "deluxe_bytes", "deluxe_edge_bytes", "phi_bytes", "coarse_bytes", "n_front_max", and the setup
  * phase wall times "t_symbolic_ms", "t_upload_ms", "t_factor_dirichlet_ms",
  * "t_factor_neumann_ms", "t_factor_deluxe_ms", "t_deluxe_extract_ms",
  * "t_deluxe_combine_ms", "t_coarse_rhs_ms", "t_coarse_solves_ms",

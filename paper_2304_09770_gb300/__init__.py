@@ -204,7 +204,10 @@ class VemSystem:
 
 
 class Bddc:
-    """bddc_setup + bddc_apply + pcg_solve over a VemSystem."""
+    """bddc_setup + bddc_apply + pcg_solve over a VemSystem.
+
+    scaling: 0 multiplicity (1/card), 1 deluxe on macro faces (1/card on
+    edges), 2 deluxe on macro faces and macro edges."""
 
     def __init__(self, system, part, constraints=15, scaling=1, leaf=0, precision=0, refine=0, use_graph=0,
                  adaptive=0.0, tc_update=0):

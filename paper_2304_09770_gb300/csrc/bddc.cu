@@ -16,6 +16,8 @@
 #include <cstdio>
 #include <numeric>
 #include <chrono>
+#include <map>
+#include <utility>
 #include <string>
 #include <type_traits>
 
@@ -76,7 +78,7 @@ struct bddc {
       d_vadj, d_vcon_ptr, d_vcon_id, d_iface, d_elloc, d_elloc_ptr, d_share, d_gpos, d_gif;
   vb::DBuf<int64_t> d_vdof, d_press, d_coarse, d_mdofs, d_fvoff;
   std::vector<int64_t> h_fvoff;
-  vb::DBuf<double> d_vcon_coef, d_wmean, d_hv, d_tau, d_deluxe;
+  vb::DBuf<double> d_vcon_coef, d_wmean, d_hv, d_tau, d_deluxe, d_deluxe_e;
   std::vector<vb::NodeDev> h_nodes;
   std::vector<vb::ProbDev> h_probs;
   std::vector<vb::SubDev> h_subs;
@@ -176,6 +178,7 @@ static BddcView make_view(bddc* b) {
   V.gpos = b->d_gpos.p;
   V.gif = b->d_gif.p;
   V.deluxe = b->d_deluxe.p;
+  V.deluxe_e = b->d_deluxe_e.p;
   V.ncv = b->ncv;
   V.nc = b->nc;
   return V;
@@ -481,6 +484,67 @@ struct KDeluxeFront {
   }
 };
 
+// deluxe on macro edges (scaling 2): W = sum of the dual blocks S_s of the
+// subdomains sharing the edge, one CTA per edge
+struct KDeluxeEdgeSum {
+  BddcView V;
+  const int* edges;
+  const int64_t* sd_ptr;   // per edge: first of its blocks in sd_off
+  const int64_t* sd_off;   // offsets of the blocks S_s in SD, sharing-list order
+  const double* SD;
+  double* W;
+  const int64_t* w_off;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const MacroDev G = V.macros[edges[blk]];
+    const int64_t nn = (int64_t)G.ndual * G.ndual;
+    const int64_t* so = sd_off + sd_ptr[blk];
+    double* w = W + w_off[blk];
+    for (int64_t idx = ex.tid; idx < nn; idx += ex.nt) {
+      double acc = 0.0;
+      for (int s = 0; s < G.nshare; ++s) acc += SD[so[s] + idx];
+      w[idx] = acc;
+    }
+  }
+};
+
+// D_s = W^{-1} S_s with the Cholesky factor W = G G^T (lower, column-major):
+// one CTA per (edge, sharing subdomain), one column of S_s per thread
+// (forward then backward substitution in place in the output column)
+struct KDeluxeEdgeSolve {
+  BddcView V;
+  const int* edges;
+  const int* task_edge;
+  const int* task_share;
+  const int64_t* sd_ptr;
+  const int64_t* sd_off;
+  const double* SD;
+  const double* W;
+  const int64_t* w_off;
+  double* DE;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int t = task_edge[blk], q = task_share[blk];
+    const MacroDev G = V.macros[edges[t]];
+    const int nd = G.ndual;
+    const double* L = W + w_off[t];
+    const double* S = SD + sd_off[sd_ptr[t] + q];
+    double* D = DE + G.deluxe_e_off + (int64_t)q * nd * nd;
+    for (int c = ex.tid; c < nd; c += ex.nt) {
+      double* x = D + (int64_t)c * nd;
+      for (int i = 0; i < nd; ++i) x[i] = S[(int64_t)c * nd + i];
+      for (int j = 0; j < nd; ++j) {
+        const double xj = x[j] / L[(int64_t)j * nd + j];
+        x[j] = xj;
+        for (int i = j + 1; i < nd; ++i) x[i] -= L[(int64_t)j * nd + i] * xj;
+      }
+      for (int j = nd - 1; j >= 0; --j) {
+        double acc = x[j];
+        for (int i = j + 1; i < nd; ++i) acc -= L[(int64_t)j * nd + i] * x[i];
+        x[j] = acc / L[(int64_t)j * nd + j];
+      }
+    }
+  }
+};
+
 struct GemmTile {
   int face, ti, tj;
 };
@@ -758,8 +822,17 @@ struct KScaleToNeumann {
         double v = 0.0;
         if (a >= G.r) {
           const int k = a - G.r;
-          if (G.deluxe_off >= 0) v = si == 0 ? dtr[k] : dr[k] - dtr[k];
-          else v = dr[k] / G.nshare;
+          if (G.deluxe_off >= 0) {
+            v = si == 0 ? dtr[k] : dr[k] - dtr[k];
+          } else if (G.deluxe_e_off >= 0) {
+            // deluxe edge: (D_s^T r)_k, column k of D_s
+            const double* Dk = V.deluxe_e + G.deluxe_e_off + ((int64_t)si * G.ndual + k) * G.ndual;
+            double acc = 0.0;
+            for (int i = 0; i < G.ndual; ++i) acc += Dk[i] * dr[i];
+            v = acc;
+          } else {
+            v = dr[k] / G.nshare;
+          }
         }
         c[a] = v;
       }
@@ -881,10 +954,21 @@ struct KAverageDual {
       for (int a = ex.tid; a < G.n; a += ex.nt) w[a] = wloc[S.iface_off + gi[a]];
       ex.sync();
       hh_T_par(ex, V, G, w, red);
-      for (int k = ex.tid; k < G.ndual; k += ex.nt) {
-        const double v = w[G.r + k];
-        if (G.deluxe_off >= 0) (si == 0 ? w0 : w1)[G.dual_off + k] = v;
-        else w0[G.dual_off + k] += v / G.nshare;
+      if (G.deluxe_e_off >= 0) {
+        // deluxe edge: w0 += D_s w_s (row k of D_s)
+        ex.sync();
+        const double* Ds = V.deluxe_e + G.deluxe_e_off + (int64_t)si * G.ndual * G.ndual;
+        for (int k = ex.tid; k < G.ndual; k += ex.nt) {
+          double acc = 0.0;
+          for (int i = 0; i < G.ndual; ++i) acc += Ds[(int64_t)i * G.ndual + k] * w[G.r + i];
+          w0[G.dual_off + k] += acc;
+        }
+      } else {
+        for (int k = ex.tid; k < G.ndual; k += ex.nt) {
+          const double v = w[G.r + k];
+          if (G.deluxe_off >= 0) (si == 0 ? w0 : w1)[G.dual_off + k] = v;
+          else w0[G.dual_off + k] += v / G.nshare;
+        }
       }
       ex.sync();
     }
@@ -1978,14 +2062,17 @@ static void setup_core(bddc* b, const int32_t* part) {
         }
       }
       D.deluxe_off = -1;
+      D.deluxe_e_off = -1;
     }
     b->ndual = dual;
     // deluxe problems
     std::vector<int> dl_probs, dl_roots;
     for (size_t q = 0; q < H.probs.size(); ++q)
       if (H.probs[q].kind == PK_DELUXE) { dl_probs.push_back((int)q); dl_roots.push_back(b->h_probs[q].root); }
-    std::vector<int> faces;
+    std::vector<int> faces, edges;
     std::vector<int64_t> sd_i, sd_j, sd_off_v, work_off_v, cw_off;
+    std::vector<int64_t> e_sd, e_sd_ptr(1, 0);
+    int64_t deluxe_e_n = 0;
     {
       // dual block offsets per deluxe problem
       int64_t o = 0, w = 0;
@@ -2015,6 +2102,29 @@ static void setup_core(bddc* b, const int32_t* part) {
       for (int g : faces) {
         cw_off.push_back(c);
         c += (int64_t)b->h_macros[g].ndual * b->h_macros[g].ndual;
+      }
+      // deluxe edges: the dual blocks of all sharing subdomains, in the
+      // order of the entity's sharing list
+      if (b->opt.scaling == BDDC_SCALING_DELUXE_EDGES) {
+        std::map<std::pair<int, int>, int> tq;   // (macro, subdomain) -> deluxe problem
+        for (size_t t = 0; t < dl_probs.size(); ++t)
+          tq[{H.probs[dl_probs[t]].macro, H.probs[dl_probs[t]].sub}] = (int)t;
+        for (size_t g = 0; g < H.macros.size(); ++g) {
+          MacroDev& G = b->h_macros[g];
+          if (G.kind != 1 || G.ndual == 0) continue;
+          std::vector<int64_t> offs;
+          for (int sd : H.macros[g].share) {
+            auto it = tq.find({(int)g, sd});
+            if (it == tq.end()) break;
+            offs.push_back(sd_off_v[it->second]);
+          }
+          if (offs.size() != H.macros[g].share.size()) continue;
+          edges.push_back((int)g);
+          e_sd.insert(e_sd.end(), offs.begin(), offs.end());
+          e_sd_ptr.push_back((int64_t)e_sd.size());
+          G.deluxe_e_off = deluxe_e_n;
+          deluxe_e_n += (int64_t)G.nshare * G.ndual * G.ndual;
+        }
       }
     }
     // ---------------- upload structure
@@ -2096,7 +2206,8 @@ static void setup_core(bddc* b, const int32_t* part) {
     // bounded memory; each chunk's root update matrices are rotated to the
     // dual coordinates and kept, the partial factors are released
     b->d_deluxe.alloc(std::max<int64_t>(deluxe_n, 1));
-    if (!faces.empty()) {
+    b->d_deluxe_e.alloc(std::max<int64_t>(deluxe_e_n, 1));
+    if (!faces.empty() || !edges.empty()) {
       int64_t sdn = 0;
       for (size_t t = 0; t < dl_probs.size(); ++t) {
         const MacroDev& G = b->h_macros[H.probs[dl_probs[t]].macro];
@@ -2154,6 +2265,7 @@ static void setup_core(bddc* b, const int32_t* part) {
         VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe factorization: zero or wrong-signed pivot");
       }
       mark("t_factor_deluxe_ms");
+      if (!faces.empty()) {
       DBuf<int> df;
       DBuf<int64_t> dsi, dsj, dpo, duo;
       std::vector<int64_t> po, uo;
@@ -2188,6 +2300,45 @@ static void setup_core(bddc* b, const int32_t* part) {
       mark("t_deluxe_combine_ms");
       auto stv = status.download(st);
       VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe: face Schur complement sum not positive definite");
+      }
+      if (!edges.empty()) {
+        // deluxe edges: W = sum_s S_s, W = G G^T, D_s = W^{-1} S_s
+        std::vector<DenseItem> items;
+        std::vector<int64_t> wo;
+        std::vector<int> te, ts;
+        int64_t wn = 0;
+        for (size_t t = 0; t < edges.size(); ++t) {
+          const MacroDev& G = b->h_macros[edges[t]];
+          wo.push_back(wn);
+          items.push_back({G.ndual, wn, 0, 0});
+          wn += (int64_t)G.ndual * G.ndual;
+          for (int q = 0; q < G.nshare; ++q) {
+            te.push_back((int)t);
+            ts.push_back(q);
+          }
+        }
+        DBuf<int> de, dte, dts, est(1);
+        DBuf<int64_t> desp, deso, dewo;
+        DBuf<DenseItem> dit;
+        upload_vec(de, edges, st);
+        upload_vec(dte, te, st);
+        upload_vec(dts, ts, st);
+        upload_vec(desp, e_sd_ptr, st);
+        upload_vec(deso, e_sd, st);
+        upload_vec(dewo, wo, st);
+        upload_vec(dit, items, st);
+        DBuf<double> WE(std::max<int64_t>(wn, 1));
+        est.zero(st);
+        V = make_view(b);
+        launch(KDeluxeEdgeSum{V, de.p, desp.p, deso.p, SD.p, WE.p, dewo.p}, (int)edges.size(), 256, 0, st);
+        launch(KCholesky{WE.p, dit.p, est.p}, (int)edges.size(), 256, 0, st);
+        auto ev = est.download(st);
+        VB_CHECK(ev[0] == 0, VEM_ESINGULAR, "deluxe: edge Schur complement sum not positive definite");
+        launch(KDeluxeEdgeSolve{V, de.p, dte.p, dts.p, desp.p, deso.p, SD.p, WE.p, dewo.p, b->d_deluxe_e.p},
+               (int64_t)te.size(), 256, 0, st);
+        VB_CUDA(cudaStreamSynchronize(st));
+        mark("t_deluxe_edges_ms");
+      }
       if (b->keep_sf) {
         b->d_sf = std::move(SD);
         b->sf_faces = faces;
@@ -2342,6 +2493,8 @@ static void configure(bddc* b, vem_system* s, uint32_t constraints, int scaling,
   b->sys = s;
   b->stream = s->stream;
   b->opt.constraints = constraints;
+  VB_CHECK(scaling >= BDDC_SCALING_MULTIPLICITY && scaling <= BDDC_SCALING_DELUXE_EDGES, VEM_EINVAL,
+           "bddc_setup: scaling must be 0 (multiplicity), 1 (deluxe faces) or 2 (deluxe faces and edges)");
   b->opt.scaling = scaling;
   if (!opts) return;
   if (opts->nd_leaf > 0) b->opt.leaf = opts->nd_leaf;
@@ -2364,7 +2517,7 @@ extern "C" int bddc_setup(vem_system* s, const int32_t* part, uint32_t constrain
   bddc* b = new bddc();
   try {
     configure(b, s, constraints, scaling, opts);
-    const bool adaptive = b->adapt_theta > 0.0 && scaling == BDDC_SCALING_DELUXE && !(constraints & BDDC_ALL);
+    const bool adaptive = b->adapt_theta > 0.0 && scaling >= BDDC_SCALING_DELUXE && !(constraints & BDDC_ALL);
     b->keep_sf = adaptive;
     setup_core(b, part);
     if (adaptive) {
@@ -2531,6 +2684,15 @@ extern "C" int bddc_info(bddc* b, const char* key, double* value) {
     double t = 0;
     for (auto& G : b->h_macros)
       if (G.deluxe_off >= 0) t += 8.0 * G.ndual * G.ndual;
+    *value = t;
+  } else if (k == "n_deluxe_edges") {
+    int c = 0;
+    for (auto& G : b->h_macros) c += G.deluxe_e_off >= 0;
+    *value = c;
+  } else if (k == "deluxe_edge_bytes") {
+    double t = 0;
+    for (auto& G : b->h_macros)
+      if (G.deluxe_e_off >= 0) t += 8.0 * G.nshare * G.ndual * G.ndual;
     *value = t;
   } else if (k == "phi_bytes") *value = 8.0 * b->d_phi.n;
   else if (k == "coarse_bytes") *value = 8.0 * b->d_Kinv.n;

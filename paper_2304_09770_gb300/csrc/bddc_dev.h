@@ -31,6 +31,7 @@ struct SubDev {
 struct MacroDev {
   int kind, n, r, nshare, ndual;
   int64_t dofs_off, hv_off, tau_off, coarse0, dual_off, share_off, gpos_off, gif_off, deluxe_off;
+  int64_t deluxe_e_off;   // deluxe edge: D^(share[s]) at deluxe_e + deluxe_e_off + s ndual^2; -1 otherwise
 };
 
 // the arrays every BDDC kernel reads
@@ -75,6 +76,7 @@ struct BddcView {
   const int* gpos;           // (entity, sharing subdomain) -> Neumann positions of its DOFs
   const int* gif;            // (entity, sharing subdomain) -> local interface index of its DOFs
   const double* deluxe;      // D^(share[0]) per deluxe face
+  const double* deluxe_e;    // D^(s) for every sharing subdomain s per deluxe edge
   int64_t ncv, nc;           // coarse velocity coordinates, all coarse coordinates
 };
 

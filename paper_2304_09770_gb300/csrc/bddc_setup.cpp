@@ -1,7 +1,8 @@
 // Host-side BDDC setup (Sec. 4-6): interface classification into macro
 // vertices, edges and faces, the primal constraints of Sec. 5.1 as a
 // Householder change of basis, and the nested-dissection symbolic analysis
-// of the subdomain Dirichlet, constrained Neumann and deluxe face problems.
+// of the subdomain Dirichlet, constrained Neumann and deluxe face (and edge)
+// problems.
 #include "bddc_setup.h"
 
 #include <algorithm>
@@ -543,12 +544,17 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
       // ---- problems
       std::vector<int> kinds = {PK_DIRICHLET, PK_NEUMANN};
       std::vector<int> dl_macro;
-      if (o.scaling == 1 && !all_primal)
-        for (int gi : S.macros)
-          if (H.macros[gi].kind == 2 && H.macros[gi].r < (int)H.macros[gi].dofs.size()) {
+      if (o.scaling >= 1 && !all_primal)
+        for (int gi : S.macros) {
+          // deluxe problems: every macro face, and every macro edge with
+          // scaling 2, that has dual coordinates
+          const Macro& M = H.macros[gi];
+          const bool dlx = M.kind == 2 || (M.kind == 1 && o.scaling == 2);
+          if (dlx && M.r < (int)M.dofs.size()) {
             kinds.push_back(PK_DELUXE);
             dl_macro.push_back(gi);
           }
+        }
       int dl = 0;
       for (int kind : kinds) {
         Problem P;
@@ -744,7 +750,7 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
         if (kind == PK_DELUXE) {
           Node& R = P.nodes.back();
           VB_CHECK(R.nb == (int)H.macros[P.macro].dofs.size(), VEM_EINVAL,
-                   "symbolic: deluxe root border differs from the face");
+                   "symbolic: deluxe root border differs from the macro entity");
           R.flags = 1;
         } else {
           VB_CHECK(P.nodes.back().nb == 0, VEM_EINVAL, "symbolic: root with a border");

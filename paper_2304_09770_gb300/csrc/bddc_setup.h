@@ -79,7 +79,7 @@ struct BddcHost {
 
 struct SetupOptions {
   uint32_t constraints = 0xF;    // 1 vertex, 2 edge, 4 face, 8 flux; 16 all-interface-primal
-  int scaling = 1;               // 0 multiplicity, 1 deluxe on faces
+  int scaling = 1;               // 0 multiplicity, 1 deluxe on faces, 2 deluxe on faces and edges
   int leaf = 4;                  // elements per nested-dissection leaf
   // adaptive primal rows (Sec. 6) per macro index: concatenated functionals
   // over the macro's DOFs (its dofs order), appended to the face constraints
