@@ -17,6 +17,10 @@ uniform offsets in ``[-a h, a h]^3`` drawn in lexicographic vertex order
 quadrilaterals, so every quadrilateral is then split into two triangles
 along the diagonal through its smallest-index vertex, giving polyhedra with
 8 vertices, 18 edges and 12 triangular faces.
+
+The OCTA family (``octa_mesh``) embeds an octahedron at the centre of every
+``2 x 2 x 2`` block of grid cubes; its vertex, edge and face counts
+reproduce the DOF counts the paper prints for its OCTA meshes.
 """
 import numpy as np
 
@@ -103,6 +107,115 @@ def cube_mesh(n, perturb=0.0, seed=None, split_quads=None):
     elem_face = np.array([f for e in elem_faces for f in e], dtype=np.int32)
     return {
         "n": n, "h": h, "xyz": xyz,
+        "face_ptr": face_ptr, "face_vtx": face_vtx,
+        "elem_ptr": elem_ptr, "elem_face": elem_face,
+        "elem_ijk": np.array(elem_ijk, dtype=np.int32),
+    }
+
+
+def octa_mesh(m, cut=0.5):
+    """OCTA family: the ``(2m)^3`` grid of cubes of [0,1]^3 in which the
+    common vertex of every ``2 x 2 x 2`` block of cubes is cut away by an
+    octahedron whose six vertices lie on the six grid edges at that vertex,
+    at distance ``cut * h`` from it (h = 1/(2m)).  Elements: ``m^3``
+    octahedra and ``8 m^3`` cubes with one corner truncated (3
+    quadrilaterals, 3 pentagons, 1 triangle), ``9 m^3`` in all; grid faces
+    through a removed vertex become pentagons.  Element order: the cubes in
+    lexicographic order (x fastest), then the octahedra by block.
+    ``elem_ijk`` gives each cube its grid cell and each octahedron the
+    lowest cell of its block, so that ``box_partition`` with box edges on
+    block boundaries keeps every block in one box.
+    """
+    n = 2 * m
+    h = 1.0 / n
+
+    def centre(i, j, l):
+        return i % 2 == 1 and j % 2 == 1 and l % 2 == 1
+
+    vid, xyz = {}, []
+    for l in range(n + 1):
+        for j in range(n + 1):
+            for i in range(n + 1):
+                if not centre(i, j, l):
+                    vid[(i, j, l)] = len(xyz)
+                    xyz.append((i * h, j * h, l * h))
+    blocks = [(2 * a + 1, 2 * b + 1, 2 * c + 1) for c in range(m) for b in range(m) for a in range(m)]
+    ov = {}   # (block centre, axis, sign) -> octahedron vertex
+    for ctr in blocks:
+        for axis in range(3):
+            for sg in (-1, 1):
+                p = [ctr[0] * h, ctr[1] * h, ctr[2] * h]
+                p[axis] += sg * cut * h
+                ov[(ctr, axis, sg)] = len(xyz)
+                xyz.append(tuple(p))
+
+    def toward(ctr, q):
+        d = [q[t] - ctr[t] for t in range(3)]
+        axis = int(np.nonzero(d)[0][0])
+        return ov[(ctr, axis, int(np.sign(d[axis])))]
+
+    def loop(corners):
+        out = []
+        for t, q in enumerate(corners):
+            if centre(*q):
+                out.append(toward(q, corners[t - 1]))
+                out.append(toward(q, corners[(t + 1) % len(corners)]))
+            else:
+                out.append(vid[q])
+        return tuple(out)
+
+    faces, fx, fy, fz = [], {}, {}, {}
+    for l in range(n):
+        for j in range(n):
+            for i in range(n + 1):
+                fx[(i, j, l)] = len(faces)
+                faces.append(loop([(i, j, l), (i, j + 1, l), (i, j + 1, l + 1), (i, j, l + 1)]))
+    for l in range(n):
+        for j in range(n + 1):
+            for i in range(n):
+                fy[(i, j, l)] = len(faces)
+                faces.append(loop([(i, j, l), (i, j, l + 1), (i + 1, j, l + 1), (i + 1, j, l)]))
+    for l in range(n + 1):
+        for j in range(n):
+            for i in range(n):
+                fz[(i, j, l)] = len(faces)
+                faces.append(loop([(i, j, l), (i + 1, j, l), (i + 1, j + 1, l), (i, j + 1, l)]))
+    # octahedron faces, oriented outward from the octahedron (normal along
+    # the sign vector s; the loop x, y, z has normal sx sy sz * s)
+    tri = {}
+    for ctr in blocks:
+        for sz in (-1, 1):
+            for sy in (-1, 1):
+                for sx in (-1, 1):
+                    t = [ov[(ctr, 0, sx)], ov[(ctr, 1, sy)], ov[(ctr, 2, sz)]]
+                    if sx * sy * sz < 0:
+                        t = t[::-1]
+                    tri[(ctr, sx, sy, sz)] = len(faces)
+                    faces.append(tuple(t))
+
+    elem_faces, elem_ijk = [], []
+    for l in range(n):
+        for j in range(n):
+            for i in range(n):
+                ef = [-(fx[(i, j, l)] + 1), fx[(i + 1, j, l)] + 1, -(fy[(i, j, l)] + 1), fy[(i, j + 1, l)] + 1,
+                      -(fz[(i, j, l)] + 1), fz[(i, j, l + 1)] + 1]
+                ci, cj, cl = (i if i % 2 else i + 1), (j if j % 2 else j + 1), (l if l % 2 else l + 1)
+                s = (1 if i == ci else -1, 1 if j == cj else -1, 1 if l == cl else -1)
+                ef.append(-(tri[((ci, cj, cl),) + s] + 1))
+                elem_faces.append(ef)
+                elem_ijk.append((i, j, l))
+    for ctr in blocks:
+        elem_faces.append([tri[(ctr, sx, sy, sz)] + 1 for sz in (-1, 1) for sy in (-1, 1) for sx in (-1, 1)])
+        elem_ijk.append((ctr[0] - 1, ctr[1] - 1, ctr[2] - 1))
+
+    face_ptr = np.zeros(len(faces) + 1, dtype=np.int32)
+    face_ptr[1:] = np.cumsum([len(f) for f in faces])
+    face_vtx = np.array([v for f in faces for v in f], dtype=np.int32)
+    elem_ptr = np.zeros(len(elem_faces) + 1, dtype=np.int32)
+    elem_ptr[1:] = np.cumsum([len(e) for e in elem_faces])
+    elem_face = np.array([f for e in elem_faces for f in e], dtype=np.int32)
+    return {
+        "n": n, "h": h, "xyz": np.array(xyz, dtype=np.float64),
         "face_ptr": face_ptr, "face_vtx": face_vtx,
         "elem_ptr": elem_ptr, "elem_face": elem_face,
         "elem_ijk": np.array(elem_ijk, dtype=np.int32),
