@@ -6,7 +6,7 @@ returns the arrays; nothing here computes anything of the method.
 """
 import numpy as np
 
-from .mesh import cube_mesh, box_partition, greedy_partition, element_vertex_average
+from .mesh import cube_mesh, octa_mesh, box_partition, greedy_partition, element_vertex_average
 from .fields import manufactured_f, sinker_centres, sinker_viscosity, sinker_load
 
 CONFIGS = {
@@ -35,14 +35,26 @@ CONFIGS = {
     "tri6_greedy": dict(n=6, perturb=0.15, seed=11, k=2, greedy=(8, 31), load="manufactured"),
     "sinker8": dict(n=8, perturb=0.0, seed=None, k=2, parts=(2, 2, 2), load="sinker",
                     sinkers=(8, 5), dr=1e4),
+    # OCTA family (octahedra in 2x2x2 blocks of cubes): 9 m^3 elements; the
+    # 15,552-element mesh of the paper's OCTA tests, and small parity cases
+    # with one block (9 elements) per subdomain
+    "octa12_k2": dict(family="octa", m=12, k=2, parts=(4, 4, 4), load="manufactured"),
+    "octa2_k2": dict(family="octa", m=2, k=2, parts=(2, 2, 2), load="manufactured"),
+    "octa2_k3": dict(family="octa", m=2, k=3, parts=(2, 2, 2), load="manufactured"),
+    "octa2_k4": dict(family="octa", m=2, k=4, parts=(2, 2, 2), load="manufactured"),
+    "octa2_sinker": dict(family="octa", m=2, k=2, parts=(2, 2, 2), load="sinker", sinkers=(8, 5), dr=1e4),
 }
 
 
 def make_config(name, **override):
     c = dict(CONFIGS[name])
     c.update(override)
-    mesh = cube_mesh(c["n"], c["perturb"], c["seed"])
-    ne = c["n"] ** 3
+    if c.get("family") == "octa":
+        mesh = octa_mesh(c["m"])
+        ne = 9 * c["m"] ** 3
+    else:
+        mesh = cube_mesh(c["n"], c["perturb"], c["seed"])
+        ne = c["n"] ** 3
     xk = element_vertex_average(mesh)
     if c["load"] == "sinker":
         centres = sinker_centres(*c["sinkers"])
