@@ -109,11 +109,22 @@ class DofMap:
     component), face DOFs (per face, per P_{k-2} monomial, (n, t1, t2)),
     then per element D4 and D5.  Pressure: per element, dim P_{k-1}
     coefficients of the scaled monomials.
+
+    reduced: the reduced scheme (Remark after the convergence theorem, Sec.
+    3): the velocity is restricted to fields whose element divergence
+    moments of degree >= 1 vanish (every D5 DOF is fixed to zero, like a
+    Dirichlet DOF) and the pressure to one constant per element.  The
+    velocity of the full scheme is divergence-free, so it lies in that
+    subspace and the two schemes give the same velocity.
     """
 
-    def __init__(self, topo, k):
+    def __init__(self, topo, k, reduced=False):
         self.k = k
-        c = counts(k)
+        self.reduced = reduced
+        c = dict(counts(k))
+        self.press_full = c["press"]
+        if reduced:
+            c["press"] = 1
         self.c = c
         self.off_v = 0
         self.off_e = topo.nV * 3
@@ -128,6 +139,10 @@ class DofMap:
             fixed[self.off_e + ed * c["edge"]: self.off_e + (ed + 1) * c["edge"]] = True
         for f in np.nonzero(topo.bnd_face)[0]:
             fixed[self.off_f + f * c["face"]: self.off_f + (f + 1) * c["face"]] = True
+        if reduced:
+            for e in range(topo.nE):
+                b = self.off_k + e * self.n_elem_int + c["d4"]
+                fixed[b:b + c["d5"]] = True
         self.fixed = fixed
         self.free = np.nonzero(~fixed)[0]
         self.free_index = -np.ones(self.nvel, dtype=np.int64)
@@ -610,9 +625,9 @@ class System:
     """Global saddle system (Eq. MatrixForm) over all velocity DOFs and the
     element pressures; Dirichlet velocity DOFs are eliminated on solve."""
 
-    def __init__(self, mesh, k, nu, f=None, load_deg=None, elements=None):
+    def __init__(self, mesh, k, nu, f=None, load_deg=None, elements=None, reduced=False):
         self.topo = Topology(mesh)
-        self.dm = DofMap(self.topo, k)
+        self.dm = DofMap(self.topo, k, reduced)
         self.k = k
         topo, dm = self.topo, self.dm
         ne = topo.nE
@@ -632,10 +647,10 @@ class System:
             pr = np.arange(e * npk, (e + 1) * npk)
             brow.append(np.repeat(pr, len(d)))
             bcol.append(np.tile(d, npk))
-            bval.append(el.B.ravel())
+            bval.append(el.B[:npk].ravel())
             if f is not None:
                 F[d] += el.load(f)
-            self.wmean[pr] = el.vq_w @ mono3(k - 1, el.xi)     # int_K m_a
+            self.wmean[pr] = (el.vq_w @ mono3(k - 1, el.xi))[:npk]     # int_K m_a
             self.elements[e] = el
         self.A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                                shape=(dm.nvel, dm.nvel))
@@ -660,7 +675,7 @@ class System:
             cols.append(np.tile(dk, len(dk)))
             vals.append(Ak.ravel())
             pr = nvf + np.arange(e * npk, (e + 1) * npk)
-            Bk = el.B[:, keep]
+            Bk = el.B[:npk, keep]
             rows.append(np.repeat(pr, len(dk)))
             cols.append(np.tile(dk, len(pr)))
             vals.append(Bk.ravel())
@@ -700,3 +715,23 @@ class System:
         u[fx] = ud
         p = x[len(fr):len(fr) + dm.npress]
         return u, p
+
+    def full_pressure(self, u, p0, F=None):
+        """Reduced scheme: the P_{k-1} pressure coefficients of every element
+        from the velocity u (all DOFs) and the element constants p0.  The
+        higher coefficients p^ follow from the element's D5 velocity rows,
+        A_5 u + B_0,5^T p0 + B^_5^T p^ = F_5 (B^_5 = |K| I on the D5 DOFs)."""
+        dm = self.dm
+        assert dm.reduced
+        F = self.F if F is None else F
+        npf = dm.press_full
+        Au = self.A @ u
+        p = np.zeros(self.topo.nE * npf)
+        for e, el in self.elements.items():
+            j = np.arange(el.off_5, el.nK)
+            g = el.dofs[j]
+            rhs = F[g] - Au[g] - el.B[0, j] * p0[e]
+            p[e * npf] = p0[e]
+            if len(j):
+                p[e * npf + 1:(e + 1) * npf] = np.linalg.solve(el.B[1:, j].T, rhs)
+        return p
