@@ -87,7 +87,19 @@ typedef struct bddc bddc;
  * pressures (Eq. MatrixForm).  nu_per_element: host [nE].  Synchronizes. */
 int vem_assemble(const vem_mesh* mesh, int k, const double* nu_per_element, vem_system** out);
 
-/* Statistics by name: "nnz" (nonzeros of K), "n_elements", and the
+/* The reduced scheme (the remark after the convergence theorem, Sec. 3):
+ * as vem_assemble, but the velocity is restricted to fields whose element
+ * divergence moments of degree >= 1 vanish (every D5 DOF is eliminated like
+ * a Dirichlet DOF, with value 0) and the pressure to one constant per
+ * element (B keeps its first row, the face fluxes).  The full scheme's
+ * velocity is divergence-free and therefore lies in this space, so the
+ * velocity is the same; the system has nE * (2 dim P_{k-1} - 2) fewer
+ * unknowns.  vem_dof_layout reports nE pressures; every other call works
+ * unchanged on the reduced system. */
+int vem_assemble_reduced(const vem_mesh* mesh, int k, const double* nu_per_element, vem_system** out);
+
+/* Statistics by name: "nnz" (nonzeros of K), "n_elements", "reduced" (1 for
+ * a system of vem_assemble_reduced), and the
  * vem_assemble phase wall times (host clock) "t_topology_ms" (topology, DOF
  * numbering, element records), "t_element_launch_ms" (uploads and the
  * element kernel launch), "t_pattern_ms" (CSR pattern on the host while the

@@ -47,6 +47,7 @@ def lib():
         i64p = ctypes.POINTER(ctypes.c_int64)
         L.vem_assemble.argtypes = [ctypes.POINTER(_Mesh), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(P)]
+        L.vem_assemble_reduced.argtypes = L.vem_assemble.argtypes
         L.vem_dof_layout.argtypes = [P, i64p, i64p, i64p]
         L.vem_free_dofs.argtypes = [P, i64p]
         L.vem_quad_points.argtypes = [P, ctypes.c_int, i64p, P]
@@ -104,9 +105,10 @@ def _dptr(t):
 
 
 class VemSystem:
-    """vem_assemble: VEM discretization of degree k on a polyhedral mesh."""
+    """vem_assemble: VEM discretization of degree k on a polyhedral mesh
+    (reduced=True: vem_assemble_reduced, the reduced scheme)."""
 
-    def __init__(self, mesh, k, nu):
+    def __init__(self, mesh, k, nu, reduced=False):
         L = lib()
         self._keep = dict(
             xyz=np.ascontiguousarray(mesh["xyz"], dtype=np.float64),
@@ -122,10 +124,12 @@ class VemSystem:
                   len(kp["ep"]) - 1, kp["ep"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                   kp["ef"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
         h = ctypes.c_void_p()
-        _check(L.vem_assemble(ctypes.byref(m), int(k), nu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                              ctypes.byref(h)))
+        fn = L.vem_assemble_reduced if reduced else L.vem_assemble
+        _check(fn(ctypes.byref(m), int(k), nu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(h)))
         self.h = h
         self.k = k
+        self.reduced = bool(reduced)
+        self.nE = len(kp["ep"]) - 1
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(L.vem_dof_layout(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         self.n_vel_free, self.n_press, self.n_vel = a.value, b.value, c.value
@@ -176,7 +180,7 @@ class VemSystem:
         # probe size with the first element
         e0 = elems[:1]
         _check(lib().vem_element_matrices(self.h, _ptr(e0), 1, ctypes.byref(nk), None, None, None))
-        n, npk = nk.value, {2: 4, 3: 10, 4: 20}[self.k]
+        n, npk = nk.value, self.n_press // self.nE
         A = np.zeros((len(elems), n, n))
         B = np.zeros((len(elems), npk, n))
         D = np.zeros((len(elems), n), dtype=np.int64)

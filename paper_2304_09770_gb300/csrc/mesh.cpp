@@ -143,14 +143,19 @@ void build_topology(const vem_mesh* m, Topo& t) {
   }
 }
 
-void number_dofs(const Topo& t, int k, DofNumbering& d) {
+// reduced: the reduced scheme (the remark after the convergence theorem):
+// every D5 DOF (element divergence moment of degree >= 1) is fixed to zero
+// like a Dirichlet DOF, and the pressure keeps one constant per element
+void number_dofs(const Topo& t, int k, DofNumbering& d, bool reduced) {
   VB_CHECK(k >= 2 && k <= 4, VEM_EINVAL, "degree k must be 2, 3 or 4");
   d.k = k;
   d.ce = 3 * (k - 1);
   d.cf = 3 * pdim2(k - 2);
   d.n4 = n_d4(k);
   d.n5 = n_d5(k);
-  d.np = pdim3(k - 1);
+  d.np_full = pdim3(k - 1);
+  d.np = reduced ? 1 : d.np_full;
+  d.reduced = reduced;
   d.off_e = 3LL * t.nV;
   d.off_f = d.off_e + (int64_t)t.nEd * d.ce;
   d.off_k = d.off_f + (int64_t)t.nF * d.cf;
@@ -162,6 +167,9 @@ void number_dofs(const Topo& t, int k, DofNumbering& d) {
     if (t.bnd_e[e]) for (int j = 0; j < d.ce; ++j) fixed[d.off_e + (int64_t)e * d.ce + j] = 1;
   for (int f = 0; f < t.nF; ++f)
     if (t.bnd_f[f]) for (int j = 0; j < d.cf; ++j) fixed[d.off_f + (int64_t)f * d.cf + j] = 1;
+  if (reduced)
+    for (int e = 0; e < t.nE; ++e)
+      for (int j = 0; j < d.n5; ++j) fixed[d.off_k + (int64_t)e * (d.n4 + d.n5) + d.n4 + j] = 1;
   d.free_index.assign(d.nvel, -1);
   d.free_to_global.clear();
   for (int64_t g = 0; g < d.nvel; ++g)

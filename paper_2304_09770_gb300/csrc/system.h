@@ -37,6 +37,8 @@ struct Topo {
 struct DofNumbering {
   int k = 2;
   int ce = 0, cf = 0, n4 = 0, n5 = 0, np = 0;      // per entity / element counts
+  int np_full = 0;                                 // dim P_{k-1} (np is 1 in the reduced scheme)
+  bool reduced = false;                            // D5 fixed to zero, element-constant pressure
   int64_t off_e = 0, off_f = 0, off_k = 0, nvel = 0;
   int64_t nvf = 0, npress = 0;                     // free velocity, pressures
   std::vector<int64_t> free_index;                 // global velocity -> free index or -1
@@ -44,7 +46,7 @@ struct DofNumbering {
 };
 
 void build_topology(const vem_mesh* m, Topo& t);
-void number_dofs(const Topo& t, int k, DofNumbering& d);
+void number_dofs(const Topo& t, int k, DofNumbering& d, bool reduced = false);
 // element-local velocity DOFs (global numbers) in the element-local order
 void element_global_dofs(const Topo& t, const DofNumbering& d, int e, std::vector<int64_t>& out);
 void build_elem_records(const Topo& t, const DofNumbering& d, std::vector<ElemRec>& recs);

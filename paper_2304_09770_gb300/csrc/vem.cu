@@ -263,6 +263,19 @@ struct KGatherRhs {
   }
 };
 
+// reduced scheme: keep row 0 (the constant-pressure row, the face fluxes) of
+// every element's B_K, one CTA per element
+struct KCompactB {
+  const double* Bfull;
+  double* B;
+  const int64_t* offK;
+  int npf;
+  VB_HD void operator()(const KExec& ex, int e) const {
+    const int64_t o = offK[e], nK = offK[e + 1] - o;
+    for (int64_t c = ex.tid; c < nK; c += ex.nt) B[o + c] = Bfull[(int64_t)npf * o + c];
+  }
+};
+
 template <int K>
 static void launch_elements(vem_system* s, const DBuf<int64_t>& offK, const DBuf<int64_t>& offK2) {
   const int nE = s->topo.nE;
@@ -272,13 +285,29 @@ static void launch_elements(vem_system* s, const DBuf<int64_t>& offK, const DBuf
   DBuf<int> status(1);
   status.zero(s->stream);
   size_t smem = ((sizeof(ElemShared<K>) + 7) / 8) * 8 + sizeof(ElemRec);
-  DBuf<double> wm((size_t)nE * pdim3(K - 1));
-  KElement<K> f{s->d_rec.p, s->d_xyz.p, s->d_nu.p, offK.p, offK2.p, s->d_tab.p, s->d_A.p, s->d_B.p,
+  const int npf = pdim3(K - 1);
+  DBuf<double> wm((size_t)nE * npf);
+  // the reduced scheme keeps one B row per element: the full rows go to a
+  // temporary and row 0 is copied out
+  DBuf<double> Bfull;
+  double* Bdst = s->d_B.p;
+  if (s->dof.reduced) {
+    Bfull.alloc((size_t)npf * s->h_eoff.back());
+    Bdst = Bfull.p;
+  }
+  KElement<K> f{s->d_rec.p, s->d_xyz.p, s->d_nu.p, offK.p, offK2.p, s->d_tab.p, s->d_A.p, Bdst,
                 s->d_P0.p, wm.p, scratch.p, stride, nE, grid, status.p};
   launch(f, grid, 128, smem, s->stream);
+  if (s->dof.reduced) launch(KCompactB{Bfull.p, s->d_B.p, offK.p, npf}, nE, 128, 0, s->stream);
   auto st = status.download(s->stream);
   VB_CHECK(st[0] == 0, VEM_ESINGULAR, "element projector system singular (degenerate element)");
-  s->elem_wmean = wm.download(s->stream);
+  std::vector<double> w = wm.download(s->stream);
+  if (s->dof.reduced) {
+    s->elem_wmean.assign(nE, 0.0);
+    for (int e = 0; e < nE; ++e) s->elem_wmean[e] = w[(size_t)e * npf];
+  } else {
+    s->elem_wmean = std::move(w);
+  }
 }
 
 static void load_tables(vem_system* s) {
@@ -298,7 +327,7 @@ static int fail(const Error& e) {
 
 extern "C" const char* vem_last_error(void) { return vb::g_last_error.c_str(); }
 
-extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_system** out) {
+static int assemble(const vem_mesh* mesh, int k, const double* nu, bool reduced, vem_system** out) {
   if (!out || !nu) { set_last_error("vem_assemble: null argument"); return VEM_EINVAL; }
   *out = nullptr;
   if (k < 2 || k > 4) { set_last_error("vem_assemble: degree k must be 2, 3 or 4"); return VEM_EINVAL; }
@@ -311,7 +340,7 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
       t0 = t1;
     };
     build_topology(mesh, s->topo);
-    number_dofs(s->topo, k, s->dof);
+    number_dofs(s->topo, k, s->dof, reduced);
     const Topo& t = s->topo;
     const DofNumbering& d = s->dof;
     std::vector<ElemRec> recs;
@@ -410,11 +439,20 @@ extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_s
   }
 }
 
+extern "C" int vem_assemble(const vem_mesh* mesh, int k, const double* nu, vem_system** out) {
+  return assemble(mesh, k, nu, false, out);
+}
+
+extern "C" int vem_assemble_reduced(const vem_mesh* mesh, int k, const double* nu, vem_system** out) {
+  return assemble(mesh, k, nu, true, out);
+}
+
 extern "C" int vem_info(const vem_system* s, const char* key, double* value) {
   if (!s || !key || !value) { set_last_error("vem_info: null argument"); return VEM_EINVAL; }
   const std::string k(key);
   if (k == "nnz") { *value = (double)s->nnz; return VEM_OK; }
   if (k == "n_elements") { *value = s->topo.nE; return VEM_OK; }
+  if (k == "reduced") { *value = s->dof.reduced ? 1.0 : 0.0; return VEM_OK; }
   for (auto& pr : s->times)
     if (pr.first == k) { *value = pr.second; return VEM_OK; }
   set_last_error("vem_info: unknown key " + k);

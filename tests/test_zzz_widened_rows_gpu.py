@@ -1,4 +1,4 @@
-"""GPU parity, through the C-ABI, of two extensions of the BDDC-PCG path
+"""GPU parity, through the C-ABI, of three extensions of the BDDC-PCG path
 against the CPU oracle:
 
 * deluxe scaling on macro edges (bddc_setup scaling 2): D_E^(k) =
@@ -8,7 +8,11 @@ against the CPU oracle:
 * the OCTA mesh family (octahedra embedded in 2x2x2 blocks of cubes, cubes
   with one truncated corner, pentagonal faces): element matrices at k = 2,
   3, 4, global CSR and load, BDDC-PCG, and the paper's 15,552-element OCTA
-  mesh by properties.
+  mesh by properties;
+* the reduced scheme (vem_assemble_reduced: D5 eliminated with value 0,
+  element-constant pressure): element matrices, CSR and load against the
+  oracle's reduced System, BDDC-PCG against the oracle's BDDC on it, and
+  the velocity against the full scheme's direct solve.
 
 Tolerances as in the other parity tests: element matrices and assembly to
 rounding; PCG within +-1 iteration (+-3 at viscosity contrast), lambda_max
@@ -162,3 +166,54 @@ def test_octa_full_size_properties(pkg):
     r = rhs - g.apply(u)
     assert torch.linalg.norm(r).item() <= 1e-7 * torch.linalg.norm(rhs).item()
     assert torch.abs(r[g.n_vel_free:]).max().item() <= 1e-7 * torch.abs(rhs).max().item()
+
+
+def _setup_reduced(pkg, name):
+    cfg = make_config(name)
+    k = cfg["k"]
+    deg = k + 9
+    g = pkg.VemSystem(cfg["mesh"], k, cfg["nu"], reduced=True)
+    rhs = g.load(deg, cfg["f"](g.quad_points(deg)))
+    S = System(cfg["mesh"], k, cfg["nu"], f=cfg["f"], load_deg=deg, reduced=True)
+    F = np.concatenate([S.F[S.dm.free], np.zeros(S.dm.npress)])
+    return cfg, g, rhs, S, F
+
+
+@pytest.mark.parametrize("name", ["tri4_k2", "octa2_k3"])
+def test_reduced_system_matches_oracle(pkg, name):
+    cfg, g, rhs, S, F = _setup_reduced(pkg, name)
+    assert g.info("reduced") == 1.0
+    assert g.n_press == S.topo.nE and np.array_equal(g.free_dofs(), S.dm.free)
+    elems = [0, 5, 21]
+    A, B, D = g.element_matrices(elems)
+    for i, e in enumerate(elems):
+        el = S.elements[e]
+        assert np.abs(A[i] - el.A).max() <= 1e-11 * np.abs(el.A).max()
+        assert B.shape[1] == 1 and np.abs(B[i, 0] - el.B[0]).max() <= 1e-11 * np.abs(el.B[0]).max()
+    Kg = g.csr().toarray()
+    Ko = S.free_matrix().toarray()
+    assert np.abs(Kg - Ko).max() <= 1e-12 * np.abs(Ko).max()
+    assert np.abs(rhs.cpu().numpy() - F).max() <= 1e-12 * np.abs(F).max()
+
+
+@pytest.mark.parametrize("name,scaling", [("tri4_k2", "deluxe"), ("octa2_k3", "deluxe_edges"),
+                                          ("tri6_k2", "deluxe")])
+def test_reduced_pcg_matches_oracle(pkg, name, scaling):
+    import torch
+    cfg, g, rhs, S, F = _setup_reduced(pkg, name)
+    bd = pkg.Bddc(g, cfg["part"], scaling=SCALING[scaling])
+    u = torch.zeros_like(rhs)
+    res = bd.solve(rhs, u, rtol=1e-8, maxit=300)
+    assert res["status"] == 0 and res["lam_min"] > 1.0 - 1e-8
+    ro = BDDC(S, cfg["part"], scaling=scaling).pcg(F, rtol=1e-8)
+    assert abs(res["iters"] - ro["iters"]) <= 1
+    nvf = len(S.dm.free)
+    x = u.cpu().numpy()
+    tol = 1e-10 if res["iters"] == ro["iters"] else 1e-8
+    assert np.linalg.norm(x[:nvf] - ro["x"][:nvf]) <= tol * np.linalg.norm(ro["x"][:nvf])
+    # the same velocity as the full scheme (its direct solve), within the CG tolerance
+    full = System(cfg["mesh"], cfg["k"], cfg["nu"], f=cfg["f"], load_deg=cfg["k"] + 9)
+    ud, _ = full.solve_direct()
+    ur = np.zeros(S.dm.nvel)
+    ur[S.dm.free] = x[:nvf]
+    assert np.linalg.norm(ur - ud) <= 1e-6 * np.linalg.norm(ud)
