@@ -336,6 +336,17 @@ CONFIG_RUNS = [
     ("sinker32_dr1e4", 0, 0.0), ("sinker32_dr1e4", 1, 0.0), ("sinker32_dr1e4", 0, 10.0), ("sinker32_dr1e4", 1, 10.0),
     ("sinker32_dr1e6", 0, 0.0), ("sinker32_dr1e6", 0, 10.0), ("sinker32_dr1e6", 1, 10.0),
 ]
+# further runs (workload, precision, theta, options): theta (nu_tol) sweep on
+# configurations 2 and 4, deluxe scaling on edges at viscosity contrast, the
+# paper's 15,552-element OCTA mesh, and the reduced scheme
+EXTRA_RUNS = [
+    ("tri32_k2", 0, 2.0, {}), ("tri32_k2", 0, 5.0, {}), ("tri16_k4", 0, 2.0, {}), ("tri16_k4", 0, 5.0, {}),
+    ("sinker32_dr1e4", 0, 0.0, {"scaling": 2}), ("sinker32_dr1e4", 1, 0.0, {"scaling": 2}),
+    ("sinker32_dr1e6", 0, 0.0, {"scaling": 2}), ("sinker32_dr1e6", 0, 10.0, {"scaling": 2}),
+    ("octa12_k2", 0, 0.0, {}), ("octa12_k2", 1, 0.0, {}), ("octa12_k2", 0, 2.0, {}),
+    ("tri32_k2", 0, 0.0, {"reduced": True}), ("tri32_k2", 1, 0.0, {"reduced": True}),
+    ("tri16_k4", 0, 0.0, {"reduced": True}),
+]
 
 
 def run_configs(args):
@@ -349,7 +360,8 @@ def run_configs(args):
     from synth import make_config
     only = set(args.only.split(",")) if args.only else None
     cache = {}
-    for name, prec, theta in CONFIG_RUNS:
+    runs = [r + ({},) for r in CONFIG_RUNS] + (EXTRA_RUNS if args.extra else [])
+    for name, prec, theta, opt in runs:
         if only and name not in only:
             continue
         cfg = cache.get(name) or make_config(name)
@@ -357,12 +369,14 @@ def run_configs(args):
         cache[name] = cfg
         k = cfg["k"]
         deg = 2 * k - 2   # load rule: enough for the solver study, small host arrays at 48^3
-        line = {"workload": name, "precision": prec, "adaptive": theta, "k": k,
+        scaling, reduced = opt.get("scaling", 1), bool(opt.get("reduced", False))
+        line = {"workload": name, "precision": prec, "adaptive": theta, "scaling": scaling, "reduced": reduced,
+                "k": k,
                 "elements": int(cfg["mesh"]["elem_ptr"].shape[0] - 1), "subdomains": int(cfg["part"].max() + 1)}
         try:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            g = pkg.VemSystem(cfg["mesh"], k, cfg["nu"])
+            g = pkg.VemSystem(cfg["mesh"], k, cfg["nu"], reduced=reduced)
             t1 = time.perf_counter()
             fq = cfg["f"](g.quad_points(deg))
             t2 = time.perf_counter()
@@ -372,7 +386,7 @@ def run_configs(args):
             # solves too inexact (viscosity contrast, degree 4)
             refine = 2 if prec and (np.ptp(cfg["nu"]) > 0 or k >= 4) else 0
             line["refine"] = refine if prec else None
-            bd = pkg.Bddc(g, cfg["part"], precision=prec, refine=refine, adaptive=theta)
+            bd = pkg.Bddc(g, cfg["part"], precision=prec, refine=refine, adaptive=theta, scaling=scaling)
             t4 = time.perf_counter()
             u = torch.zeros_like(rhs)
             res = bd.solve(rhs, u, rtol=1e-8, maxit=2000)
@@ -408,6 +422,8 @@ def main():
     ap.add_argument("--configs", action="store_true",
                     help="one solve per benchmark configuration and form (JSON line each)")
     ap.add_argument("--only", default="", help="with --configs: comma-separated workload names")
+    ap.add_argument("--extra", action="store_true",
+                    help="with --configs: also the theta sweep, edge deluxe, OCTA and reduced-scheme runs")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
