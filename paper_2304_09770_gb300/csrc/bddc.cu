@@ -2266,40 +2266,40 @@ static void setup_core(bddc* b, const int32_t* part) {
       }
       mark("t_factor_deluxe_ms");
       if (!faces.empty()) {
-      DBuf<int> df;
-      DBuf<int64_t> dsi, dsj, dpo, duo;
-      std::vector<int64_t> po, uo;
-      std::vector<GemmTile> tiles;
-      int64_t pn = 0, un = 0;
-      for (size_t t = 0; t < faces.size(); ++t) {
-        const int nd = b->h_macros[faces[t]].ndual;
-        po.push_back(pn);
-        pn += (int64_t)2 * nd * nd;
-        uo.push_back(un);
-        un += (int64_t)nd * nd;
-        const int nt = (nd + 63) / 64;
-        for (int ti = 0; ti < nt; ++ti)
-          for (int tj = 0; tj < nt; ++tj) tiles.push_back({(int)t, ti, tj});
-      }
-      upload_vec(df, faces, st);
-      upload_vec(dsi, sd_i, st);
-      upload_vec(dsj, sd_j, st);
-      upload_vec(dpo, po, st);
-      upload_vec(duo, uo, st);
-      DBuf<GemmTile> dtiles;
-      upload_vec(dtiles, tiles, st);
-      DBuf<double> PAN(std::max<int64_t>(pn, 1)), UPD(std::max<int64_t>(un, 1));
-      V = make_view(b);
-      // one CTA per face, four groups of 256 threads on separate trailing tiles
-      int ndmax = 0;
-      for (int g : faces) ndmax = std::max(ndmax, b->h_macros[g].ndual);
-      launch(KDeluxeFront{V, df.p, dsi.p, dsj.p, SD.p, PAN.p, UPD.p, dpo.p, duo.p, status.p}, (int)faces.size(), 1024,
-             sizeof(double) * (std::max(4 * 2 * 64 * 32 + 32, ndmax) + 8), st);
-      launch(KDeluxeGemm{V, dtiles.p, df.p, PAN.p, dpo.p, b->d_deluxe.p}, (int64_t)tiles.size(), 256,
-             sizeof(double) * (2 * 32 * 64 + 8), st);
-      mark("t_deluxe_combine_ms");
-      auto stv = status.download(st);
-      VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe: face Schur complement sum not positive definite");
+        DBuf<int> df;
+        DBuf<int64_t> dsi, dsj, dpo, duo;
+        std::vector<int64_t> po, uo;
+        std::vector<GemmTile> tiles;
+        int64_t pn = 0, un = 0;
+        for (size_t t = 0; t < faces.size(); ++t) {
+          const int nd = b->h_macros[faces[t]].ndual;
+          po.push_back(pn);
+          pn += (int64_t)2 * nd * nd;
+          uo.push_back(un);
+          un += (int64_t)nd * nd;
+          const int nt = (nd + 63) / 64;
+          for (int ti = 0; ti < nt; ++ti)
+            for (int tj = 0; tj < nt; ++tj) tiles.push_back({(int)t, ti, tj});
+        }
+        upload_vec(df, faces, st);
+        upload_vec(dsi, sd_i, st);
+        upload_vec(dsj, sd_j, st);
+        upload_vec(dpo, po, st);
+        upload_vec(duo, uo, st);
+        DBuf<GemmTile> dtiles;
+        upload_vec(dtiles, tiles, st);
+        DBuf<double> PAN(std::max<int64_t>(pn, 1)), UPD(std::max<int64_t>(un, 1));
+        V = make_view(b);
+        // one CTA per face, four groups of 256 threads on separate trailing tiles
+        int ndmax = 0;
+        for (int g : faces) ndmax = std::max(ndmax, b->h_macros[g].ndual);
+        launch(KDeluxeFront{V, df.p, dsi.p, dsj.p, SD.p, PAN.p, UPD.p, dpo.p, duo.p, status.p}, (int)faces.size(), 1024,
+               sizeof(double) * (std::max(4 * 2 * 64 * 32 + 32, ndmax) + 8), st);
+        launch(KDeluxeGemm{V, dtiles.p, df.p, PAN.p, dpo.p, b->d_deluxe.p}, (int64_t)tiles.size(), 256,
+               sizeof(double) * (2 * 32 * 64 + 8), st);
+        mark("t_deluxe_combine_ms");
+        auto stv = status.download(st);
+        VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "deluxe: face Schur complement sum not positive definite");
       }
       if (!edges.empty()) {
         // deluxe edges: W = sum_s S_s, W = G G^T, D_s = W^{-1} S_s
