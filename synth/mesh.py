@@ -20,7 +20,10 @@ along the diagonal through its smallest-index vertex, giving polyhedra with
 
 The OCTA family (``octa_mesh``) embeds an octahedron at the centre of every
 ``2 x 2 x 2`` block of grid cubes; its vertex, edge and face counts
-reproduce the DOF counts the paper prints for its OCTA meshes.
+reproduce the DOF counts the paper prints for its OCTA meshes.  The CVT
+family (``cvt_mesh``) is a seeded, Lloyd-relaxed centroidal Voronoi
+tessellation of the cube (general convex polyhedra, faces of up to about 9
+vertices).
 """
 import numpy as np
 
@@ -220,6 +223,129 @@ def octa_mesh(m, cut=0.5):
         "elem_ptr": elem_ptr, "elem_face": elem_face,
         "elem_ijk": np.array(elem_ijk, dtype=np.int32),
     }
+
+
+def _clipped_cells(pts):
+    """Voronoi cells of ``pts`` clipped to [0,1]^3: per cell, the vertices
+    (halfspace intersection) and the polygons on its bounding planes, each
+    tagged with the neighbour (>= 0) or the cube face (-1 - axis*2 - side)."""
+    from scipy.spatial import Voronoi, HalfspaceIntersection
+    vor = Voronoi(pts)
+    nbr = [[] for _ in range(len(pts))]
+    for a, b in vor.ridge_points:
+        nbr[a].append(int(b))
+        nbr[b].append(int(a))
+    cells = []
+    for i, p in enumerate(pts):
+        hs, tags = [], []
+        for j in nbr[i]:
+            d = pts[j] - p
+            hs.append(np.concatenate([d, [-(pts[j] @ pts[j] - p @ p) / 2.0]]))
+            tags.append(j)
+        for axis in range(3):
+            for side in range(2):
+                n = np.zeros(3)
+                n[axis] = 1.0 if side else -1.0
+                hs.append(np.concatenate([n, [-1.0 if side else 0.0]]))
+                tags.append(-1 - 2 * axis - side)
+        hs = np.array(hs)
+        V = HalfspaceIntersection(hs, p).intersections
+        polys = []
+        for h, tag in zip(hs, tags):
+            nrm = np.linalg.norm(h[:3])
+            on = np.nonzero(np.abs(V @ h[:3] + h[3]) <= 1e-10 * nrm)[0]
+            if len(on) < 3:
+                continue
+            polys.append((tag, h[:3] / nrm, on))
+        cells.append((V, polys))
+    return cells
+
+
+def cvt_mesh(ncells, seed, iters=30, weld=1e-9):
+    """CVT family: a centroidal Voronoi tessellation of [0,1]^3 from
+    ``ncells`` seeds drawn U(0,1)^3 by ``numpy.random.default_rng(seed)``,
+    relaxed by ``iters`` Lloyd steps (each seed moved to the centroid of its
+    clipped cell).  Vertices closer than ``weld`` are merged; every interior
+    face is the polygon of the lower-numbered cell, referenced with opposite
+    signs by the two cells; faces are planar and convex, elements convex.
+    """
+    rng = np.random.default_rng(seed)
+    pts = rng.uniform(0.0, 1.0, size=(ncells, 3))
+    for _ in range(iters):
+        cells = _clipped_cells(pts)
+        newp = np.empty_like(pts)
+        for i, (V, polys) in enumerate(cells):
+            # centroid of the convex cell: tetrahedra from the vertex mean
+            c0 = V.mean(0)
+            vol, cm = 0.0, np.zeros(3)
+            for _, n, on in polys:
+                P = _ordered(V[on], n)
+                for a in range(1, len(P) - 1):
+                    t = abs(np.linalg.det(np.array([P[0] - c0, P[a] - c0, P[a + 1] - c0]))) / 6.0
+                    vol += t
+                    cm += t * (c0 + P[0] + P[a] + P[a + 1]) / 4.0
+            newp[i] = cm / vol
+        pts = newp
+    cells = _clipped_cells(pts)
+    # weld vertices
+    allv = np.concatenate([V for V, _ in cells])
+    key = np.round(allv / weld).astype(np.int64)
+    uniq, inv = np.unique(key, axis=0, return_inverse=True)
+    inv = inv.ravel()
+    xyz = np.zeros((len(uniq), 3))
+    cnt = np.zeros(len(uniq))
+    np.add.at(xyz, inv, allv)
+    np.add.at(cnt, inv, 1.0)
+    xyz /= cnt[:, None]
+    base = np.cumsum([0] + [len(V) for V, _ in cells])
+    faces, fkey, elem_faces = [], {}, []
+    for i, (V, polys) in enumerate(cells):
+        ef = []
+        for tag, n, on in polys:
+            order = _order_idx(V[on], n)
+            loop = []
+            for q in on[order]:
+                g = int(inv[base[i] + q])
+                if not loop or loop[-1] != g:
+                    loop.append(g)
+            if len(loop) > 1 and loop[0] == loop[-1]:
+                loop.pop()
+            if len(loop) < 3:
+                continue
+            if tag >= 0:
+                k = (min(i, tag), max(i, tag))
+                if k in fkey:
+                    f = fkey[k]
+                    if set(faces[f]) != set(loop):
+                        raise ValueError("cvt_mesh: the two sides of a face differ after welding")
+                    ef.append(-(f + 1))
+                    continue
+                fkey[k] = len(faces)
+            ef.append(len(faces) + 1)
+            faces.append(tuple(loop))
+        elem_faces.append(ef)
+    face_ptr = np.zeros(len(faces) + 1, dtype=np.int32)
+    face_ptr[1:] = np.cumsum([len(f) for f in faces])
+    face_vtx = np.array([v for f in faces for v in f], dtype=np.int32)
+    elem_ptr = np.zeros(len(elem_faces) + 1, dtype=np.int32)
+    elem_ptr[1:] = np.cumsum([len(e) for e in elem_faces])
+    elem_face = np.array([f for e in elem_faces for f in e], dtype=np.int32)
+    return {"xyz": xyz, "face_ptr": face_ptr, "face_vtx": face_vtx, "elem_ptr": elem_ptr,
+            "elem_face": elem_face, "seeds": pts}
+
+
+def _order_idx(P, n):
+    """Indices ordering the coplanar points P counter-clockwise about n."""
+    c = P.mean(0)
+    a = P[0] - c
+    a = a - n * (a @ n)
+    a /= np.linalg.norm(a)
+    b = np.cross(n, a)
+    return np.argsort(np.arctan2((P - c) @ b, (P - c) @ a))
+
+
+def _ordered(P, n):
+    return P[_order_idx(P, n)]
 
 
 def element_vertex_average(mesh):
