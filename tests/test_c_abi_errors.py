@@ -90,3 +90,16 @@ def test_no_cpu_path_without_a_gpu(pkg):
     st, msg, h = _assemble(pkg, _mesh())
     assert st != 0, "the library assembled a system without a GPU"
     assert "cuda" in msg.lower() or "device" in msg.lower()
+
+
+def test_cvt_cells_beyond_the_element_records_are_rejected(pkg):
+    """Voronoi cells with more vertices or edges than an element record holds
+    (16 and 32) are rejected on the host, before any device work."""
+    from synth.mesh import cvt_mesh
+    st, msg, _ = _assemble(pkg, cvt_mesh(27, seed=5, iters=20))
+    assert st == VEM_EINVAL and ("too large" in msg or "vertex count" in msg), msg
+
+
+def test_reduced_entry_point_checks_its_arguments(pkg):
+    h = ctypes.c_void_p()
+    assert pkg.lib().vem_assemble_reduced(None, 2, None, ctypes.byref(h)) == VEM_EINVAL
