@@ -1,7 +1,9 @@
-"""Named synthetic workloads shaped like the paper's CUBE experiments.
+"""Named synthetic workloads shaped like the paper's CUBE and OCTA
+experiments.
 
-Each entry fixes the mesh (grid size, perturbation bound and seed), the
-degree k, the viscosity, the load and the partition.  ``make_config``
+Each entry fixes the mesh (CUBE grid size, perturbation bound and seed, or
+the OCTA block count), the degree k, the viscosity, the load and the
+partition.  ``make_config``
 returns the arrays; nothing here computes anything of the method.
 """
 import numpy as np
