@@ -103,3 +103,15 @@ def test_cvt_cells_beyond_the_element_records_are_rejected(pkg):
 def test_reduced_entry_point_checks_its_arguments(pkg):
     h = ctypes.c_void_p()
     assert pkg.lib().vem_assemble_reduced(None, 2, None, ctypes.byref(h)) == VEM_EINVAL
+
+
+def test_octa_mesh_passes_the_host_checks(pkg):
+    """OCTA elements (truncated cubes with pentagons, octahedra) fit the
+    element records: on a machine without a GPU the call gets past every
+    host check and fails only at the first device call."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the call would succeed")
+    from synth.mesh import octa_mesh
+    st, msg, _ = _assemble(pkg, octa_mesh(2))
+    assert st != VEM_EINVAL and ("cuda" in msg.lower() or "device" in msg.lower()), msg
