@@ -191,7 +191,8 @@ def measure(pkg, torch, cfg, fq, precision, steps, warmup, stream, with_e2e, ran
             "t_coarse_rhs_ms", "t_coarse_solves_ms", "t_coarse_gram_ms", "t_coarse_inverse_ms",
             "gflop_factor_dirichlet", "gflop_factor_neumann", "gflop_factor_deluxe")
     info = {k2: bd.info(k2) for k2 in keys}
-    vkeys = ("t_topology_ms", "t_element_launch_ms", "t_pattern_ms", "t_pattern_upload_ms", "t_gpu_finish_ms")
+    vkeys = ("t_topology_ms", "t_element_launch_ms", "t_pattern_ms", "t_element_wait_ms", "t_pattern_upload_ms",
+             "t_gpu_finish_ms")
     vinfo = {k2: g.info(k2) for k2 in vkeys}
     r = torch.randn(g.n, dtype=torch.float64, device="cuda")
     z = torch.empty_like(r)

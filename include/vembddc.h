@@ -103,8 +103,9 @@ int vem_assemble_reduced(const vem_mesh* mesh, int k, const double* nu_per_eleme
  * vem_assemble phase wall times (host clock) "t_topology_ms" (topology, DOF
  * numbering, element records), "t_element_launch_ms" (uploads and the
  * element kernel launch), "t_pattern_ms" (CSR pattern on the host while the
- * element kernel runs), "t_pattern_upload_ms" (pattern upload, assembly
- * launch), "t_gpu_finish_ms" (waiting for the GPU).  Unknown keys: VEM_EINVAL. */
+ * element kernel runs), "t_element_wait_ms" (waiting for the element kernel
+ * after that), "t_pattern_upload_ms" (pattern upload, assembly launch),
+ * "t_gpu_finish_ms" (waiting for the GPU).  Unknown keys: VEM_EINVAL. */
 int vem_info(const vem_system* sys, const char* key, double* value);
 
 /* Sizes: free velocity DOFs, element pressures, all velocity DOFs. */

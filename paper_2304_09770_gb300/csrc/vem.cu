@@ -276,38 +276,53 @@ struct KCompactB {
   }
 };
 
+// the element kernel's working buffers and outputs still to be checked: the
+// kernel runs while the host builds the CSR pattern, and finish_elements
+// reads its status afterwards (the buffers live until then)
+struct ElemPending {
+  DBuf<double> scratch, wm, Bfull;
+  DBuf<int> status;
+  int npf = 0;
+};
+
 template <int K>
-static void launch_elements(vem_system* s, const DBuf<int64_t>& offK, const DBuf<int64_t>& offK2) {
+static void launch_elements(vem_system* s, const DBuf<int64_t>& offK, const DBuf<int64_t>& offK2,
+                            ElemPending& pe) {
   const int nE = s->topo.nE;
   const int grid = std::min(nE, 152 * (K == 2 ? 8 : (K == 3 ? 4 : 2)));
   size_t stride = ElemScratch<K>::size(s->nKmax);
-  DBuf<double> scratch((size_t)grid * stride);
-  DBuf<int> status(1);
-  status.zero(s->stream);
+  pe.scratch.alloc((size_t)grid * stride);
+  pe.status.alloc(1);
+  pe.status.zero(s->stream);
   size_t smem = ((sizeof(ElemShared<K>) + 7) / 8) * 8 + sizeof(ElemRec);
-  const int npf = pdim3(K - 1);
-  DBuf<double> wm((size_t)nE * npf);
+  pe.npf = pdim3(K - 1);
+  pe.wm.alloc((size_t)nE * pe.npf);
   // the reduced scheme keeps one B row per element: the full rows go to a
   // temporary and row 0 is copied out
-  DBuf<double> Bfull;
   double* Bdst = s->d_B.p;
   if (s->dof.reduced) {
-    Bfull.alloc((size_t)npf * s->h_eoff.back());
-    Bdst = Bfull.p;
+    pe.Bfull.alloc((size_t)pe.npf * s->h_eoff.back());
+    Bdst = pe.Bfull.p;
   }
   KElement<K> f{s->d_rec.p, s->d_xyz.p, s->d_nu.p, offK.p, offK2.p, s->d_tab.p, s->d_A.p, Bdst,
-                s->d_P0.p, wm.p, scratch.p, stride, nE, grid, status.p};
+                s->d_P0.p, pe.wm.p, pe.scratch.p, stride, nE, grid, pe.status.p};
   launch(f, grid, 128, smem, s->stream);
-  if (s->dof.reduced) launch(KCompactB{Bfull.p, s->d_B.p, offK.p, npf}, nE, 128, 0, s->stream);
-  auto st = status.download(s->stream);
+  if (s->dof.reduced) launch(KCompactB{pe.Bfull.p, s->d_B.p, offK.p, pe.npf}, nE, 128, 0, s->stream);
+}
+
+static void finish_elements(vem_system* s, ElemPending& pe) {
+  const int nE = s->topo.nE;
+  auto st = pe.status.download(s->stream);
   VB_CHECK(st[0] == 0, VEM_ESINGULAR, "element projector system singular (degenerate element)");
-  std::vector<double> w = wm.download(s->stream);
+  std::vector<double> w = pe.wm.download(s->stream);
   if (s->dof.reduced) {
     s->elem_wmean.assign(nE, 0.0);
-    for (int e = 0; e < nE; ++e) s->elem_wmean[e] = w[(size_t)e * npf];
+    for (int e = 0; e < nE; ++e) s->elem_wmean[e] = w[(size_t)e * pe.npf];
   } else {
     s->elem_wmean = std::move(w);
   }
+  pe.scratch.release();
+  pe.Bfull.release();
 }
 
 static void load_tables(vem_system* s) {
@@ -374,9 +389,10 @@ static int assemble(const vem_mesh* mesh, int k, const double* nu, bool reduced,
     s->d_P0.alloc((size_t)3 * pdim3(k) * offK[t.nE]);
     s->d_sysdof.upload(s->h_sysdof, s->stream);
     load_tables(s);
-    if (k == 2) launch_elements<2>(s, dK, dK2);
-    else if (k == 3) launch_elements<3>(s, dK, dK2);
-    else launch_elements<4>(s, dK, dK2);
+    ElemPending pe;
+    if (k == 2) launch_elements<2>(s, dK, dK2, pe);
+    else if (k == 3) launch_elements<3>(s, dK, dK2, pe);
+    else launch_elements<4>(s, dK, dK2, pe);
     mark("t_element_launch_ms");
     // CSR pattern and row adjacency (host, overlapping the element kernel)
     const int64_t nvf = d.nvf, np = d.np;
@@ -410,6 +426,8 @@ static int assemble(const vem_mesh* mesh, int k, const double* nu, bool reduced,
     build_csr_pattern(recs, offK, s->h_sysdof, s->h_adj_ptr, s->h_adj_elem, s->h_adj_loc, nvf, (int)np, s->n,
                       rowptr, cols);
     mark("t_pattern_ms");
+    finish_elements(s, pe);
+    mark("t_element_wait_ms");
     VB_CHECK(s->n < (int64_t)INT32_MAX, VEM_EINVAL, "system too large for 32-bit column indices");
     s->nnz = rowptr[s->n];
     s->d_rowptr.upload(rowptr, s->stream);
