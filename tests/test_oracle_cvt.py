@@ -113,10 +113,10 @@ def test_patch_test_on_cvt():
 
 
 def test_bddc_pcg_on_cvt():
-    """64-cell CVT, two subdomains split by the seed's x coordinate: PCG
+    """27-cell CVT, two subdomains split by the seed's x coordinate: PCG
     reproduces the direct solve and lambda_min = 1."""
     from synth.fields import manufactured_f
-    mesh = _mesh(64, 3, 20)
+    mesh = _mesh(27, 5, 20)
     nE = len(mesh["elem_ptr"]) - 1
     part = (mesh["seeds"][:, 0] > 0.5).astype(np.int32)
     S = System(mesh, 2, np.ones(nE), f=lambda x: manufactured_f(x, 1.0), load_deg=6)

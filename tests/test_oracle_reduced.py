@@ -37,8 +37,8 @@ def _zero_mean(S, p, w):
     return p - (w @ p) / (w @ one) * one
 
 
-@pytest.fixture(scope="module", params=[("tri4_k2", {}), ("tri4_k3", {"n": 2}), ("octa2_k2", {})],
-                ids=["tri4_k2", "tri2_k3", "octa2_k2"])
+@pytest.fixture(scope="module", params=[("tri4_k2", {}), ("tri4_k3", {"n": 2}), ("octa2_k2", {"m": 1})],
+                ids=["tri4_k2", "tri2_k3", "octa1_k2"])
 def pair(request):
     name, over = request.param
     return _pair(name, **over)
