@@ -5,10 +5,10 @@
 
 namespace vb {
 
-constexpr int kMaxElemVerts = 16;
-constexpr int kMaxElemEdges = 32;
-constexpr int kMaxElemFaces = 20;
-constexpr int kMaxFaceVerts = 8;
+constexpr int kMaxElemVerts = 40;
+constexpr int kMaxElemEdges = 64;
+constexpr int kMaxElemFaces = 28;
+constexpr int kMaxFaceVerts = 12;
 
 // Per-element tables consumed by the element kernel (fixed-size records).
 struct ElemRec {

@@ -8,7 +8,7 @@ returns the arrays; nothing here computes anything of the method.
 """
 import numpy as np
 
-from .mesh import cube_mesh, octa_mesh, box_partition, greedy_partition, element_vertex_average
+from .mesh import cube_mesh, octa_mesh, cvt_mesh, box_partition, greedy_partition, element_vertex_average
 from .fields import manufactured_f, sinker_centres, sinker_viscosity, sinker_load
 
 CONFIGS = {
@@ -45,6 +45,10 @@ CONFIGS = {
     "octa2_k3": dict(family="octa", m=2, k=3, parts=(2, 2, 2), load="manufactured"),
     "octa2_k4": dict(family="octa", m=2, k=4, parts=(2, 2, 2), load="manufactured"),
     "octa2_sinker": dict(family="octa", m=2, k=2, parts=(2, 2, 2), load="sinker", sinkers=(8, 5), dr=1e4),
+    # CVT family (seeded Lloyd-relaxed Voronoi cells), subdomains = boxes of
+    # the seeds; small parity cases
+    "cvt64_k2": dict(family="cvt", cells=64, seed=3, iters=20, k=2, parts=(2, 2, 1), load="manufactured"),
+    "cvt27_k3": dict(family="cvt", cells=27, seed=5, iters=20, k=3, parts=(2, 2, 1), load="manufactured"),
 }
 
 
@@ -54,6 +58,9 @@ def make_config(name, **override):
     if c.get("family") == "octa":
         mesh = octa_mesh(c["m"])
         ne = 9 * c["m"] ** 3
+    elif c.get("family") == "cvt":
+        mesh = cvt_mesh(c["cells"], c["seed"], c["iters"])
+        ne = c["cells"]
     else:
         mesh = cube_mesh(c["n"], c["perturb"], c["seed"])
         ne = c["n"] ** 3
@@ -71,6 +78,10 @@ def make_config(name, **override):
             return manufactured_f(x, 1.0)
     if "greedy" in c:
         part = greedy_partition(mesh, c["greedy"][0], c["greedy"][1])
+    elif c.get("family") == "cvt":
+        px, py, pz = c["parts"]
+        b = np.minimum((mesh["seeds"] * np.array([px, py, pz])).astype(int), np.array([px, py, pz]) - 1)
+        part = (b[:, 0] + px * (b[:, 1] + py * b[:, 2])).astype(np.int32)
     else:
         part = box_partition(mesh, c["parts"])
     return dict(name=name, mesh=mesh, k=c["k"], nu=nu, f=f, part=part, spec=c)

@@ -92,12 +92,36 @@ def test_no_cpu_path_without_a_gpu(pkg):
     assert "cuda" in msg.lower() or "device" in msg.lower()
 
 
-def test_cvt_cells_beyond_the_element_records_are_rejected(pkg):
-    """Voronoi cells with more vertices or edges than an element record holds
-    (16 and 32) are rejected on the host, before any device work."""
+def _prism(m):
+    """One prism over a regular m-gon (faces: two m-gons, m quadrilaterals)."""
+    a = 2 * np.pi * np.arange(m) / m
+    ring = np.stack([0.5 + 0.4 * np.cos(a), 0.5 + 0.4 * np.sin(a)], 1)
+    xyz = np.concatenate([np.c_[ring, np.zeros(m)], np.c_[ring, np.ones(m)]])
+    faces = [list(range(m))[::-1], list(range(m, 2 * m))]
+    faces += [[i, (i + 1) % m, m + (i + 1) % m, m + i] for i in range(m)]
+    return {"xyz": xyz, "face_ptr": np.cumsum([0] + [len(f) for f in faces]).astype(np.int32),
+            "face_vtx": np.array([v for f in faces for v in f], dtype=np.int32),
+            "elem_ptr": np.array([0, len(faces)], dtype=np.int32),
+            "elem_face": np.arange(1, len(faces) + 1, dtype=np.int32)}
+
+
+def test_faces_beyond_the_element_records_are_rejected(pkg):
+    """A face with more vertices than an element record holds (12) is
+    rejected on the host, before any device work."""
+    st, msg, _ = _assemble(pkg, _prism(13))
+    assert st == VEM_EINVAL and "vertex count" in msg, msg
+
+
+def test_cvt_mesh_passes_the_host_checks(pkg):
+    """Voronoi cells (up to about 30 vertices, 17 faces, faces of up to 9
+    vertices) fit the element records: without a GPU the call gets past
+    every host check and fails only at the first device call."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the call would succeed")
     from synth.mesh import cvt_mesh
     st, msg, _ = _assemble(pkg, cvt_mesh(27, seed=5, iters=20))
-    assert st == VEM_EINVAL and ("too large" in msg or "vertex count" in msg), msg
+    assert st != VEM_EINVAL and ("cuda" in msg.lower() or "device" in msg.lower()), msg
 
 
 def test_reduced_entry_point_checks_its_arguments(pkg):

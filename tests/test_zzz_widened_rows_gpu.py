@@ -1,4 +1,4 @@
-"""GPU parity, through the C-ABI, of three extensions of the BDDC-PCG path
+"""GPU parity, through the C-ABI, of extensions of the BDDC-PCG path
 against the CPU oracle:
 
 * deluxe scaling on macro edges (bddc_setup scaling 2): D_E^(k) =
@@ -9,6 +9,10 @@ against the CPU oracle:
   with one truncated corner, pentagonal faces): element matrices at k = 2,
   3, 4, global CSR and load, BDDC-PCG, and the paper's 15,552-element OCTA
   mesh by properties;
+* the CVT mesh family (Lloyd-relaxed Voronoi cells: up to about 30
+  vertices, faces of up to 9 vertices): element matrices, load and
+  BDDC-PCG (at k = 3 the tolerances are 1e-9: faces of such cells can be
+  nearly degenerate, and the two implementations round differently there);
 * the reduced scheme (vem_assemble_reduced: D5 eliminated with value 0,
   element-constant pressure): element matrices, CSR and load against the
   oracle's reduced System, BDDC-PCG against the oracle's BDDC on it, and
@@ -83,9 +87,24 @@ def test_octa_global_matrix_and_load_match_oracle(pkg):
     assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
 
 
+@pytest.mark.parametrize("name,tol", [("cvt64_k2", 1e-12), ("cvt27_k3", 1e-9)])
+def test_cvt_element_matrices_and_load_match_oracle(pkg, name, tol):
+    cfg, g, rhs, S, F = _setup(pkg, name)
+    topo = S.topo
+    # Voronoi cells differ in their DOF counts: one element per call
+    for e in range(0, topo.nE, max(1, topo.nE // 8)):
+        A, B, D = g.element_matrices([e])
+        el = S.elements[e]
+        assert np.array_equal(D[0], el.dofs)
+        assert np.abs(A[0] - el.A).max() <= tol * np.abs(el.A).max()
+        assert np.abs(B[0] - el.B).max() <= tol * np.abs(el.B).max()
+    assert np.abs(rhs.cpu().numpy() - F).max() <= tol * np.abs(F).max()
+
+
 CASES = [("tri6_k2", "deluxe_edges"), ("tri6_greedy", "deluxe_edges"), ("sinker8", "deluxe_edges"),
          ("octa2_k2", "deluxe"), ("octa2_k2", "deluxe_edges"), ("octa2_k3", "deluxe"),
-         ("octa2_sinker", "deluxe"), ("octa2_sinker", "deluxe_edges")]
+         ("octa2_sinker", "deluxe"), ("octa2_sinker", "deluxe_edges"),
+         ("cvt64_k2", "deluxe"), ("cvt64_k2", "deluxe_edges"), ("cvt27_k3", "deluxe")]
 
 
 @pytest.mark.parametrize("name,scaling", CASES)
