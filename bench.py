@@ -339,12 +339,14 @@ CONFIG_RUNS = [
 ]
 # further runs (workload, precision, theta, options): theta (nu_tol) sweep on
 # configurations 2 and 4, deluxe scaling on edges at viscosity contrast, the
-# paper's 15,552-element OCTA mesh, and the reduced scheme
+# paper's 15,552-element OCTA mesh, a 4,000-cell CVT mesh, and the reduced
+# scheme
 EXTRA_RUNS = [
     ("tri32_k2", 0, 2.0, {}), ("tri32_k2", 0, 5.0, {}), ("tri16_k4", 0, 2.0, {}), ("tri16_k4", 0, 5.0, {}),
     ("sinker32_dr1e4", 0, 0.0, {"scaling": 2}), ("sinker32_dr1e4", 1, 0.0, {"scaling": 2}),
     ("sinker32_dr1e6", 0, 0.0, {"scaling": 2}), ("sinker32_dr1e6", 0, 10.0, {"scaling": 2}),
     ("octa12_k2", 0, 0.0, {}), ("octa12_k2", 1, 0.0, {}), ("octa12_k2", 0, 2.0, {}),
+    ("cvt4000_k2", 0, 0.0, {}), ("cvt4000_k2", 1, 0.0, {}),
     ("tri32_k2", 0, 0.0, {"reduced": True}), ("tri32_k2", 1, 0.0, {"reduced": True}),
     ("tri16_k4", 0, 0.0, {"reduced": True}),
 ]

@@ -48,6 +48,8 @@ CONFIGS = {
     # CVT family (seeded Lloyd-relaxed Voronoi cells), subdomains = boxes of
     # the seeds; small parity cases
     "cvt64_k2": dict(family="cvt", cells=64, seed=3, iters=20, k=2, parts=(2, 2, 1), load="manufactured"),
+    # 4,000 cells: the size of the paper's CVT strong-scaling and sinker mesh
+    "cvt4000_k2": dict(family="cvt", cells=4000, seed=7, iters=10, k=2, parts=(4, 4, 4), load="manufactured"),
     "cvt27_k3": dict(family="cvt", cells=27, seed=5, iters=20, k=3, parts=(2, 2, 1), load="manufactured"),
 }
 
