@@ -13,8 +13,10 @@ Modules
 poly    scaled monomials, polynomial algebra, quadrature rules
 vem     DOFs (Sec. 3, D1-D5), face/element projectors, local matrices
         A_K (Eq. discreteA), B_K, load (Eq. discreteF), global assembly and
-        the bordered direct solve of the saddle system (Eq. MatrixForm)
+        the bordered direct solve of the saddle system (Eq. MatrixForm);
+        the reduced scheme (the remark after the convergence theorem)
 bddc    interface classification, primal constraints (Sec. 5.1), change of
-        basis, deluxe scaling (Sec. 6), BDDC apply (Eq. BDDCprec), PCG and
-        the Lanczos condition-number estimate
+        basis, deluxe scaling on faces (Sec. 6) and optionally on edges,
+        the adaptive coarse space (Sec. 6), BDDC apply (Eq. BDDCprec), PCG
+        and the Lanczos condition-number estimate
 """
