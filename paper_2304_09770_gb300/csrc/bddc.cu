@@ -17,6 +17,7 @@
 #include <numeric>
 #include <chrono>
 #include <map>
+#include <tuple>
 #include <utility>
 #include <string>
 #include <type_traits>
@@ -1116,7 +1117,9 @@ static void upload_vec(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
 static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool with_vectors) {
   B.probs = probs;
   int64_t vec = 0, uv = 0, nF = 0, nU = 0;
-  std::vector<std::pair<int, int>> hn;   // (height, node)
+  // (height, -front cost, node): within a tree level the largest fronts come
+  // first, so that the CTAs of the smallest ones fill the tail of the launch
+  std::vector<std::tuple<int, double, int>> hn;
   B.maxnf = 1;
   B.maxh = 0;
   for (int q : probs) {
@@ -1139,7 +1142,8 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
       nU += (int64_t)N.nb * N.nb;
       N.uvec_off = uv;
       uv += N.nb;
-      hn.push_back({N.height, gid});
+      const double nf = N.np + N.nb;
+      hn.push_back({N.height, -(double)N.np * nf * nf, gid});
       B.maxh = std::max(B.maxh, N.height);
       B.maxnf = std::max(B.maxnf, N.np + N.nb);
     }
@@ -1148,8 +1152,8 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
   B.level_ptr.assign(B.maxh + 2, 0);
   B.h_levels.clear();
   for (auto& pr : hn) {
-    B.level_ptr[pr.first + 1]++;
-    B.h_levels.push_back(pr.second);
+    B.level_ptr[std::get<0>(pr) + 1]++;
+    B.h_levels.push_back(std::get<2>(pr));
   }
   for (int h = 0; h <= B.maxh; ++h) B.level_ptr[h + 1] += B.level_ptr[h];
   // front-vector offsets and solve tasks per level
