@@ -28,3 +28,16 @@ def test_reference_arm_two_ranks_gloo():
     for key in ("metric", "value", "unit", "higher_is_better", "cpu_baseline", "e2e", "config"):
         assert key in line
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_bench_runs_name_existing_workloads():
+    """Every workload of bench.py --configs (and --extra) is a named
+    configuration, and the extra runs only use options bddc_setup takes."""
+    import bench
+    from synth.configs import CONFIGS
+    runs = [r + ({},) for r in bench.CONFIG_RUNS] + list(bench.EXTRA_RUNS)
+    for name, prec, theta, opt in runs:
+        assert name in CONFIGS, name
+        assert prec in (0, 1, 2) and theta >= 0.0
+        assert set(opt) <= {"scaling", "reduced"}
+        assert opt.get("scaling", 1) in (0, 1, 2)
