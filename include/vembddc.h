@@ -283,6 +283,14 @@ int bddc_time_local_solves(bddc* b, int nrep, double* ms, double* bytes);
  * *max_ref: max |D_fp64|.  Returns VEM_ETIMEOUT if the bounded wait for the
  * product gave up.  Uses the current device; synchronizes it. */
 int vem_tc_selftest(double* max_err, double* max_ref);
+/* Diagnostics of failure detection: the bounded mbarrier wait that every
+ * tensor-core kernel uses, run on an mbarrier that nothing ever arrives on,
+ * polled at most `limit` times (0 <= limit <= 2^30).  Returns VEM_ETIMEOUT,
+ * the status the tensor-core kernels report when their wait gives up, and
+ * leaves the context usable; VEM_ECUDA if the wait completed; VEM_EINVAL
+ * for a limit out of range.  No counterpart in the paper (failure
+ * detection).  Uses the current device; synchronizes it. */
+int vem_wait_selftest(long long limit);
 
 int bddc_set_stream(bddc* b, void* cuda_stream);
 void bddc_free(bddc* b);

@@ -136,15 +136,19 @@ def op_lap3(n):
     return M
 
 
-def op_lap2(n):
+def op_lap2(n, G=None):
+    """sum_pq G_pq d_p d_q (the Laplacian for G = I): P_n -> P_{n-2}."""
+    G = np.eye(2) if G is None else G
     m = max(n - 2, 0)
     M = np.zeros((dim2(m), dim2(n)))
     tgt = index2(m)
     for c, (a, b) in enumerate(exps2(n)):
         if a >= 2:
-            M[tgt[(a - 2, b)], c] += a * (a - 1)
+            M[tgt[(a - 2, b)], c] += G[0, 0] * a * (a - 1)
+        if a >= 1 and b >= 1:
+            M[tgt[(a - 1, b - 1)], c] += 2.0 * G[0, 1] * a * b
         if b >= 2:
-            M[tgt[(a, b - 2)], c] += b * (b - 1)
+            M[tgt[(a, b - 2)], c] += G[1, 1] * b * (b - 1)
     return M
 
 

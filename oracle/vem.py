@@ -180,7 +180,35 @@ def face_frame(xyz, loop):
     t2 = np.cross(nrm, t1)
     xc = P.mean(axis=0)
     hf = max(np.linalg.norm(P[i] - P[j]) for i in range(len(P)) for j in range(i + 1, len(P)))
-    return dict(P=P, n=nrm, t1=t1, t2=t2, xc=xc, h=hf, area=np.linalg.norm(area_vec))
+    return dict(P=P, n=nrm, t1=t1, t2=t2, xc=xc, h=hf, area=np.linalg.norm(area_vec),
+                W=face_whitening(P, xc, t1, t2))
+
+
+def face_whitening(P, xc, t1, t2):
+    """Face-local coordinates of the scaled monomials: (s, t) = W (xi1, xi2)
+    with xi = ((x - xc).t1, (x - xc).t2) and W = Sigma^{-1/2} / sqrt(24),
+    Sigma = (1/|f|) int_f xi xi^T dA (second moments about xc, exact on the
+    fan triangles from vertex 0).  The paper leaves the polynomial basis of
+    the face moments open; P_n(f) and its homogeneous parts about xc are
+    invariant under this linear map, so only the basis changes, and it stays
+    well conditioned on thin faces.  For a square W = I / diam, the plain
+    diameter scaling."""
+    q = np.stack([(P - xc) @ t1, (P - xc) @ t2], axis=1)
+    S = np.zeros((2, 2))
+    area = 0.0
+    for i in range(1, len(q) - 1):
+        a, b, c = q[0], q[i], q[i + 1]
+        ar = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]))
+        sm = a + b + c
+        S += ar / 12.0 * (np.outer(a, a) + np.outer(b, b) + np.outer(c, c) + np.outer(sm, sm))
+        area += ar
+    S /= area
+    # inverse square root of a 2x2 SPD matrix in closed form:
+    # sqrt(S) = (S + d I) / tau, d = sqrt(det S), tau = sqrt(tr S + 2 d)
+    d = np.sqrt(S[0, 0] * S[1, 1] - S[0, 1] ** 2)
+    tau = np.sqrt(S[0, 0] + S[1, 1] + 2.0 * d)
+    adj = np.array([[S[1, 1] + d, -S[0, 1]], [-S[0, 1], S[0, 0] + d]])
+    return adj / (d * tau * np.sqrt(24.0))
 
 
 def face_quadrature(F, deg):
@@ -198,7 +226,7 @@ def face_quadrature(F, deg):
 
 def face_local(F, x):
     d = x - F["xc"]
-    return np.stack([d @ F["t1"], d @ F["t2"]], axis=1) / F["h"]
+    return np.stack([d @ F["t1"], d @ F["t2"]], axis=1) @ F["W"].T
 
 
 # ------------------------------------------------------------------ face projectors
@@ -216,17 +244,18 @@ def face_projectors(xyz, loop, k):
     nb = m * k
     nint = dim2(k - 2)
     ns = nb + nint
-    hf = F["h"]
+    Wf = F["W"]
     qp, qw = face_quadrature(F, 2 * k + 4)
     st = face_local(F, qp)
     Nk = dim2(k)
-    # stiffness and boundary rows of the Pi^nabla system
-    Gx = [dmono2(k, st, j) / hf for j in range(2)]
+    # stiffness and boundary rows of the Pi^nabla system; the gradient in
+    # the (t1, t2) frame is W^T grad_st
+    Gx = [Wf[0, j] * dmono2(k, st, 0) + Wf[1, j] * dmono2(k, st, 1) for j in range(2)]
     G = sum((g * qw[:, None]).T @ g for g in Gx)
     Bv = np.zeros((Nk, ns))
-    # -int Lap m_b v  via internal moments: Lap m_b = (1/h^2) Lap_st m_b in P_{k-2}
+    # -int Lap m_b v  via internal moments: Lap m_b = tr(W W^T Hess_st m_b) in P_{k-2}
     if k >= 2:
-        L = op_lap2(k)[:nint, :] / hf ** 2         # [nint, Nk]
+        L = op_lap2(k, Wf @ Wf.T)[:nint, :]        # [nint, Nk]
         Bv[:, nb:] -= F["area"] * L.T
     # boundary terms
     gl = gauss_lobatto_interior(k)
@@ -248,7 +277,8 @@ def face_projectors(xyz, loop, k):
         ne = np.cross(d, F["n"])
         x = A[None, :] + np.outer(gq, B - A)
         stq = face_local(F, x)
-        dn = (dmono2(k, stq, 0) * (F["t1"] @ ne) + dmono2(k, stq, 1) * (F["t2"] @ ne)) / hf
+        nw = Wf @ np.array([F["t1"] @ ne, F["t2"] @ ne])
+        dn = dmono2(k, stq, 0) * nw[0] + dmono2(k, stq, 1) * nw[1]
         # map of the k+1 nodal values (traversal order) to s indices
         idx = [i] + [m + i * (k - 1) + j for j in range(k - 1)] + [(i + 1) % m]
         W = gw * le
@@ -625,7 +655,11 @@ class System:
     """Global saddle system (Eq. MatrixForm) over all velocity DOFs and the
     element pressures; Dirichlet velocity DOFs are eliminated on solve."""
 
-    def __init__(self, mesh, k, nu, f=None, load_deg=None, elements=None, reduced=False):
+    def __init__(self, mesh, k, nu, f=None, load_deg=None, elements=None, reduced=False, prebuilt=None):
+        """``prebuilt``: optional {e: (Element, F_K or None)} made elsewhere by
+        ``build_element`` and ``Element.load`` with these same arguments (the
+        test suite builds elements in worker processes); the assembly below
+        is the same either way."""
         self.topo = Topology(mesh)
         self.dm = DofMap(self.topo, k, reduced)
         self.k = k
@@ -639,7 +673,13 @@ class System:
         self.elements = {}
         els = range(ne) if elements is None else elements
         for e in els:
-            el = build_element(topo, dm, e, nu[e], load_deg)
+            if prebuilt is not None:
+                el, fk = prebuilt[e]
+                el._topo = topo
+                el._topo_xyz = topo.xyz
+            else:
+                el = build_element(topo, dm, e, nu[e], load_deg)
+                fk = el.load(f) if f is not None else None
             d = el.dofs
             rows.append(np.repeat(d, len(d)))
             cols.append(np.tile(d, len(d)))
@@ -648,8 +688,8 @@ class System:
             brow.append(np.repeat(pr, len(d)))
             bcol.append(np.tile(d, npk))
             bval.append(el.B[:npk].ravel())
-            if f is not None:
-                F[d] += el.load(f)
+            if fk is not None:
+                F[d] += fk
             self.wmean[pr] = (el.vq_w @ mono3(k - 1, el.xi))[:npk]     # int_K m_a
             self.elements[e] = el
         self.A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),

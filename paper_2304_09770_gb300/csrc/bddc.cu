@@ -2594,7 +2594,10 @@ extern "C" int pcg_solve(bddc* b, const double* f, double* u, double rtol, int m
     std::vector<double> al, be;
     int it = 0;
     int status = VEM_OK;
-    if (n0 > 1e-14 * nf && maxit == 0) {
+    if (!std::isfinite(n0) || !std::isfinite(nf)) {
+      // a non-finite right-hand side or initial residual: no iteration
+      status = VEM_EBREAKDOWN;
+    } else if (n0 > 1e-14 * nf && maxit == 0) {
       status = VEM_ENOTCONV;
     } else if (n0 > 1e-14 * nf && b->use_graph) {
       // the whole loop as one graph launch: a conditional while node runs
@@ -2659,7 +2662,9 @@ extern "C" int pcg_solve(bddc* b, const double* f, double* u, double rtol, int m
     if (lam_max) *lam_max = lmax;
     if (kappa) *kappa = lmax / lmin;
     VB_CUDA(cudaStreamSynchronize(st));
-    if (status != VEM_OK) set_last_error(status == VEM_ENOTCONV ? "CG did not reach rtol" : "CG breakdown");
+    if (status != VEM_OK)
+      set_last_error(status == VEM_ENOTCONV ? "CG did not reach rtol"
+                                            : "CG breakdown (p^T K p <= 0, or a non-finite residual)");
     return status;
   } catch (const Error& e) {
     return bfail(e);

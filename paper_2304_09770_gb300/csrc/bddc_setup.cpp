@@ -63,6 +63,202 @@ void face_frame(const Topo& t, int f, double* n, double* t1, double* t2, double&
   t2[2] = n[0] * t1[1] - n[1] * t1[0];
 }
 
+// Area centroid of face f (fan triangles from loop vertex 0).
+static void face_centroid(const Topo& t, int f, double* c) {
+  int b = t.face_ptr[f], m = t.face_ptr[f + 1] - b;
+  const double* p0 = &t.xyz[3 * t.face_vtx[b]];
+  double acc[3] = {0, 0, 0}, at = 0;
+  for (int i = 1; i < m - 1; ++i) {
+    const double* p1 = &t.xyz[3 * t.face_vtx[b + i]];
+    const double* p2 = &t.xyz[3 * t.face_vtx[b + i + 1]];
+    double u[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+    double v[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+    double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    double a = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    for (int q = 0; q < 3; ++q) acc[q] += a * (p0[q] + p1[q] + p2[q]) / 3.0;
+    at += a;
+  }
+  for (int q = 0; q < 3; ++q) c[q] = acc[q] / at;
+}
+
+// Smallest over largest eigenvalue of a symmetric 6 x 6 matrix (cyclic Jacobi).
+static double eig_ratio6(double G[6][6]) {
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < 6; ++p)
+      for (int q = p + 1; q < 6; ++q) off += G[p][q] * G[p][q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < 6; ++p)
+      for (int q = p + 1; q < 6; ++q) {
+        if (G[p][q] == 0.0) continue;
+        double th = 0.5 * (G[q][q] - G[p][p]) / G[p][q];
+        double tt = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        double c = 1.0 / std::sqrt(tt * tt + 1.0), sn = tt * c;
+        for (int r = 0; r < 6; ++r) {
+          double a = G[r][p], b = G[r][q];
+          G[r][p] = c * a - sn * b;
+          G[r][q] = sn * a + c * b;
+        }
+        for (int r = 0; r < 6; ++r) {
+          double a = G[p][r], b = G[q][r];
+          G[p][r] = c * a - sn * b;
+          G[q][r] = sn * a + c * b;
+        }
+      }
+  }
+  double lo = G[0][0], hi = G[0][0];
+  for (int p = 1; p < 6; ++p) { lo = std::min(lo, G[p][p]); hi = std::max(hi, G[p][p]); }
+  return hi > 0 ? lo / hi : 0.0;
+}
+
+// Sec. 5.1 (the recipe that satisfies the assumption on the coarse space):
+// the primal constraints of a subdomain must control its rigid body modes,
+// checked numerically.  For every floating subdomain (no Dirichlet DOF) the
+// vertex, edge and face constraints it takes part in are evaluated on the
+// six rigid body modes (translations, and rotations about its centroid
+// scaled by its diameter); fewer than six independent values leave the
+// local Neumann problem singular: VEM_ESINGULAR.  Adaptive rows only add
+// constraints and are not needed for the check.
+static void check_rigid_modes(const vem_system* s, const int32_t* part, const SetupOptions& o, const BddcHost& H) {
+  const Topo& t = s->topo;
+  const DofNumbering& d = s->dof;
+  const int N = H.N;
+  std::vector<char> floating(N, 1);
+  for (int e = 0; e < t.nE; ++e)
+    for (int64_t q = s->h_eoff[e]; q < s->h_eoff[e + 1]; ++q)
+      if (s->h_sysdof[q] < 0) floating[part[e]] = 0;
+  const std::vector<double> gl = lobatto_interior(d.k);
+  // position of a nodal DOF (vertex or edge node); false for other DOFs
+  auto node_pos = [&](int64_t g, double* x, int& comp) {
+    if (g < d.off_e) {
+      const int v = (int)(g / 3);
+      comp = (int)(g % 3);
+      for (int q = 0; q < 3; ++q) x[q] = t.xyz[3 * v + q];
+      return true;
+    }
+    if (g < d.off_f) {
+      const int64_t r = g - d.off_e;
+      const int ed = (int)(r / d.ce), j = (int)((r % d.ce) / 3);
+      comp = (int)(r % 3);
+      const double* a = &t.xyz[3 * t.edge_a[ed]];
+      const double* b = &t.xyz[3 * t.edge_b[ed]];
+      for (int q = 0; q < 3; ++q) x[q] = a[q] + gl[j] * (b[q] - a[q]);
+      return true;
+    }
+    return false;
+  };
+  for (int i = 0; i < N; ++i) {
+    if (!floating[i]) continue;
+    // centroid and diameter (bounding box) of the subdomain's vertices
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, cen[3] = {0, 0, 0};
+    int nvx = 0;
+    for (int e : H.subs[i].elems)
+      for (int v : t.elem_verts[e]) {
+        for (int q = 0; q < 3; ++q) {
+          lo[q] = std::min(lo[q], t.xyz[3 * v + q]);
+          hi[q] = std::max(hi[q], t.xyz[3 * v + q]);
+          cen[q] += t.xyz[3 * v + q];
+        }
+        ++nvx;
+      }
+    double Hd = 0;
+    for (int q = 0; q < 3; ++q) { cen[q] /= nvx; Hd = std::max(Hd, hi[q] - lo[q]); }
+    // rigid mode l at x, component c
+    auto rigid = [&](int l, const double* x, int c) {
+      if (l < 3) return c == l ? 1.0 : 0.0;
+      const double y[3] = {(x[0] - cen[0]) / Hd, (x[1] - cen[1]) / Hd, (x[2] - cen[2]) / Hd};
+      const int a = l - 3;                       // e_a x y
+      const double cr[3] = {a == 1 ? y[2] * 1.0 : (a == 2 ? -y[1] : 0.0),
+                            a == 2 ? y[0] : (a == 0 ? -y[2] : 0.0),
+                            a == 0 ? y[1] : (a == 1 ? -y[0] : 0.0)};
+      return cr[c];
+    };
+    std::vector<std::array<double, 6>> rows;
+    for (size_t gi = 0; gi < H.macros.size(); ++gi) {
+      const Macro& G = H.macros[gi];
+      if (!std::binary_search(G.share.begin(), G.share.end(), i)) continue;
+      if (G.kind == 0) {
+        if (!(o.constraints & 1)) continue;
+        for (int64_t r : G.dofs) {
+          double x[3];
+          int c;
+          if (!node_pos(d.free_to_global[r], x, c)) continue;
+          std::array<double, 6> row;
+          for (int l = 0; l < 6; ++l) row[l] = rigid(l, x, c);
+          rows.push_back(row);
+        }
+      } else if (G.kind == 1) {
+        if (!(o.constraints & 2)) continue;
+        for (int c = 0; c < 3; ++c) {
+          std::array<double, 6> row{};
+          int cnt = 0;
+          for (int64_t r : G.dofs) {
+            double x[3];
+            int cc;
+            if (!node_pos(d.free_to_global[r], x, cc) || cc != c) continue;
+            for (int l = 0; l < 6; ++l) row[l] += rigid(l, x, c);
+            ++cnt;
+          }
+          for (auto& v : row) v /= std::max(cnt, 1);
+          rows.push_back(row);
+        }
+      } else {
+        // faces: component means sum_f |f| v(x_f) and the normal flux
+        std::array<double, 6> comp[3] = {}, flux{};
+        std::vector<int> fs;
+        for (int64_t r : G.dofs) {
+          int ty;
+          int64_t id;
+          dof_entity(d, d.free_to_global[r], ty, id);
+          if (ty == 2 && (d.free_to_global[r] - d.off_f) % d.cf == 0) fs.push_back((int)id);
+        }
+        for (int f : fs) {
+          double nrm[3], t1[3], t2[3], area, xc[3];
+          face_frame(t, f, nrm, t1, t2, area);
+          face_centroid(t, f, xc);
+          // orientation: outward from the first sharing subdomain, as in the flux constraint
+          const int64_t fr = d.free_index[d.off_f + (int64_t)f * d.cf];
+          int sgn = 0;
+          for (int64_t q = s->h_adj_ptr[fr]; q < s->h_adj_ptr[fr + 1]; ++q) {
+            const int e = s->h_adj_elem[q];
+            if (part[e] != G.share[0]) continue;
+            for (int fi = t.elem_ptr[e]; fi < t.elem_ptr[e + 1]; ++fi)
+              if (std::abs(t.elem_face[fi]) - 1 == f) sgn = t.elem_face[fi] > 0 ? 1 : -1;
+          }
+          for (int l = 0; l < 6; ++l) {
+            double fl = 0;
+            for (int c = 0; c < 3; ++c) {
+              comp[c][l] += area * rigid(l, xc, c);
+              fl += nrm[c] * rigid(l, xc, c);
+            }
+            flux[l] += sgn * area * fl;
+          }
+        }
+        if (o.constraints & 4)
+          for (int c = 0; c < 3; ++c) rows.push_back(comp[c]);
+        if (o.constraints & 8) rows.push_back(flux);
+      }
+    }
+    double Gm[6][6] = {};
+    for (auto& r : rows) {
+      double nr = 0;
+      for (double v : r) nr += v * v;
+      if (nr == 0) continue;
+      for (int p = 0; p < 6; ++p)
+        for (int q = 0; q < 6; ++q) Gm[p][q] += r[p] * r[q] / nr;
+    }
+    const double ratio = eig_ratio6(Gm);
+    if (!(ratio > 1e-14)) {
+      char msg[240];
+      std::snprintf(msg, sizeof msg,
+                    "subdomain %d touches no Dirichlet boundary and its primal constraints do not control its "
+                    "rigid body modes (eigenvalue ratio %.1e): its local Neumann problem is singular",
+                    i, ratio);
+      throw Error(VEM_ESINGULAR, msg);
+    }
+  }
+}
+
 // Householder QR with rank detection of the n x m column-major matrix A
 // (columns = constraint functionals); keeps the reflectors of the
 // independent columns.
@@ -357,6 +553,7 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
     }
     H.macros.push_back(std::move(G));
   }
+  if (!(o.constraints & 16)) check_rigid_modes(s, part, o, H);
   // coarse numbering
   int64_t cc = 0;
   for (auto& G : H.macros) {

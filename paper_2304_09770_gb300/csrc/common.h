@@ -109,6 +109,7 @@ __host__ __device__ constexpr int n_d5(int k) { return pdim3(k - 1) - 1; }
 
 // Gauss-Legendre rule on [0,1] with n points (Newton on P_n), host side.
 void gauss01(int n, std::vector<double>& x, std::vector<double>& w);
+void gauss01(int n, double* x, double* w);   // the same rule into caller-owned arrays
 // interior Gauss-Lobatto nodes on [0,1] for degree k (k-1 nodes), host side
 std::vector<double> lobatto_interior(int k);
 

@@ -62,6 +62,9 @@ struct ElemShared {
   double xK[3], hK, vol;
   double fn[kMaxElemFaces][3], ft1[kMaxElemFaces][3], ft2[kMaxElemFaces][3], fxc[kMaxElemFaces][3];
   double fh[kMaxElemFaces], farea[kMaxElemFaces];
+  // face-local coordinates (s, t) = fw (xi1, xi2), xi = ((x - xc).t1, (x - xc).t2):
+  // fw = Sigma^{-1/2} / sqrt(24), Sigma the second moments of the face about xc
+  double fw[kMaxElemFaces][4];
   double mu[S::NMOM];
   double Minv0[S::NP0 * S::NP0];   // inverse mass on P_{k-1}
   double Minv1[S::NP1 * S::NP1];   // inverse mass on P_k
@@ -222,9 +225,61 @@ struct ElemBuilder {
         lt = sqrt(lt);
         for (int d = 0; d < 3; ++d) { sh.ft1[f][d] = t1[d] / lt; sh.fxc[f][d] = xc[d] / m; }
         cross3(sh.fn[f], sh.ft1[f], sh.ft2[f]);
+        face_whitening(f);
       }
     }
     ex.sync();
+  }
+
+  // Second moments Sigma = (1/|f|) int_f xi xi^T of the face about xc in the
+  // (t1, t2) frame, exact on the fan triangles from loop vertex 0, and
+  // fw = Sigma^{-1/2} / sqrt(24) in closed form: sqrt(S) = (S + d I) / tau
+  // with d = sqrt(det S), tau = sqrt(tr S + 2 d).  Polynomial spaces on the
+  // face are invariant under this linear map of the centred coordinates; the
+  // scaled monomials stay well conditioned on thin faces.
+  VB_HD void face_whitening(int f) {
+    const int m = R.fnv[f];
+    const double* xc = sh.fxc[f];
+    const double *t1 = sh.ft1[f], *t2 = sh.ft2[f];
+    double q[kMaxFaceVerts][2];
+    for (int i = 0; i < m; ++i) {
+      const double* P = sh.X[R.floopv[f][i]];
+      double dx[3] = {P[0] - xc[0], P[1] - xc[1], P[2] - xc[2]};
+      q[i][0] = dx[0] * t1[0] + dx[1] * t1[1] + dx[2] * t1[2];
+      q[i][1] = dx[0] * t2[0] + dx[1] * t2[1] + dx[2] * t2[2];
+    }
+    double s00 = 0, s01 = 0, s11 = 0, area = 0;
+    for (int i = 1; i < m - 1; ++i) {
+      const double *a = q[0], *b = q[i], *c = q[i + 1];
+      double ar = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]));
+      double sm0 = a[0] + b[0] + c[0], sm1 = a[1] + b[1] + c[1];
+      double w = ar / 12.0;
+      s00 += w * (a[0] * a[0] + b[0] * b[0] + c[0] * c[0] + sm0 * sm0);
+      s01 += w * (a[0] * a[1] + b[0] * b[1] + c[0] * c[1] + sm0 * sm1);
+      s11 += w * (a[1] * a[1] + b[1] * b[1] + c[1] * c[1] + sm1 * sm1);
+      area += ar;
+    }
+    s00 /= area;
+    s01 /= area;
+    s11 /= area;
+    double d = sqrt(s00 * s11 - s01 * s01);
+    double tau = sqrt(s00 + s11 + 2.0 * d);
+    double sc = 1.0 / (d * tau * sqrt(24.0));
+    sh.fw[f][0] = (s11 + d) * sc;
+    sh.fw[f][1] = -s01 * sc;
+    sh.fw[f][2] = -s01 * sc;
+    sh.fw[f][3] = (s00 + d) * sc;
+  }
+
+  // face-local coordinates of the point x on face f
+  VB_HD void face_st(int f, const double* x, double& s, double& t) const {
+    const double* xc = sh.fxc[f];
+    const double *t1 = sh.ft1[f], *t2 = sh.ft2[f];
+    double dx[3] = {x[0] - xc[0], x[1] - xc[1], x[2] - xc[2]};
+    double a = dx[0] * t1[0] + dx[1] * t1[1] + dx[2] * t1[2];
+    double b = dx[0] * t2[0] + dx[1] * t2[1] + dx[2] * t2[2];
+    s = sh.fw[f][0] * a + sh.fw[f][1] * b;
+    t = sh.fw[f][2] * a + sh.fw[f][3] * b;
   }
 
   // ------------------------------------------------ volume moments mu_a = int xi^a
@@ -290,9 +345,12 @@ struct ElemBuilder {
   VB_HD bool face(int f) {
     const int m = R.fnv[f];
     const int nsf = ns(f);
-    const double hf = sh.fh[f], hfi = 1.0 / hf;
-    const double* xc = sh.fxc[f];
     const double *t1 = sh.ft1[f], *t2 = sh.ft2[f];
+    const double* fw = sh.fw[f];
+    // metric of the face-local coordinates: grad_x m . grad_x n = grad_st m^T (fw fw^T) grad_st n
+    const double g00 = fw[0] * fw[0] + fw[1] * fw[1];
+    const double g01 = fw[0] * fw[2] + fw[1] * fw[3];
+    const double g11 = fw[2] * fw[2] + fw[3] * fw[3];
     // face quadrature (fan from loop vertex 0, collapsed Gauss); 2D moments
     // nu_g = int_f s^g1 t^g2 and W[a][b] = int_f m3_a m2_b
     const int nq = T.nq_face;
@@ -315,9 +373,8 @@ struct ElemBuilder {
             double w = T.qf_w[iu] * T.qf_w[iv] * (1 - U) * J;
             double x[3];
             for (int d = 0; d < 3; ++d) x[d] = P0[d] + U * u1[d] + V * u2[d];
-            double dx[3] = {x[0] - xc[0], x[1] - xc[1], x[2] - xc[2]};
-            double s = (dx[0] * t1[0] + dx[1] * t1[1] + dx[2] * t1[2]) * hfi;
-            double tt = (dx[0] * t2[0] + dx[1] * t2[1] + dx[2] * t2[2]) * hfi;
+            double s, tt;
+            face_st(f, x, s, tt);
             if (a < 0) {
               acc += w * ipow(s, g1) * ipow(tt, g2);
             } else {
@@ -340,9 +397,10 @@ struct ElemBuilder {
       const Exp2 eb = T.e2[b], eg = T.e2[g];
       double v = 0.0;
       if (b > 0) {
-        if (eb.a > 0 && eg.a > 0) v += eb.a * eg.a * sh.nu2[idx2(eb.a + eg.a - 2, eb.b + eg.b)];
-        if (eb.b > 0 && eg.b > 0) v += eb.b * eg.b * sh.nu2[idx2(eb.a + eg.a, eb.b + eg.b - 2)];
-        v *= hfi * hfi;
+        if (eb.a > 0 && eg.a > 0) v += g00 * eb.a * eg.a * sh.nu2[idx2(eb.a + eg.a - 2, eb.b + eg.b)];
+        if (eb.b > 0 && eg.b > 0) v += g11 * eb.b * eg.b * sh.nu2[idx2(eb.a + eg.a, eb.b + eg.b - 2)];
+        const int mx = eb.a * eg.b + eb.b * eg.a;   // d_s m_b d_t m_g + d_t m_b d_s m_g
+        if (mx > 0) v += g01 * mx * sh.nu2[idx2(eb.a + eg.a - 1, eb.b + eg.b - 1)];
       }
       sh.G2[idx] = v;
     }
@@ -352,8 +410,10 @@ struct ElemBuilder {
       // interior moments: -int_f Lap m_b v = -|f| sum_g L[g][b] s_g
       for (int b = 1; b < S::NF1; ++b) {
         const Exp2 eb = T.e2[b];
-        if (eb.a >= 2) sh.rhs[b * nsf + m * K + idx2(eb.a - 2, eb.b)] -= sh.farea[f] * eb.a * (eb.a - 1) * hfi * hfi;
-        if (eb.b >= 2) sh.rhs[b * nsf + m * K + idx2(eb.a, eb.b - 2)] -= sh.farea[f] * eb.b * (eb.b - 1) * hfi * hfi;
+        if (eb.a >= 2) sh.rhs[b * nsf + m * K + idx2(eb.a - 2, eb.b)] -= sh.farea[f] * g00 * eb.a * (eb.a - 1);
+        if (eb.a >= 1 && eb.b >= 1)
+          sh.rhs[b * nsf + m * K + idx2(eb.a - 1, eb.b - 1)] -= sh.farea[f] * 2.0 * g01 * eb.a * eb.b;
+        if (eb.b >= 2) sh.rhs[b * nsf + m * K + idx2(eb.a, eb.b - 2)] -= sh.farea[f] * g11 * eb.b * (eb.b - 1);
       }
       for (int g = 0; g < S::NF1; ++g) sh.G2[g] = 0.0;
       // edges: Gauss points, Lagrange basis on (0, interior GL nodes, 1)
@@ -370,8 +430,11 @@ struct ElemBuilder {
         double du[3] = {dvec[0] / le, dvec[1] / le, dvec[2] / le};
         double ne[3];
         cross3(du, sh.fn[f], ne);
-        double n1 = ne[0] * t1[0] + ne[1] * t1[1] + ne[2] * t1[2];
-        double n2 = ne[0] * t2[0] + ne[1] * t2[1] + ne[2] * t2[2];
+        // d_n m = (fw (ne.t1, ne.t2)) . grad_st m
+        double e1 = ne[0] * t1[0] + ne[1] * t1[1] + ne[2] * t1[2];
+        double e2 = ne[0] * t2[0] + ne[1] * t2[1] + ne[2] * t2[2];
+        double n1 = fw[0] * e1 + fw[1] * e2;
+        double n2 = fw[2] * e1 + fw[3] * e2;
         int sidx[K + 1];
         sidx[0] = i;
         for (int j = 0; j < K - 1; ++j) sidx[1 + j] = m + i * (K - 1) + j;
@@ -380,9 +443,8 @@ struct ElemBuilder {
           double tq = T.qe_x[q], wq = T.qe_w[q] * le;
           double x[3];
           for (int d = 0; d < 3; ++d) x[d] = A[d] + tq * dvec[d];
-          double dx[3] = {x[0] - xc[0], x[1] - xc[1], x[2] - xc[2]};
-          double s = (dx[0] * t1[0] + dx[1] * t1[1] + dx[2] * t1[2]) * hfi;
-          double tt = (dx[0] * t2[0] + dx[1] * t2[1] + dx[2] * t2[2]) * hfi;
+          double s, tt;
+          face_st(f, x, s, tt);
           double lag[K + 1];
           for (int aa = 0; aa <= K; ++aa) {
             double l = 1.0;
@@ -398,7 +460,7 @@ struct ElemBuilder {
             } else {
               double ds = eb.a > 0 ? eb.a * ipow(s, eb.a - 1) * ipow(tt, eb.b) : 0.0;
               double dt = eb.b > 0 ? eb.b * ipow(s, eb.a) * ipow(tt, eb.b - 1) : 0.0;
-              double dn = (ds * n1 + dt * n2) * hfi;
+              double dn = ds * n1 + dt * n2;
               for (int aa = 0; aa <= K; ++aa) sh.rhs[b * nsf + sidx[aa]] += wq * dn * lag[aa];
             }
             sh.G2[b] += wq * mb;     // row 0 of G2: int_df m_b
@@ -864,9 +926,6 @@ struct ElemBuilder {
   // (1/|f|)-free face moment int_f m3_a m2_b, recomputed by quadrature
   VB_HD double facemom_(int f, int a, int b) const {
     const int m = R.fnv[f];
-    const double hfi = 1.0 / sh.fh[f];
-    const double* xc = sh.fxc[f];
-    const double *t1 = sh.ft1[f], *t2 = sh.ft2[f];
     const int nq = T.nq_face;
     const Exp3 ea = T.e3[a];
     const Exp2 eb = T.e2[b];
@@ -886,9 +945,8 @@ struct ElemBuilder {
           double w = T.qf_w[iu] * T.qf_w[iv] * (1 - U) * J;
           double x[3];
           for (int d = 0; d < 3; ++d) x[d] = P0[d] + U * u1[d] + V * u2[d];
-          double dx[3] = {x[0] - xc[0], x[1] - xc[1], x[2] - xc[2]};
-          double s = (dx[0] * t1[0] + dx[1] * t1[1] + dx[2] * t1[2]) * hfi;
-          double tt = (dx[0] * t2[0] + dx[1] * t2[1] + dx[2] * t2[2]) * hfi;
+          double s, tt;
+          face_st(f, x, s, tt);
           double px = (x[0] - sh.xK[0]) * hk, py = (x[1] - sh.xK[1]) * hk, pz = (x[2] - sh.xK[2]) * hk;
           acc += w * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c) * ipow(s, eb.a) * ipow(tt, eb.b);
         }

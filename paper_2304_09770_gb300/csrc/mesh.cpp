@@ -13,11 +13,11 @@ thread_local std::string g_last_error;
 std::atomic<int64_t> g_launches{0};
 void set_last_error(const std::string& m) { g_last_error = m; }
 
-void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
+void gauss01(int n, double* x, double* w) {
   // roots of the Legendre polynomial P_n by Newton iteration from the
-  // Chebyshev-like first guess; weights 2 / ((1 - z^2) P_n'(z)^2)
-  x.assign(n, 0.0);
-  w.assign(n, 0.0);
+  // Chebyshev-like first guess; weights 2 / ((1 - z^2) P_n'(z)^2); mapped
+  // to (0, 1).  The first guesses, and so the roots, decrease with i: they
+  // are stored in reverse for increasing nodes.
   for (int i = 0; i < n; ++i) {
     double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
     double pp = 1.0;
@@ -42,13 +42,16 @@ void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
       p1 = p2;
     }
     pp = n * (z * p1 - p0) / (z * z - 1.0);
-    x[i] = z;
-    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    x[n - 1 - i] = 0.5 * (z + 1.0);
+    w[n - 1 - i] = 0.5 * (2.0 / ((1.0 - z * z) * pp * pp));
   }
-  std::vector<std::pair<double, double>> xw(n);
-  for (int i = 0; i < n; ++i) xw[i] = {0.5 * (x[i] + 1.0), 0.5 * w[i]};
-  std::sort(xw.begin(), xw.end());
-  for (int i = 0; i < n; ++i) { x[i] = xw[i].first; w[i] = xw[i].second; }
+  for (int i = 1; i < n; ++i) VB_CHECK(x[i] > x[i - 1], VEM_EINVAL, "gauss01: nodes out of order");
+}
+
+void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  gauss01(n, x.data(), w.data());
 }
 
 std::vector<double> lobatto_interior(int k) {

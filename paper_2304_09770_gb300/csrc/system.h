@@ -50,6 +50,19 @@ void number_dofs(const Topo& t, int k, DofNumbering& d, bool reduced = false);
 // element-local velocity DOFs (global numbers) in the element-local order
 void element_global_dofs(const Topo& t, const DofNumbering& d, int e, std::vector<int64_t>& out);
 void build_elem_records(const Topo& t, const DofNumbering& d, std::vector<ElemRec>& recs);
+
+// Tetrahedra of an element's load rule: (x_K, fan triangle) for every fan
+// triangle of every face; one definition for the host point count
+// (vem_quad_points, vem_load) and the device offsets (vem_load_noalloc).
+template <class FaceVerts>
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int elem_fan_tets(int nf, FaceVerts fnv) {
+  int nt = 0;
+  for (int f = 0; f < nf; ++f) nt += fnv(f) - 2;
+  return nt;
+}
 // CSR pattern of K = [A B^T; B 0] over the system layout (free velocity,
 // then element pressures): row r holds the columns of every element
 // adjacent to r (velocity rows also the element's pressures); sorted rows

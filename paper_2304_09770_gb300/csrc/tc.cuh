@@ -136,6 +136,14 @@ __device__ inline void tc_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Polls the mbarrier phase at most `limit` times; false when it gave up.
+__device__ inline bool tc_wait_bounded(uint32_t mbar, uint32_t phase, long long limit) {
+  long long it = 0;
+  bool done = false;
+  while (!(done = tc_try_wait(mbar, phase)) && it < limit) ++it;
+  return done;
+}
+
 // D = A B^T for the staged 128 x 32 tiles (A: rows of the output, B: its
 // columns), split-TF32, into TMEM; thread 0 issues and waits (bounded), the
 // outcome is shared through the CTA.  Returns false after a failed wait.
@@ -163,14 +171,11 @@ __device__ inline bool tc_product(const KExec& ex, TcCtx& c) {
                      tc_smem_addr(c.mbar))
                  : "memory");
     const uint32_t mb = tc_smem_addr(c.mbar);
-    long long it = 0;
-    bool done = false;
-    while (!(done = tc_try_wait(mb, c.phase)) && it < TC_WAIT_LIMIT) ++it;
+    bool done = tc_wait_bounded(mb, c.phase, TC_WAIT_LIMIT);
     if (!done) {
       // gave up: record it, wait once more (bounded) for the MMAs in flight
       flag_error(c.status, 4);
-      it = 0;
-      while (!(done = tc_try_wait(mb, c.phase)) && it < TC_WAIT_LIMIT) ++it;
+      done = tc_wait_bounded(mb, c.phase, TC_WAIT_LIMIT);
     }
     tc_ok = done ? 1 : 0;
   }

@@ -69,9 +69,44 @@ struct KTcCheck {
   }
 };
 
+// The bounded wait of the tensor-core kernels on an mbarrier that nothing
+// arrives on: it must give up after `limit` polls and report it (status 4).
+struct KWaitCheck {
+  long long limit;
+  int* status;
+  __device__ void operator()(const KExec& ex, int) const {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(ex.smem);
+    if (ex.tid == 0)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_addr(mbar)), "r"(1) : "memory");
+    ex.sync();
+    if (ex.tid == 0 && !tc_wait_bounded(tc_smem_addr(mbar), 0u, limit)) flag_error(status, 4);
+    ex.sync();
+  }
+};
+
 }  // namespace vb
 
 using namespace vb;
+
+extern "C" int vem_wait_selftest(long long limit) {
+  if (limit < 0 || limit > (1ll << 30)) { set_last_error("vem_wait_selftest: limit out of range"); return VEM_EINVAL; }
+  try {
+    DBuf<int> status(1);
+    status.zero();
+    launch(KWaitCheck{limit, status.p}, 1, 32, 16, 0);
+    VB_CUDA(cudaDeviceSynchronize());
+    const auto st = status.download();
+    if (st[0] == 4) {
+      set_last_error("vem_wait_selftest: the bounded mbarrier wait gave up, as it must");
+      return VEM_ETIMEOUT;
+    }
+    set_last_error("vem_wait_selftest: the wait on an mbarrier nobody arrives on completed");
+    return VEM_ECUDA;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.status;
+  }
+}
 
 extern "C" int vem_tc_selftest(double* max_err, double* max_ref) {
   if (!max_err || !max_ref) { set_last_error("vem_tc_selftest: null argument"); return VEM_EINVAL; }

@@ -496,17 +496,16 @@ static void load_offsets(vem_system* s, int degree, std::vector<int64_t>& qoff, 
   int nq = (degree + 3) / 2 + 1;
   L = LoadRule{};
   L.nq = nq;
-  std::vector<double> x, w;
-  gauss01(nq, x, w);
-  for (int i = 0; i < nq; ++i) { L.x[i] = x[i]; L.w[i] = w[i]; }
+  gauss01(nq, L.x, L.w);
   const Topo& t = s->topo;
   qoff.assign(t.nE + 1, 0);
   for (int e = 0; e < t.nE; ++e) {
-    int ntets = 0;
-    for (int i = t.elem_ptr[e]; i < t.elem_ptr[e + 1]; ++i) {
-      int f = std::abs(t.elem_face[i]) - 1;
-      ntets += t.face_ptr[f + 1] - t.face_ptr[f] - 2;
-    }
+    // face loop sizes as in the element records (build_elem_records)
+    const int* ef = &t.elem_face[t.elem_ptr[e]];
+    const int ntets = elem_fan_tets(t.elem_ptr[e + 1] - t.elem_ptr[e], [&](int fi) {
+      const int f = std::abs(ef[fi]) - 1;
+      return t.face_ptr[f + 1] - t.face_ptr[f];
+    });
     qoff[e + 1] = qoff[e] + (int64_t)ntets * nq * nq * nq;
   }
 }
@@ -664,39 +663,6 @@ static unsigned char* load_scratch_address() {
   return static_cast<unsigned char*>(addr[dev]);
 }
 
-// Gauss-Legendre rule on [0,1] with n <= 16 points into fixed arrays, in
-// increasing node order; the same Newton iteration and arithmetic as
-// gauss01, so the nodes and weights agree bit for bit.
-static void gauss01_fixed(int n, double* x, double* w) {
-  for (int i = 0; i < n; ++i) {
-    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
-    double pp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int j = 2; j <= n; ++j) {
-        double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
-        p0 = p1;
-        p1 = p2;
-      }
-      if (n == 1) { p1 = z; p0 = 1.0; }
-      pp = n * (z * p1 - p0) / (z * z - 1.0);
-      double z1 = z;
-      z = z1 - p1 / pp;
-      if (std::fabs(z - z1) < 1e-15) break;
-    }
-    double p0 = 1.0, p1 = z;
-    for (int j = 2; j <= n; ++j) {
-      double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
-      p0 = p1;
-      p1 = p2;
-    }
-    pp = n * (z * p1 - p0) / (z * z - 1.0);
-    // the Newton roots decrease with i: store them in reverse for increasing nodes
-    x[n - 1 - i] = 0.5 * (z + 1.0);
-    w[n - 1 - i] = 0.5 * (2.0 / ((1.0 - z * z) * pp * pp));
-  }
-}
-
 // qoff[e] = first load-rule point of element e, qoff[nE] = total: one CTA,
 // each thread owns a contiguous run of elements; exclusive scan of the run
 // totals in shared memory
@@ -707,9 +673,7 @@ struct KLoadOffsets {
   int64_t* qoff;
   __device__ int64_t count(int e) const {
     const ElemRec& R = rec[e];
-    int nt = 0;
-    for (int f = 0; f < R.nf; ++f) nt += R.fnv[f] - 2;
-    return (int64_t)nt * pts_per_tet;
+    return (int64_t)elem_fan_tets(R.nf, [&](int f) { return R.fnv[f]; }) * pts_per_tet;
   }
   __device__ void operator()(const KExec& ex, int) const {
     int64_t* run = reinterpret_cast<int64_t*>(ex.smem);
@@ -760,7 +724,7 @@ extern "C" int vem_load_noalloc(vem_system* s, int degree, const double* fq, dou
     double* rloc = reinterpret_cast<double*>(base + off_bytes);
     LoadRule L;
     L.nq = (degree + 3) / 2 + 1;
-    gauss01_fixed(L.nq, L.x, L.w);
+    gauss01(L.nq, L.x, L.w);
     const int64_t nq3 = (int64_t)L.nq * L.nq * L.nq;
     launch(KLoadOffsets{s->d_rec.p, nE, nq3, qoff}, 1, 1024, sizeof(int64_t) * 1024, s->stream);
     const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4 + 6 * KLoadLocal<2>::CH);

@@ -1,0 +1,119 @@
+"""Test infrastructure: the oracle's System of a named synthetic workload,
+built once per test session.  Its elements are built in worker processes
+(a ``spawn`` pool, started before or after CUDA without harm): each worker
+rebuilds the workload from its seed and returns finished elements, which
+``oracle.vem.System`` then assembles exactly as it would its own."""
+import multiprocessing as mp
+import os
+
+_POOL = None
+_SYSTEMS = {}
+
+
+_ONE_THREAD = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _pool():
+    """Workers run single-threaded BLAS (the element systems are tiny; one
+    BLAS thread pool per worker would oversubscribe the cores)."""
+    global _POOL
+    if _POOL is None:
+        n = max(1, min(os.cpu_count() or 1, 32))
+        saved = {v: os.environ.get(v) for v in _ONE_THREAD}
+        for v in _ONE_THREAD:
+            os.environ[v] = "1"
+        try:
+            _POOL = mp.get_context("spawn").Pool(n)
+        finally:
+            for v, x in saved.items():
+                if x is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = x
+    return _POOL
+
+
+def _build_chunk(args):
+    name, overrides, deg, reduced, elems = args
+    from synth import make_config
+    from oracle.vem import Topology, DofMap, build_element
+    cfg = make_config(name, **overrides)
+    topo = Topology(cfg["mesh"])
+    dm = DofMap(topo, cfg["k"], reduced)
+    out = {}
+    for e in elems:
+        el = build_element(topo, dm, e, cfg["nu"][e], deg)
+        fk = el.load(cfg["f"])
+        el._topo = None            # the parent reattaches its own topology
+        el._topo_xyz = None
+        out[e] = (el, fk)
+    return out
+
+
+def load_degree(cfg):
+    k = cfg["k"]
+    return k + 9 if cfg["spec"]["load"] == "manufactured" else 2 * k + 2
+
+
+def oracle_system(name, deg=None, reduced=False, **overrides):
+    """(cfg, System) for a named workload; the System is cached per session."""
+    from synth import make_config
+    from oracle.vem import System
+    cfg = make_config(name, **overrides)
+    deg = load_degree(cfg) if deg is None else deg
+    key = (name, tuple(sorted(overrides.items())), deg, reduced)
+    if key not in _SYSTEMS:
+        ne = len(cfg["nu"])
+        nw = _pool()._processes
+        step = max(1, -(-ne // (4 * nw)))
+        chunks = [(name, overrides, deg, reduced, list(range(a, min(ne, a + step)))) for a in range(0, ne, step)]
+        built = {}
+        for part in _pool().map(_build_chunk, chunks):
+            built.update(part)
+        _SYSTEMS[key] = System(cfg["mesh"], cfg["k"], cfg["nu"], f=cfg["f"], load_deg=deg, reduced=reduced,
+                               prebuilt=built)
+    return cfg, _SYSTEMS[key]
+
+
+_BDDC = {}
+
+
+def oracle_bddc(name, scaling="deluxe", adaptive=None, reduced=False, deg=None, **overrides):
+    """(cfg, System, BDDC, F) with the oracle's BDDC setup cached per session;
+    F is the right-hand side of the free saddle system."""
+    import numpy as np
+    from oracle.bddc import BDDC
+    cfg, S = oracle_system(name, deg=deg, reduced=reduced, **overrides)
+    key = (name, tuple(sorted(overrides.items())), deg, reduced, scaling, adaptive)
+    if key not in _BDDC:
+        kw = {} if adaptive is None else {"adaptive": adaptive}
+        _BDDC[key] = BDDC(S, cfg["part"], scaling=scaling, **kw)
+    F = np.concatenate([S.F[S.dm.free], np.zeros(S.dm.npress)])
+    return cfg, S, _BDDC[key], F
+
+
+def check_pcg_parity(S, ob, F, res, x, tol=1e-10, label=""):
+    """FP64 parity of a GPU BDDC-PCG run with the oracle's: iteration counts
+    within +-1 and, at equal iteration counts (the oracle re-run with maxit =
+    the GPU's count when the two stop one step apart), the velocity and the
+    zero-mean pressure within ``tol`` relative; Lanczos lambda_max within
+    1e-6 relative.  Returns the measured differences."""
+    import numpy as np
+    ro = ob.pcg(F, rtol=1e-8)
+    assert abs(res["iters"] - ro["iters"]) <= 1, (res["iters"], ro["iters"])
+    if res["iters"] != ro["iters"]:
+        ro = ob.pcg(F, rtol=0.0, maxit=res["iters"])
+        assert ro["iters"] == res["iters"]
+    nvf = len(S.dm.free)
+    xo = ro["x"]
+    ev = np.linalg.norm(x[:nvf] - xo[:nvf]) / np.linalg.norm(xo[:nvf])
+    pz = lambda p: p - (S.wmean @ p) / S.wmean.sum()
+    po = pz(xo[nvf:])
+    ep = np.linalg.norm(pz(x[nvf:]) - po) / max(np.linalg.norm(po), 1e-300)
+    el = abs(res["lam_max"] - ro["lam_max"]) / ro["lam_max"]
+    print(f"PARITY {label} iters gpu {res['iters']} oracle {ro['iters']} vel {ev:.3e} press {ep:.3e} "
+          f"lam_max {el:.3e}")
+    assert ev <= tol, ev
+    assert ep <= tol, ep
+    assert el <= 1e-6, el
+    return dict(vel=ev, press=ep, lam=el, oracle=ro)

@@ -5,6 +5,7 @@ import pytest
 
 from synth import make_config, cube_mesh
 from oracle.vem import Topology, DofMap, System, build_element
+from oracle_cache import oracle_system
 
 pytestmark = pytest.mark.gpu
 
@@ -39,11 +40,10 @@ def test_element_matrices_match_oracle(pkg, name, tol):
 @pytest.mark.parametrize("name", ["cube4_k2", "tri4_k2", "tri4_k3"])
 def test_global_matrix_and_load_match_oracle(pkg, name):
     import torch
-    cfg = make_config(name)
+    cfg, S = oracle_system(name)
     k = cfg["k"]
     deg = k + 9                                   # exact for the manufactured load
     g = pkg.VemSystem(cfg["mesh"], k, cfg["nu"])
-    S = System(cfg["mesh"], k, cfg["nu"], f=cfg["f"], load_deg=deg)
     assert g.n_vel_free == len(S.dm.free) and g.n_press == S.dm.npress
     assert np.array_equal(g.free_dofs(), S.dm.free)
     Kg = g.csr().toarray()

@@ -32,11 +32,12 @@ def _system(pkg, name, **override):
 
 def test_noalloc_load_matches_load_on_two_calls_in_a_row(pkg):
     import torch
-    # two different problems back to back: a k = 3 mesh, then a k = 2 mesh
-    # with fewer DOFs, so stale contents of the shared scratch from the first
-    # call would show in the second result
+    # different problems back to back: a k = 3 split-hex mesh, OCTA and CVT
+    # meshes (pentagonal and larger faces, cells of uneven point counts), then
+    # a k = 2 mesh with fewer DOFs, so stale contents of the shared scratch
+    # from an earlier call would show in a later result
     outs = []
-    for name in ("tri4_k3", "tri6_k2"):
+    for name in ("tri4_k3", "octa2_k3", "cvt27_k3", "tri6_k2"):
         cfg, g, deg = _system(pkg, name)
         fq = np.ascontiguousarray(cfg["f"](g.quad_points(deg)))
         ref = g.load(deg, fq)                      # vem_load (host f, allocating)

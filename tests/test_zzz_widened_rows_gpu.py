@@ -10,26 +10,24 @@ against the CPU oracle:
   3, 4, global CSR and load, BDDC-PCG, and the paper's 15,552-element OCTA
   mesh by properties;
 * the CVT mesh family (Lloyd-relaxed Voronoi cells: up to about 30
-  vertices, faces of up to 9 vertices): element matrices, load and
-  BDDC-PCG (at k = 3 the tolerances are 1e-9: faces of such cells can be
-  nearly degenerate, and the two implementations round differently there);
+  vertices, faces of up to 9 vertices, some of them thin): element
+  matrices, load and BDDC-PCG;
 * the reduced scheme (vem_assemble_reduced: D5 eliminated with value 0,
   element-constant pressure): element matrices, CSR and load against the
   oracle's reduced System, BDDC-PCG against the oracle's BDDC on it, and
   the velocity against the full scheme's direct solve.
 
 Tolerances as in the other parity tests: element matrices and assembly to
-rounding; PCG within +-1 iteration (+-3 at viscosity contrast), lambda_max
-to 1e-6, solution 1e-10 relative to the oracle's PCG solution (1e-8 at
-contrast or when the two runs stop one step apart: both stopped iterates
-are within kappa * rtol of the solution).
+rounding; PCG within +-1 iteration and, at equal iteration counts, the
+velocity and the zero-mean pressure within 1e-10 of the oracle's iterate,
+lambda_max within 1e-6.
 """
 import numpy as np
 import pytest
 
 from synth import make_config
 from oracle.vem import Topology, DofMap, System, build_element
-from oracle.bddc import BDDC
+from oracle_cache import oracle_system, oracle_bddc, check_pcg_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -46,12 +44,11 @@ def pkg():
 
 
 def _setup(pkg, name):
-    cfg = make_config(name)
+    cfg, S = oracle_system(name)
     k = cfg["k"]
     deg = k + 9 if cfg["spec"]["load"] == "manufactured" else 2 * k + 2
     g = pkg.VemSystem(cfg["mesh"], k, cfg["nu"])
     rhs = g.load(deg, cfg["f"](g.quad_points(deg)))
-    S = System(cfg["mesh"], k, cfg["nu"], f=cfg["f"], load_deg=deg)
     F = np.concatenate([S.F[S.dm.free], np.zeros(S.dm.npress)])
     return cfg, g, rhs, S, F
 
@@ -87,7 +84,7 @@ def test_octa_global_matrix_and_load_match_oracle(pkg):
     assert np.abs(y - yo).max() <= 1e-12 * np.abs(yo).max()
 
 
-@pytest.mark.parametrize("name,tol", [("cvt64_k2", 1e-12), ("cvt27_k3", 1e-9)])
+@pytest.mark.parametrize("name,tol", [("cvt64_k2", 1e-12), ("cvt27_k3", 1e-11)])
 def test_cvt_element_matrices_and_load_match_oracle(pkg, name, tol):
     cfg, g, rhs, S, F = _setup(pkg, name)
     topo = S.topo
@@ -117,15 +114,9 @@ def test_pcg_matches_oracle(pkg, name, scaling):
     u = torch.zeros_like(rhs)
     res = bd.solve(rhs, u, rtol=1e-8, maxit=300)
     assert res["status"] == 0
-    ro = BDDC(S, cfg["part"], scaling=scaling).pcg(F, rtol=1e-8)
-    contrast = np.ptp(cfg["nu"]) > 0
-    assert abs(res["iters"] - ro["iters"]) <= (3 if contrast else 1)
     assert res["lam_min"] > 1.0 - 1e-8
-    assert abs(res["lam_max"] - ro["lam_max"]) <= 1e-6 * ro["lam_max"]
-    x = u.cpu().numpy()
-    nvf = len(S.dm.free)
-    tol = 1e-8 if contrast or res["iters"] != ro["iters"] else 1e-10
-    assert np.linalg.norm(x[:nvf] - ro["x"][:nvf]) <= tol * np.linalg.norm(ro["x"][:nvf])
+    _, _, ob, _ = oracle_bddc(name, scaling=scaling)
+    check_pcg_parity(S, ob, F, res, u.cpu().numpy(), label=f"{name}-{scaling}")
 
 
 @pytest.mark.parametrize("name,scaling", [("tri6_k2", "deluxe_edges"), ("tri6_greedy", "deluxe_edges"),
@@ -134,7 +125,7 @@ def test_preconditioner_matches_oracle(pkg, name, scaling):
     import torch
     cfg, g, rhs, S, F = _setup(pkg, name)
     bd = pkg.Bddc(g, cfg["part"], scaling=SCALING[scaling])
-    ob = BDDC(S, cfg["part"], scaling=scaling)
+    _, _, ob, _ = oracle_bddc(name, scaling=scaling)
     r = F - ob.K @ ob.initial_guess(F)
     zo = ob.apply(r)
     z = bd.apply(torch.tensor(r, device="cuda")).cpu().numpy()
@@ -188,12 +179,11 @@ def test_octa_full_size_properties(pkg):
 
 
 def _setup_reduced(pkg, name):
-    cfg = make_config(name)
+    cfg, S = oracle_system(name, reduced=True)
     k = cfg["k"]
     deg = k + 9
     g = pkg.VemSystem(cfg["mesh"], k, cfg["nu"], reduced=True)
     rhs = g.load(deg, cfg["f"](g.quad_points(deg)))
-    S = System(cfg["mesh"], k, cfg["nu"], f=cfg["f"], load_deg=deg, reduced=True)
     F = np.concatenate([S.F[S.dm.free], np.zeros(S.dm.npress)])
     return cfg, g, rhs, S, F
 
@@ -224,14 +214,12 @@ def test_reduced_pcg_matches_oracle(pkg, name, scaling):
     u = torch.zeros_like(rhs)
     res = bd.solve(rhs, u, rtol=1e-8, maxit=300)
     assert res["status"] == 0 and res["lam_min"] > 1.0 - 1e-8
-    ro = BDDC(S, cfg["part"], scaling=scaling).pcg(F, rtol=1e-8)
-    assert abs(res["iters"] - ro["iters"]) <= 1
+    _, _, ob, _ = oracle_bddc(name, scaling=scaling, reduced=True)
+    check_pcg_parity(S, ob, F, res, u.cpu().numpy(), label=f"reduced-{name}-{scaling}")
     nvf = len(S.dm.free)
     x = u.cpu().numpy()
-    tol = 1e-10 if res["iters"] == ro["iters"] else 1e-8
-    assert np.linalg.norm(x[:nvf] - ro["x"][:nvf]) <= tol * np.linalg.norm(ro["x"][:nvf])
     # the same velocity as the full scheme (its direct solve), within the CG tolerance
-    full = System(cfg["mesh"], cfg["k"], cfg["nu"], f=cfg["f"], load_deg=cfg["k"] + 9)
+    _, full = oracle_system(name)
     ud, _ = full.solve_direct()
     ur = np.zeros(S.dm.nvel)
     ur[S.dm.free] = x[:nvf]
