@@ -75,7 +75,7 @@ struct bddc {
   vb::DBuf<vb::ProbDev> d_probs;
   vb::DBuf<vb::SubDev> d_subs;
   vb::DBuf<vb::MacroDev> d_macros;
-  vb::DBuf<int> d_border, d_children, d_rel, d_dtype, d_dsrc, d_elpos, d_elptr, d_pv, d_sub_elems, d_vadj_ptr,
+  vb::DBuf<int> d_border, d_children, d_rel, d_dtype, d_dsrc, d_bgrp, d_elpos, d_elptr, d_pv, d_sub_elems, d_vadj_ptr,
       d_vadj, d_vcon_ptr, d_vcon_id, d_iface, d_elloc, d_elloc_ptr, d_share, d_gpos, d_gif;
   vb::DBuf<int64_t> d_vdof, d_press, d_coarse, d_mdofs, d_fvoff;
   std::vector<int64_t> h_fvoff;
@@ -156,6 +156,7 @@ static BddcView make_view(bddc* b) {
   V.rel = b->d_rel.p;
   V.dtype = b->d_dtype.p;
   V.dsrc = b->d_dsrc.p;
+  V.bgrp = b->d_bgrp.p;
   V.elpos = b->d_elpos.p;
   V.elptr = b->d_elptr.p;
   V.pos_of_vdof = b->d_pv.p;
@@ -402,28 +403,31 @@ struct KCoarseAssemble {
   }
 };
 
-// deluxe: S_FF of one side from the root update matrix, rotated to the dual
-// coordinates: Sd = (H^T S H)[r:, r:]
+// deluxe: S_FF of one side from the root update matrix of its subdomain's
+// deluxe problem (the entity's DOFs are the contiguous root-border block
+// b0 .. b0 + n), rotated to the dual coordinates: Sd = (H^T S H)[r:, r:]
+struct DeluxeTask {
+  int prob, root, macro, b0;
+  int64_t work_off, sd_off;
+};
+
 template <class T>
 struct KDeluxeExtract {
   BddcView V;
-  const int* probs;       // deluxe problem ids
-  const int* roots;       // root node per problem
+  const DeluxeTask* tasks;
   const T* U;             // deluxe batch update store
-  double* work;           // n x n per problem
-  const int64_t* work_off;
+  double* work;           // n x n per task
   double* SD;             // dual blocks
-  const int64_t* sd_off;
   VB_HD void operator()(const KExec& ex, int blk) const {
-    const ProbDev P = V.probs[probs[blk]];
-    const NodeDev R = V.nodes[roots[blk]];
-    const MacroDev F = V.macros[P.macro];
-    const int n = F.n, r = F.r, nd = n - r;
+    const DeluxeTask tk = tasks[blk];
+    const NodeDev R = V.nodes[tk.root];
+    const MacroDev F = V.macros[tk.macro];
+    const int n = F.n, r = F.r, nd = n - r, nbU = R.nb, b0 = tk.b0;
     const T* Ur = U + R.upd_off;
-    double* S = work + work_off[blk];
+    double* S = work + tk.work_off;
     for (int64_t idx = ex.tid; idx < (int64_t)n * n; idx += ex.nt) {
       const int k = (int)(idx / n), i = (int)(idx % n);
-      S[idx] = (double)(i >= k ? Ur[(int64_t)k * n + i] : Ur[(int64_t)i * n + k]);
+      S[idx] = (double)(i >= k ? Ur[(int64_t)(b0 + k) * nbU + b0 + i] : Ur[(int64_t)(b0 + i) * nbU + b0 + k]);
     }
     ex.sync();
     // S <- H^T S (columns), then S <- (H^T S^T)^T = H^T S H using symmetry of S
@@ -447,7 +451,7 @@ struct KDeluxeExtract {
       }
       ex.sync();
     }
-    double* sd = SD + sd_off[blk];
+    double* sd = SD + tk.sd_off;
     for (int64_t idx = ex.tid; idx < (int64_t)nd * nd; idx += ex.nt) {
       const int k = (int)(idx / nd), i = (int)(idx % nd);
       sd[idx] = 0.5 * (S[(int64_t)(r + k) * n + r + i] + S[(int64_t)(r + i) * n + r + k]);
@@ -1201,14 +1205,28 @@ static void build_batch(bddc* b, Batch& B, const std::vector<int>& probs, bool w
   (void)with_vectors;
 }
 
-// factorization flops of a batch (partial LDL^T plus the L11 inversion)
+// factorization flops of a batch (partial LDL^T plus the L11 inversion);
+// for deluxe problems without the skipped update blocks between two
+// different entities at the root border
 static double batch_gflop(bddc* b, const std::vector<int>& probs) {
   double f = 0;
-  for (int q : probs)
-    for (const Node& Nd : b->H.probs[q].nodes) {
+  for (int q : probs) {
+    const Problem& HP = b->H.probs[q];
+    std::vector<double> cnt(HP.dl_macros.size());
+    for (const Node& Nd : HP.nodes) {
       const double np = Nd.np, nf = Nd.np + Nd.nb;
       f += np * nf * nf - nf * np * np + np * np * np / 3.0 + np * np * np / 3.0;
+      if (cnt.empty()) continue;
+      std::fill(cnt.begin(), cnt.end(), 0.0);
+      double tot = 0, diag = 0;
+      for (int a = 0; a < Nd.nb; ++a) {
+        const int g = HP.bgrp[HP.border[Nd.border_off + a]];
+        if (g >= 0) { cnt[g] += 1; tot += 1; }
+      }
+      for (double c : cnt) diag += c * c;
+      f -= np * (tot * tot - diag);
     }
+  }
   return f * 1e-9;
 }
 
@@ -1904,7 +1922,7 @@ static void setup_core(bddc* b, const int32_t* part) {
     const int N = H.N;
     const int np = s->dof.np;
     // ---------------- flatten
-    std::vector<int> border, children, rel, dtype, dsrc, elpos, elptr, pv, sub_elems, vadj_ptr, vadj, vcon_ptr,
+    std::vector<int> border, children, rel, dtype, dsrc, bgrp, elpos, elptr, pv, sub_elems, vadj_ptr, vadj, vcon_ptr,
         vcon_id, iface, elloc, elloc_ptr, share, gpos, gif;
     std::vector<int64_t> vdof, press, coarse, mdofs;
     std::vector<double> vcon_coef, wmean, hv, tau, mcon_coef;
@@ -1997,6 +2015,7 @@ static void setup_core(bddc* b, const int32_t* part) {
       D.macro = P.macro;
       D.pos_off = (int64_t)dtype.size();
       dtype.insert(dtype.end(), P.dtype.begin(), P.dtype.end());
+      bgrp.insert(bgrp.end(), P.bgrp.begin(), P.bgrp.end());
       for (int64_t x : P.dsrc) dsrc.push_back((int)x);
       D.elpos_off = (int64_t)elpos.size();
       elpos.insert(elpos.end(), P.elpos.begin(), P.elpos.end());
@@ -2069,36 +2088,38 @@ static void setup_core(bddc* b, const int32_t* part) {
       D.deluxe_e_off = -1;
     }
     b->ndual = dual;
-    // deluxe problems
-    std::vector<int> dl_probs, dl_roots;
+    // deluxe problems (one per subdomain) and their (problem, entity) tasks
+    std::vector<int> dl_probs;
+    std::vector<DeluxeTask> dtasks;
+    std::vector<int> dtask_prob;   // task -> index into dl_probs
     for (size_t q = 0; q < H.probs.size(); ++q)
-      if (H.probs[q].kind == PK_DELUXE) { dl_probs.push_back((int)q); dl_roots.push_back(b->h_probs[q].root); }
+      if (H.probs[q].kind == PK_DELUXE) dl_probs.push_back((int)q);
     std::vector<int> faces, edges;
-    std::vector<int64_t> sd_i, sd_j, sd_off_v, work_off_v, cw_off;
+    std::vector<int64_t> sd_i, sd_j, cw_off;
     std::vector<int64_t> e_sd, e_sd_ptr(1, 0);
-    int64_t deluxe_e_n = 0;
+    int64_t deluxe_e_n = 0, sdn = 0;
     {
-      // dual block offsets per deluxe problem
-      int64_t o = 0, w = 0;
-      for (int q : dl_probs) {
-        const MacroDev& G = b->h_macros[H.probs[q].macro];
-        sd_off_v.push_back(o);
-        o += (int64_t)G.ndual * G.ndual;
-        work_off_v.push_back(w);
-        w += (int64_t)G.n * G.n;
+      std::map<std::pair<int, int>, int> tq;   // (macro, subdomain) -> task
+      for (size_t t = 0; t < dl_probs.size(); ++t) {
+        const Problem& HP = H.probs[dl_probs[t]];
+        for (size_t m = 0; m < HP.dl_macros.size(); ++m) {
+          const MacroDev& G = b->h_macros[HP.dl_macros[m]];
+          DeluxeTask tk{dl_probs[t], b->h_probs[dl_probs[t]].root, HP.dl_macros[m], HP.dl_b0[m], 0, sdn};
+          sdn += (int64_t)G.ndual * G.ndual;
+          tq[{HP.dl_macros[m], HP.sub}] = (int)dtasks.size();
+          dtasks.push_back(tk);
+          dtask_prob.push_back((int)t);
+        }
       }
       for (size_t g = 0; g < H.macros.size(); ++g) {
         MacroDev& G = b->h_macros[g];
         if (G.kind != 2 || G.ndual == 0) continue;
-        int qa = -1, qb = -1;
-        for (size_t t = 0; t < dl_probs.size(); ++t)
-          if (H.probs[dl_probs[t]].macro == (int)g) {
-            if (H.probs[dl_probs[t]].sub == H.macros[g].share[0]) qa = (int)t; else qb = (int)t;
-          }
-        if (qa < 0 || qb < 0) continue;
+        auto ia = tq.find({(int)g, H.macros[g].share[0]});
+        auto ib = tq.find({(int)g, H.macros[g].share[1]});
+        if (ia == tq.end() || ib == tq.end()) continue;
         faces.push_back((int)g);
-        sd_i.push_back(sd_off_v[qa]);
-        sd_j.push_back(sd_off_v[qb]);
+        sd_i.push_back(dtasks[ia->second].sd_off);
+        sd_j.push_back(dtasks[ib->second].sd_off);
         G.deluxe_off = deluxe_n;
         deluxe_n += (int64_t)G.ndual * G.ndual;
       }
@@ -2110,9 +2131,6 @@ static void setup_core(bddc* b, const int32_t* part) {
       // deluxe edges: the dual blocks of all sharing subdomains, in the
       // order of the entity's sharing list
       if (b->opt.scaling == BDDC_SCALING_DELUXE_EDGES) {
-        std::map<std::pair<int, int>, int> tq;   // (macro, subdomain) -> deluxe problem
-        for (size_t t = 0; t < dl_probs.size(); ++t)
-          tq[{H.probs[dl_probs[t]].macro, H.probs[dl_probs[t]].sub}] = (int)t;
         for (size_t g = 0; g < H.macros.size(); ++g) {
           MacroDev& G = b->h_macros[g];
           if (G.kind != 1 || G.ndual == 0) continue;
@@ -2120,7 +2138,7 @@ static void setup_core(bddc* b, const int32_t* part) {
           for (int sd : H.macros[g].share) {
             auto it = tq.find({(int)g, sd});
             if (it == tq.end()) break;
-            offs.push_back(sd_off_v[it->second]);
+            offs.push_back(dtasks[it->second].sd_off);
           }
           if (offs.size() != H.macros[g].share.size()) continue;
           edges.push_back((int)g);
@@ -2136,6 +2154,7 @@ static void setup_core(bddc* b, const int32_t* part) {
     upload_vec(b->d_children, children, st);
     upload_vec(b->d_rel, rel, st);
     upload_vec(b->d_dtype, dtype, st);
+    upload_vec(b->d_bgrp, bgrp, st);
     upload_vec(b->d_dsrc, dsrc, st);
     upload_vec(b->d_elpos, elpos, st);
     upload_vec(b->d_elptr, elptr, st);
@@ -2206,41 +2225,39 @@ static void setup_core(bddc* b, const int32_t* part) {
       VB_CHECK(stv[0] != 2, VEM_EINVAL, "local factorization: matrix entry outside the symbolic front");
       VB_CHECK(stv[0] == 0, VEM_ESINGULAR, "local factorization: zero or wrong-signed pivot");
     }
-    // ---------------- deluxe blocks (S6): face problems factored in chunks of
-    // bounded memory; each chunk's root update matrices are rotated to the
-    // dual coordinates and kept, the partial factors are released
+    // ---------------- deluxe blocks (S6): one problem per subdomain (the
+    // Dirichlet pivots with all its deluxe entities' DOFs at the root),
+    // factored in chunks of bounded memory; the root update matrix holds
+    // every entity's block S_FF, each rotated to the dual coordinates and
+    // kept, the partial factors are released
     b->d_deluxe.alloc(std::max<int64_t>(deluxe_n, 1));
     b->d_deluxe_e.alloc(std::max<int64_t>(deluxe_e_n, 1));
     if (!faces.empty() || !edges.empty()) {
-      int64_t sdn = 0;
-      for (size_t t = 0; t < dl_probs.size(); ++t) {
-        const MacroDev& G = b->h_macros[H.probs[dl_probs[t]].macro];
-        sdn += (int64_t)G.ndual * G.ndual;
-      }
       DBuf<double> SD(std::max<int64_t>(sdn, 1));
       const double budget = 96.0 * (1 << 30);
-      size_t t0c = 0;
+      const double vbytes = b->prec == 0 ? 8.0 : 4.0;
+      size_t t0c = 0, k0c = 0;   // first problem and first task of the chunk
       while (t0c < dl_probs.size()) {
         double bytes = 0;
         size_t t1c = t0c;
         while (t1c < dl_probs.size()) {
           const Problem& HP = H.probs[dl_probs[t1c]];
           double pb = 0;
-          for (const Node& Nd : HP.nodes) pb += 8.0 * ((double)(Nd.np + Nd.nb) * Nd.np + (double)Nd.nb * Nd.nb);
-          const MacroDev& G = b->h_macros[HP.macro];
-          pb += 8.0 * G.n * G.n;
+          for (const Node& Nd : HP.nodes) pb += vbytes * ((double)(Nd.np + Nd.nb) * Nd.np + (double)Nd.nb * Nd.nb);
+          for (int g : HP.dl_macros) pb += 8.0 * b->h_macros[g].n * b->h_macros[g].n;
           if (t1c > t0c && bytes + pb > budget) break;
           bytes += pb;
           ++t1c;
         }
         std::vector<int> cp(dl_probs.begin() + t0c, dl_probs.begin() + t1c);
-        std::vector<int> cr(dl_roots.begin() + t0c, dl_roots.begin() + t1c);
-        std::vector<int64_t> cso(sd_off_v.begin() + t0c, sd_off_v.begin() + t1c), cwo;
+        size_t k1c = k0c;
         int64_t w = 0;
-        for (int q : cp) {
-          cwo.push_back(w);
-          const MacroDev& G = b->h_macros[H.probs[q].macro];
-          w += (int64_t)G.n * G.n;
+        std::vector<DeluxeTask> ct;
+        while (k1c < dtasks.size() && dtask_prob[k1c] < (int)t1c) {
+          DeluxeTask tk = dtasks[k1c++];
+          tk.work_off = w;
+          w += (int64_t)b->h_macros[tk.macro].n * b->h_macros[tk.macro].n;
+          ct.push_back(tk);
         }
         Batch Bc;
         build_batch(b, Bc, cp, false);
@@ -2248,20 +2265,16 @@ static void setup_core(bddc* b, const int32_t* part) {
         upload_levels(b, Bc);
         V = make_view(b);
         factor_batch(b, Bc, V, status);
-        DBuf<int> dp, dr;
-        DBuf<int64_t> dso, dwo;
-        upload_vec(dp, cp, st);
-        upload_vec(dr, cr, st);
-        upload_vec(dso, cso, st);
-        upload_vec(dwo, cwo, st);
+        DBuf<DeluxeTask> dct;
+        upload_vec(dct, ct, st);
         DBuf<double> work(std::max<int64_t>(w, 1));
         if (b->prec == 0)
-          launch(KDeluxeExtract<double>{V, dp.p, dr.p, Bc.U.p, work.p, dwo.p, SD.p, dso.p}, (int)cp.size(), 256, 0, st);
+          launch(KDeluxeExtract<double>{V, dct.p, Bc.U.p, work.p, SD.p}, (int)ct.size(), 256, 0, st);
         else
-          launch(KDeluxeExtract<float>{V, dp.p, dr.p, Bc.U32.p, work.p, dwo.p, SD.p, dso.p}, (int)cp.size(), 256, 0,
-                 st);
+          launch(KDeluxeExtract<float>{V, dct.p, Bc.U32.p, work.p, SD.p}, (int)ct.size(), 256, 0, st);
         VB_CUDA(cudaStreamSynchronize(st));
         t0c = t1c;
+        k0c = k1c;
       }
       {
         auto stv = status.download(st);

@@ -52,6 +52,7 @@ struct BddcView {
   const int* rel;
   const int* dtype;
   const int* dsrc;
+  const int* bgrp;           // per position: deluxe entity of a root-border DOF, -1 otherwise
   const int* elpos;
   const int* elptr;
   const int* pos_of_vdof;

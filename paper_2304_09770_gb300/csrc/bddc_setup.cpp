@@ -740,27 +740,25 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
       }
       // ---- problems
       std::vector<int> kinds = {PK_DIRICHLET, PK_NEUMANN};
+      // deluxe: every macro face, and every macro edge with scaling 2, that
+      // has dual coordinates; one problem per subdomain holds all of them
+      // (Dirichlet pivots, the entities' DOFs at the root, entity by entity)
       std::vector<int> dl_macro;
       if (o.scaling >= 1 && !all_primal)
         for (int gi : S.macros) {
-          // deluxe problems: every macro face, and every macro edge with
-          // scaling 2, that has dual coordinates
           const Macro& M = H.macros[gi];
           const bool dlx = M.kind == 2 || (M.kind == 1 && o.scaling == 2);
-          if (dlx && M.r < (int)M.dofs.size()) {
-            kinds.push_back(PK_DELUXE);
-            dl_macro.push_back(gi);
-          }
+          if (dlx && M.r < (int)M.dofs.size()) dl_macro.push_back(gi);
         }
-      int dl = 0;
+      if (!dl_macro.empty()) kinds.push_back(PK_DELUXE);
       for (int kind : kinds) {
         Problem P;
         P.sub = i;
         P.kind = kind;
-        P.macro = kind == PK_DELUXE ? dl_macro[dl++] : -1;
+        P.macro = -1;
+        if (kind == PK_DELUXE) P.dl_macros = dl_macro;
         // pivots per node
         std::vector<std::vector<int>> vel_at(nnodes), prs_at(nnodes);
-        std::vector<char> border_only(nv, 0);
         for (int v = 0; v < nv; ++v) {
           bool iface = H.mult[S.vdof[v]] >= 2;
           bool active;
@@ -768,8 +766,6 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
           else active = !iface;
           if (active) vel_at[vnode[v]].push_back(v);
         }
-        if (kind == PK_DELUXE)
-          for (int64_t g : H.macros[P.macro].dofs) border_only[lv(g)] = 1;
         for (int le = 0; le < ne; ++le)
           for (int a = 0; a < np; ++a) {
             int nd;
@@ -820,13 +816,17 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
           P.nodes.push_back(Nd);
         }
         P.npiv = pos;
-        if (kind == PK_DELUXE)
-          for (int64_t g : H.macros[P.macro].dofs) {
+        P.bgrp.assign(pos, -1);
+        for (size_t t = 0; t < P.dl_macros.size(); ++t) {
+          P.dl_b0.push_back(pos - P.npiv);
+          for (int64_t g : H.macros[P.dl_macros[t]].dofs) {
             int v = lv(g);
             P.pos_of_vdof[v] = pos++;
             P.dtype.push_back(DT_BORDER);
             P.dsrc.push_back(v);
+            P.bgrp.push_back((int)t);
           }
+        }
         P.n = pos;
         // element column -> position
         P.elpos_off.assign(ne + 1, 0);
@@ -946,8 +946,7 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
         }
         if (kind == PK_DELUXE) {
           Node& R = P.nodes.back();
-          VB_CHECK(R.nb == (int)H.macros[P.macro].dofs.size(), VEM_EINVAL,
-                   "symbolic: deluxe root border differs from the macro entity");
+          VB_CHECK(R.nb == P.n - P.npiv, VEM_EINVAL, "symbolic: deluxe root border differs from the entities' DOFs");
           R.flags = 1;
         } else {
           VB_CHECK(P.nodes.back().nb == 0, VEM_EINVAL, "symbolic: root with a border");

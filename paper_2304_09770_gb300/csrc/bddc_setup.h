@@ -37,6 +37,11 @@ struct Node {
 
 struct Problem {
   int sub = 0, kind = 0, macro = -1;
+  // deluxe problem of a subdomain: its deluxe entities (macro ids), the
+  // first root-border index of each (their DOFs follow one another at the
+  // root, entity by entity), and per position the entity's index in
+  // dl_macros for those border positions (-1 for the pivots)
+  std::vector<int> dl_macros, dl_b0, bgrp;
   int n = 0, npiv = 0;           // positions (pivots first, then border-only)
   int mult0 = 0, nmult = 0;      // multiplier positions [mult0, mult0 + nmult)
   std::vector<int> dtype;        // per position

@@ -34,8 +34,28 @@ VB_HD inline int front_index(const NodeDev& N, const int* bord, int x) {
 // column) as three TF32 parts, runs the split product into TMEM and
 // subtracts it from the front
 // (pivot columns in the panel, the rest in the update matrix).
+// Front index -> deluxe entity group of a root-border DOF (-1: pivot or
+// other border).  Only the diagonal entity blocks of the deluxe root update
+// are used, and border DOFs are never pivots, so update entries between two
+// different entities are never needed: trailing tiles lying entirely in
+// such a block are skipped.  Border positions of a deluxe problem are
+// grouped by entity in increasing position order.
+struct FrontGroups {
+  const int* bord;   // the front's border positions
+  const int* pgrp;   // per problem position, or null (no deluxe problem)
+  int np;
+  VB_HD int of(int fi) const { return fi < np ? -1 : pgrp[bord[fi - np]]; }
+  // lower tile rows [i0, ..), columns [k0, klast]: every pair in two different entities
+  VB_HD bool cross(int i0, int k0, int klast) const {
+    if (!pgrp || k0 < np) return false;
+    const int gk = of(k0);
+    return gk >= 0 && of(klast) < of(i0);
+  }
+};
+
 __device__ inline bool tc_trailing_update(const KExec& ex, TcCtx& c, float* pan, float* upd, int np, int nb, int ld,
-                                          int nf, int jb, int nbk, int c0, int m, const float* sd) {
+                                          int nf, int jb, int nbk, int c0, int m, const float* sd,
+                                          const FrontGroups& fg) {
   float* A = c.tiles;                                // TF32 parts of the tile rows
   float* B = c.tiles + TC_PARTS * TC_TILE_FLOATS;    // TF32 parts of the tile columns
   const int nt = (m + TC_M - 1) / TC_M;
@@ -51,6 +71,7 @@ __device__ inline bool tc_trailing_update(const KExec& ex, TcCtx& c, float* pan,
     }
     for (int ti = tk; ti < nt; ++ti) {
       const int i0 = c0 + ti * TC_M;
+      if (fg.cross(i0, k0, min(k0 + TC_N, nf) - 1)) continue;
       for (int q = ex.tid; q < TC_M * TC_K; q += ex.nt) {
         const int col = q / TC_M, mm = q % TC_M;
         const float x = (col < nbk && i0 + mm < nf) ? pan[(int64_t)(jb + col) * ld + i0 + mm] : 0.0f;
@@ -98,7 +119,7 @@ VB_HD inline void group_sync(const KExec& ex, int ngrp, int grp) {
 // positive; pressure and multiplier negative); a violation sets status 3.
 template <class T>
 VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, int ld, const int* piv_type,
-                             int* status, TcCtx* tc = nullptr) {
+                             int* status, TcCtx* tc = nullptr, FrontGroups fg = FrontGroups{nullptr, nullptr, 0}) {
     const int nf = np + nb;
     // blocked right-looking partial LDL^T: panels of NBK columns, then a
     // rank-NBK update of the trailing front in TT x TT tiles staged in
@@ -142,7 +163,7 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, in
       if constexpr (std::is_same<T, float>::value) {
         if (tc && m > TT) {
           // tensor-core tiles (split TF32, 128 x 128, accumulators in TMEM)
-          if (!tc_trailing_update(ex, *tc, pan, upd, np, nb, ld, nf, jb, nbk, c0, m, sd)) return;
+          if (!tc_trailing_update(ex, *tc, pan, upd, np, nb, ld, nf, jb, nbk, c0, m, sd, fg)) return;
           continue;
         }
       }
@@ -152,7 +173,7 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, in
       const int rounds = (ntot + ngrp - 1) / ngrp;
       for (int rr = 0; rr < rounds; ++rr) {
           const int tt = rr * ngrp + grp;
-          const bool act = tt < ntot;
+          bool act = tt < ntot;
           int tk = 0, ti = 0;
           if (act) {
             int rem = tt;
@@ -160,6 +181,7 @@ VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, in
             ti = tk + rem;
           }
           const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
+          if (act && fg.cross(i0, k0, (k0 + TT < nf ? k0 + TT : nf) - 1)) act = false;
           if (act)
             for (int q = gt; q < TT * NBK; q += gnt) {
               const int r = q % TT, c = q / TT;
@@ -330,7 +352,8 @@ struct KFactor {
       }
       ex.sync();
     }
-    front_ldlt<T>(ex, pan, upd, np, nb, ld, V.dtype + P.pos_off + N.p0, status, tc);
+    const FrontGroups fg{bord, P.kind == PK_DELUXE ? V.bgrp + P.pos_off : nullptr, np};
+    front_ldlt<T>(ex, pan, upd, np, nb, ld, V.dtype + P.pos_off + N.p0, status, tc, fg);
   }
 };
 
