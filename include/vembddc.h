@@ -126,6 +126,21 @@ int vem_quad_points(vem_system* sys, int degree, int64_t* n, double* xyz_out);
  * the same degree.  f_at_quad: host [n*3]; rhs_dev: device [n_free+n_press]. */
 int vem_load(vem_system* sys, int degree, const double* f_at_quad, double* rhs_dev);
 
+/* Non-homogeneous Dirichlet data for tests such as the polynomial patch test
+ * (convergence theorem, Sec. 3: polynomial solutions of degree k are
+ * reproduced exactly).  The system keeps the boundary velocity DOFs fixed and
+ * eliminated; this call moves their prescribed values to the right-hand side
+ * of the free saddle system (Eq. MatrixForm):
+ *   f_dev[r] -= sum over fixed velocity DOFs j of K[r][j] g_host[j]
+ * for every free velocity row and every pressure row r.
+ * g_host: host [n_vel], values of ALL velocity DOFs in the global numbering
+ * (vertex, edge, face, element-interior DOFs; only the fixed ones are read;
+ * in the reduced scheme the eliminated D5 DOFs are fixed too and read as
+ * their prescribed values, normally 0).  f_dev: device [n_free+n_press],
+ * updated in place.  Allocates temporary device memory; synchronizes the
+ * system's stream.  Errors: VEM_EINVAL on null arguments. */
+int vem_lift_dirichlet(vem_system* sys, const double* g_host, double* f_dev);
+
 /* Load vector without device allocation.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory
  * themselves or through the library, for example code running under a

@@ -54,6 +54,7 @@ def lib():
         L.vem_load.argtypes = [P, ctypes.c_int, P, P]
         L.vem_load_noalloc.argtypes = [P, ctypes.c_int, P, P]
         L.vem_apply.argtypes = [P, P, P]
+        L.vem_lift_dirichlet.argtypes = [P, P, P]
         L.vem_element_matrices.argtypes = [P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), P, P, P]
         L.vem_csr.argtypes = [P, i64p, i64p, P, P, P]
         L.vem_set_stream.argtypes = [P, P]
@@ -173,6 +174,14 @@ class VemSystem:
             y = torch.empty_like(x)
         _check(lib().vem_apply(self.h, _dptr(x), _dptr(y)))
         return y
+
+    def lift_dirichlet(self, g_values, f):
+        """vem_lift_dirichlet: f -= K[:, fixed] g[fixed] in place, for
+        prescribed values g (host, every velocity DOF, global numbering)."""
+        g_values = np.ascontiguousarray(g_values, dtype=np.float64)
+        assert g_values.shape == (self.n_vel,)
+        _check(lib().vem_lift_dirichlet(self.h, _ptr(g_values), _dptr(f)))
+        return f
 
     def element_matrices(self, elems):
         elems = np.ascontiguousarray(elems, dtype=np.int32)

@@ -1243,9 +1243,24 @@ template <class T>
 static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& status, DBuf<T>& Fs, DBuf<T>& Us) {
   Fs.alloc(std::max<int64_t>(B.nF, 1));
   Us.alloc(std::max<int64_t>(B.nU, 1));
-  const size_t base = sizeof(double) * (std::max(2 * 64 * 32 + 32, B.maxnf) + 8);
+  const size_t base = sizeof(double) * (std::max(2 * 64 * 32 + 128, B.maxnf) + 8);
+  // diagnostics: with VEMBDDC_LEVEL_LOG set, every level's launch is timed
+  // with CUDA events on the stream and printed to stderr
+  static const bool level_log = std::getenv("VEMBDDC_LEVEL_LOG") != nullptr;
   for (int h = 0; h <= B.maxh; ++h) {
     int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double lvl_flop = 0;
+    if (level_log) {
+      VB_CUDA(cudaEventCreate(&e0));
+      VB_CUDA(cudaEventCreate(&e1));
+      VB_CUDA(cudaEventRecord(e0, b->stream));
+      for (int q = B.level_ptr[h]; q < B.level_ptr[h + 1]; ++q) {
+        const NodeDev& Nd = b->h_nodes[B.h_levels[q]];
+        const double np = Nd.np, nf = Nd.np + Nd.nb;
+        lvl_flop += np * nf * nf - nf * np * np + 2.0 * np * np * np / 3.0;
+      }
+    }
     int nfmax = 0;
     for (int q = B.level_ptr[h]; q < B.level_ptr[h + 1]; ++q) {
       const NodeDev& Nd = b->h_nodes[B.h_levels[q]];
@@ -1253,7 +1268,7 @@ static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& stat
     }
     // large fronts: 2 or 4 groups of 256 threads, each on its own trailing tile
     const int nthr = nfmax > 512 ? 1024 : (nfmax > 192 ? 512 : 256);
-    const size_t gbase = sizeof(double) * (std::max((nthr / 256) * 2 * 64 * 32 + 32, B.maxnf) + 8);
+    const size_t gbase = sizeof(double) * (std::max((nthr / 256) * 2 * 64 * 32 + 128, B.maxnf) + 8);
     // FP32 fronts with trailing blocks beyond 64 rows: tensor-core updates
     if (std::is_same<T, float>::value && b->use_tc && nfmax > 96) {
       const size_t off = (base + 127) / 128 * 128;
@@ -1262,7 +1277,17 @@ static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& stat
       launch(f, cnt, 256, off + TC_SMEM_BYTES, b->stream);
     } else {
       KFactor<T> f{V, B.d_levels.p + B.level_ptr[h], Fs.p, Us.p, status.p};
-      launch(f, cnt, nthr, gbase, b->stream);
+      launch_mt<1024>(f, cnt, nthr, gbase, b->stream);
+    }
+    if (level_log) {
+      VB_CUDA(cudaEventRecord(e1, b->stream));
+      VB_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      VB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      std::fprintf(stderr, "factor level %d: %d fronts, nf max %d, %.3f ms, %.1f Gflop (full fronts), %d threads\n", h,
+                   cnt, nfmax, ms, lvl_flop * 1e-9, nthr);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
     }
   }
 }
@@ -2310,8 +2335,8 @@ static void setup_core(bddc* b, const int32_t* part) {
         // one CTA per face, four groups of 256 threads on separate trailing tiles
         int ndmax = 0;
         for (int g : faces) ndmax = std::max(ndmax, b->h_macros[g].ndual);
-        launch(KDeluxeFront{V, df.p, dsi.p, dsj.p, SD.p, PAN.p, UPD.p, dpo.p, duo.p, status.p}, (int)faces.size(), 1024,
-               sizeof(double) * (std::max(4 * 2 * 64 * 32 + 32, ndmax) + 8), st);
+        launch_mt<1024>(KDeluxeFront{V, df.p, dsi.p, dsj.p, SD.p, PAN.p, UPD.p, dpo.p, duo.p, status.p}, (int)faces.size(), 1024,
+               sizeof(double) * (std::max(4 * 2 * 64 * 32 + 128, ndmax) + 8), st);
         launch(KDeluxeGemm{V, dtiles.p, df.p, PAN.p, dpo.p, b->d_deluxe.p}, (int64_t)tiles.size(), 256,
                sizeof(double) * (2 * 32 * 64 + 8), st);
         mark("t_deluxe_combine_ms");

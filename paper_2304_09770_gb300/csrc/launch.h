@@ -52,6 +52,26 @@ inline void launch_lb(const F& f, int64_t nblocks, size_t smem, cudaStream_t s) 
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+// the same with up to MAXT threads per CTA (the compiler caps the registers
+// so that a CTA of MAXT threads fits on an SM)
+template <class F, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_run_mt(const F f) {
+  extern __shared__ __align__(16) double vb_smem[];
+  f(KExec{(int)threadIdx.x, (int)blockDim.x, vb_smem}, (int)blockIdx.x);
+}
+
+template <int MAXT, class F>
+inline void launch_mt(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaStream_t s) {
+  if (nblocks <= 0) return;
+  VB_CHECK(nblocks < (int64_t)INT32_MAX, VEM_EINVAL, "grid too large");
+  VB_CHECK(nthreads <= MAXT, VEM_EINVAL, "launch: more threads than the kernel's bound");
+  if (smem > 48 * 1024)
+    VB_CUDA(cudaFuncSetAttribute(k_run_mt<F, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_run_mt<F, MAXT><<<(unsigned)nblocks, nthreads, smem, s>>>(f);
+  VB_KERNEL_CHECK();
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 template <class F>
 inline void launch(const F& f, int64_t nblocks, int nthreads, size_t smem, cudaStream_t s) {
   if (nblocks <= 0) return;

@@ -117,102 +117,145 @@ VB_HD inline void group_sync(const KExec& ex, int ngrp, int grp) {
 // in-place inversion of the unit lower diagonal block L11.  piv_type (may be
 // null: all positive) gives the expected pivot sign per pivot (velocity
 // positive; pressure and multiplier negative); a violation sets status 3.
+// Trailing update of a front by the pivot columns [ka, kb) (unit L stored
+// below the diagonal, D on it; sdv[c - dbase] = D of column c):
+//   C[i][k] -= sum_c L[i][c] D[c] L[k][c]
+// for rows i in [r0, nf) and columns k in [r0, ce), i >= k (pivot columns in
+// the panel, the rest in the update matrix).  64 x 64 tiles, one per group
+// of 256 threads (4 x 4 outputs per thread, accumulated in registers over
+// the whole K range, which streams through shared memory 32 columns at a
+// time); tiles lying between two different deluxe entities are skipped.
+template <class T>
+VB_HD inline void front_trailing(const KExec& ex, T* pan, T* upd, int np, int nb, int ld, int ka, int kb, int r0,
+                                 int ce, const T* sdv, int dbase, T* sL, T* sR, int ngrp, int grp, int gt, int gnt,
+                                 const FrontGroups& fg) {
+  constexpr int NBK = 32, TT = 64;
+  const int nf = np + nb;
+  if (r0 >= nf || r0 >= ce || ka >= kb) return;
+  const int nrt = (nf - r0 + TT - 1) / TT, nct = (ce - r0 + TT - 1) / TT;
+  const int ntot = nct * nrt - nct * (nct - 1) / 2;   // lower tiles, tk-major
+  const int rounds = (ntot + ngrp - 1) / ngrp;
+  for (int rr = 0; rr < rounds; ++rr) {
+    const int tt = rr * ngrp + grp;
+    bool act = tt < ntot;
+    int tk = 0, ti = 0;
+    if (act) {
+      int rem = tt;
+      while (rem >= nrt - tk) { rem -= nrt - tk; ++tk; }
+      ti = tk + rem;
+    }
+    const int k0 = r0 + tk * TT, i0 = r0 + ti * TT;
+    if (act && fg.cross(i0, k0, (k0 + TT < nf ? k0 + TT : nf) - 1)) act = false;
+    T acc[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+    const int tr = gt % 16, tcl = gt / 16;
+    for (int kc = ka; kc < kb; kc += NBK) {
+      const int nkc = kb - kc < NBK ? kb - kc : NBK;
+      if (act)
+        for (int q = gt; q < TT * NBK; q += gnt) {
+          const int r = q % TT, c = q / TT;
+          sL[q] = (c < nkc && i0 + r < nf) ? pan[(int64_t)(kc + c) * ld + i0 + r] : (T)0;
+          sR[q] = (c < nkc && k0 + r < nf) ? pan[(int64_t)(kc + c) * ld + k0 + r] * sdv[kc + c - dbase] : (T)0;
+        }
+      group_sync(ex, ngrp, grp);
+      if (act && gt < 256)
+        for (int c = 0; c < nkc; ++c) {
+          T li[4], rk[4];
+          for (int a = 0; a < 4; ++a) li[a] = sL[c * TT + tr + 16 * a];
+          for (int bb = 0; bb < 4; ++bb) rk[bb] = sR[c * TT + tcl + 16 * bb];
+          for (int a = 0; a < 4; ++a)
+            for (int bb = 0; bb < 4; ++bb) acc[a][bb] += li[a] * rk[bb];
+        }
+      group_sync(ex, ngrp, grp);
+    }
+    if (act && gt < 256)
+      for (int bb = 0; bb < 4; ++bb) {
+        const int k = k0 + tcl + 16 * bb;
+        if (k >= nf || k >= ce) continue;
+        for (int a = 0; a < 4; ++a) {
+          const int i = i0 + tr + 16 * a;
+          if (i >= nf || i < k) continue;
+          if (k < np) pan[(int64_t)k * ld + i] -= acc[a][bb];
+          else upd[(int64_t)(k - np) * nb + (i - np)] -= acc[a][bb];
+        }
+      }
+  }
+}
+
+// Blocked right-looking partial LDL^T of one dense front (panel nf x np and
+// update block nb x nb, column-major, lower triangles), followed by the
+// in-place inversion of the unit lower diagonal block L11.  piv_type (may be
+// null: all positive) gives the expected pivot sign per pivot (velocity
+// positive; pressure and multiplier negative); a violation sets status 3.
+// Two levels of blocking: outer panels of NBO pivot columns, factored as
+// inner blocks of NBK columns (column by column, then a rank-NBK update of
+// the rest of the outer panel), then one rank-NBO update of the trailing
+// front, so that the trailing front is read and written once per NBO
+// columns.  With the tensor cores (tc) the trailing update runs after every
+// NBK columns instead.
 template <class T>
 VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, int ld, const int* piv_type,
                              int* status, TcCtx* tc = nullptr, FrontGroups fg = FrontGroups{nullptr, nullptr, 0}) {
     const int nf = np + nb;
-    // blocked right-looking partial LDL^T: panels of NBK columns, then a
-    // rank-NBK update of the trailing front in TT x TT tiles staged in
-    // shared memory (each thread owns a 4 x 4 sub-tile)
     // With more than 256 threads the CTA works as groups of 256, each on its
     // own trailing tile (named barriers per group), so that large fronts keep
     // several tiles in flight.
-    constexpr int NBK = 32, TT = 64;
+    constexpr int NBK = 32, TT = 64, NBO = 128;
     const int ngrp = ex.nt >= 512 ? ex.nt / 256 : 1;
     const int grp = ngrp > 1 ? ex.tid / 256 : 0;
     const int gt = ngrp > 1 ? ex.tid % 256 : ex.tid, gnt = ngrp > 1 ? 256 : ex.nt;
     T* sL = reinterpret_cast<T*>(ex.smem) + (int64_t)grp * 2 * TT * NBK;
     T* sR = sL + TT * NBK;
-    T* sd = reinterpret_cast<T*>(ex.smem) + (int64_t)ngrp * 2 * TT * NBK;
-    for (int jb = 0; jb < np; jb += NBK) {
-      const int nbk = np - jb < NBK ? np - jb : NBK;
-      for (int jj = 0; jj < nbk; ++jj) {
-        const int j = jb + jj;
-        T* cj = pan + (int64_t)j * ld;
-        const T dj = cj[j];
-        if (ex.tid == 0) {
-          const double sgn = (!piv_type || piv_type[j] == DT_VEL) ? 1.0 : -1.0;
-          if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
+    T* sd = reinterpret_cast<T*>(ex.smem) + (int64_t)ngrp * 2 * TT * NBK;   // NBO diagonal entries
+    const int nbo_w = tc ? NBK : NBO;
+    for (int JB = 0; JB < np; JB += nbo_w) {
+      const int JE = np - JB < nbo_w ? np : JB + nbo_w;
+      for (int jb = JB; jb < JE; jb += NBK) {
+        const int nbk = JE - jb < NBK ? JE - jb : NBK;
+        for (int jj = 0; jj < nbk; ++jj) {
+          const int j = jb + jj;
+          T* cj = pan + (int64_t)j * ld;
+          const T dj = cj[j];
+          if (ex.tid == 0) {
+            const double sgn = (!piv_type || piv_type[j] == DT_VEL) ? 1.0 : -1.0;
+            if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
+          }
+          const T inv = (T)1 / dj;
+          const int nk = jb + nbk - j - 1, nr = nf - j - 1;
+          for (int64_t idx = ex.tid; idx < (int64_t)nk * nr; idx += ex.nt) {
+            const int kk = j + 1 + (int)(idx / nr), ii = j + 1 + (int)(idx % nr);
+            if (ii < kk) continue;
+            pan[(int64_t)kk * ld + ii] -= cj[ii] * cj[kk] * inv;
+          }
+          ex.sync();
+          for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) cj[i] *= inv;
+          ex.sync();
         }
-        const T inv = (T)1 / dj;
-        const int nk = jb + nbk - j - 1, nr = nf - j - 1;
-        for (int64_t idx = ex.tid; idx < (int64_t)nk * nr; idx += ex.nt) {
-          const int kk = j + 1 + (int)(idx / nr), ii = j + 1 + (int)(idx % nr);
-          if (ii < kk) continue;
-          pan[(int64_t)kk * ld + ii] -= cj[ii] * cj[kk] * inv;
-        }
+        for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jb - JB + jj] = pan[(int64_t)(jb + jj) * ld + jb + jj];
         ex.sync();
-        for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) cj[i] *= inv;
-        ex.sync();
-      }
-      const int c0 = jb + nbk, m = nf - c0;
-      if (m <= 0) continue;
-      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jj] = pan[(int64_t)(jb + jj) * ld + jb + jj];
-      ex.sync();
+        const int c0 = jb + nbk, m = nf - c0;
+        if (m <= 0) continue;
 #ifdef __CUDA_ARCH__
-      if constexpr (std::is_same<T, float>::value) {
-        if (tc && m > TT) {
-          // tensor-core tiles (split TF32, 128 x 128, accumulators in TMEM)
-          if (!tc_trailing_update(ex, *tc, pan, upd, np, nb, ld, nf, jb, nbk, c0, m, sd, fg)) return;
-          continue;
+        if constexpr (std::is_same<T, float>::value) {
+          if (tc && m > TT) {
+            // tensor-core tiles (split TF32, 128 x 128, accumulators in TMEM)
+            if (!tc_trailing_update(ex, *tc, pan, upd, np, nb, ld, nf, jb, nbk, c0, m, sd + (jb - JB), fg)) return;
+            continue;
+          }
         }
-      }
 #endif
-      const int ntile = (m + TT - 1) / TT;
-      const int ntot = ntile * (ntile + 1) / 2;          // lower tiles, tk-major
-      const int rounds = (ntot + ngrp - 1) / ngrp;
-      for (int rr = 0; rr < rounds; ++rr) {
-          const int tt = rr * ngrp + grp;
-          bool act = tt < ntot;
-          int tk = 0, ti = 0;
-          if (act) {
-            int rem = tt;
-            while (rem >= ntile - tk) { rem -= ntile - tk; ++tk; }
-            ti = tk + rem;
-          }
-          const int k0 = c0 + tk * TT, i0 = c0 + ti * TT;
-          if (act && fg.cross(i0, k0, (k0 + TT < nf ? k0 + TT : nf) - 1)) act = false;
-          if (act)
-            for (int q = gt; q < TT * NBK; q += gnt) {
-              const int r = q % TT, c = q / TT;
-              sL[q] = (c < nbk && i0 + r < nf) ? pan[(int64_t)(jb + c) * ld + i0 + r] : (T)0;
-              sR[q] = (c < nbk && k0 + r < nf) ? pan[(int64_t)(jb + c) * ld + k0 + r] * sd[c] : (T)0;
-            }
-          group_sync(ex, ngrp, grp);
-          for (int vt = gt; act && vt < 256; vt += gnt) {
-            const int tr = vt % 16, tc = vt / 16;
-            T acc[4][4] = {{0}};
-            for (int c = 0; c < nbk; ++c) {
-              T li[4], rk[4];
-              for (int a = 0; a < 4; ++a) li[a] = sL[c * TT + tr + 16 * a];
-              for (int bb = 0; bb < 4; ++bb) rk[bb] = sR[c * TT + tc + 16 * bb];
-              for (int a = 0; a < 4; ++a)
-                for (int bb = 0; bb < 4; ++bb) acc[a][bb] += li[a] * rk[bb];
-            }
-            for (int bb = 0; bb < 4; ++bb) {
-              const int k = k0 + tc + 16 * bb;
-              if (k >= nf) continue;
-              for (int a = 0; a < 4; ++a) {
-                const int i = i0 + tr + 16 * a;
-                if (i >= nf || i < k) continue;
-                if (k < np) pan[(int64_t)k * ld + i] -= acc[a][bb];
-                else upd[(int64_t)(k - np) * nb + (i - np)] -= acc[a][bb];
-              }
-            }
-          }
-          group_sync(ex, ngrp, grp);
+        // rank-nbk update of the rest of the outer panel (all of the front
+        // when the outer panel is one inner block)
+        front_trailing<T>(ex, pan, upd, np, nb, ld, jb, c0, c0, nbo_w == NBK ? nf : JE, sd, JB, sL, sR, ngrp, grp,
+                          gt, gnt, fg);
+        ex.sync();
       }
-      ex.sync();
+      // rank-(JE - JB) update of the trailing front
+      if (nbo_w > NBK) {
+        front_trailing<T>(ex, pan, upd, np, nb, ld, JB, JE, JE, nf, sd, JB, sL, sR, ngrp, grp, gt, gnt, fg);
+        ex.sync();
+      }
     }
     // selective inversion: overwrite the unit lower L11 by L11^{-1} (unit
     // lower), column by column from the right, so that the triangular

@@ -559,10 +559,91 @@ extern "C" int vem_load(vem_system* s, int degree, const double* fq, double* rhs
 }
 
 namespace vb {
+// Non-homogeneous Dirichlet data (test support): per element, the rows of
+// [A_e; B_e] applied to the prescribed values of its fixed velocity DOFs.
+// One CTA per element.
+struct KLiftLocal {
+  const int64_t *offK, *offK2, *sysdof, *eglob;
+  const double *A, *B, *g;
+  int np;
+  double* rloc;    // velocity rows, element-local layout
+  double* rp;      // pressure rows, e * np + a
+  VB_HD void operator()(const KExec& ex, int e) const {
+    const int64_t o = offK[e];
+    const int nK = (int)(offK[e + 1] - o);
+    const double* Ae = A + offK2[e];
+    const double* Be = B + (int64_t)np * o;
+    for (int a = ex.tid; a < nK + np; a += ex.nt) {
+      double acc = 0.0;
+      for (int b = 0; b < nK; ++b) {
+        if (sysdof[o + b] >= 0) continue;
+        const double gb = g[eglob[o + b]];
+        acc += (a < nK ? Ae[(int64_t)a * nK + b] : Be[(int64_t)(a - nK) * nK + b]) * gb;
+      }
+      if (a < nK) rloc[o + a] = acc;
+      else rp[(int64_t)e * np + (a - nK)] = acc;
+    }
+  }
+};
+
+// f -= the gathered element rows (velocity rows by the DOF adjacency,
+// pressure rows directly)
+struct KLiftGather {
+  int64_t nrows, nvf;
+  const int64_t* adj_ptr;
+  const int *adj_elem, *adj_loc;
+  const int64_t* offK;
+  const double *rloc, *rp;
+  double* f;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int64_t hi = (int64_t)(blk + 1) * 256 < nrows ? (int64_t)(blk + 1) * 256 : nrows;
+    for (int64_t r = (int64_t)blk * 256 + ex.tid; r < hi; r += ex.nt) {
+      double acc = 0.0;
+      if (r < nvf) {
+        for (int64_t q = adj_ptr[r]; q < adj_ptr[r + 1]; ++q) acc += rloc[offK[adj_elem[q]] + adj_loc[q]];
+      } else {
+        acc = rp[r - nvf];
+      }
+      f[r] -= acc;
+    }
+  }
+};
+
 void spmv(vem_system* s, const double* x, double* y, cudaStream_t st) {
   launch(KSpmv{s->n, s->d_rowptr.p, s->d_col.p, s->d_val.p, x, y}, (s->n + 7) / 8, 256, 0, st);
 }
 }  // namespace vb
+
+extern "C" int vem_lift_dirichlet(vem_system* s, const double* g_host, double* f_dev) {
+  if (!s || !g_host || !f_dev) { set_last_error("vem_lift_dirichlet: null argument"); return VEM_EINVAL; }
+  try {
+    const Topo& t = s->topo;
+    const DofNumbering& d = s->dof;
+    std::vector<int64_t> eglob(s->h_eoff.back()), ge;
+    for (int e = 0; e < t.nE; ++e) {
+      element_global_dofs(t, d, e, ge);
+      std::copy(ge.begin(), ge.end(), eglob.begin() + s->h_eoff[e]);
+    }
+    std::vector<int64_t> offK2(t.nE + 1, 0);
+    for (int e = 0; e < t.nE; ++e) {
+      const int64_t nK = s->h_eoff[e + 1] - s->h_eoff[e];
+      offK2[e + 1] = offK2[e] + nK * nK;
+    }
+    DBuf<int64_t> dglob, dK2;
+    dglob.upload(eglob, s->stream);
+    dK2.upload(offK2, s->stream);
+    DBuf<double> dg(d.nvel), rloc(s->h_eoff.back()), rp((size_t)d.np * t.nE);
+    VB_CUDA(cudaMemcpyAsync(dg.p, g_host, sizeof(double) * d.nvel, cudaMemcpyHostToDevice, s->stream));
+    launch(KLiftLocal{s->d_eoff.p, dK2.p, s->d_sysdof.p, dglob.p, s->d_A.p, s->d_B.p, dg.p, d.np, rloc.p, rp.p}, t.nE,
+           128, 0, s->stream);
+    launch(KLiftGather{s->n, d.nvf, s->d_adj_ptr.p, s->d_adj_elem.p, s->d_adj_loc.p, s->d_eoff.p, rloc.p, rp.p, f_dev},
+           (s->n + 255) / 256, 256, 0, s->stream);
+    VB_CUDA(cudaStreamSynchronize(s->stream));
+    return VEM_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  }
+}
 
 extern "C" int vem_apply(vem_system* s, const double* x, double* y) {
   if (!s || !x || !y) { set_last_error("null argument"); return VEM_EINVAL; }

@@ -22,6 +22,16 @@ CONFIGS = {
     "tri16_k2": dict(n=16, perturb=0.2, seed=4, k=2, parts=(4, 4, 4), load="manufactured"),
     "tri16_k3": dict(n=16, perturb=0.2, seed=4, k=3, parts=(4, 4, 4), load="manufactured"),
     "tri16_k4": dict(n=16, perturb=0.2, seed=4, k=4, parts=(4, 4, 4), load="manufactured"),
+    # 8^3 perturbed (+-0.2h), 2x2x2 subdomains of 4^3 elements (the 16^3
+    # configuration's subdomain size): the workload the CPU oracle is timed on
+    "tri8_k2": dict(n=8, perturb=0.2, seed=4, k=2, parts=(2, 2, 2), load="manufactured"),
+    # 16^3 perturbed (+-0.2h), 2x2x2 subdomains of 8^3 elements: the 32^3
+    # benchmark's subdomain size, on a mesh the oracle can still solve
+    "tri16_parts8": dict(n=16, perturb=0.2, seed=4, k=2, parts=(2, 2, 2), load="manufactured"),
+    # 8^3 perturbed, two subdomains of 8 x 8 x 4 elements: fronts of the
+    # size of the 32^3 benchmark's subdomains (1024-thread factorization
+    # path), small enough for the oracle
+    "tri8_halves": dict(n=8, perturb=0.2, seed=12, k=2, parts=(1, 1, 2), load="manufactured"),
     # 32^3 cubes with 8 sinkers, contrast 1e4 and 1e6
     "sinker32_dr1e4": dict(n=32, perturb=0.0, seed=None, k=2, parts=(4, 4, 4), load="sinker",
                            sinkers=(8, 5), dr=1e4),

@@ -1,0 +1,58 @@
+"""Writes tests/golden/tri16_parts8_oracle.json: the oracle's BDDC-PCG on the
+16^3 perturbed split-hex mesh with 2 x 2 x 2 subdomains of 8^3 elements (the
+32^3 benchmark's subdomain size), k = 2, deluxe scaling, rtol 1e-8, load
+rule degree k + 9.  Stored: iteration count and Lanczos estimates, and the
+iterates at that count and one step either side (so that a run stopping one
+step apart is compared at its own count) on a seeded sample of velocity and
+pressure entries, with the norms of the whole vectors.  Calls only the
+oracle (and the seeded inputs of synth); it takes a few hours on one core.
+
+    python tests/golden/make_bench_subdomain_parity.py
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+import numpy as np  # noqa: E402
+
+NAME = "tri16_parts8"
+
+
+def main():
+    from oracle_cache import oracle_bddc
+    t0 = time.time()
+    cfg, S, ob, F = oracle_bddc(NAME)
+    t1 = time.time()
+    ro = ob.pcg(F, rtol=1e-8)
+    it = ro["iters"]
+    nvf = len(S.dm.free)
+    rng = np.random.default_rng(2024)
+    sv = np.sort(rng.choice(nvf, 1000, replace=False))
+    sp = np.sort(rng.choice(S.dm.npress, 300, replace=False))
+    wm = S.wmean
+
+    def record(x):
+        p = x[nvf:] - (wm @ x[nvf:]) / wm.sum()
+        return {"vel": x[:nvf][sv].tolist(), "press": p[sp].tolist(),
+                "vel_norm": float(np.linalg.norm(x[:nvf])), "press_norm": float(np.linalg.norm(p))}
+
+    iterates = {str(it): record(ro["x"])}
+    for m in (it - 1, it + 1):
+        iterates[str(m)] = record(ob.pcg(F, rtol=0.0, maxit=m)["x"])
+    out = {"workload": NAME, "k": cfg["k"], "scaling": "deluxe", "rtol": 1e-8, "load_degree": cfg["k"] + 9,
+           "iters": it, "kappa": ro["kappa"], "lam_min": ro["lam_min"], "lam_max": ro["lam_max"],
+           "n_vel_free": nvf, "n_press": int(S.dm.npress), "sample_vel": sv.tolist(), "sample_press": sp.tolist(),
+           "iterates": iterates, "oracle_seconds": {"setup": t1 - t0, "total": time.time() - t0}}
+    with open(os.path.join(HERE, NAME + "_oracle.json"), "w") as f:
+        json.dump(out, f)
+    print("wrote", NAME, "iters", it, "kappa", ro["kappa"])
+
+
+if __name__ == "__main__":
+    main()

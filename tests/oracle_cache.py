@@ -113,19 +113,21 @@ def _oracle_iterate_sensitivity(ob, F, iters, eps=1e-15, seeds=(1, 2)):
     return out
 
 
-def check_pcg_parity(S, ob, F, res, x, tol=1e-10, label=""):
+def check_pcg_parity(S, ob, F, res, x, tol=1e-10, label="", deep=None):
     """FP64 parity of a GPU BDDC-PCG run with the oracle's.
 
-    Iteration counts within +-1; then, at equal iteration counts (the
-    oracle re-run with maxit = the GPU's count when the two stop one step
-    apart): the velocity and the whole solution [u; p - mean(p)] within
-    ``tol`` = 1e-10 relative, and the Lanczos lambda_max within 1e-6.
-
-    Where CG itself amplifies rounding beyond that bar (viscosity
-    contrast, kappa ~ 100 over 60 iterations), no FP64 implementation can
-    meet it: the bar is then the oracle's own reproducibility, the largest
-    change of its iterate when every preconditioner output is perturbed by
-    a seeded relative 1e-15 (two seeds).  Returns the measured differences."""
+    (1) At rtol 1e-8: iteration counts within +-1, the Lanczos lambda_max
+    within 1e-6 relative, and, at equal iteration counts (the oracle re-run
+    with maxit = the GPU's count when the two stop one step apart), the
+    velocity and the whole zero-mean solution [u; p - mean(p)] within tol.
+    Where the oracle cannot reproduce its own iterate to better than tol/10
+    under a seeded relative 1e-15 perturbation of every preconditioner output
+    (CG amplifies rounding: viscosity contrast, thin CVT faces), that
+    comparison is reported, not asserted, and (2) carries the bar.
+    (2) deep: a callable running the GPU solve to a given rtol; both sides
+    are run to rtol 1e-11, where the discrete solution is determined to
+    better than tol, and must agree within tol (velocity and whole
+    solution).  Returns the measured differences."""
     import numpy as np
     ro = ob.pcg(F, rtol=1e-8)
     assert abs(res["iters"] - ro["iters"]) <= 1, (res["iters"], ro["iters"])
@@ -135,21 +137,29 @@ def check_pcg_parity(S, ob, F, res, x, tol=1e-10, label=""):
     nvf = len(S.dm.free)
     pz = lambda v: np.concatenate([v[:nvf], v[nvf:] - (S.wmean @ v[nvf:]) / S.wmean.sum()])
     xo = pz(ro["x"])
-    xg = pz(x)
-    def diffs(a):
-        return (np.linalg.norm(a[:nvf] - xo[:nvf]) / np.linalg.norm(xo[:nvf]),
-                np.linalg.norm(a - xo) / np.linalg.norm(xo),
-                np.linalg.norm(a[nvf:] - xo[nvf:]) / max(np.linalg.norm(xo[nvf:]), 1e-300))
-    ev, ex, ep = diffs(xg)
+
+    def diffs(a, b):
+        return (np.linalg.norm(a[:nvf] - b[:nvf]) / np.linalg.norm(b[:nvf]),
+                np.linalg.norm(a - b) / np.linalg.norm(b))
+    ev, ex = diffs(pz(x), xo)
     el = abs(res["lam_max"] - ro["lam_max"]) / ro["lam_max"]
-    bar_v = bar_x = tol
-    if ev > tol or ex > tol:
-        sens = [diffs(pz(xs)) for xs in _oracle_iterate_sensitivity(ob, F, res["iters"])]
-        bar_v = max(tol, max(d[0] for d in sens))
-        bar_x = max(tol, max(d[1] for d in sens))
-    print(f"PARITY {label} iters gpu {res['iters']} oracle {ro['iters']} vel {ev:.3e} (bar {bar_v:.1e}) "
-          f"all {ex:.3e} (bar {bar_x:.1e}) press {ep:.3e} lam_max {el:.3e}")
-    assert ev <= bar_v, (ev, bar_v)
-    assert ex <= bar_x, (ex, bar_x)
     assert el <= 1e-6, el
-    return dict(vel=ev, all=ex, press=ep, lam=el, oracle=ro)
+    sens = None
+    if ev > tol or ex > tol:
+        sens = max(max(diffs(pz(xs), xo)) for xs in _oracle_iterate_sensitivity(ob, F, res["iters"]))
+    line = (f"PARITY {label} iters gpu {res['iters']} oracle {ro['iters']} rtol 1e-8: vel {ev:.3e} all {ex:.3e}"
+            + ("" if sens is None else f" (oracle reproducibility {sens:.1e})"))
+    out = dict(vel=ev, all=ex, lam=el, oracle=ro, reproducibility=sens)
+    if sens is None or sens <= 0.1 * tol:
+        assert ev <= tol and ex <= tol, (ev, ex)
+    if deep is not None:
+        rd, xd = deep(1e-11)
+        rod = ob.pcg(F, rtol=1e-11)
+        dv, dx = diffs(pz(xd), pz(rod["x"]))
+        line += f" | rtol 1e-11: iters {rd['iters']}/{rod['iters']} vel {dv:.3e} all {dx:.3e}"
+        out.update(deep_vel=dv, deep_all=dx)
+        assert dv <= tol and dx <= tol, (dv, dx)
+    else:
+        assert sens is None or sens <= 0.1 * tol, "needs the deep comparison"
+    print(line)
+    return out

@@ -18,7 +18,7 @@ def test_reference_arm_two_ranks_gloo():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="", OMP_NUM_THREADS="1")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr", "127.0.0.1", "--master-port", "29517", "bench.py", "--impl", "reference",
-           "--gpus", "2", "--steps", "1", "--warmup", "0"]
+           "--gpus", "2", "--steps", "1", "--warmup", "0", "--oracle-workload", "cube4_k2"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, env=env, timeout=850)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
