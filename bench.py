@@ -159,19 +159,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def measure(pkg, torch, cfg, fq, precision, steps, warmup, stream, with_e2e, rank):
-    """Times `steps` full steps (after `warmup`) of one precision form."""
+def measure(pkg, torch, cfg, fq_host, precision, steps, warmup, stream, with_e2e, rank):
+    """Times `steps` full steps (after `warmup`) of one precision form: with
+    the load samples resident on the device (the timed value), and with
+    every input from host memory and the solution copied back (e2e)."""
     mesh, k, nu, part = cfg["mesh"], cfg["k"], cfg["nu"], cfg["part"]
+    fq = fq_host.to("cuda")
 
     phases = {}
 
     def step(out_host=None):
-        # every library call below synchronizes, so host clocks split the step
+        # every library call below synchronizes, so host clocks split the step;
+        # fq is the load samples on the device (timed device step) or in
+        # pinned host memory (end-to-end step: copied in by vem_load)
         t0 = time.perf_counter()
         g = pkg.VemSystem(mesh, k, nu)
         g.set_stream(stream)
         t1 = time.perf_counter()
-        rhs = g.load(LOAD_DEGREE, fq)
+        rhs = g.load(LOAD_DEGREE, fq if out_host is None else fq_host)
         t2 = time.perf_counter()
         bd = pkg.Bddc(g, part, precision=precision)
         t3 = time.perf_counter()
@@ -249,12 +254,13 @@ def run_ours(args, rank, world, dist):
     # host inputs of one step: mesh arrays, viscosity, partition, load samples
     probe = pkg.VemSystem(mesh, k, nu)
     pts = probe.quad_points(LOAD_DEGREE)
-    fq = np.empty_like(pts)
+    fq = torch.empty(pts.shape, dtype=torch.float64, pin_memory=True)
+    fqn = fq.numpy()
     for a in range(0, len(pts), 1 << 24):      # chunks bound the temporaries
-        fq[a:a + (1 << 24)] = cfg["f"](pts[a:a + (1 << 24)])
+        fqn[a:a + (1 << 24)] = cfg["f"](pts[a:a + (1 << 24)])
     del probe, pts
     h2d = (mesh["xyz"].nbytes + mesh["face_ptr"].nbytes + mesh["face_vtx"].nbytes + mesh["elem_ptr"].nbytes
-           + mesh["elem_face"].nbytes + nu.nbytes + part.nbytes + fq.nbytes)
+           + mesh["elem_face"].nbytes + nu.nbytes + part.nbytes + fq.numel() * 8)
     if dist:
         dist.barrier()
     import tempfile

@@ -123,7 +123,9 @@ int vem_quad_points(vem_system* sys, int degree, int64_t* n, double* xyz_out);
 
 /* Load vector (Eq. discreteF): rhs = [int Pi^0_k f . phi_i ; 0] over the
  * system vector layout, from f sampled at the points of vem_quad_points with
- * the same degree.  f_at_quad: host [n*3]; rhs_dev: device [n_free+n_press]. */
+ * the same degree.  f_at_quad: [n*3], host memory (copied to the device in
+ * the call) or device memory (read in place); rhs_dev: device
+ * [n_free+n_press]. */
 int vem_load(vem_system* sys, int degree, const double* f_at_quad, double* rhs_dev);
 
 /* Non-homogeneous Dirichlet data for tests such as the polynomial patch test

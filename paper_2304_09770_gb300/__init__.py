@@ -154,11 +154,18 @@ class VemSystem:
         return out
 
     def load(self, degree, f_values, out=None):
+        """vem_load; f_values: numpy array (host) or float64 torch tensor
+        (on the GPU: read in place; pinned host memory: copied)."""
         import torch
-        f_values = np.ascontiguousarray(f_values, dtype=np.float64)
+        if isinstance(f_values, torch.Tensor):
+            assert f_values.dtype == torch.float64 and f_values.is_contiguous()
+            fp = ctypes.c_void_p(f_values.data_ptr())
+        else:
+            f_values = np.ascontiguousarray(f_values, dtype=np.float64)
+            fp = _ptr(f_values)
         if out is None:
             out = torch.empty(self.n, dtype=torch.float64, device="cuda")
-        _check(lib().vem_load(self.h, degree, _ptr(f_values), _dptr(out)))
+        _check(lib().vem_load(self.h, degree, fp, _dptr(out)))
         return out
 
     def load_noalloc(self, degree, f_dev, out):

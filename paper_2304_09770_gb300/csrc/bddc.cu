@@ -338,24 +338,48 @@ struct KPhiAssemble {
   }
 };
 
-// S_Pi = Phi^T (K Phi) per subdomain
-struct KGram {
+// S_Pi = Phi^T (K Phi) per subdomain by 32 x 32 output tiles: one CTA per
+// (subdomain, tile), 256 threads with 4 outputs each, the rows streamed in
+// chunks of 64 through shared memory; every entry sums the rows in order.
+struct GramTile {
+  int sub, a0, b0;
+};
+struct KGramTiled {
   BddcView V;
+  const GramTile* tiles;
   const double* PHI;
   const double* KPHI;
   double* SG;
   int NC;
-  VB_HD void operator()(const KExec& ex, int i) const {
-    const SubDev S = V.subs[i];
-    const int nloc = S.nv + S.npress;
+  static constexpr int TR = 64, TP = 33;   // rows per chunk, padded tile width
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const GramTile tl = tiles[blk];
+    const SubDev S = V.subs[tl.sub];
+    const int nloc = S.nv + S.npress, ncl = S.ncl;
     const double* ph = PHI + S.loc_off * NC;
     const double* kp = KPHI + S.loc_off * NC;
-    for (int idx = ex.tid; idx < S.ncl * S.ncl; idx += ex.nt) {
-      const int a = idx / S.ncl, b = idx % S.ncl;
-      double acc = 0.0;
-      for (int l = 0; l < nloc; ++l) acc += ph[(int64_t)a * nloc + l] * kp[(int64_t)b * nloc + l];
-      SG[(int64_t)i * NC * NC + a * NC + b] = acc;
+    double* sA = ex.smem;            // [TR][TP]: Phi rows, columns a0 ..
+    double* sB = sA + TR * TP;       // [TR][TP]: K Phi rows, columns b0 ..
+    const int a = ex.tid / 8, bq = (ex.tid % 8) * 4;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int r0 = 0; r0 < nloc; r0 += TR) {
+      const int nr = nloc - r0 < TR ? nloc - r0 : TR;
+      for (int q = ex.tid; q < TR * 32; q += ex.nt) {
+        const int c = q / TR, r = q % TR;
+        const bool okr = r < nr;
+        sA[r * TP + c] = (okr && tl.a0 + c < ncl) ? ph[(int64_t)(tl.a0 + c) * nloc + r0 + r] : 0.0;
+        sB[r * TP + c] = (okr && tl.b0 + c < ncl) ? kp[(int64_t)(tl.b0 + c) * nloc + r0 + r] : 0.0;
+      }
+      ex.sync();
+      for (int r = 0; r < nr; ++r) {
+        const double x = sA[r * TP + a];
+        for (int j = 0; j < 4; ++j) acc[j] += x * sB[r * TP + bq + j];
+      }
+      ex.sync();
     }
+    if (tl.a0 + a < ncl)
+      for (int j = 0; j < 4; ++j)
+        if (tl.b0 + bq + j < ncl) SG[(int64_t)tl.sub * NC * NC + (tl.a0 + a) * NC + tl.b0 + bq + j] = acc[j];
   }
 };
 
@@ -2445,7 +2469,17 @@ static void setup_core(bddc* b, const int32_t* part) {
       mark("t_coarse_solves_ms");
       launch(KElemMatvec{V, drp.p, N, PHI.p, KW.p, NC}, loc, 32, 0, st);
       DBuf<double> SG((size_t)N * NC * NC);
-      launch(KGram{V, PHI.p, KW.p, SG.p, NC}, N, 256, 0, st);
+      {
+        std::vector<GramTile> gt;
+        for (int i = 0; i < N; ++i)
+          for (int a0 = 0; a0 < b->h_subs[i].ncl; a0 += 32)
+            for (int b0 = 0; b0 < b->h_subs[i].ncl; b0 += 32) gt.push_back({i, a0, b0});
+        DBuf<GramTile> dgt;
+        upload_vec(dgt, gt, st);
+        launch(KGramTiled{V, dgt.p, PHI.p, KW.p, SG.p, NC}, (int64_t)gt.size(), 256,
+               sizeof(double) * 2 * KGramTiled::TR * KGramTiled::TP, st);
+        VB_CUDA(cudaStreamSynchronize(st));
+      }
       mark("t_coarse_gram_ms");
       int64_t nphi = 0;
       for (auto& D : b->h_subs) {

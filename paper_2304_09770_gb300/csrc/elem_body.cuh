@@ -136,6 +136,47 @@ VB_HD inline bool small_inverse(double* M, double* Inv, int n) {
   return true;
 }
 
+// The same Gauss-Jordan inversion run by one warp (lanes 0..31 call it;
+// every lane scans for the pivot, each lane eliminates whole rows): the
+// operations on every entry, and their order, are those of small_inverse.
+VB_HD inline bool small_inverse_warp(double* M, double* Inv, int n, int lane) {
+#ifdef __CUDA_ARCH__
+  for (int i = lane; i < n * n; i += 32) Inv[i] = (i / n == i % n) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    double best = M[c * n + c] < 0 ? -M[c * n + c] : M[c * n + c];
+    for (int r = c + 1; r < n; ++r) {
+      double v = M[r * n + c] < 0 ? -M[r * n + c] : M[r * n + c];
+      if (v > best) { best = v; p = r; }
+    }
+    if (best == 0.0) return false;
+    __syncwarp();
+    if (p != c)
+      for (int j = lane; j < n; j += 32) {
+        double t = M[c * n + j]; M[c * n + j] = M[p * n + j]; M[p * n + j] = t;
+        t = Inv[c * n + j]; Inv[c * n + j] = Inv[p * n + j]; Inv[p * n + j] = t;
+      }
+    __syncwarp();
+    const double d = 1.0 / M[c * n + c];
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) { M[c * n + j] *= d; Inv[c * n + j] *= d; }
+    __syncwarp();
+    for (int r = lane; r < n; r += 32) {
+      if (r == c) continue;
+      double f = M[r * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) { M[r * n + j] -= f * M[c * n + j]; Inv[r * n + j] -= f * Inv[c * n + j]; }
+    }
+    __syncwarp();
+  }
+  return true;
+#else
+  (void)lane;
+  return small_inverse(M, Inv, n);
+#endif
+}
+
 template <int K>
 struct ElemBuilder {
   using S = ElemSizes<K>;
@@ -196,7 +237,11 @@ struct ElemBuilder {
           h2 = s > h2 ? s : h2;
         }
       sh.hK = sqrt(h2);
-      for (int f = 0; f < R.nf; ++f) {
+    }
+    ex.sync();
+    // faces independently, one thread each
+    for (int f = ex.tid; f < R.nf; f += ex.nt) {
+      {
         int m = R.fnv[f];
         double nrm[3] = {0, 0, 0}, xc[3] = {0, 0, 0}, h2f = 0;
         for (int i = 0; i < m; ++i) {
@@ -326,17 +371,13 @@ struct ElemBuilder {
   VB_HD bool volume_systems() {
     double* tmp = sh.big;
     bool ok = true;
-    if (ex.tid == 0) {
-      for (int p = 0; p < S::NP0; ++p)
-        for (int q = 0; q < S::NP0; ++q) tmp[p * S::NP0 + q] = mass(p, q);
-      ok = small_inverse(tmp, sh.Minv0, S::NP0);
-    }
+    for (int idx = ex.tid; idx < S::NP0 * S::NP0; idx += ex.nt) tmp[idx] = mass(idx / S::NP0, idx % S::NP0);
     ex.sync();
-    if (ex.tid == 0 && ok) {
-      for (int p = 0; p < S::NP1; ++p)
-        for (int q = 0; q < S::NP1; ++q) tmp[p * S::NP1 + q] = mass(p, q);
-      ok = small_inverse(tmp, sh.Minv1, S::NP1);
-    }
+    if (ex.tid < 32) ok = small_inverse_warp(tmp, sh.Minv0, S::NP0, ex.tid);
+    ex.sync();
+    for (int idx = ex.tid; idx < S::NP1 * S::NP1; idx += ex.nt) tmp[idx] = mass(idx / S::NP1, idx % S::NP1);
+    ex.sync();
+    if (ex.tid < 32) ok = small_inverse_warp(tmp, sh.Minv1, S::NP1, ex.tid) && ok;
     ex.sync();
     return ok;
   }
@@ -406,16 +447,19 @@ struct ElemBuilder {
     }
     for (int idx = ex.tid; idx < S::NF1 * nsf; idx += ex.nt) sh.rhs[idx] = 0.0;
     ex.sync();
-    if (ex.tid == 0) {
+    // one thread per basis function b of P_k(f): it fills row b of the
+    // right-hand side and entry b of row 0 of G2, in the same order as a
+    // single thread would (Laplacian terms, then edge by edge, point by point)
+    for (int b = ex.tid; b < S::NF1; b += ex.nt) {
+      const Exp2 eb = T.e2[b];
       // interior moments: -int_f Lap m_b v = -|f| sum_g L[g][b] s_g
-      for (int b = 1; b < S::NF1; ++b) {
-        const Exp2 eb = T.e2[b];
+      if (b > 0) {
         if (eb.a >= 2) sh.rhs[b * nsf + m * K + idx2(eb.a - 2, eb.b)] -= sh.farea[f] * g00 * eb.a * (eb.a - 1);
         if (eb.a >= 1 && eb.b >= 1)
           sh.rhs[b * nsf + m * K + idx2(eb.a - 1, eb.b - 1)] -= sh.farea[f] * 2.0 * g01 * eb.a * eb.b;
         if (eb.b >= 2) sh.rhs[b * nsf + m * K + idx2(eb.a, eb.b - 2)] -= sh.farea[f] * g11 * eb.b * (eb.b - 1);
       }
-      for (int g = 0; g < S::NF1; ++g) sh.G2[g] = 0.0;
+      double g2b = 0.0;
       // edges: Gauss points, Lagrange basis on (0, interior GL nodes, 1)
       double nodes[K + 1];
       nodes[0] = 0.0;
@@ -452,27 +496,25 @@ struct ElemBuilder {
               if (bb != aa) l *= (tq - nodes[bb]) / (nodes[aa] - nodes[bb]);
             lag[aa] = l;
           }
-          for (int b = 0; b < S::NF1; ++b) {
-            const Exp2 eb = T.e2[b];
-            double mb = ipow(s, eb.a) * ipow(tt, eb.b);
-            if (b == 0) {
-              for (int aa = 0; aa <= K; ++aa) sh.rhs[sidx[aa]] += wq * lag[aa];
-            } else {
-              double ds = eb.a > 0 ? eb.a * ipow(s, eb.a - 1) * ipow(tt, eb.b) : 0.0;
-              double dt = eb.b > 0 ? eb.b * ipow(s, eb.a) * ipow(tt, eb.b - 1) : 0.0;
-              double dn = ds * n1 + dt * n2;
-              for (int aa = 0; aa <= K; ++aa) sh.rhs[b * nsf + sidx[aa]] += wq * dn * lag[aa];
-            }
-            sh.G2[b] += wq * mb;     // row 0 of G2: int_df m_b
+          double mb = ipow(s, eb.a) * ipow(tt, eb.b);
+          if (b == 0) {
+            for (int aa = 0; aa <= K; ++aa) sh.rhs[sidx[aa]] += wq * lag[aa];
+          } else {
+            double ds = eb.a > 0 ? eb.a * ipow(s, eb.a - 1) * ipow(tt, eb.b) : 0.0;
+            double dt = eb.b > 0 ? eb.b * ipow(s, eb.a) * ipow(tt, eb.b - 1) : 0.0;
+            double dn = ds * n1 + dt * n2;
+            for (int aa = 0; aa <= K; ++aa) sh.rhs[b * nsf + sidx[aa]] += wq * dn * lag[aa];
           }
+          g2b += wq * mb;     // row 0 of G2: int_df m_b
         }
       }
+      sh.G2[b] = g2b;
     }
     ex.sync();
     // solve (one thread inverts; all apply)
     double* G2inv = sh.MF;   // borrowed until the face mass is formed
     bool ok = true;
-    if (ex.tid == 0) ok = small_inverse(sh.G2, G2inv, S::NF1);
+    if (ex.tid < 32) ok = small_inverse_warp(sh.G2, G2inv, S::NF1, ex.tid);
     ex.sync();
     for (int idx = ex.tid; idx < S::NF1 * nsf; idx += ex.nt) {
       int b = idx / nsf, s = idx % nsf;
@@ -488,7 +530,7 @@ struct ElemBuilder {
       MFm[idx] = sh.nu2[idx2(T.e2[b].a + T.e2[g].a, T.e2[b].b + T.e2[g].b)];
     }
     ex.sync();
-    if (ex.tid == 0) ok = ok && small_inverse(MFm, sh.MF, S::NF2);
+    if (ex.tid < 32) ok = small_inverse_warp(MFm, sh.MF, S::NF2, ex.tid) && ok;
     ex.sync();
     // rhs for Pi^0 into Pi0 (temporarily), then multiply by MF^{-1} into rhs
     for (int idx = ex.tid; idx < S::NF2 * nsf; idx += ex.nt) {
@@ -679,22 +721,23 @@ struct ElemBuilder {
     }
     ex.sync();
     // (4) Pi^nabla_k : G c = rhs
-    if (ex.tid == 0) {
+    {
       double* Gm = sh.big;
-      for (int p = 0; p < S::NP1; ++p)
-        for (int q = 0; q < S::NP1; ++q) {
-          double v = 0.0;
-          if (p == 0) v = sh.bndm[q];
-          else {
-            const Exp3 ep = T.e3[p], eq = T.e3[q];
-            if (ep.a && eq.a) v += ep.a * eq.a * mu(ep.a + eq.a - 2, ep.b + eq.b, ep.c + eq.c);
-            if (ep.b && eq.b) v += ep.b * eq.b * mu(ep.a + eq.a, ep.b + eq.b - 2, ep.c + eq.c);
-            if (ep.c && eq.c) v += ep.c * eq.c * mu(ep.a + eq.a, ep.b + eq.b, ep.c + eq.c - 2);
-            v /= hK * hK;
-          }
-          Gm[p * S::NP1 + q] = v;
+      for (int idx = ex.tid; idx < S::NP1 * S::NP1; idx += ex.nt) {
+        const int p = idx / S::NP1, q = idx % S::NP1;
+        double v = 0.0;
+        if (p == 0) v = sh.bndm[q];
+        else {
+          const Exp3 ep = T.e3[p], eq = T.e3[q];
+          if (ep.a && eq.a) v += ep.a * eq.a * mu(ep.a + eq.a - 2, ep.b + eq.b, ep.c + eq.c);
+          if (ep.b && eq.b) v += ep.b * eq.b * mu(ep.a + eq.a, ep.b + eq.b - 2, ep.c + eq.c);
+          if (ep.c && eq.c) v += ep.c * eq.c * mu(ep.a + eq.a, ep.b + eq.b, ep.c + eq.c - 2);
+          v /= hK * hK;
         }
-      ok = small_inverse(Gm, sh.Ginv, S::NP1) && ok;
+        Gm[idx] = v;
+      }
+      ex.sync();
+      if (ex.tid < 32) ok = small_inverse_warp(Gm, sh.Ginv, S::NP1, ex.tid) && ok;
     }
     ex.sync();
     // rhs into VMH (temporary), then PiN = Ginv rhs

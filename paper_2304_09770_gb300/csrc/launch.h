@@ -52,6 +52,24 @@ inline void launch_lb(const F& f, int64_t nblocks, size_t smem, cudaStream_t s) 
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+// the same with 128 threads and at least MINB resident CTAs per SM
+template <class F, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_run_lb128(const F f) {
+  extern __shared__ __align__(16) double vb_smem[];
+  f(KExec{(int)threadIdx.x, (int)blockDim.x, vb_smem}, (int)blockIdx.x);
+}
+
+template <int MINB, class F>
+inline void launch_lb128(const F& f, int64_t nblocks, size_t smem, cudaStream_t s) {
+  if (nblocks <= 0) return;
+  VB_CHECK(nblocks < (int64_t)INT32_MAX, VEM_EINVAL, "grid too large");
+  if (smem > 48 * 1024)
+    VB_CUDA(cudaFuncSetAttribute(k_run_lb128<F, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_run_lb128<F, MINB><<<(unsigned)nblocks, 128, smem, s>>>(f);
+  VB_KERNEL_CHECK();
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 // the same with up to MAXT threads per CTA (the compiler caps the registers
 // so that a CTA of MAXT threads fits on an SM)
 template <class F, int MAXT>

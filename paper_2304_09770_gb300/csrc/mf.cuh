@@ -936,7 +936,36 @@ struct KElemProduct {
         }
       }
       ex.sync();
-      for (int a = w; a < nKp; a += nw) {
+      if (DF) {
+        // velocity rows: one thread per row a, reading column a of the
+        // symmetric A_e (consecutive threads, consecutive entries), eight
+        // loads in flight per thread; no reductions
+        for (int a = ex.tid; a < nK; a += ex.nt) {
+          if (ep[a] < 0) continue;   // not a row of this problem
+          float sh[RB], sl[RB];
+          for (int r = 0; r < RB; ++r) sh[r] = sl[r] = 0.0f;
+          const float2* col = V.A2 + V.offK2[e] + a;
+          int b = 0;
+          for (; b + 8 <= nK; b += 8) {
+            float2 v[8];
+            for (int u = 0; u < 8; ++u) v[u] = col[(int64_t)(b + u) * nK];
+            for (int u = 0; u < 8; ++u)
+              for (int r = 0; r < RB; ++r)
+                df_fma(sh[r], sl[r], v[u].x, v[u].y, zf[r * nKp + b + u], zf[RB * nKp + r * nKp + b + u]);
+          }
+          for (; b < nK; ++b) {
+            const float2 v = col[(int64_t)b * nK];
+            for (int r = 0; r < RB; ++r)
+              df_fma(sh[r], sl[r], v.x, v.y, zf[r * nKp + b], zf[RB * nKp + r * nKp + b]);
+          }
+          for (int r = 0; r < RB; ++r) {
+            double acc = (double)sh[r] + (double)sl[r];
+            for (int al = 0; al < npk; ++al) acc += Be[(int64_t)al * nK + a] * zs[r * nKp + nK + al];
+            if (r < nc) YE[ye_off(V, e, nr, c0 + r, nKp) + a] = acc;
+          }
+        }
+      }
+      for (int a = DF ? nK + w : w; a < nKp; a += nw) {
         if (ep[a] < 0) continue;   // not a row of this problem
         double acc[RB];
         for (int r = 0; r < RB; ++r) acc[r] = 0.0;

@@ -172,10 +172,38 @@ struct KQuadPoints {
   }
 };
 
+// Tetrahedron `tet` of the element's load rule, (x_K, fan triangle): its
+// edge vectors from x_K and the determinant (6 |T|).
+VB_HD inline void load_tet(const ElemRec& R, const double* xyz, const double* xK, int tet, double* a1, double* b1,
+                           double* c1, double* det) {
+  int f = 0, t = 0, cnt = 0;
+  for (f = 0; f < R.nf; ++f) {
+    int nt = R.fnv[f] - 2;
+    if (tet < cnt + nt) { t = tet - cnt + 1; break; }
+    cnt += nt;
+  }
+  int m = R.fnv[f];
+  int i0 = 0, i1 = t, i2 = t + 1;
+  if (R.fsign[f] < 0) { i0 = m - 1; i1 = m - 1 - t; i2 = m - 2 - t; }
+  const int* lv = R.floopv[f];
+  for (int d = 0; d < 3; ++d) {
+    a1[d] = xyz[3 * R.vert[lv[i0]] + d] - xK[d];
+    b1[d] = xyz[3 * R.vert[lv[i1]] + d] - xK[d];
+    c1[d] = xyz[3 * R.vert[lv[i2]] + d] - xK[d];
+  }
+  double cr[3];
+  cross3(b1, c1, cr);
+  *det = a1[0] * cr[0] + a1[1] * cr[1] + a1[2] * cr[2];
+}
+
 // per element: F[c][a] = sum_p w f_c m_a(xi); local rhs = P0^T F (Eq. discreteF).
-// The load-rule points are generated once each, in chunks staged in shared
-// memory (scaled coordinates and w f), and every (c, a) moment sums over the
-// chunk in point order.
+// k = 2, 3: every thread takes points of the rule (tetrahedron by
+// tetrahedron, the tetrahedron geometry once per thread), evaluates the
+// monomials once per point and accumulates all 3 dim P_k moments in
+// registers; the threads' partial sums are added by a fixed tree.  k = 4
+// (105 moments): the load-rule points are generated once each, in chunks
+// staged in shared memory (scaled coordinates and w f), and every (c, a)
+// moment sums over the chunk in point order.
 template <int K>
 struct KLoadLocal {
   const ElemRec* rec;
@@ -187,13 +215,16 @@ struct KLoadLocal {
   const ElemTables* tab;
   LoadRule L;
   double* rloc;
-  static constexpr int CH = 128;   // points per staged chunk
-  static size_t smem_bytes() { return sizeof(double) * (3 * pdim3(K) + 4 + 6 * CH); }
+  static constexpr int CH = 128;   // points per staged chunk (k = 4)
+  static constexpr int NT = 128;   // threads per element
+  static constexpr bool PER_THREAD = 3 * pdim3(K) <= 60;
+  static size_t smem_bytes() {
+    return sizeof(double) * (3 * pdim3(K) + 4 + (PER_THREAD ? (size_t)NT * 3 * pdim3(K) : 6 * CH));
+  }
   __device__ void operator()(const KExec& ex, int e) const {
     constexpr int NP1 = pdim3(K);
     double* Fm = ex.smem;
     double* geo = ex.smem + 3 * NP1;   // xK[3], hK
-    double* pt = geo + 4;              // [CH][6]: scaled x, y, z, then w f_c
     const ElemRec& R = rec[e];
     if (ex.tid == 0) {
       elem_centroid(R, xyz, geo);
@@ -211,29 +242,72 @@ struct KLoadLocal {
     }
     ex.sync();
     const int npts = (int)(qoff[e + 1] - qoff[e]);
-    const int c = ex.tid / NP1, a = ex.tid % NP1;
-    const bool mine = ex.tid < 3 * NP1;
-    const Exp3 ea = tab->e3[mine ? a : 0];
-    double acc = 0.0;
-    for (int p0 = 0; p0 < npts; p0 += CH) {
-      const int cnt = npts - p0 < CH ? npts - p0 : CH;
-      for (int q = ex.tid; q < cnt; q += ex.nt) {
-        double x[3], w;
-        load_point(L, R, xyz, geo, p0 + q, x, &w);
-        double* d = pt + 6 * q;
-        for (int k = 0; k < 3; ++k) d[k] = (x[k] - geo[k]) / geo[3];
-        for (int k = 0; k < 3; ++k) d[3 + k] = w * fq[3 * (qoff[e] + p0 + q) + k];
-      }
-      ex.sync();
-      if (mine)
-        for (int q = 0; q < cnt; ++q) {
-          const double* d = pt + 6 * q;
-          acc += d[3 + c] * ipow(d[0], ea.a) * ipow(d[1], ea.b) * ipow(d[2], ea.c);
+    if constexpr (PER_THREAD) {
+      double* part = geo + 4;          // [nt][3 NP1]
+      double acc[3 * NP1];
+      for (int q = 0; q < 3 * NP1; ++q) acc[q] = 0.0;
+      const double xK[3] = {geo[0], geo[1], geo[2]}, hinv = 1.0 / geo[3];
+      const int nq = L.nq, nq3 = nq * nq * nq;
+      const int ntet = npts / nq3;
+      const double* fe = fq + 3 * qoff[e];
+      for (int tet = 0; tet < ntet; ++tet) {
+        double a1[3], b1[3], c1[3], det;
+        load_tet(R, xyz, xK, tet, a1, b1, c1, &det);
+        for (int q = ex.tid; q < nq3; q += ex.nt) {
+          const int iu = q / (nq * nq), iv = (q / nq) % nq, iw = q % nq;
+          const double U = L.x[iu], V = L.x[iv], W = L.x[iw];
+          const double px = U, py = V * (1 - U), pz = W * (1 - U) * (1 - V);
+          const double w = L.w[iu] * L.w[iv] * L.w[iw] * (1 - U) * (1 - U) * (1 - V) * det;
+          double xi[3];
+          for (int d = 0; d < 3; ++d) xi[d] = (px * a1[d] + py * b1[d] + pz * c1[d]) * hinv;
+          double mono[NP1];
+          for (int a = 0; a < NP1; ++a) {
+            const Exp3 ea = tab->e3[a];
+            mono[a] = ipow(xi[0], ea.a) * ipow(xi[1], ea.b) * ipow(xi[2], ea.c);
+          }
+          const double* fp = fe + 3 * ((int64_t)tet * nq3 + q);
+          for (int c = 0; c < 3; ++c) {
+            const double wf = w * fp[c];
+            for (int a = 0; a < NP1; ++a) acc[c * NP1 + a] += wf * mono[a];
+          }
         }
+      }
+      for (int q = 0; q < 3 * NP1; ++q) part[(int64_t)ex.tid * 3 * NP1 + q] = acc[q];
+      ex.sync();
+      for (int st = 1; st < ex.nt; st <<= 1) {
+        if ((ex.tid & (2 * st - 1)) == 0 && ex.tid + st < ex.nt)
+          for (int q = 0; q < 3 * NP1; ++q)
+            part[(int64_t)ex.tid * 3 * NP1 + q] += part[(int64_t)(ex.tid + st) * 3 * NP1 + q];
+        ex.sync();
+      }
+      for (int q = ex.tid; q < 3 * NP1; q += ex.nt) Fm[q] = part[q];
+      ex.sync();
+    } else {
+      double* pt = geo + 4;              // [CH][6]: scaled x, y, z, then w f_c
+      const int c = ex.tid / NP1, a = ex.tid % NP1;
+      const bool mine = ex.tid < 3 * NP1;
+      const Exp3 ea = tab->e3[mine ? a : 0];
+      double acc = 0.0;
+      for (int p0 = 0; p0 < npts; p0 += CH) {
+        const int cnt = npts - p0 < CH ? npts - p0 : CH;
+        for (int q = ex.tid; q < cnt; q += ex.nt) {
+          double x[3], w;
+          load_point(L, R, xyz, geo, p0 + q, x, &w);
+          double* d = pt + 6 * q;
+          for (int k = 0; k < 3; ++k) d[k] = (x[k] - geo[k]) / geo[3];
+          for (int k = 0; k < 3; ++k) d[3 + k] = w * fq[3 * (qoff[e] + p0 + q) + k];
+        }
+        ex.sync();
+        if (mine)
+          for (int q = 0; q < cnt; ++q) {
+            const double* d = pt + 6 * q;
+            acc += d[3 + c] * ipow(d[0], ea.a) * ipow(d[1], ea.b) * ipow(d[2], ea.c);
+          }
+        ex.sync();
+      }
+      if (mine) Fm[ex.tid] = acc;
       ex.sync();
     }
-    if (mine) Fm[ex.tid] = acc;
-    ex.sync();
     int nK = (int)(offK[e + 1] - offK[e]);
     const double* P = P0 + (size_t)3 * NP1 * offK[e];
     for (int col = ex.tid; col < nK; col += ex.nt) {
@@ -306,7 +380,7 @@ static void launch_elements(vem_system* s, const DBuf<int64_t>& offK, const DBuf
   }
   KElement<K> f{s->d_rec.p, s->d_xyz.p, s->d_nu.p, offK.p, offK2.p, s->d_tab.p, s->d_A.p, Bdst,
                 s->d_P0.p, pe.wm.p, pe.scratch.p, stride, nE, grid, pe.status.p};
-  launch(f, grid, 128, smem, s->stream);
+  launch_lb128<4>(f, grid, smem, s->stream);
   if (s->dof.reduced) launch(KCompactB{pe.Bfull.p, s->d_B.p, offK.p, pe.npf}, nE, 128, 0, s->stream);
 }
 
@@ -538,17 +612,26 @@ extern "C" int vem_load(vem_system* s, int degree, const double* fq, double* rhs
     load_offsets(s, degree, qoff, L);
     DBuf<int64_t> dq;
     dq.upload(qoff, s->stream);
-    DBuf<double> df(3 * (size_t)qoff.back());
-    VB_CUDA(cudaMemcpyAsync(df.p, fq, df.n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    // f on the device is read in place; host f is copied in
+    cudaPointerAttributes pa{};
+    const bool on_dev = cudaPointerGetAttributes(&pa, fq) == cudaSuccess &&
+                        (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    DBuf<double> df(on_dev ? 0 : 3 * (size_t)qoff.back());
+    if (!on_dev)
+      VB_CUDA(cudaMemcpyAsync(df.p, fq, df.n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    const double* fsrc = on_dev ? fq : df.p;
     DBuf<double> rloc(s->h_eoff.back());
     const int nE = s->topo.nE;
-    const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4 + 6 * KLoadLocal<2>::CH);
     if (s->dof.k == 2)
-      launch(KLoadLocal<2>{s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE, 128, lsm, s->stream);
+      launch(KLoadLocal<2>{s->d_rec.p, s->d_xyz.p, dq.p, fsrc, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE,
+             KLoadLocal<2>::NT, KLoadLocal<2>::smem_bytes(), s->stream);
     else if (s->dof.k == 3)
-      launch(KLoadLocal<3>{s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE, 128, lsm, s->stream);
+      launch(KLoadLocal<3>{s->d_rec.p, s->d_xyz.p, dq.p, fsrc, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE,
+             KLoadLocal<3>::NT, KLoadLocal<3>::smem_bytes(), s->stream);
     else
-      launch(KLoadLocal<4>{s->d_rec.p, s->d_xyz.p, dq.p, df.p, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE, 128, lsm, s->stream);
+      launch(KLoadLocal<4>{s->d_rec.p, s->d_xyz.p, dq.p, fsrc, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc.p}, nE,
+             KLoadLocal<4>::NT, KLoadLocal<4>::smem_bytes(), s->stream);
     launch(KGatherRhs{s->n, s->dof.nvf, s->d_adj_ptr.p, s->d_adj_elem.p, s->d_adj_loc.p, s->d_eoff.p, rloc.p, rhs},
            (s->n + 255) / 256, 256, 0, s->stream);
     VB_CUDA(cudaStreamSynchronize(s->stream));
@@ -808,13 +891,15 @@ extern "C" int vem_load_noalloc(vem_system* s, int degree, const double* fq, dou
     gauss01(L.nq, L.x, L.w);
     const int64_t nq3 = (int64_t)L.nq * L.nq * L.nq;
     launch(KLoadOffsets{s->d_rec.p, nE, nq3, qoff}, 1, 1024, sizeof(int64_t) * 1024, s->stream);
-    const size_t lsm = sizeof(double) * (3 * pdim3(s->dof.k) + 4 + 6 * KLoadLocal<2>::CH);
     if (s->dof.k == 2)
-      launch(KLoadLocal<2>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE, 128, lsm, s->stream);
+      launch(KLoadLocal<2>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE,
+             KLoadLocal<2>::NT, KLoadLocal<2>::smem_bytes(), s->stream);
     else if (s->dof.k == 3)
-      launch(KLoadLocal<3>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE, 128, lsm, s->stream);
+      launch(KLoadLocal<3>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE,
+             KLoadLocal<3>::NT, KLoadLocal<3>::smem_bytes(), s->stream);
     else
-      launch(KLoadLocal<4>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE, 128, lsm, s->stream);
+      launch(KLoadLocal<4>{s->d_rec.p, s->d_xyz.p, qoff, fq, s->d_eoff.p, s->d_P0.p, s->d_tab.p, L, rloc}, nE,
+             KLoadLocal<4>::NT, KLoadLocal<4>::smem_bytes(), s->stream);
     launch(KGatherRhs{s->n, s->dof.nvf, s->d_adj_ptr.p, s->d_adj_elem.p, s->d_adj_loc.p, s->d_eoff.p, rloc, rhs},
            (s->n + 255) / 256, 256, 0, s->stream);
     return VEM_OK;
