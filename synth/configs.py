@@ -25,9 +25,10 @@ CONFIGS = {
     # 8^3 perturbed (+-0.2h), 2x2x2 subdomains of 4^3 elements (the 16^3
     # configuration's subdomain size): the workload the CPU oracle is timed on
     "tri8_k2": dict(n=8, perturb=0.2, seed=4, k=2, parts=(2, 2, 2), load="manufactured"),
-    # 16^3 perturbed (+-0.2h), 2x2x2 subdomains of 8^3 elements: the 32^3
-    # benchmark's subdomain size, on a mesh the oracle can still solve
-    "tri16_parts8": dict(n=16, perturb=0.2, seed=4, k=2, parts=(2, 2, 2), load="manufactured"),
+    # 12^3 perturbed (+-0.2h), 2x2x1 subdomains of 6 x 6 x 12 = 432 elements
+    # (the 32^3 benchmark's have 512): fronts of the benchmark's size, macro
+    # faces and a macro edge, on a mesh the oracle can still solve
+    "tri12_quarters": dict(n=12, perturb=0.2, seed=4, k=2, parts=(2, 2, 1), load="manufactured"),
     # 8^3 perturbed, two subdomains of 8 x 8 x 4 elements: fronts of the
     # size of the 32^3 benchmark's subdomains (1024-thread factorization
     # path), small enough for the oracle

@@ -1,11 +1,11 @@
-"""Writes tests/golden/tri16_parts8_oracle.json: the oracle's BDDC-PCG on the
-16^3 perturbed split-hex mesh with 2 x 2 x 2 subdomains of 8^3 elements (the
-32^3 benchmark's subdomain size), k = 2, deluxe scaling, rtol 1e-8, load
-rule degree k + 9.  Stored: iteration count and Lanczos estimates, and the
+"""Writes tests/golden/tri12_quarters_oracle.json: the oracle's BDDC-PCG on the
+12^3 perturbed split-hex mesh with 2 x 2 x 1 subdomains of 6 x 6 x 12 = 432
+elements (the 32^3 benchmark's have 512), k = 2, deluxe scaling, rtol 1e-8,
+load rule degree k + 9.  Stored: iteration count and Lanczos estimates, and the
 iterates at that count and one step either side (so that a run stopping one
 step apart is compared at its own count) on a seeded sample of velocity and
 pressure entries, with the norms of the whole vectors.  Calls only the
-oracle (and the seeded inputs of synth); it takes a few hours on one core.
+oracle (and the seeded inputs of synth); it takes about an hour.
 
     python tests/golden/make_bench_subdomain_parity.py
 """
@@ -21,7 +21,7 @@ sys.path.insert(0, os.path.join(ROOT, "tests"))
 
 import numpy as np  # noqa: E402
 
-NAME = "tri16_parts8"
+NAME = "tri12_quarters"
 
 
 def main():

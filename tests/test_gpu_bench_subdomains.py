@@ -1,9 +1,11 @@
-"""GPU parity at the benchmark's subdomain size: the 16^3 perturbed split-hex
-mesh in 2 x 2 x 2 subdomains of 8^3 elements (the 32^3 benchmark has 64 of
-them), so that the paths only large fronts take (1024-thread fronts, root
-fronts of several thousand rows, many-CTA sweep levels) are compared with the
-oracle.  The oracle's run is too long for the test itself: it is stored in
-tests/golden/tri16_parts8_oracle.json by the committed script
+"""GPU parity at nearly the benchmark's subdomain size: the 12^3 perturbed
+split-hex mesh in 2 x 2 x 1 subdomains of 6 x 6 x 12 = 432 elements (the
+32^3 benchmark has 64 subdomains of 512), so that the paths only large
+fronts take (1024-thread fronts, root fronts of thousands of rows, many-CTA
+sweep levels) are compared with the oracle, with macro faces and a macro
+edge in the interface.  The oracle's run is too long for the test itself:
+it is stored in tests/golden/tri12_quarters_oracle.json by the committed
+script
 tests/golden/make_bench_subdomain_parity.py, which calls only the oracle
 (iteration count, Lanczos estimates, and the iterates at that count and one
 step either side on a seeded sample of entries).
@@ -21,7 +23,7 @@ import pytest
 from synth import make_config
 
 pytestmark = pytest.mark.gpu
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tri16_parts8_oracle.json")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tri12_quarters_oracle.json")
 
 
 @pytest.fixture(scope="module")
