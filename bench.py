@@ -33,6 +33,12 @@ METRIC = "BDDC-PCG time-to-solution at rtol 1e-8 and BDDC applies/s, FP32-local 
 WORKLOAD = "tri32_k2"
 LOAD_DEGREE = 11            # k + 9: exact for the degree-9 manufactured load at k = 2
 ORACLE_WORKLOAD = "tri8_k2"
+# DRAM bytes the sweep kernels move per algorithmic factor byte: 1,931.7 MB
+# against 1.79 GB in one ncu capture of an apply on the 16^3 member
+# (profiles/bddc_apply_tri16_k2_fp32local_dram.md); the traffic scales with
+# the factor bytes, so the 32^3 sweep pair's traffic is this ratio times its
+# algorithmic bytes
+SWEEP_TRAFFIC_RATIO = 1931.7 / 1790.0
 
 
 def peaks():
@@ -203,6 +209,7 @@ def measure(pkg, torch, cfg, fq_host, precision, steps, warmup, stream, with_e2e
     torch.cuda.synchronize()
     dev_ms = ev0.elapsed_time(ev1) / steps
     launches = (pkg.kernel_launches() - l0) // steps
+    dev_phases = dict(phases)   # phases of the last device-timed step
     e2e_ms = None
     if with_e2e:
         host_u = torch.empty(g.n, dtype=torch.float64, pin_memory=True)
@@ -236,7 +243,7 @@ def measure(pkg, torch, cfg, fq_host, precision, steps, warmup, stream, with_e2e
     apply_ms = ev0.elapsed_time(ev1) / napp
     sweep_ms, sweep_bytes = bd.time_local_solves(5)
     return dict(dev_ms=dev_ms, e2e_ms=e2e_ms, launches=launches, res=res, info=info, vinfo=vinfo,
-                phases=dict(phases), apply_ms=apply_ms,
+                phases=dev_phases, e2e_phases=dict(phases) if with_e2e else None, apply_ms=apply_ms,
                 sweep_ms=sweep_ms, sweep_bytes=sweep_bytes, n=g.n, n_coarse=bd.info("n_coarse"))
 
 
@@ -280,7 +287,8 @@ def run_ours(args, rank, world, dist):
         ach = m["sweep_bytes"] / (m["sweep_ms"] * 1e-3) / 1e9
         return {"kernel": "local triangular sweeps (level GEMV kernels, forward+backward, Neumann+Dirichlet "
                           "factors)", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "peak_kind": kind, "traffic": None,
+                "frac": ach / hbm, "peak_kind": kind, "traffic": SWEEP_TRAFFIC_RATIO * m["sweep_bytes"],
+                "traffic_source": "ncu DRAM bytes of the sweep kernels on the 16^3 member, scaled by factor bytes",
                 "bytes_per_sweep_pair": m["sweep_bytes"], "ms_per_sweep_pair": m["sweep_ms"]}
 
     cpu = None
@@ -304,7 +312,8 @@ def run_ours(args, rank, world, dist):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iterations": res["iters"], "kappa": res["kappa"], "lam_min": res["lam_min"],
         "bddc_applies_per_s": 1e3 / m32["apply_ms"], "ms_per_apply": m32["apply_ms"],
-        "setup_phases_ms": m32["info"], "step_phases_ms": m32["phases"], "assemble_phases_ms": m32["vinfo"],
+        "setup_phases_ms": m32["info"], "step_phases_ms": m32["phases"], "e2e_step_phases_ms": m32["e2e_phases"],
+        "assemble_phases_ms": m32["vinfo"],
         "fp64": {"value": dev64 / 1e3, "unit": "s", "iterations": m64["res"]["iters"],
                  "kappa": m64["res"]["kappa"], "lam_min": m64["res"]["lam_min"],
                  "bddc_applies_per_s": 1e3 / m64["apply_ms"], "ms_per_apply": m64["apply_ms"],
