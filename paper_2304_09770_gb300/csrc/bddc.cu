@@ -1271,6 +1271,8 @@ static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& stat
   // diagnostics: with VEMBDDC_LEVEL_LOG set, every level's launch is timed
   // with CUDA events on the stream and printed to stderr
   static const bool level_log = std::getenv("VEMBDDC_LEVEL_LOG") != nullptr;
+  // diagnostics: VEMBDDC_NO_SPLIT keeps every front of every level in one CTA
+  static const bool split_off = std::getenv("VEMBDDC_NO_SPLIT") != nullptr;
   for (int h = 0; h <= B.maxh; ++h) {
     int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1299,6 +1301,43 @@ static void factor_batch_t(bddc* b, Batch& B, const BddcView& V, DBuf<int>& stat
       KFactor<float, true> f{V, B.d_levels.p + B.level_ptr[h], reinterpret_cast<float*>(Fs.p),
                              reinterpret_cast<float*>(Us.p), status.p, off};
       launch(f, cnt, 256, off + TC_SMEM_BYTES, b->stream);
+    } else if (cnt <= 2 * 152 && nfmax >= 1024 && !split_off) {
+      // few large fronts (the top of the trees): split form.  One CTA per
+      // front assembles it, factors each outer panel and finally inverts
+      // L11; the trailing update after each outer panel runs as one CTA
+      // per 64 x 64 tile of every front, so that all SMs take part.
+      KFactor<T> f{V, B.d_levels.p + B.level_ptr[h], Fs.p, Us.p, status.p};
+      f.mode = 1;
+      launch_mt<1024>(f, cnt, nthr, gbase, b->stream);
+      int npmax = 0;
+      for (int q = B.level_ptr[h]; q < B.level_ptr[h + 1]; ++q) npmax = std::max(npmax, b->h_nodes[B.h_levels[q]].np);
+      constexpr int NBO = FrontSmem<T>::NBO;
+      std::vector<FrontTile> tl;
+      std::vector<int64_t> tptr(1, 0);
+      for (int JB = 0; JB < npmax; JB += NBO) {
+        for (int q = B.level_ptr[h]; q < B.level_ptr[h + 1]; ++q) {
+          const int t = B.h_levels[q];
+          const NodeDev& Nd = b->h_nodes[t];
+          if (Nd.np <= JB) continue;
+          const int JE = std::min(Nd.np, JB + NBO), nf = Nd.np + Nd.nb;
+          const int nrt = (nf - JE + 63) / 64;
+          for (int tk = 0; tk < nrt; ++tk)
+            for (int ti = tk; ti < nrt; ++ti) tl.push_back({t, JE + 64 * ti, JE + 64 * tk});
+        }
+        tptr.push_back((int64_t)tl.size());
+      }
+      DBuf<FrontTile> dtl;
+      upload_vec(dtl, tl, b->stream);
+      const size_t tsm = sizeof(T) * (2 * 64 * 32 + NBO);
+      for (int p = 0, JB = 0; JB < npmax; JB += NBO, ++p) {
+        f.mode = 2;
+        f.JB = JB;
+        launch_mt<1024>(f, cnt, nthr, gbase, b->stream);
+        launch(KFactorTiles<T>{V, dtl.p + tptr[p], Fs.p, Us.p, JB}, tptr[p + 1] - tptr[p], 256, tsm, b->stream);
+      }
+      f.mode = 3;
+      launch_mt<1024>(f, cnt, nthr, gbase, b->stream);
+      VB_CUDA(cudaStreamSynchronize(b->stream));   // the tile list is freed below
     } else {
       KFactor<T> f{V, B.d_levels.p + B.level_ptr[h], Fs.p, Us.p, status.p};
       launch_mt<1024>(f, cnt, nthr, gbase, b->stream);

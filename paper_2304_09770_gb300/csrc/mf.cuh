@@ -112,24 +112,64 @@ VB_HD inline void group_sync(const KExec& ex, int ngrp, int grp) {
   ex.sync();
 }
 
-// Blocked right-looking partial LDL^T of one dense front (panel nf x np and
-// update block nb x nb, column-major, lower triangles), followed by the
-// in-place inversion of the unit lower diagonal block L11.  piv_type (may be
-// null: all positive) gives the expected pivot sign per pivot (velocity
-// positive; pressure and multiplier negative); a violation sets status 3.
-// Trailing update of a front by the pivot columns [ka, kb) (unit L stored
-// below the diagonal, D on it; sdv[c - dbase] = D of column c):
-//   C[i][k] -= sum_c L[i][c] D[c] L[k][c]
-// for rows i in [r0, nf) and columns k in [r0, ce), i >= k (pivot columns in
-// the panel, the rest in the update matrix).  64 x 64 tiles, one per group
-// of 256 threads (4 x 4 outputs per thread, accumulated in registers over
-// the whole K range, which streams through shared memory 32 columns at a
-// time); tiles lying between two different deluxe entities are skipped.
+// One 64 x 64 tile (rows i0.., columns k0..) of the trailing update of a
+// front by the pivot columns [ka, kb) (unit L below the diagonal, D on it;
+// sdv[c - dbase] = D of column c), by a group of 256 threads (gt, gnt: index
+// and size in the group, 4 x 4 outputs per thread accumulated in registers
+// over the whole K range, which streams through shared memory 32 columns at
+// a time):  C[i][k] -= sum_c L[i][c] D[c] L[k][c]  for i >= k, k < ce (pivot
+// columns in the panel, the rest in the update matrix).
+template <class T>
+VB_HD inline void trailing_tile(const KExec& ex, T* pan, T* upd, int np, int nb, int ld, int ka, int kb, int i0,
+                                int k0, int ce, const T* sdv, int dbase, T* sL, T* sR, int ngrp, int grp, int gt,
+                                int gnt, bool act) {
+  constexpr int NBK = 32, TT = 64;
+  const int nf = np + nb;
+  T acc[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+  const int tr = gt % 16, tcl = gt / 16;
+  for (int kc = ka; kc < kb; kc += NBK) {
+    const int nkc = kb - kc < NBK ? kb - kc : NBK;
+    if (act)
+      for (int q = gt; q < TT * NBK; q += gnt) {
+        const int r = q % TT, c = q / TT;
+        sL[q] = (c < nkc && i0 + r < nf) ? pan[(int64_t)(kc + c) * ld + i0 + r] : (T)0;
+        sR[q] = (c < nkc && k0 + r < nf) ? pan[(int64_t)(kc + c) * ld + k0 + r] * sdv[kc + c - dbase] : (T)0;
+      }
+    group_sync(ex, ngrp, grp);
+    if (act && gt < 256)
+      for (int c = 0; c < nkc; ++c) {
+        T li[4], rk[4];
+        for (int a = 0; a < 4; ++a) li[a] = sL[c * TT + tr + 16 * a];
+        for (int bb = 0; bb < 4; ++bb) rk[bb] = sR[c * TT + tcl + 16 * bb];
+        for (int a = 0; a < 4; ++a)
+          for (int bb = 0; bb < 4; ++bb) acc[a][bb] += li[a] * rk[bb];
+      }
+    group_sync(ex, ngrp, grp);
+  }
+  if (act && gt < 256)
+    for (int bb = 0; bb < 4; ++bb) {
+      const int k = k0 + tcl + 16 * bb;
+      if (k >= nf || k >= ce) continue;
+      for (int a = 0; a < 4; ++a) {
+        const int i = i0 + tr + 16 * a;
+        if (i >= nf || i < k) continue;
+        if (k < np) pan[(int64_t)k * ld + i] -= acc[a][bb];
+        else upd[(int64_t)(k - np) * nb + (i - np)] -= acc[a][bb];
+      }
+    }
+}
+
+// Trailing update of a front by the pivot columns [ka, kb) for rows in
+// [r0, nf) and columns in [r0, ce): every lower 64 x 64 tile, one per group
+// of 256 threads; tiles lying between two different deluxe entities are
+// skipped.
 template <class T>
 VB_HD inline void front_trailing(const KExec& ex, T* pan, T* upd, int np, int nb, int ld, int ka, int kb, int r0,
                                  int ce, const T* sdv, int dbase, T* sL, T* sR, int ngrp, int grp, int gt, int gnt,
                                  const FrontGroups& fg) {
-  constexpr int NBK = 32, TT = 64;
+  constexpr int TT = 64;
   const int nf = np + nb;
   if (r0 >= nf || r0 >= ce || ka >= kb) return;
   const int nrt = (nf - r0 + TT - 1) / TT, nct = (ce - r0 + TT - 1) / TT;
@@ -146,40 +186,89 @@ VB_HD inline void front_trailing(const KExec& ex, T* pan, T* upd, int np, int nb
     }
     const int k0 = r0 + tk * TT, i0 = r0 + ti * TT;
     if (act && fg.cross(i0, k0, (k0 + TT < nf ? k0 + TT : nf) - 1)) act = false;
-    T acc[4][4];
-    for (int a = 0; a < 4; ++a)
-      for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
-    const int tr = gt % 16, tcl = gt / 16;
-    for (int kc = ka; kc < kb; kc += NBK) {
-      const int nkc = kb - kc < NBK ? kb - kc : NBK;
-      if (act)
-        for (int q = gt; q < TT * NBK; q += gnt) {
-          const int r = q % TT, c = q / TT;
-          sL[q] = (c < nkc && i0 + r < nf) ? pan[(int64_t)(kc + c) * ld + i0 + r] : (T)0;
-          sR[q] = (c < nkc && k0 + r < nf) ? pan[(int64_t)(kc + c) * ld + k0 + r] * sdv[kc + c - dbase] : (T)0;
-        }
-      group_sync(ex, ngrp, grp);
-      if (act && gt < 256)
-        for (int c = 0; c < nkc; ++c) {
-          T li[4], rk[4];
-          for (int a = 0; a < 4; ++a) li[a] = sL[c * TT + tr + 16 * a];
-          for (int bb = 0; bb < 4; ++bb) rk[bb] = sR[c * TT + tcl + 16 * bb];
-          for (int a = 0; a < 4; ++a)
-            for (int bb = 0; bb < 4; ++bb) acc[a][bb] += li[a] * rk[bb];
-        }
-      group_sync(ex, ngrp, grp);
+    trailing_tile<T>(ex, pan, upd, np, nb, ld, ka, kb, i0, k0, ce, sdv, dbase, sL, sR, ngrp, grp, gt, gnt, act);
+  }
+}
+
+// Columns [jb, jb + nbk) of a front, one by one: pivot sign check, rank-1
+// update of the rest of the block, scaling by the pivot.
+template <class T>
+VB_HD inline void front_columns(const KExec& ex, T* pan, int nf, int ld, const int* piv_type, int* status, int jb,
+                                int nbk) {
+  for (int jj = 0; jj < nbk; ++jj) {
+    const int j = jb + jj;
+    T* cj = pan + (int64_t)j * ld;
+    const T dj = cj[j];
+    if (ex.tid == 0) {
+      const double sgn = (!piv_type || piv_type[j] == DT_VEL) ? 1.0 : -1.0;
+      if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
     }
-    if (act && gt < 256)
-      for (int bb = 0; bb < 4; ++bb) {
-        const int k = k0 + tcl + 16 * bb;
-        if (k >= nf || k >= ce) continue;
-        for (int a = 0; a < 4; ++a) {
-          const int i = i0 + tr + 16 * a;
-          if (i >= nf || i < k) continue;
-          if (k < np) pan[(int64_t)k * ld + i] -= acc[a][bb];
-          else upd[(int64_t)(k - np) * nb + (i - np)] -= acc[a][bb];
-        }
-      }
+    const T inv = (T)1 / dj;
+    const int nk = jb + nbk - j - 1, nr = nf - j - 1;
+    for (int64_t idx = ex.tid; idx < (int64_t)nk * nr; idx += ex.nt) {
+      const int kk = j + 1 + (int)(idx / nr), ii = j + 1 + (int)(idx % nr);
+      if (ii < kk) continue;
+      pan[(int64_t)kk * ld + ii] -= cj[ii] * cj[kk] * inv;
+    }
+    ex.sync();
+    for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) cj[i] *= inv;
+    ex.sync();
+  }
+}
+
+// selective inversion: overwrite the unit lower L11 by L11^{-1} (unit
+// lower), column by column from the right, so that the triangular sweeps
+// become matrix-vector products over independent rows/columns
+template <class T>
+VB_HD inline void front_invert(const KExec& ex, T* pan, int np, int ld) {
+  T* tmp = reinterpret_cast<T*>(ex.smem);
+  for (int j = np - 2; j >= 0; --j) {
+    for (int k = j + 1 + ex.tid; k < np; k += ex.nt) tmp[k] = pan[(int64_t)j * ld + k];
+    ex.sync();
+    for (int i = j + 1 + ex.tid; i < np; i += ex.nt) {
+      T acc = tmp[i];
+      for (int k = j + 1; k < i; ++k) acc += pan[(int64_t)k * ld + i] * tmp[k];
+      pan[(int64_t)j * ld + i] = -acc;
+    }
+    ex.sync();
+  }
+}
+
+// Shared-memory layout of the factorization of one front: per group of 256
+// threads two 64 x 32 operand tiles, then the NBO diagonal entries of the
+// current outer panel.
+template <class T>
+struct FrontSmem {
+  static constexpr int NBK = 32, TT = 64, NBO = 128;
+  T *sL, *sR, *sd;
+  int ngrp, grp, gt, gnt;
+  VB_HD explicit FrontSmem(const KExec& ex) {
+    ngrp = ex.nt >= 512 ? ex.nt / 256 : 1;
+    grp = ngrp > 1 ? ex.tid / 256 : 0;
+    gt = ngrp > 1 ? ex.tid % 256 : ex.tid;
+    gnt = ngrp > 1 ? 256 : ex.nt;
+    sL = reinterpret_cast<T*>(ex.smem) + (int64_t)grp * 2 * TT * NBK;
+    sR = sL + TT * NBK;
+    sd = reinterpret_cast<T*>(ex.smem) + (int64_t)ngrp * 2 * TT * NBK;
+  }
+};
+
+// Outer panel [JB, JE) of a front on the FMA units: inner blocks of NBK
+// columns, each factored column by column and followed by the rank-NBK
+// update of the rest of the outer panel; leaves the panel's D in sm.sd.
+template <class T>
+VB_HD inline void front_panel(const KExec& ex, const FrontSmem<T>& sm, T* pan, T* upd, int np, int nb, int ld,
+                              const int* piv_type, int* status, int JB, int JE, const FrontGroups& fg) {
+  const int nf = np + nb;
+  for (int jb = JB; jb < JE; jb += FrontSmem<T>::NBK) {
+    const int nbk = JE - jb < FrontSmem<T>::NBK ? JE - jb : FrontSmem<T>::NBK;
+    front_columns<T>(ex, pan, nf, ld, piv_type, status, jb, nbk);
+    for (int jj = ex.tid; jj < nbk; jj += ex.nt) sm.sd[jb - JB + jj] = pan[(int64_t)(jb + jj) * ld + jb + jj];
+    ex.sync();
+    const int c0 = jb + nbk;
+    front_trailing<T>(ex, pan, upd, np, nb, ld, jb, c0, c0, JE, sm.sd, JB, sm.sL, sm.sR, sm.ngrp, sm.grp, sm.gt,
+                      sm.gnt, fg);
+    ex.sync();
   }
 }
 
@@ -192,85 +281,52 @@ VB_HD inline void front_trailing(const KExec& ex, T* pan, T* upd, int np, int nb
 // inner blocks of NBK columns (column by column, then a rank-NBK update of
 // the rest of the outer panel), then one rank-NBO update of the trailing
 // front, so that the trailing front is read and written once per NBO
-// columns.  With the tensor cores (tc) the trailing update runs after every
-// NBK columns instead.
+// columns.  With more than 256 threads the CTA works as groups of 256, each
+// on its own trailing tile (named barriers per group).  With the tensor
+// cores (tc) the trailing update runs after every NBK columns instead.
+// want_update = false: the update matrix (border x border block) is not
+// needed by the caller and is not computed (the border rows of the panel,
+// L21, are).
 template <class T>
 VB_HD inline void front_ldlt(const KExec& ex, T* pan, T* upd, int np, int nb, int ld, const int* piv_type,
-                             int* status, TcCtx* tc = nullptr, FrontGroups fg = FrontGroups{nullptr, nullptr, 0}) {
-    const int nf = np + nb;
-    // With more than 256 threads the CTA works as groups of 256, each on its
-    // own trailing tile (named barriers per group), so that large fronts keep
-    // several tiles in flight.
-    constexpr int NBK = 32, TT = 64, NBO = 128;
-    const int ngrp = ex.nt >= 512 ? ex.nt / 256 : 1;
-    const int grp = ngrp > 1 ? ex.tid / 256 : 0;
-    const int gt = ngrp > 1 ? ex.tid % 256 : ex.tid, gnt = ngrp > 1 ? 256 : ex.nt;
-    T* sL = reinterpret_cast<T*>(ex.smem) + (int64_t)grp * 2 * TT * NBK;
-    T* sR = sL + TT * NBK;
-    T* sd = reinterpret_cast<T*>(ex.smem) + (int64_t)ngrp * 2 * TT * NBK;   // NBO diagonal entries
-    const int nbo_w = tc ? NBK : NBO;
-    for (int JB = 0; JB < np; JB += nbo_w) {
-      const int JE = np - JB < nbo_w ? np : JB + nbo_w;
-      for (int jb = JB; jb < JE; jb += NBK) {
-        const int nbk = JE - jb < NBK ? JE - jb : NBK;
-        for (int jj = 0; jj < nbk; ++jj) {
-          const int j = jb + jj;
-          T* cj = pan + (int64_t)j * ld;
-          const T dj = cj[j];
-          if (ex.tid == 0) {
-            const double sgn = (!piv_type || piv_type[j] == DT_VEL) ? 1.0 : -1.0;
-            if (!((double)dj * sgn > 0.0)) flag_error(status, 3);
-          }
-          const T inv = (T)1 / dj;
-          const int nk = jb + nbk - j - 1, nr = nf - j - 1;
-          for (int64_t idx = ex.tid; idx < (int64_t)nk * nr; idx += ex.nt) {
-            const int kk = j + 1 + (int)(idx / nr), ii = j + 1 + (int)(idx % nr);
-            if (ii < kk) continue;
-            pan[(int64_t)kk * ld + ii] -= cj[ii] * cj[kk] * inv;
-          }
-          ex.sync();
-          for (int i = j + 1 + ex.tid; i < nf; i += ex.nt) cj[i] *= inv;
-          ex.sync();
-        }
-        for (int jj = ex.tid; jj < nbk; jj += ex.nt) sd[jb - JB + jj] = pan[(int64_t)(jb + jj) * ld + jb + jj];
-        ex.sync();
-        const int c0 = jb + nbk, m = nf - c0;
-        if (m <= 0) continue;
-#ifdef __CUDA_ARCH__
-        if constexpr (std::is_same<T, float>::value) {
-          if (tc && m > TT) {
-            // tensor-core tiles (split TF32, 128 x 128, accumulators in TMEM)
-            if (!tc_trailing_update(ex, *tc, pan, upd, np, nb, ld, nf, jb, nbk, c0, m, sd + (jb - JB), fg)) return;
-            continue;
-          }
-        }
-#endif
-        // rank-nbk update of the rest of the outer panel (all of the front
-        // when the outer panel is one inner block)
-        front_trailing<T>(ex, pan, upd, np, nb, ld, jb, c0, c0, nbo_w == NBK ? nf : JE, sd, JB, sL, sR, ngrp, grp,
-                          gt, gnt, fg);
-        ex.sync();
-      }
+                             int* status, TcCtx* tc = nullptr, FrontGroups fg = FrontGroups{nullptr, nullptr, 0},
+                             bool want_update = true) {
+  const int nf = np + nb;
+  const int ce_all = want_update ? nf : np;
+  const FrontSmem<T> sm(ex);
+  constexpr int NBK = FrontSmem<T>::NBK, TT = FrontSmem<T>::TT, NBO = FrontSmem<T>::NBO;
+  if (!tc) {
+    for (int JB = 0; JB < np; JB += NBO) {
+      const int JE = np - JB < NBO ? np : JB + NBO;
+      front_panel<T>(ex, sm, pan, upd, np, nb, ld, piv_type, status, JB, JE, fg);
       // rank-(JE - JB) update of the trailing front
-      if (nbo_w > NBK) {
-        front_trailing<T>(ex, pan, upd, np, nb, ld, JB, JE, JE, nf, sd, JB, sL, sR, ngrp, grp, gt, gnt, fg);
-        ex.sync();
-      }
-    }
-    // selective inversion: overwrite the unit lower L11 by L11^{-1} (unit
-    // lower), column by column from the right, so that the triangular
-    // sweeps become matrix-vector products over independent rows/columns
-    T* tmp = reinterpret_cast<T*>(ex.smem);
-    for (int j = np - 2; j >= 0; --j) {
-      for (int k = j + 1 + ex.tid; k < np; k += ex.nt) tmp[k] = pan[(int64_t)j * ld + k];
-      ex.sync();
-      for (int i = j + 1 + ex.tid; i < np; i += ex.nt) {
-        T acc = tmp[i];
-        for (int k = j + 1; k < i; ++k) acc += pan[(int64_t)k * ld + i] * tmp[k];
-        pan[(int64_t)j * ld + i] = -acc;
-      }
+      front_trailing<T>(ex, pan, upd, np, nb, ld, JB, JE, JE, ce_all, sm.sd, JB, sm.sL, sm.sR, sm.ngrp, sm.grp,
+                        sm.gt, sm.gnt, fg);
       ex.sync();
     }
+  } else {
+    for (int jb = 0; jb < np; jb += NBK) {
+      const int nbk = np - jb < NBK ? np - jb : NBK;
+      front_columns<T>(ex, pan, nf, ld, piv_type, status, jb, nbk);
+      for (int jj = ex.tid; jj < nbk; jj += ex.nt) sm.sd[jj] = pan[(int64_t)(jb + jj) * ld + jb + jj];
+      ex.sync();
+      const int c0 = jb + nbk, m = nf - c0;
+      if (m <= 0) continue;
+#ifdef __CUDA_ARCH__
+      if constexpr (std::is_same<T, float>::value) {
+        if (m > TT) {
+          // tensor-core tiles (split TF32, 128 x 128, accumulators in TMEM)
+          if (!tc_trailing_update(ex, *tc, pan, upd, np, nb, ld, nf, jb, nbk, c0, m, sm.sd, fg)) return;
+          continue;
+        }
+      }
+#endif
+      front_trailing<T>(ex, pan, upd, np, nb, ld, jb, c0, c0, ce_all, sm.sd, jb, sm.sL, sm.sR, sm.ngrp, sm.grp,
+                        sm.gt, sm.gnt, fg);
+      ex.sync();
+    }
+  }
+  front_invert<T>(ex, pan, np, ld);
 }
 
 template <class T, bool UseTC = false>
@@ -281,7 +337,15 @@ struct KFactor {
   T* U;
   int* status;
   size_t tc_smem_off = 0;   // UseTC: byte offset of the tensor-core tiles in shared memory
+  // mode 0: the whole front; the split form of a level with few large
+  // fronts: 1 assembly only, 2 the outer panel [JB, JB + NBO) (its trailing
+  // update is KFactorTiles), 3 the inversion of L11 only
+  int mode = 0, JB = 0;
   __device__ void operator()(const KExec& ex, int blk) const {
+    if (mode != 0) {
+      split_step(ex, blk);
+      return;
+    }
     if constexpr (UseTC) {
       TcCtx c;
       c.tiles = reinterpret_cast<float*>(reinterpret_cast<char*>(ex.smem) + tc_smem_off);
@@ -295,7 +359,36 @@ struct KFactor {
     }
     body(ex, blk, nullptr);
   }
+  __device__ void split_step(const KExec& ex, int blk) const {
+    const int t = list[blk];
+    const NodeDev N = V.nodes[t];
+    const ProbDev P = V.probs[N.prob];
+    const int np = N.np, nb = N.nb, ld = N.ld;
+    T* pan = F + N.panel_off;
+    T* upd = U + N.upd_off;
+    if (mode == 1) {
+      assemble(ex, blk);
+    } else if (mode == 2) {
+      if (JB >= np) return;
+      const int JE = np - JB < FrontSmem<T>::NBO ? np : JB + FrontSmem<T>::NBO;
+      const FrontSmem<T> sm(ex);
+      const FrontGroups fg{V.border + N.border_off, P.kind == PK_DELUXE ? V.bgrp + P.pos_off : nullptr, np};
+      front_panel<T>(ex, sm, pan, upd, np, nb, ld, V.dtype + P.pos_off + N.p0, status, JB, JE, fg);
+    } else {
+      front_invert<T>(ex, pan, np, ld);
+    }
+  }
   __device__ void body(const KExec& ex, int blk, TcCtx* tc) const {
+    assemble(ex, blk);
+    const int t = list[blk];
+    const NodeDev N = V.nodes[t];
+    const ProbDev P = V.probs[N.prob];
+    const FrontGroups fg{V.border + N.border_off, P.kind == PK_DELUXE ? V.bgrp + P.pos_off : nullptr, N.np};
+    front_ldlt<T>(ex, F + N.panel_off, U + N.upd_off, N.np, N.nb, N.ld, V.dtype + P.pos_off + N.p0, status, tc, fg);
+  }
+  // zero the front, add the original matrix entries of its pivot columns
+  // and the children's update matrices
+  __device__ void assemble(const KExec& ex, int blk) const {
     const int t = list[blk];
     const NodeDev N = V.nodes[t];
     const ProbDev P = V.probs[N.prob];
@@ -395,8 +488,39 @@ struct KFactor {
       }
       ex.sync();
     }
-    const FrontGroups fg{bord, P.kind == PK_DELUXE ? V.bgrp + P.pos_off : nullptr, np};
-    front_ldlt<T>(ex, pan, upd, np, nb, ld, V.dtype + P.pos_off + N.p0, status, tc, fg);
+    (void)bord;
+  }
+};
+
+// The trailing update of the split form: one 64 x 64 tile per CTA of 256
+// threads, of one front of the level, by the pivot columns [JB, JE) of its
+// current outer panel (D read from the panel's diagonal).
+struct FrontTile {
+  int node, i0, k0;
+};
+template <class T>
+struct KFactorTiles {
+  BddcView V;
+  const FrontTile* tiles;
+  T* F;
+  T* U;
+  int JB;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    const FrontTile tl = tiles[blk];
+    const NodeDev N = V.nodes[tl.node];
+    const ProbDev P = V.probs[N.prob];
+    const int np = N.np, nb = N.nb, nf = np + nb, ld = N.ld;
+    const int JE = np - JB < FrontSmem<T>::NBO ? np : JB + FrontSmem<T>::NBO;
+    const FrontGroups fg{V.border + N.border_off, P.kind == PK_DELUXE ? V.bgrp + P.pos_off : nullptr, np};
+    if (fg.cross(tl.i0, tl.k0, (tl.k0 + 64 < nf ? tl.k0 + 64 : nf) - 1)) return;
+    T* pan = F + N.panel_off;
+    T* sL = reinterpret_cast<T*>(ex.smem);
+    T* sR = sL + 64 * 32;
+    T* sd = sR + 64 * 32;
+    for (int c = ex.tid; c < JE - JB; c += ex.nt) sd[c] = pan[(int64_t)(JB + c) * ld + JB + c];
+    ex.sync();
+    trailing_tile<T>(ex, pan, U + N.upd_off, np, nb, ld, JB, JE, tl.i0, tl.k0, nf, sd, JB, sL, sR, 1, 0, ex.tid,
+                     ex.nt, true);
   }
 };
 
