@@ -210,44 +210,125 @@ VB_HD inline void hh_inplace(const BddcView& V, const MacroDev& G, double* c) {
   }
 }
 
-// Y = K_i X on subdomain-local dense blocks (rows: local velocity DOFs, then
-// local pressures; NC columns, column-major with leading dimension nloc).
-struct KElemMatvec {
-  BddcView V;
+// Column-major subdomain blocks (entry (row, c) of subdomain i at
+// loc_off*NC + c*nloc + row) to one row-major array over all local rows
+// (global local row g = loc_off + row at g*NC + c); DF: as FP32 (high, low)
+// pairs.  One CTA per 32 consecutive local rows, NC in tiles of 32.
+template <bool DF>
+struct KToRowMajor {
   const int64_t* row_ptr;   // prefix of nloc over subdomains
   int nsub;
+  int64_t loc;
   const double* X;
+  void* Y;
+  int NC;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    double* tile = ex.smem;   // [32][33]
+    const int tr = ex.tid & 31, tc = ex.tid >> 5, ntc = ex.nt >> 5;
+    const int64_t g = (int64_t)blk * 32 + tr;
+    int lo = 0, hi = nsub - 1;
+    if (g < loc)
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (row_ptr[mid] <= g) lo = mid; else hi = mid - 1;
+      }
+    const int64_t off = row_ptr[lo], nloc = row_ptr[lo + 1] - off;
+    for (int c0 = 0; c0 < NC; c0 += 32) {
+      for (int c = tc; c < 32; c += ntc)
+        tile[tr * 33 + c] = (g < loc && c0 + c < NC) ? X[off * NC + (int64_t)(c0 + c) * nloc + (g - off)] : 0.0;
+      ex.sync();
+      for (int r = tc; r < 32; r += ntc) {
+        const int64_t gr = (int64_t)blk * 32 + r;
+        if (gr >= loc || c0 + tr >= NC) continue;
+        const double v = tile[r * 33 + tr];
+        if (DF) {
+          const float h = (float)v;
+          reinterpret_cast<float2*>(Y)[gr * NC + c0 + tr] = make_float2(h, (float)(v - (double)h));
+        } else {
+          reinterpret_cast<double*>(Y)[gr * NC + c0 + tr] = v;
+        }
+      }
+      ex.sync();
+    }
+  }
+};
+
+// Y = K_i X on the subdomain-local dense blocks, X and Y row-major over all
+// local rows (row g at g*NC; local velocity DOFs, then local pressures).
+// One warp per row, each lane 4 columns of a 128-column block, so that every
+// load of X serves the 32 lanes from consecutive addresses.  DF: X given as
+// FP32 (high, low) pairs and the A_e terms in double-float arithmetic on the
+// FP32 units from V.A2; the B_e terms stay FP64.
+template <bool DF>
+struct KElemMatvecRM {
+  BddcView V;
+  const int64_t* row_ptr;
+  int nsub;
+  const void* X;
   double* Y;
   int NC;
-  VB_HD void operator()(const KExec& ex, int blk) const {
+  __device__ double xval(int64_t i) const {
+    if (DF) {
+      const float2 x = reinterpret_cast<const float2*>(X)[i];
+      return (double)x.x + (double)x.y;
+    }
+    return reinterpret_cast<const double*>(X)[i];
+  }
+  __device__ void operator()(const KExec& ex, int blk) const {
     int lo = 0, hi = nsub - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
       if (row_ptr[mid] <= blk) lo = mid; else hi = mid - 1;
     }
     const SubDev S = V.subs[lo];
-    const int nloc = S.nv + S.npress;
     const int row = (int)(blk - row_ptr[lo]);
-    const double* Xs = X + S.loc_off * NC;
-    double* Ys = Y + S.loc_off * NC;
+    const int64_t xb = S.loc_off * NC;   // row l of the subdomain at xb + l*NC
     const int npk = V.np;
     const int* ellp = V.elloc_ptr + S.ellocptr_off;
-    for (int c = ex.tid; c < NC; c += ex.nt) {
-      double acc = 0.0;
+    const int lane = ex.tid;
+    for (int cb = 0; cb < NC; cb += 128) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+      bool ok[4];
+      for (int j = 0; j < 4; ++j) ok[j] = cb + lane + 32 * j < NC;
       if (row < S.nv) {
         const int* vp = V.vadj_ptr + S.vadj_ptr_off;
         for (int q = vp[row]; q < vp[row + 1]; ++q) {
           const int le = V.vadj[S.vadj_off + 2 * q], a = V.vadj[S.vadj_off + 2 * q + 1];
           const int e = V.sub_elems[S.elem_off + le];
           const int nK = (int)(V.offK[e + 1] - V.offK[e]);
-          const double* Ae = V.A + V.offK2[e];
           const double* Be = V.B + (int64_t)npk * V.offK[e];
           const int* el = V.elloc + S.elloc_off + ellp[le];
-          for (int b = 0; b < nK + npk; ++b) {
+          if (DF) {
+            const float2* Ae2 = V.A2 + V.offK2[e] + (int64_t)a * nK;
+            for (int b = 0; b < nK; ++b) {
+              const int l = el[b];
+              if (l < 0) continue;
+              const float2 v = Ae2[b];
+              const float2* xr = reinterpret_cast<const float2*>(X) + xb + (int64_t)l * NC + cb + lane;
+              for (int j = 0; j < 4; ++j)
+                if (ok[j]) {
+                  const float2 x = xr[32 * j];
+                  df_fma(sh[j], sl[j], v.x, v.y, x.x, x.y);
+                }
+            }
+          } else {
+            const double* Ae = V.A + V.offK2[e] + (int64_t)a * nK;
+            for (int b = 0; b < nK; ++b) {
+              const int l = el[b];
+              if (l < 0) continue;
+              const double v = Ae[b];
+              const double* xr = reinterpret_cast<const double*>(X) + xb + (int64_t)l * NC + cb + lane;
+              for (int j = 0; j < 4; ++j)
+                if (ok[j]) acc[j] += v * xr[32 * j];
+            }
+          }
+          for (int b = nK; b < nK + npk; ++b) {
             const int l = el[b];
             if (l < 0) continue;
-            const double v = b < nK ? Ae[(int64_t)a * nK + b] : Be[(int64_t)(b - nK) * nK + a];
-            acc += v * Xs[(int64_t)c * nloc + l];
+            const double v = Be[(int64_t)(b - nK) * nK + a];
+            for (int j = 0; j < 4; ++j)
+              if (ok[j]) acc[j] += v * xval(xb + (int64_t)l * NC + cb + lane + 32 * j);
           }
         }
       } else {
@@ -260,11 +341,94 @@ struct KElemMatvec {
         for (int b = 0; b < nK; ++b) {
           const int l = el[b];
           if (l < 0) continue;
-          acc += Be[(int64_t)a * nK + b] * Xs[(int64_t)c * nloc + l];
+          const double v = Be[(int64_t)a * nK + b];
+          for (int j = 0; j < 4; ++j)
+            if (ok[j]) acc[j] += v * xval(xb + (int64_t)l * NC + cb + lane + 32 * j);
         }
       }
-      Ys[(int64_t)c * nloc + row] = acc;
+      for (int j = 0; j < 4; ++j)
+        if (ok[j]) Y[xb + (int64_t)row * NC + cb + lane + 32 * j] = acc[j] + (DF ? (double)sh[j] + (double)sl[j] : 0.0);
     }
+  }
+};
+
+// Y = K_i W for the coarse basis before its Neumann correction.  Row l of W
+// is nonzero only in the columns [wcols[l].x, wcols[l].x + wcols[l].y): the
+// primal coordinates of the entity holding interface DOF l, or the p_0
+// column at a constant pressure coefficient.  One warp per row walks the
+// row's element entries in the order of the dense product (element, then
+// column) and adds only the terms whose W row is nonzero, so every column
+// sums the same nonzero terms in the same order as K_i W formed densely.
+// Y must be cleared beforehand: rows without such terms are not written.
+struct KElemMatvecW {
+  BddcView V;
+  const int64_t* row_ptr;   // prefix of nloc over subdomains
+  int nsub;
+  const double* X;
+  const int2* wcols;        // per local row at loc_off: first column, count
+  double* Y;
+  int NC;
+  __device__ void operator()(const KExec& ex, int blk) const {
+    int lo = 0, hi = nsub - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (row_ptr[mid] <= blk) lo = mid; else hi = mid - 1;
+    }
+    const SubDev S = V.subs[lo];
+    const int nloc = S.nv + S.npress;
+    const int row = (int)(blk - row_ptr[lo]);
+    const double* Xs = X + S.loc_off * NC;
+    const int2* wc = wcols + S.loc_off;
+    const int npk = V.np;
+    const int* ellp = V.elloc_ptr + S.ellocptr_off;
+    const int lane = ex.tid;
+    double* acc = ex.smem;   // [NC]
+    for (int c = lane; c < NC; c += 32) acc[c] = 0.0;
+    bool any = false;
+    // the entries [0, nb) of one element row: coefficient coef(b), local index el[b]
+    auto walk = [&](const int* el, int nb, auto coef) {
+      for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        const int l = b < nb ? el[b] : -1;
+        const int2 w = l >= 0 ? wc[l] : make_int2(0, 0);
+        const double v = w.y > 0 ? coef(b) : 0.0;
+        unsigned m = __ballot_sync(0xffffffffu, w.y > 0);
+        any |= m != 0;
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const int ls = __shfl_sync(0xffffffffu, l, src);
+          const int c0 = __shfl_sync(0xffffffffu, w.x, src), cn = __shfl_sync(0xffffffffu, w.y, src);
+          const double vs = __shfl_sync(0xffffffffu, v, src);
+          __syncwarp();
+          for (int t = lane; t < cn; t += 32) acc[c0 + t] += vs * Xs[(int64_t)(c0 + t) * nloc + ls];
+        }
+      }
+    };
+    if (row < S.nv) {
+      const int* vp = V.vadj_ptr + S.vadj_ptr_off;
+      for (int q = vp[row]; q < vp[row + 1]; ++q) {
+        const int le = V.vadj[S.vadj_off + 2 * q], a = V.vadj[S.vadj_off + 2 * q + 1];
+        const int e = V.sub_elems[S.elem_off + le];
+        const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+        const double* Ae = V.A + V.offK2[e];
+        const double* Be = V.B + (int64_t)npk * V.offK[e];
+        walk(V.elloc + S.elloc_off + ellp[le], nK + npk, [&](int b) {
+          return b < nK ? Ae[(int64_t)a * nK + b] : Be[(int64_t)(b - nK) * nK + a];
+        });
+      }
+    } else {
+      const int q = row - S.nv;
+      const int le = q / npk, a = q % npk;
+      const int e = V.sub_elems[S.elem_off + le];
+      const int nK = (int)(V.offK[e + 1] - V.offK[e]);
+      const double* Be = V.B + (int64_t)npk * V.offK[e];
+      walk(V.elloc + S.elloc_off + ellp[le], nK, [&](int b) { return Be[(int64_t)a * nK + b]; });
+    }
+    __syncwarp();
+    if (!any) return;
+    double* Ys = Y + S.loc_off * NC;
+    for (int c = lane; c < NC; c += 32) Ys[(int64_t)c * nloc + row] = acc[c];
   }
 };
 
@@ -347,8 +511,8 @@ struct GramTile {
 struct KGramTiled {
   BddcView V;
   const GramTile* tiles;
-  const double* PHI;
-  const double* KPHI;
+  const double* PHI;    // column-major subdomain blocks
+  const double* KPHI;   // row-major over all local rows (row g at g*NC)
   double* SG;
   int NC;
   static constexpr int TR = 64, TP = 33;   // rows per chunk, padded tile width
@@ -357,7 +521,7 @@ struct KGramTiled {
     const SubDev S = V.subs[tl.sub];
     const int nloc = S.nv + S.npress, ncl = S.ncl;
     const double* ph = PHI + S.loc_off * NC;
-    const double* kp = KPHI + S.loc_off * NC;
+    const double* kp = KPHI + S.loc_off * NC;   // row l at l*NC
     double* sA = ex.smem;            // [TR][TP]: Phi rows, columns a0 ..
     double* sB = sA + TR * TP;       // [TR][TP]: K Phi rows, columns b0 ..
     const int a = ex.tid / 8, bq = (ex.tid % 8) * 4;
@@ -366,9 +530,9 @@ struct KGramTiled {
       const int nr = nloc - r0 < TR ? nloc - r0 : TR;
       for (int q = ex.tid; q < TR * 32; q += ex.nt) {
         const int c = q / TR, r = q % TR;
-        const bool okr = r < nr;
-        sA[r * TP + c] = (okr && tl.a0 + c < ncl) ? ph[(int64_t)(tl.a0 + c) * nloc + r0 + r] : 0.0;
-        sB[r * TP + c] = (okr && tl.b0 + c < ncl) ? kp[(int64_t)(tl.b0 + c) * nloc + r0 + r] : 0.0;
+        sA[r * TP + c] = (r < nr && tl.a0 + c < ncl) ? ph[(int64_t)(tl.a0 + c) * nloc + r0 + r] : 0.0;
+        const int c2 = q % 32, r2 = q / 32;
+        sB[r2 * TP + c2] = (r2 < nr && tl.b0 + c2 < ncl) ? kp[(int64_t)(r0 + r2) * NC + tl.b0 + c2] : 0.0;
       }
       ex.sync();
       for (int r = 0; r < nr; ++r) {
@@ -509,7 +673,8 @@ struct KDeluxeFront {
     }
     for (int64_t idx = ex.tid; idx < (int64_t)nd * nd; idx += ex.nt) upd[idx] = 0.0;
     ex.sync();
-    front_ldlt<double>(ex, pan, upd, nd, nd, nf, nullptr, status);
+    // only L21 = S_i L11^{-T} Dg^{-1} is used: the border block is not formed
+    front_ldlt<double>(ex, pan, upd, nd, nd, nf, nullptr, status, nullptr, FrontGroups{nullptr, nullptr, 0}, false);
   }
 };
 
@@ -720,6 +885,55 @@ VB_HD inline void hh_par(const KExec& ex, const BddcView& V, const MacroDev& G, 
     ex.sync();
   }
 }
+
+// Coarse basis columns before the Neumann correction: entity g's primal
+// coordinate q in sharing subdomain share[si] is the column H e_q of the
+// entity's change of basis, scattered to the subdomain's local velocity
+// DOFs (local column c0 + q); W is zero elsewhere (cleared beforehand).
+struct CoarseWTask {
+  int g, si, c0;
+};
+struct KCoarseW {
+  BddcView V;
+  const CoarseWTask* tasks;
+  double* W;      // per subdomain: ncl columns, leading dimension nv + npress, at loc_off NC
+  int2* wcols;    // per local row: the columns where W is nonzero (first, count)
+  int NC;
+  VB_HD void operator()(const KExec& ex, int t) const {
+    const CoarseWTask T = tasks[t];
+    const MacroDev G = V.macros[T.g];
+    const SubDev S = V.subs[V.share[G.share_off + T.si]];
+    const int nloc = S.nv + S.npress;
+    const int* gi = V.gif + G.gif_off + (int64_t)T.si * G.n;
+    double* c = ex.smem;
+    double* red = ex.smem + G.n;
+    for (int q = 0; q < G.r; ++q) {
+      for (int a = ex.tid; a < G.n; a += ex.nt) c[a] = a == q ? 1.0 : 0.0;
+      ex.sync();
+      hh_par(ex, V, G, c, red);
+      double* col = W + S.loc_off * NC + (int64_t)(T.c0 + q) * nloc;
+      for (int a = ex.tid; a < G.n; a += ex.nt) col[V.iface[S.iface_off + gi[a]]] = c[a];
+      ex.sync();
+    }
+    for (int a = ex.tid; a < G.n; a += ex.nt) wcols[S.loc_off + V.iface[S.iface_off + gi[a]]] = make_int2(T.c0, G.r);
+  }
+};
+// the last local column: the subdomain's constant pressure p_0 = 1
+struct KCoarseWP0 {
+  BddcView V;
+  double* W;
+  int2* wcols;
+  int NC;
+  VB_HD void operator()(const KExec& ex, int i) const {
+    const SubDev S = V.subs[i];
+    const int nloc = S.nv + S.npress;
+    double* col = W + S.loc_off * NC + (int64_t)(S.ncl - 1) * nloc + S.nv;
+    for (int le = ex.tid; le < S.ne; le += ex.nt) {
+      col[(int64_t)le * V.np] = 1.0;
+      wcols[S.loc_off + S.nv + (int64_t)le * V.np] = make_int2(S.ncl - 1, 1);
+    }
+  }
+};
 
 // (1) r_G -> c = H^T r_G: primal part to the coarse rhs, dual part kept
 struct KRestrict {
@@ -2457,42 +2671,40 @@ static void setup_core(bddc* b, const int32_t* part) {
     int NC = 1;
     for (auto& S : b->h_subs) NC = std::max(NC, S.ncl);
     {
-      std::vector<double> W((size_t)loc * NC, 0.0);
+      // W on the device: the primal columns H e_q of every (entity, sharing
+      // subdomain) pair, then the p_0 columns
+      std::vector<CoarseWTask> wt;
       for (int i = 0; i < N; ++i) {
         const Subdomain& S = H.subs[i];
-        const SubDev& D = b->h_subs[i];
-        const int nloc = D.nv + D.npress;
-        double* Ws = &W[(size_t)D.loc_off * NC];
         int c = 0;
         for (int gi : S.macros) {
           const Macro& G = H.macros[gi];
-          const int n = (int)G.dofs.size();
-          std::vector<double> e(n), col(n);
-          for (int q = 0; q < G.r; ++q, ++c) {
-            if (G.hv.empty()) {
-              std::fill(col.begin(), col.end(), 0.0);
-              col[q] = 1.0;
-            } else {
-              std::fill(e.begin(), e.end(), 0.0);
-              e[q] = 1.0;
-              hh_apply(G, e.data(), col.data());
-            }
-            for (int a = 0; a < n; ++a) {
-              int v = (int)(std::lower_bound(S.vdof.begin(), S.vdof.end(), G.dofs[a]) - S.vdof.begin());
-              Ws[(size_t)c * nloc + v] = col[a];
-            }
-          }
+          const int si = (int)(std::find(G.share.begin(), G.share.end(), i) - G.share.begin());
+          VB_CHECK(si < (int)G.share.size(), VEM_EINVAL, "coarse basis: entity not shared by its subdomain");
+          if (G.r > 0) wt.push_back({gi, si, c});
+          c += G.r;
         }
-        for (int le = 0; le < D.ne; ++le) Ws[(size_t)c * nloc + D.nv + le * np] = 1.0;   // p_0 column
-        VB_CHECK(c + 1 == D.ncl, VEM_EINVAL, "coarse column count mismatch");
+        VB_CHECK(c + 1 == b->h_subs[i].ncl, VEM_EINVAL, "coarse column count mismatch");
       }
-      DBuf<double> dW, KW((size_t)loc * NC), PHI((size_t)loc * NC);
-      upload_vec(dW, W, st);
+      DBuf<double> dW((size_t)loc * NC), KW((size_t)loc * NC), PHI((size_t)loc * NC);
+      DBuf<int2> wcols(std::max<int64_t>(loc, 1));
+      dW.zero(st);
+      wcols.zero(st);
+      {
+        DBuf<CoarseWTask> dwt;
+        upload_vec(dwt, wt, st);
+        if (!wt.empty())
+          launch(KCoarseW{V, dwt.p, dW.p, wcols.p, NC}, (int64_t)wt.size(), 256,
+                 sizeof(double) * (max_macro_n(b) + 256 + 8), st);
+        launch(KCoarseWP0{V, dW.p, wcols.p, NC}, N, 256, 0, st);
+        VB_CUDA(cudaStreamSynchronize(st));
+      }
       std::vector<int64_t> rp(N + 1, 0);
       for (int i = 0; i < N; ++i) rp[i + 1] = rp[i] + b->h_subs[i].nv + b->h_subs[i].npress;
       DBuf<int64_t> drp;
       upload_vec(drp, rp, st);
-      launch(KElemMatvec{V, drp.p, N, dW.p, KW.p, NC}, loc, 32, 0, st);
+      KW.zero(st);
+      launch(KElemMatvecW{V, drp.p, N, dW.p, wcols.p, KW.p, NC}, loc, 32, sizeof(double) * NC, st);
       mark("t_coarse_rhs_ms");
       // constrained Neumann solves for the coarse basis, CH columns at a time
       // (the right-hand-side, front-vector and refinement stores scale with CH)
@@ -2506,7 +2718,15 @@ static void setup_core(bddc* b, const int32_t* part) {
         launch(KPhiAssemble{V, dW.p, b->XN.p, PHI.p, NC, c0, ch}, (int64_t)N * ch, 256, sizeof(double) * 256, st);
       }
       mark("t_coarse_solves_ms");
-      launch(KElemMatvec{V, drp.p, N, PHI.p, KW.p, NC}, loc, 32, 0, st);
+      // K Phi with Phi and the product row-major (coalesced over columns):
+      // the Phi copy takes the buffer of W, the product that of K W
+      if (V.A2) {
+        launch(KToRowMajor<true>{drp.p, N, loc, PHI.p, dW.p, NC}, (loc + 31) / 32, 256, sizeof(double) * 32 * 33, st);
+        launch(KElemMatvecRM<true>{V, drp.p, N, dW.p, KW.p, NC}, loc, 32, 0, st);
+      } else {
+        launch(KToRowMajor<false>{drp.p, N, loc, PHI.p, dW.p, NC}, (loc + 31) / 32, 256, sizeof(double) * 32 * 33, st);
+        launch(KElemMatvecRM<false>{V, drp.p, N, dW.p, KW.p, NC}, loc, 32, 0, st);
+      }
       DBuf<double> SG((size_t)N * NC * NC);
       {
         std::vector<GramTile> gt;
