@@ -57,6 +57,7 @@ struct Batch {
   DBuf<SolveTask> d_ptask, d_btask, d_fptask;
   DBuf<double> FV;
   int fv_nrhs = 0;
+  DBuf<float> XF;                         // FP32 sweeps: right-hand sides and solutions in FP32
 };
 
 }  // namespace vb
@@ -1582,15 +1583,41 @@ static void invalidate_graphs(bddc* b) {
   if (b->app_exec) { cudaGraphExecDestroy(b->app_exec); b->app_exec = nullptr; }
 }
 
+template <class S, class D>
+struct KCast {   // y = x converted, n entries
+  const S* x;
+  D* y;
+  int64_t n;
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const int64_t i = (int64_t)blk * ex.nt + ex.tid;
+    if (i < n) y[i] = (D)x[i];
+  }
+};
+
+// The sweep vectors are kept in the factor's precision T: for FP32 factors
+// X is converted once on entry and once on exit, and the front and update
+// vectors are FP32 views of their stores.
 template <class T, int RB>
-static void sweep_batch_rb(bddc* b, Batch& B, const BddcView& V, const T* Fp, double* X, double* UV, int nrhs) {
+static void sweep_batch_rb(bddc* b, Batch& B, const BddcView& V, const T* Fp, double* Xd, double* UVd, int nrhs) {
   cudaStream_t st = b->stream;
   if (B.fv_nrhs < nrhs) {
     invalidate_graphs(b);
     B.FV.alloc(std::max<int64_t>(B.nfv * nrhs, 1));
     B.fv_nrhs = nrhs;
   }
-  const size_t sm = sizeof(double) * (RB * (B.maxnf + 8));
+  const int64_t nx = B.vec_n * nrhs;
+  T* X = reinterpret_cast<T*>(Xd);
+  T* UV = reinterpret_cast<T*>(UVd);
+  T* FV = reinterpret_cast<T*>(B.FV.p);
+  if constexpr (std::is_same<T, float>::value) {
+    if ((int64_t)B.XF.n < nx) {
+      invalidate_graphs(b);
+      B.XF.alloc(std::max<int64_t>(nx, 1));
+    }
+    X = B.XF.p;
+    launch(KCast<double, float>{Xd, X, nx}, (nx + 255) / 256, 256, 0, st);
+  }
+  const size_t sm = sizeof(T) * (RB * (B.maxnf + 8));
   const size_t smf = sm + sizeof(double) * FWARPS * FVEC * 4 * RB;   // + partial sums of the warps
   VB_CHECK(smf <= 227 * 1024, VEM_EINVAL, "front too large for the sweep kernels' shared memory");
   const int64_t* fvo = b->d_fvoff.p;
@@ -1598,30 +1625,31 @@ static void sweep_batch_rb(bddc* b, Batch& B, const BddcView& V, const T* Fp, do
     const int cnt = B.level_ptr[h + 1] - B.level_ptr[h];
     const int fp_t = B.fptask_ptr[h + 1] - B.fptask_ptr[h];
     const int nb_t = B.btask_ptr[h + 1] - B.btask_ptr[h];
-    launch(KFwdGather{V, B.d_levels.p + B.level_ptr[h], X, UV, B.FV.p, fvo, nrhs}, cnt, 128, 0, st);
+    launch(KFwdGather<T>{V, B.d_levels.p + B.level_ptr[h], X, UV, FV, fvo, nrhs}, cnt, 128, 0, st);
     // FP32, single right-hand side: registers capped for 6 (forward) or 5
     // (backward) resident CTAs per SM
     // (these kernels wait on memory; occupancy hides the latency)
     if constexpr (RB == 1 && std::is_same<T, float>::value) {
-      launch_lb<6>(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, fp_t, smf, st);
-      launch_lb<6>(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, smf, st);
+      launch_lb<6>(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, FV, fvo, X, nrhs}, fp_t, smf, st);
+      launch_lb<6>(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, FV, fvo, X, UV, nrhs}, nb_t, smf, st);
     } else {
-      launch(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, fp_t, 32 * FWARPS, smf,
+      launch(KFwdPivots<T, RB>{V, B.d_fptask.p + B.fptask_ptr[h], Fp, FV, fvo, X, nrhs}, fp_t, 32 * FWARPS, smf,
              st);
-      launch(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, B.FV.p, fvo, X, UV, nrhs}, nb_t, 32 * FWARPS,
+      launch(KFwdBorder<T, RB>{V, B.d_btask.p + B.btask_ptr[h], Fp, FV, fvo, X, UV, nrhs}, nb_t, 32 * FWARPS,
              smf, st);
     }
   }
   for (int h = B.maxh; h >= 0; --h) {
     const int np_t = B.ptask_ptr[h + 1] - B.ptask_ptr[h];
     if constexpr (RB == 1 && std::is_same<T, float>::value) {
-      launch_lb<5>(KBwdBorder<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, B.FV.p, fvo, nrhs}, np_t, sm, st);
-      launch_lb<5>(KBwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, sm, st);
+      launch_lb<5>(KBwdBorder<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, FV, fvo, nrhs}, np_t, sm, st);
+      launch_lb<5>(KBwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, FV, fvo, X, nrhs}, np_t, sm, st);
     } else {
-      launch(KBwdBorder<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, B.FV.p, fvo, nrhs}, np_t, 256, sm, st);
-      launch(KBwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, B.FV.p, fvo, X, nrhs}, np_t, 256, sm, st);
+      launch(KBwdBorder<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, X, FV, fvo, nrhs}, np_t, 256, sm, st);
+      launch(KBwdPivots<T, RB>{V, B.d_ptask.p + B.ptask_ptr[h], Fp, FV, fvo, X, nrhs}, np_t, 256, sm, st);
     }
   }
+  if constexpr (std::is_same<T, float>::value) launch(KCast<float, double>{X, Xd, nx}, (nx + 255) / 256, 256, 0, st);
 }
 
 template <class T>
@@ -2451,6 +2479,7 @@ static void setup_core(bddc* b, const int32_t* part) {
         }
       }
     }
+    mark("t_flatten_ms");
     // ---------------- upload structure
     upload_vec(b->d_border, border, st);
     upload_vec(b->d_children, children, st);

@@ -547,14 +547,18 @@ struct SolveTask {
 constexpr int TASK = 128;
 constexpr int BCOLS = 32;   // pivot columns per backward-sweep task (4 per warp)
 
+// The vectors of a sweep (right-hand sides and solutions X, front vectors
+// FV, update vectors UV) are held in the factor's precision T.
+
 // forward (1): front vector of each node = its own right-hand side entries
 // plus the children's update vectors (extend-add), one CTA per node
+template <class T>
 struct KFwdGather {
   BddcView V;
   const int* list;
-  const double* X;   // [vec_off*nrhs + r*n + pos]
-  const double* UV;  // [uvec_off*nrhs + r*nb + i]
-  double* FV;        // [fv_off*nrhs + r*nf + i]
+  const T* X;    // [vec_off*nrhs + r*n + pos]
+  const T* UV;   // [uvec_off*nrhs + r*nb + i]
+  T* FV;         // [fv_off*nrhs + r*nf + i]
   const int64_t* fv_off;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
@@ -563,14 +567,14 @@ struct KFwdGather {
     const ProbDev P = V.probs[N.prob];
     const int np = N.np, nf = N.np + N.nb;
     for (int r = 0; r < nrhs; ++r) {
-      const double* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
-      double* f = FV + fv_off[t] * nrhs + (int64_t)r * nf;
-      for (int i = ex.tid; i < nf; i += ex.nt) f[i] = i < np ? x[N.p0 + i] : 0.0;
+      const T* x = X + P.vec_off * nrhs + (int64_t)r * P.n;
+      T* f = FV + fv_off[t] * nrhs + (int64_t)r * nf;
+      for (int i = ex.tid; i < nf; i += ex.nt) f[i] = i < np ? x[N.p0 + i] : (T)0;
       ex.sync();
       for (int c = 0; c < N.nchild; ++c) {
         const NodeDev C = V.nodes[V.children[N.first_child + c]];
         const int* rel = V.rel + C.rel_off;
-        const double* uc = UV + C.uvec_off * nrhs + (int64_t)r * C.nb;
+        const T* uc = UV + C.uvec_off * nrhs + (int64_t)r * C.nb;
         for (int i = ex.tid; i < C.nb; i += ex.nt) f[rel[i]] += uc[i];
         ex.sync();
       }
@@ -607,10 +611,10 @@ VB_HD inline void vload(const float* p, float* o) {
   o[3] = v.w;
 }
 
-// The sweeps accumulate in the factor's precision: FP64 arithmetic runs at
-// a small fraction of the FP32 rate on this GPU, and an FP32-local solve
-// is followed by refinement with an FP64 residual anyway.  Right-hand sides
-// are staged in shared memory in that precision too.
+// The sweeps accumulate and store in the factor's precision: FP64 arithmetic
+// (conversions included) runs at a small fraction of the FP32 rate on this
+// GPU, and an FP32-local solve is followed by refinement with an FP64
+// residual anyway.
 
 // Forward tasks cover up to FVEC W-row vectors (one per lane); the warps of
 // the CTA split the column range and their partial sums are added in a
@@ -665,9 +669,9 @@ struct KFwdPivots {
   BddcView V;
   const SolveTask* tasks;   // {node, first vector, vectors}
   const T* F;
-  const double* FV;
+  const T* FV;
   const int64_t* fv_off;
-  double* X;
+  T* X;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
     constexpr int W = VecW<T>::W;
@@ -687,7 +691,7 @@ struct KFwdPivots {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
       for (int q = ex.tid; q < RB * kmax; q += ex.nt) {
         const int r = q / kmax, k = q % kmax;
-        fs[q] = r < nr ? (T)FV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + k] : (T)0;
+        fs[q] = r < nr ? FV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + k] : (T)0;
       }
       ex.sync();
       for (int v = lane; v < tk.count; v += ws) {
@@ -721,10 +725,10 @@ struct KFwdBorder {
   BddcView V;
   const SolveTask* tasks;
   const T* F;
-  const double* FV;
+  const T* FV;
   const int64_t* fv_off;
-  const double* X;
-  double* UV;
+  const T* X;
+  T* UV;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
     constexpr int W = VecW<T>::W;
@@ -743,7 +747,7 @@ struct KFwdBorder {
       const int nr = nrhs - r0 < RB ? nrhs - r0 : RB;
       for (int q = ex.tid; q < RB * np; q += ex.nt) {
         const int r = q / np, k = q % np;
-        ys[q] = r < nr ? (T)X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + k] : (T)0;
+        ys[q] = r < nr ? X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + k] : (T)0;
       }
       ex.sync();
       for (int v = lane; v < tk.count; v += ws) {
@@ -762,8 +766,8 @@ struct KFwdBorder {
         for (int r = 0; r < nr; ++r) {
           T s = (T)0;
           for (int u = 0; u < nw; ++u) s += red[((u * FVEC + v) * W + j) * RB + r];
-          const double* f = FV + fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf;
-          UV[N.uvec_off * nrhs + (int64_t)(r0 + r) * N.nb + (row - np)] = f[row] - (double)s;
+          const T* f = FV + fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf;
+          UV[N.uvec_off * nrhs + (int64_t)(r0 + r) * N.nb + (row - np)] = f[row] - s;
         }
       }
       ex.sync();
@@ -848,8 +852,8 @@ struct KBwdBorder {
   BddcView V;
   const SolveTask* tasks;
   const T* F;
-  const double* X;
-  double* TV;        // [fv_off*nrhs + r*nf + j] (reuses the front-vector store)
+  const T* X;
+  T* TV;             // [fv_off*nrhs + r*nf + j] (reuses the front-vector store)
   const int64_t* fv_off;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
@@ -872,7 +876,7 @@ struct KBwdBorder {
       for (int q = ex.tid; q < RB * xld; q += ex.nt) {
         const int r = q / xld, row = a0 + q % xld;
         xb[q] = (r < nr && row >= np && row < nf)
-                    ? (T)X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + bord[row - np]] : (T)0;
+                    ? X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + bord[row - np]] : (T)0;
       }
       ex.sync();
       const int jend = tk.start + tk.count;
@@ -887,9 +891,9 @@ struct KBwdBorder {
         col_dot_n<T, RB, BCOL>(pan + (int64_t)j0 * ld + a0, ld, ncol, a0, a0, lo, nf, xb, xld, lane, acc);
         for (int u = 0; u < ncol; ++u) {
           const int j = j0 + u;
-          const double dj = (double)pan[(int64_t)j * ld + j];
+          const T dj = pan[(int64_t)j * ld + j];
           for (int r = 0; r < nr; ++r) {
-            const double t = (double)warp_sum(acc[u][r]);
+            const T t = warp_sum(acc[u][r]);
             if (lane == 0)
               TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] =
                   X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] / dj - t;
@@ -908,9 +912,9 @@ struct KBwdPivots {
   BddcView V;
   const SolveTask* tasks;
   const T* F;
-  const double* TV;
+  const T* TV;
   const int64_t* fv_off;
-  double* X;
+  T* X;
   int nrhs;
   VB_HD void operator()(const KExec& ex, int blk) const {
     constexpr int W = VecW<T>::W;
@@ -931,7 +935,7 @@ struct KBwdPivots {
       for (int q = ex.tid; q < RB * L; q += ex.nt) {
         const int r = q / L, row = bs + q % L;
         ts[q] = (r < nr && row >= tk.start && row < np)
-                    ? (T)TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + row] : (T)0;
+                    ? TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + row] : (T)0;
       }
       ex.sync();
       const int jend = tk.start + tk.count;
@@ -949,7 +953,7 @@ struct KBwdPivots {
         for (int u = 0; u < ncol; ++u) {
           const int j = j0 + u;
           for (int r = 0; r < nr; ++r) {
-            const double t = (double)warp_sum(acc[u][r]);
+            const T t = warp_sum(acc[u][r]);
             if (lane == 0)
               X[P.vec_off * nrhs + (int64_t)(r0 + r) * P.n + N.p0 + j] =
                   TV[fv_off[tk.node] * nrhs + (int64_t)(r0 + r) * nf + j] + t;
