@@ -52,6 +52,18 @@ struct ElemSizes {
   static constexpr int N4 = n_d4(K);
   static constexpr int N5 = n_d5(K);
   static constexpr int NSMAX = kMaxFaceVerts * K + NFM;   // face-local DOFs per component
+  // quadrature: collapsed Gauss rules with NQF (triangle) and NQV
+  // (tetrahedron) points per direction (exact to degree 2k+2 and 2k)
+  static constexpr int NQF = (2 * K + 5) / 2;
+  static constexpr int NQV = K + 2;
+  // tetrahedra of the volume rule tabulated at once
+  static constexpr int TCH = 16;
+  // point tables: volume (TCH tets: weight and 3 coordinates; partial
+  // moments per tet slot) and face (one fan triangle: weight, 5 coordinates,
+  // the 3D monomials of P_{k+1} and the face monomials of degree <= 2k+2)
+  static constexpr int TABV = TCH * NQV * NQV * NQV * 4 + NMOM * TCH;
+  static constexpr int TABF = NQF * NQF * (6 + NP2 + NFMOM);
+  static constexpr int TAB = TABV > TABF ? TABV : TABF;
 };
 
 // shared (fast) working set of one element
@@ -61,7 +73,7 @@ struct ElemShared {
   double X[kMaxElemVerts][3];
   double xK[3], hK, vol;
   double fn[kMaxElemFaces][3], ft1[kMaxElemFaces][3], ft2[kMaxElemFaces][3], fxc[kMaxElemFaces][3];
-  double fh[kMaxElemFaces], farea[kMaxElemFaces];
+  double fh[kMaxElemFaces], farea[kMaxElemFaces], ifarea[kMaxElemFaces];
   // face-local coordinates (s, t) = fw (xi1, xi2), xi = ((x - xc).t1, (x - xc).t2):
   // fw = Sigma^{-1/2} / sqrt(24), Sigma the second moments of the face about xc
   double fw[kMaxElemFaces][4];
@@ -90,7 +102,7 @@ struct ElemScratch {
   static VB_HD size_t size(int nK) {
     return kMaxElemFaces * face_block() + (size_t)nK *
                (S::NP0 + S::NP2 + 3 * S::NL + 3 * S::NP1 + 12 * S::NP0 + 3 * S::NP1 + 3 * S::NP1) +
-           2 * (size_t)nK * nK;
+           2 * (size_t)nK * nK + S::TAB + (size_t)kMaxElemFaces * S::NP1 * S::NFM;
   }
 };
 
@@ -98,6 +110,27 @@ VB_HD inline void cross3(const double* a, const double* b, double* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];
   c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// 1/n for the small positive integers of the monomial calculus (folded
+// constants instead of FP64 divisions)
+VB_HD inline double inv_small(int n) {
+  switch (n) {
+    case 1: return 1.0;
+    case 2: return 1.0 / 2;
+    case 3: return 1.0 / 3;
+    case 4: return 1.0 / 4;
+    case 5: return 1.0 / 5;
+    case 6: return 1.0 / 6;
+    case 7: return 1.0 / 7;
+    case 8: return 1.0 / 8;
+    case 9: return 1.0 / 9;
+    case 10: return 1.0 / 10;
+    case 11: return 1.0 / 11;
+    case 12: return 1.0 / 12;
+    case 13: return 1.0 / 13;
+    default: return 1.0 / n;
+  }
 }
 
 VB_HD inline double ipow(double x, int p) {
@@ -189,7 +222,7 @@ struct ElemBuilder {
   int off_e, off_f, off_4, off_5;
   Exec ex;
   // scratch views
-  double *Y, *DIV, *GM, *VML, *PiN, *Rs, *E, *VMH, *Dm, *Pm;
+  double *Y, *DIV, *GM, *VML, *PiN, *Rs, *E, *VMH, *Dm, *Pm, *Tb, *FM;
 
   VB_HD ElemBuilder(const ElemRec& r, const double* x, const ElemTables& t, ElemShared<K>& s, double* sc, Exec e)
       : R(r), xyz(x), T(t), sh(s), scr(sc), ex(e) {
@@ -209,6 +242,8 @@ struct ElemBuilder {
     VMH = scr + o; o += (size_t)3 * S::NP1 * nK;
     Dm = scr + o;  o += (size_t)3 * S::NP1 * nK;
     Pm = scr + o;  o += (size_t)2 * nK * nK;
+    Tb = scr + o;  o += S::TAB;
+    FM = scr + o;  o += (size_t)kMaxElemFaces * S::NP1 * S::NFM;
   }
 
   VB_HD double mu(int a, int b, int c) const { return sh.mu[idx3(a, b, c)]; }
@@ -328,38 +363,63 @@ struct ElemBuilder {
   }
 
   // ------------------------------------------------ volume moments mu_a = int xi^a
+  // Tetrahedra (x_K, A, B, C) of the fan of every face (outward loop); the
+  // points of up to TCH tetrahedra are tabulated (weight, scaled coordinates),
+  // then every (moment, tetrahedron) pair sums over its points, and each
+  // moment adds its tetrahedra in order.
+  VB_HD void tet_of(int tet, int& f, int& t) const {
+    f = 0;
+    while (tet >= R.fnv[f] - 2) { tet -= R.fnv[f] - 2; ++f; }
+    t = 1 + tet;
+  }
   VB_HD void volume_moments() {
-    const int nq = T.nq_vol;
-    double hinv = 1.0 / sh.hK;
-    for (int a = ex.tid; a < S::NMOM; a += ex.nt) {
-      const Exp3 ea = T.e3[a];
-      double acc = 0.0;
-      for (int f = 0; f < R.nf; ++f) {
-        int m = R.fnv[f];
-        // outward loop: reverse when the global normal points inwards
-        for (int t = 1; t < m - 1; ++t) {
-          int i0 = 0, i1 = t, i2 = t + 1;
-          if (R.fsign[f] < 0) { i0 = m - 1; i1 = m - 1 - t; i2 = m - 2 - t; }
-          const double* A = sh.X[R.floopv[f][i0]];
-          const double* B = sh.X[R.floopv[f][i1]];
-          const double* C = sh.X[R.floopv[f][i2]];
-          double a1[3], b1[3], c1[3];
-          for (int d = 0; d < 3; ++d) { a1[d] = A[d] - sh.xK[d]; b1[d] = B[d] - sh.xK[d]; c1[d] = C[d] - sh.xK[d]; }
-          double cr[3];
-          cross3(b1, c1, cr);
-          double det = a1[0] * cr[0] + a1[1] * cr[1] + a1[2] * cr[2];
-          for (int iu = 0; iu < nq; ++iu)
-            for (int iv = 0; iv < nq; ++iv)
-              for (int iw = 0; iw < nq; ++iw) {
-                double U = T.qv_x[iu], V = T.qv_x[iv], Wd = T.qv_x[iw];
-                double x = U, y = V * (1 - U), z = Wd * (1 - U) * (1 - V);
-                double w = T.qv_w[iu] * T.qv_w[iv] * T.qv_w[iw] * (1 - U) * (1 - U) * (1 - V) * det;
-                double p[3];
-                for (int d = 0; d < 3; ++d) p[d] = (x * a1[d] + y * b1[d] + z * c1[d]) * hinv;
-                acc += w * ipow(p[0], ea.a) * ipow(p[1], ea.b) * ipow(p[2], ea.c);
-              }
-        }
+    constexpr int NQ = S::NQV, NPT = NQ * NQ * NQ, CH = S::TCH;
+    double* VT = Tb;                   // [CH][NPT][4]
+    double* PART = Tb + CH * NPT * 4;  // [NMOM][CH]
+    const double hinv = 1.0 / sh.hK;
+    int ntet = 0;
+    for (int f = 0; f < R.nf; ++f) ntet += R.fnv[f] - 2;
+    for (int i = ex.tid; i < S::NMOM * CH; i += ex.nt) PART[i] = 0.0;
+    for (int c0 = 0; c0 < ntet; c0 += CH) {
+      ex.sync();
+      for (int item = ex.tid; item < CH * NPT; item += ex.nt) {
+        const int j = item / NPT, q = item % NPT;
+        if (c0 + j >= ntet) continue;
+        int f, t;
+        tet_of(c0 + j, f, t);
+        const int m = R.fnv[f];
+        int i0 = 0, i1 = t, i2 = t + 1;
+        if (R.fsign[f] < 0) { i0 = m - 1; i1 = m - 1 - t; i2 = m - 2 - t; }
+        const double* A = sh.X[R.floopv[f][i0]];
+        const double* B = sh.X[R.floopv[f][i1]];
+        const double* C = sh.X[R.floopv[f][i2]];
+        double a1[3], b1[3], c1[3];
+        for (int d = 0; d < 3; ++d) { a1[d] = A[d] - sh.xK[d]; b1[d] = B[d] - sh.xK[d]; c1[d] = C[d] - sh.xK[d]; }
+        double cr[3];
+        cross3(b1, c1, cr);
+        const double det = a1[0] * cr[0] + a1[1] * cr[1] + a1[2] * cr[2];
+        const int iu = q / (NQ * NQ), iv = (q / NQ) % NQ, iw = q % NQ;
+        const double U = T.qv_x[iu], V = T.qv_x[iv], Wd = T.qv_x[iw];
+        const double x = U, y = V * (1 - U), z = Wd * (1 - U) * (1 - V);
+        double* o = VT + (size_t)item * 4;
+        o[0] = T.qv_w[iu] * T.qv_w[iv] * T.qv_w[iw] * (1 - U) * (1 - U) * (1 - V) * det;
+        for (int d = 0; d < 3; ++d) o[1 + d] = (x * a1[d] + y * b1[d] + z * c1[d]) * hinv;
       }
+      ex.sync();
+      for (int item = ex.tid; item < S::NMOM * CH; item += ex.nt) {
+        const int a = item / CH, j = item % CH;
+        if (c0 + j >= ntet) continue;
+        const Exp3 ea = T.e3[a];
+        const double* v = VT + (size_t)j * NPT * 4;
+        double acc = 0.0;
+        for (int q = 0; q < NPT; ++q, v += 4) acc += v[0] * ipow(v[1], ea.a) * ipow(v[2], ea.b) * ipow(v[3], ea.c);
+        PART[item] += acc;
+      }
+    }
+    ex.sync();
+    for (int a = ex.tid; a < S::NMOM; a += ex.nt) {
+      double acc = 0.0;
+      for (int j = 0; j < CH; ++j) acc += PART[a * CH + j];
       sh.mu[a] = acc;
     }
     ex.sync();
@@ -393,44 +453,69 @@ struct ElemBuilder {
     const double g01 = fw[0] * fw[2] + fw[1] * fw[3];
     const double g11 = fw[2] * fw[2] + fw[3] * fw[3];
     // face quadrature (fan from loop vertex 0, collapsed Gauss); 2D moments
-    // nu_g = int_f s^g1 t^g2 and W[a][b] = int_f m3_a m2_b
-    const int nq = T.nq_face;
-    for (int idx = ex.tid; idx < S::NFMOM + S::NP2 * S::NF2; idx += ex.nt) {
-      int g1 = 0, g2 = 0, a = -1, b = -1;
-      if (idx < S::NFMOM) { g1 = T.e2[idx].a; g2 = T.e2[idx].b; }
-      else { a = (idx - S::NFMOM) / S::NF2; b = (idx - S::NFMOM) % S::NF2; }
-      double acc = 0.0;
+    // nu_g = int_f s^g1 t^g2 and W[a][b] = int_f m3_a m2_b.  Per fan
+    // triangle the points are tabulated (weight, (s, t), scaled xi), then the
+    // monomials at every point, then each moment sums over the points.
+    {
+      constexpr int NQ = S::NQF, NPT = NQ * NQ, NMT = S::NP2 + S::NFMOM;
+      double* FT = Tb;                  // [NPT][6]: w, s, t, xi
+      double* M3 = Tb + NPT * 6;        // [NPT][NP2]
+      double* M2 = M3 + NPT * S::NP2;   // [NPT][NFMOM]
+      const double hk = 1.0 / sh.hK;
+      for (int idx = ex.tid; idx < S::NFMOM + S::NP2 * S::NF2; idx += ex.nt) {
+        if (idx < S::NFMOM) sh.nu2[idx] = 0.0;
+        else sh.W[idx - S::NFMOM] = 0.0;
+      }
       const double* P0 = sh.X[R.floopv[f][0]];
       for (int t = 1; t < m - 1; ++t) {
         const double* P1 = sh.X[R.floopv[f][t]];
         const double* P2 = sh.X[R.floopv[f][t + 1]];
-        double u1[3], u2[3], cr[3];
-        for (int d = 0; d < 3; ++d) { u1[d] = P1[d] - P0[d]; u2[d] = P2[d] - P0[d]; }
-        cross3(u1, u2, cr);
-        double J = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-        for (int iu = 0; iu < nq; ++iu)
-          for (int iv = 0; iv < nq; ++iv) {
-            double U = T.qf_x[iu], V = T.qf_x[iv] * (1 - U);
-            double w = T.qf_w[iu] * T.qf_w[iv] * (1 - U) * J;
-            double x[3];
-            for (int d = 0; d < 3; ++d) x[d] = P0[d] + U * u1[d] + V * u2[d];
-            double s, tt;
-            face_st(f, x, s, tt);
-            if (a < 0) {
-              acc += w * ipow(s, g1) * ipow(tt, g2);
-            } else {
-              const Exp3 ea = T.e3[a];
-              const Exp2 eb = T.e2[b];
-              double hk = 1.0 / sh.hK;
-              double px = (x[0] - sh.xK[0]) * hk, py = (x[1] - sh.xK[1]) * hk, pz = (x[2] - sh.xK[2]) * hk;
-              acc += w * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c) * ipow(s, eb.a) * ipow(tt, eb.b);
-            }
+        ex.sync();
+        for (int q = ex.tid; q < NPT; q += ex.nt) {
+          double u1[3], u2[3], cr[3];
+          for (int d = 0; d < 3; ++d) { u1[d] = P1[d] - P0[d]; u2[d] = P2[d] - P0[d]; }
+          cross3(u1, u2, cr);
+          const double J = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+          const int iu = q / NQ, iv = q % NQ;
+          const double U = T.qf_x[iu], V = T.qf_x[iv] * (1 - U);
+          double x[3];
+          for (int d = 0; d < 3; ++d) x[d] = P0[d] + U * u1[d] + V * u2[d];
+          double* o = FT + q * 6;
+          o[0] = T.qf_w[iu] * T.qf_w[iv] * (1 - U) * J;
+          face_st(f, x, o[1], o[2]);
+          for (int d = 0; d < 3; ++d) o[3 + d] = (x[d] - sh.xK[d]) * hk;
+        }
+        ex.sync();
+        for (int item = ex.tid; item < NPT * NMT; item += ex.nt) {
+          const int q = item / NMT, jm = item % NMT;
+          const double* o = FT + q * 6;
+          if (jm < S::NP2) {
+            const Exp3 ea = T.e3[jm];
+            M3[q * S::NP2 + jm] = ipow(o[3], ea.a) * ipow(o[4], ea.b) * ipow(o[5], ea.c);
+          } else {
+            const Exp2 eb = T.e2[jm - S::NP2];
+            M2[q * S::NFMOM + jm - S::NP2] = ipow(o[1], eb.a) * ipow(o[2], eb.b);
           }
+        }
+        ex.sync();
+        for (int idx = ex.tid; idx < S::NFMOM + S::NP2 * S::NF2; idx += ex.nt) {
+          double acc = 0.0;
+          if (idx < S::NFMOM) {
+            for (int q = 0; q < NPT; ++q) acc += FT[q * 6] * M2[q * S::NFMOM + idx];
+            sh.nu2[idx] += acc;
+          } else {
+            const int a = (idx - S::NFMOM) / S::NF2, b = (idx - S::NFMOM) % S::NF2;
+            for (int q = 0; q < NPT; ++q) acc += FT[q * 6] * M3[q * S::NP2 + a] * M2[q * S::NFMOM + b];
+            sh.W[a * S::NF2 + b] += acc;
+          }
+        }
       }
-      if (a < 0) sh.nu2[idx] = acc;
-      else sh.W[a * S::NF2 + b] = acc;
     }
     ex.sync();
+    // int_f m3_a m2_b for a in P_k, b in P_{k-2}(f), kept for the DOFs of the
+    // [P_k]^3 basis
+    for (int idx = ex.tid; idx < S::NP1 * S::NFM; idx += ex.nt)
+      FM[(size_t)f * S::NP1 * S::NFM + idx] = sh.W[(idx / S::NFM) * S::NF2 + idx % S::NFM];
     // Pi^nabla_{k,f}: G2 c = rhs, rows b >= 1: int grad m_b . grad m_g;
     // row 0: int_df m_g.  rhs: -int Lap m_b v + sum_e int_e d_n m_b v; row 0 int_df v
     for (int idx = ex.tid; idx < S::NF1 * S::NF1; idx += ex.nt) {
@@ -654,7 +739,8 @@ struct ElemBuilder {
     double hK = sh.hK;
     // gradient part: Q = xi_c m_b / (d+1);  int v . grad_xi Q = h int v . grad_x Q
     int qa = eb.a + (c == 0), qb = eb.b + (c == 1), qc = eb.c + (c == 2);
-    double acc = hK / (d + 1) * GM[(size_t)idx3(qa, qb, qc) * nK + col];
+    const double id1 = inv_small(d + 1);
+    double acc = hK * id1 * GM[(size_t)idx3(qa, qb, qc) * nK + col];
     if (d == 0) return acc;
     // curl part: R = -(grad m_b x e_c)/(d+1), components R_i = -(1/(d+1)) eps(i,j,c) d_j m_b
     for (int i = 0; i < 3; ++i)
@@ -665,7 +751,7 @@ struct ElemBuilder {
         if (pj == 0) continue;
         int ra = eb.a - (jd == 0), rb = eb.b - (jd == 1), rc = eb.c - (jd == 2);
         int rb_idx = idx3(ra, rb, rc);
-        double coef = -(double)eps * pj / (d + 1);
+        double coef = -(double)(eps * pj) * id1;
         double mom;
         if (d - 1 <= K - 3) mom = d4(col, rb_idx, i);
         else mom = use_enh ? enh(col, rb_idx, i) : 0.0;
@@ -684,6 +770,9 @@ struct ElemBuilder {
     bool ok = volume_systems();
     for (int f = 0; f < R.nf; ++f) ok = face(f) && ok;
     const double hK = sh.hK, vol = sh.vol;
+    const double ihK = 1.0 / hK, ivol = 1.0 / vol;
+    for (int f = ex.tid; f < R.nf; f += ex.nt) sh.ifarea[f] = 1.0 / sh.farea[f];
+    ex.sync();
     // (1) divergence: mom rows -> DIV = Minv0 mom
     for (int idx = ex.tid; idx < S::NP0 * nK; idx += ex.nt) {
       int g = idx / nK, col = idx % nK;
@@ -754,11 +843,11 @@ struct ElemBuilder {
         if (ea.a >= 2) v -= ea.a * (ea.a - 1) * VML[((size_t)c * S::NL + idx3(ea.a - 2, ea.b, ea.c)) * nK + col];
         if (ea.b >= 2) v -= ea.b * (ea.b - 1) * VML[((size_t)c * S::NL + idx3(ea.a, ea.b - 2, ea.c)) * nK + col];
         if (ea.c >= 2) v -= ea.c * (ea.c - 1) * VML[((size_t)c * S::NL + idx3(ea.a, ea.b, ea.c - 2)) * nK + col];
-        v /= hK * hK;
+        v *= ihK * ihK;
         // + int_dK v_c grad m_a . n = (1/h) sum_j a_j int_dK v_c m_{a-e_j} n_j
-        if (ea.a) v += ea.a / hK * bnd(col, c, idx3(ea.a - 1, ea.b, ea.c), 0);
-        if (ea.b) v += ea.b / hK * bnd(col, c, idx3(ea.a, ea.b - 1, ea.c), 1);
-        if (ea.c) v += ea.c / hK * bnd(col, c, idx3(ea.a, ea.b, ea.c - 1), 2);
+        if (ea.a) v += ea.a * ihK * bnd(col, c, idx3(ea.a - 1, ea.b, ea.c), 0);
+        if (ea.b) v += ea.b * ihK * bnd(col, c, idx3(ea.a, ea.b - 1, ea.c), 1);
+        if (ea.c) v += ea.c * ihK * bnd(col, c, idx3(ea.a, ea.b, ea.c - 1), 2);
       }
       VMH[idx] = v;
     }
@@ -785,7 +874,7 @@ struct ElemBuilder {
         int pj = jj == 0 ? ea.a : (jj == 1 ? ea.b : ea.c);
         if (pj > 0) {
           int bidx = idx3(ea.a - (jj == 0), ea.b - (jj == 1), ea.c - (jj == 2));
-          v -= (double)pj / hK * VML[((size_t)ii * S::NL + bidx) * nK + col];
+          v -= pj * ihK * VML[((size_t)ii * S::NL + bidx) * nK + col];
         }
         v += bnd(col, ii, a, jj);
       }
@@ -807,7 +896,7 @@ struct ElemBuilder {
       int c = cb / S::NP1, a = cb % S::NP1;
       const Exp3 ea = T.e3[a];
       double v = 0.0;
-      double hi = 1.0 / hK;
+      const double hi = ihK;
       if (row < off_e) {
         if (row % 3 == c) {
           const double* X = sh.X[row / 3];
@@ -833,9 +922,8 @@ struct ElemBuilder {
         int r = row - off_f;
         int f = r / (3 * S::NFM), b = (r / 3) % S::NFM, t = r % 3;
         double wv = t == 0 ? sh.fn[f][c] : (t == 1 ? sh.ft1[f][c] : sh.ft2[f][c]);
-        // (1/|f|) int_f m3_a m2_b : recomputed from the face quadrature table W is
-        // per face and gone; use Y? no -- evaluate with the stored face moments
-        v = wv * facemom_(f, a, b) / sh.farea[f];
+        // (1/|f|) int_f m3_a m2_b from the face moments kept by face(f)
+        v = wv * FM[((size_t)f * S::NP1 + a) * S::NFM + b] * sh.ifarea[f];
       } else if (row < off_5) {
         int jcol = row - off_4;
         // generator number g (kept ones in order, the dropped one skipped)
@@ -849,14 +937,14 @@ struct ElemBuilder {
           int eps = ((c + 1) % 3 == jd) ? 1 : -1;
           v += eps * mu(ea.a + eb.a + (jd == 0), ea.b + eb.b + (jd == 1), ea.c + eb.c + (jd == 2));
         }
-        v /= vol;
+        v *= ivol;
       } else {
         int al = row - off_5 + 1;
         // (1/|K|) int div(m_a e_c) m_al = (1/|K|) (p_c/h) int m_{a-e_c} m_al
         int pc = c == 0 ? ea.a : (c == 1 ? ea.b : ea.c);
         if (pc > 0) {
           const Exp3 el = T.e3[al];
-          v = pc * hi * mu(ea.a - (c == 0) + el.a, ea.b - (c == 1) + el.b, ea.c - (c == 2) + el.c) / vol;
+          v = pc * hi * mu(ea.a - (c == 0) + el.a, ea.b - (c == 1) + el.b, ea.c - (c == 2) + el.c) * ivol;
         }
       }
       Dm[idx] = v;
@@ -864,8 +952,13 @@ struct ElemBuilder {
     ex.sync();
     // (7) consistency Ac = sum_ij Rs_ij^T E_ij (off-diagonal pairs twice), into Pm[nK*nK ..]
     double* Ac = Pm + (size_t)nK * nK;
-    for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
-      int r = idx / nK, c = idx % nK;
+    // (symmetric: the upper triangle is formed, rows p and nK-1-p paired,
+    // and mirrored)
+    for (int idx = ex.tid; idx < ((nK + 1) / 2) * (nK + 1); idx += ex.nt) {
+      const int p = idx / (nK + 1), j = idx % (nK + 1);
+      int r, c;
+      if (j < nK - p) { r = p; c = p + j; }
+      else { r = nK - 1 - p; c = r + (j - (nK - p)); if (r == p) continue; }
       double acc = 0.0;
       for (int pr = 0; pr < 6; ++pr) {
         double w = pr < 3 ? 1.0 : 2.0;
@@ -874,17 +967,8 @@ struct ElemBuilder {
           s += Rs[((size_t)pr * S::NP0 + g) * nK + r] * E[((size_t)pr * S::NP0 + g) * nK + c];
         acc += w * s;
       }
-      Ac[idx] = acc;
-    }
-    ex.sync();
-    // symmetrize the consistency part (rounding)
-    for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
-      int r = idx / nK, c = idx % nK;
-      if (r < c) {
-        double m = 0.5 * (Ac[(size_t)r * nK + c] + Ac[(size_t)c * nK + r]);
-        Ac[(size_t)r * nK + c] = m;
-        Ac[(size_t)c * nK + r] = m;
-      }
+      Ac[(size_t)r * nK + c] = acc;
+      Ac[(size_t)c * nK + r] = acc;
     }
     ex.sync();
     // (8)-(9) A = nu (Ac + P^T diag(s) P), s_i = max(Ac_ii, h_K), with
@@ -907,28 +991,28 @@ struct ElemBuilder {
       W[idx] = acc;
     }
     ex.sync();
+    // G <- W PiN - F^T: then (P^T S P - S)[r][c] = sum_q PiN[q][r] G[q][c] - F[r][q] PiN[q][c]
     for (int idx = ex.tid; idx < nb * nK; idx += ex.nt) {
       const int a = idx / nK, c = idx % nK;
       double acc = 0.0;
       for (int bq = 0; bq < nb; ++bq) acc += W[(size_t)a * nb + bq] * PiN[(size_t)bq * nK + c];
-      G[idx] = acc;
+      G[idx] = acc - F[(size_t)c * nb + a];
     }
     ex.sync();
-    for (int idx = ex.tid; idx < nK * nK; idx += ex.nt) {
-      const int r = idx / nK, c = idx % nK;
-      if (r > c) continue;
+    // upper triangle only, rows p and nK-1-p paired (nK+1 entries per pair)
+    for (int idx = ex.tid; idx < ((nK + 1) / 2) * (nK + 1); idx += ex.nt) {
+      const int p = idx / (nK + 1), j = idx % (nK + 1);
+      int r, c;
+      if (j < nK - p) { r = p; c = p + j; }
+      else { r = nK - 1 - p; c = r + (j - (nK - p)); if (r == p) continue; }
       double acc = 0.0;
       if (r == c) {
         const double sr = Ac[(size_t)r * nK + r];
         acc = sr > hK ? sr : hK;
       }
       const double* fr = F + (size_t)r * nb;
-      const double* fc = F + (size_t)c * nb;
-      for (int q = 0; q < nb; ++q) {
-        const double pr = PiN[(size_t)q * nK + r], pc = PiN[(size_t)q * nK + c];
-        acc += pr * G[(size_t)q * nK + c] - fr[q] * pc - fc[q] * pr;
-      }
-      double v = nu * (Ac[idx] + acc);
+      for (int q = 0; q < nb; ++q) acc += PiN[(size_t)q * nK + r] * G[(size_t)q * nK + c] - fr[q] * PiN[(size_t)q * nK + c];
+      double v = nu * (Ac[(size_t)r * nK + c] + acc);
       Aout[(size_t)r * nK + c] = v;
       Aout[(size_t)c * nK + r] = v;
     }
@@ -964,37 +1048,6 @@ struct ElemBuilder {
     }
     ex.sync();
     return ok;
-  }
-
-  // (1/|f|)-free face moment int_f m3_a m2_b, recomputed by quadrature
-  VB_HD double facemom_(int f, int a, int b) const {
-    const int m = R.fnv[f];
-    const int nq = T.nq_face;
-    const Exp3 ea = T.e3[a];
-    const Exp2 eb = T.e2[b];
-    double hk = 1.0 / sh.hK;
-    double acc = 0.0;
-    const double* P0 = sh.X[R.floopv[f][0]];
-    for (int t = 1; t < m - 1; ++t) {
-      const double* P1 = sh.X[R.floopv[f][t]];
-      const double* P2 = sh.X[R.floopv[f][t + 1]];
-      double u1[3], u2[3], cr[3];
-      for (int d = 0; d < 3; ++d) { u1[d] = P1[d] - P0[d]; u2[d] = P2[d] - P0[d]; }
-      cross3(u1, u2, cr);
-      double J = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-      for (int iu = 0; iu < nq; ++iu)
-        for (int iv = 0; iv < nq; ++iv) {
-          double U = T.qf_x[iu], V = T.qf_x[iv] * (1 - U);
-          double w = T.qf_w[iu] * T.qf_w[iv] * (1 - U) * J;
-          double x[3];
-          for (int d = 0; d < 3; ++d) x[d] = P0[d] + U * u1[d] + V * u2[d];
-          double s, tt;
-          face_st(f, x, s, tt);
-          double px = (x[0] - sh.xK[0]) * hk, py = (x[1] - sh.xK[1]) * hk, pz = (x[2] - sh.xK[2]) * hk;
-          acc += w * ipow(px, ea.a) * ipow(py, ea.b) * ipow(pz, ea.c) * ipow(s, eb.a) * ipow(tt, eb.b);
-        }
-    }
-    return acc;
   }
 };
 
