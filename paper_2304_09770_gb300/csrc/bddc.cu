@@ -592,6 +592,35 @@ struct KCoarseAssemble {
   }
 };
 
+// Dirichlet factors from the deluxe factorization: the deluxe problem of a
+// subdomain has the Dirichlet problem's pivots, in the same order and tree,
+// and every front's border is the Dirichlet border followed by entity DOFs
+// (positions beyond all pivots).  Its panels therefore hold the Dirichlet
+// panels as their first np + nb_D rows (L11^{-1} in place, D, L21): copied,
+// one CTA per (node pair, 32 columns), the padding rows up to the leading
+// dimension zero as after a factorization.
+struct PanelCopyTask {
+  int dst, src, c0;   // Dirichlet node, deluxe node, first column
+};
+template <class T>
+struct KPanelCopy {
+  BddcView V;
+  const PanelCopyTask* tasks;
+  const T* FX;   // deluxe factor store
+  T* FD;         // Dirichlet factor store
+  VB_HD void operator()(const KExec& ex, int blk) const {
+    const PanelCopyTask tk = tasks[blk];
+    const NodeDev D = V.nodes[tk.dst], X = V.nodes[tk.src];
+    const int rows = D.np + D.nb;
+    const int c1 = tk.c0 + 32 < D.np ? tk.c0 + 32 : D.np;
+    for (int c = tk.c0; c < c1; ++c) {
+      const T* src = FX + X.panel_off + (int64_t)c * X.ld;
+      T* dst = FD + D.panel_off + (int64_t)c * D.ld;
+      for (int r = ex.tid; r < D.ld; r += ex.nt) dst[r] = r < rows ? src[r] : (T)0;   // padding rows zero
+    }
+  }
+};
+
 // deluxe: S_FF of one side from the root update matrix of its subdomain's
 // deluxe problem (the entity's DOFs are the contiguous root-border block
 // b0 .. b0 + n), rotated to the dual coordinates: Sd = (H^T S H)[r:, r:]
@@ -2249,6 +2278,7 @@ static void setup_core(bddc* b, const int32_t* part) {
     };
     bddc_host_setup(s, part, b->opt, H, s->elem_wmean);
     mark("t_symbolic_ms");
+    for (auto& kv : H.times) b->times.push_back(kv);
     const int N = H.N;
     const int np = s->dof.np;
     // ---------------- flatten
@@ -2258,6 +2288,42 @@ static void setup_core(bddc* b, const int32_t* part) {
     std::vector<double> vcon_coef, wmean, hv, tau, mcon_coef;
     std::vector<int> mcon_ptr, mcon_vdof;
     b->h_subs.assign(N, SubDev{});
+    // the per-subdomain tables that need searches, built in parallel:
+    // element column -> local index, and the constraint rows by multiplier
+    std::vector<std::vector<int>> ell(N), mptr(N), mvd(N);
+    std::vector<std::vector<double>> mcoef(N);
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < N; ++i) {
+      const Subdomain& S = H.subs[i];
+      const int nv = (int)S.vdof.size();
+      std::vector<int>& el = ell[i];
+      for (size_t le = 0; le < S.elems.size(); ++le) {
+        const int e = S.elems[le];
+        const int nK = (int)(s->h_eoff[e + 1] - s->h_eoff[e]);
+        for (int bb = 0; bb < nK; ++bb) {
+          const int64_t g = s->h_sysdof[s->h_eoff[e] + bb];
+          int l = -1;
+          if (g >= 0) l = (int)(std::lower_bound(S.vdof.begin(), S.vdof.end(), g) - S.vdof.begin());
+          el.push_back(l);
+        }
+        for (int a = 0; a < np; ++a) el.push_back(nv + (int)le * np + a);
+      }
+      int nm = 0;
+      for (int id : S.vcon_id) nm = std::max(nm, id + 1);
+      std::vector<int> cnt(nm + 1, 0);
+      for (int id : S.vcon_id) cnt[id + 1]++;
+      for (int m = 0; m < nm; ++m) cnt[m + 1] += cnt[m];
+      mptr[i] = cnt;
+      mvd[i].assign(cnt[nm], 0);
+      mcoef[i].assign(cnt[nm], 0.0);
+      for (int v = 0; v < nv; ++v)
+        for (int q = S.vcon_ptr[v]; q < S.vcon_ptr[v + 1]; ++q) {
+          const int m = S.vcon_id[q];
+          mvd[i][cnt[m]] = v;
+          mcoef[i][cnt[m]] = S.vcon_coef[q];
+          cnt[m]++;
+        }
+    }
     int64_t loc = 0;
     for (int i = 0; i < N; ++i) {
       const Subdomain& S = H.subs[i];
@@ -2285,23 +2351,13 @@ static void setup_core(bddc* b, const int32_t* part) {
       D.vcon_off = (int64_t)vcon_id.size();
       vcon_id.insert(vcon_id.end(), S.vcon_id.begin(), S.vcon_id.end());
       vcon_coef.insert(vcon_coef.end(), S.vcon_coef.begin(), S.vcon_coef.end());
-      {
-        // multiplier -> (local vdof, coef): the constraint rows by multiplier
-        int nm = 0;
-        for (int id : S.vcon_id) nm = std::max(nm, id + 1);
-        std::vector<std::vector<std::pair<int, double>>> rows(nm);
-        for (int v = 0; v < D.nv; ++v)
-          for (int q = S.vcon_ptr[v]; q < S.vcon_ptr[v + 1]; ++q) rows[S.vcon_id[q]].push_back({v, S.vcon_coef[q]});
-        D.mcon_ptr_off = (int64_t)mcon_ptr.size();
-        D.mcon_off = (int64_t)mcon_vdof.size();
-        int o2 = 0;
-        mcon_ptr.push_back(0);
-        for (auto& rw : rows) {
-          for (auto& pr : rw) { mcon_vdof.push_back(pr.first); mcon_coef.push_back(pr.second); }
-          o2 += (int)rw.size();
-          mcon_ptr.push_back(o2);
-        }
-      }
+      // multiplier -> (local vdof, coef): the constraint rows by multiplier
+      // (vdofs ascending within a row)
+      D.mcon_ptr_off = (int64_t)mcon_ptr.size();
+      D.mcon_off = (int64_t)mcon_vdof.size();
+      mcon_ptr.insert(mcon_ptr.end(), mptr[i].begin(), mptr[i].end());
+      mcon_vdof.insert(mcon_vdof.end(), mvd[i].begin(), mvd[i].end());
+      mcon_coef.insert(mcon_coef.end(), mcoef[i].begin(), mcoef[i].end());
       D.press_off = (int64_t)press.size();
       press.insert(press.end(), S.press.begin(), S.press.end());
       wmean.insert(wmean.end(), S.wmean.begin(), S.wmean.end());
@@ -2315,18 +2371,11 @@ static void setup_core(bddc* b, const int32_t* part) {
       int off = 0;
       for (int le = 0; le < D.ne; ++le) {
         elloc_ptr.push_back(off);
-        int e = S.elems[le];
-        int nK = (int)(s->h_eoff[e + 1] - s->h_eoff[e]);
-        for (int bb = 0; bb < nK; ++bb) {
-          int64_t g = s->h_sysdof[s->h_eoff[e] + bb];
-          int l = -1;
-          if (g >= 0) l = (int)(std::lower_bound(S.vdof.begin(), S.vdof.end(), g) - S.vdof.begin());
-          elloc.push_back(l);
-        }
-        for (int a = 0; a < np; ++a) elloc.push_back(D.nv + le * np + a);
-        off += nK + np;
+        const int e = S.elems[le];
+        off += (int)(s->h_eoff[e + 1] - s->h_eoff[e]) + np;
       }
       elloc_ptr.push_back(off);
+      elloc.insert(elloc.end(), ell[i].begin(), ell[i].end());
       D.loc_off = loc;
       loc += D.nv + D.npress;
     }
@@ -2376,7 +2425,24 @@ static void setup_core(bddc* b, const int32_t* part) {
       }
       D.root = (int)b->h_nodes.size() - 1;
     }
-    // macro entities
+    // macro entities; the (entity, sharing subdomain) position and interface
+    // index tables need searches and are built in parallel
+    const int nmac = (int)H.macros.size();
+    std::vector<std::vector<int>> mgpos(nmac), mgif(nmac);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int g = 0; g < nmac; ++g) {
+      const Macro& G = H.macros[g];
+      for (int si : G.share) {
+        const Subdomain& S = H.subs[si];
+        const Problem& PN = H.probs[H.neu_prob[si]];
+        for (int64_t g2 : G.dofs) {
+          const int v = (int)(std::lower_bound(S.vdof.begin(), S.vdof.end(), g2) - S.vdof.begin());
+          mgpos[g].push_back(PN.pos_of_vdof[v]);
+          mgif[g].push_back((int)(std::lower_bound(S.iface_vdof.begin(), S.iface_vdof.end(), v) -
+                                  S.iface_vdof.begin()));
+        }
+      }
+    }
     b->h_macros.assign(H.macros.size(), MacroDev{});
     int64_t dual = 0, deluxe_n = 0;
     for (size_t g = 0; g < H.macros.size(); ++g) {
@@ -2405,15 +2471,8 @@ static void setup_core(bddc* b, const int32_t* part) {
       share.insert(share.end(), G.share.begin(), G.share.end());
       D.gpos_off = (int64_t)gpos.size();
       D.gif_off = (int64_t)gif.size();
-      for (int si : G.share) {
-        const Subdomain& S = H.subs[si];
-        const Problem& PN = H.probs[H.neu_prob[si]];
-        for (int64_t g2 : G.dofs) {
-          int v = (int)(std::lower_bound(S.vdof.begin(), S.vdof.end(), g2) - S.vdof.begin());
-          gpos.push_back(PN.pos_of_vdof[v]);
-          gif.push_back((int)(std::lower_bound(S.iface_vdof.begin(), S.iface_vdof.end(), v) - S.iface_vdof.begin()));
-        }
-      }
+      gpos.insert(gpos.end(), mgpos[g].begin(), mgpos[g].end());
+      gif.insert(gif.end(), mgif[g].begin(), mgif[g].end());
       D.deluxe_off = -1;
       D.deluxe_e_off = -1;
     }
@@ -2541,10 +2600,50 @@ static void setup_core(bddc* b, const int32_t* part) {
     status.zero(st);
     // the update matrices are consumed by the parents during the
     // factorization and not needed afterwards: released batch by batch
-    factor_batch(b, b->bd, V, status);
-    VB_CUDA(cudaStreamSynchronize(st));
-    b->bd.U.release();
-    b->bd.U32.release();
+    // Dirichlet factors: taken from the deluxe factorization when every
+    // subdomain has a deluxe problem with the same pivots, tree and leading
+    // border (checked here), else factored
+    std::vector<PanelCopyTask> pcopy;       // per deluxe problem, in dl_probs order
+    std::vector<int64_t> pcopy_ptr(1, 0);
+    {
+      bool from_dl = !dl_probs.empty() && (int)dl_probs.size() == N;
+      std::vector<int> dl_of_sub(N, -1);
+      if (from_dl)
+        for (int q : dl_probs) {
+          const int i = H.probs[q].sub;
+          if (dl_of_sub[i] >= 0) from_dl = false;
+          else dl_of_sub[i] = q;
+        }
+      for (int i = 0; i < N && from_dl; ++i) {
+        const Problem& PD = H.probs[H.dir_prob[i]];
+        const Problem& PX = H.probs[dl_of_sub[i]];
+        if (PD.npiv != PX.npiv || PD.nodes.size() != PX.nodes.size()) { from_dl = false; break; }
+        for (size_t k = 0; k < PD.nodes.size() && from_dl; ++k) {
+          const Node &nd = PD.nodes[k], &nx = PX.nodes[k];
+          if (nd.p0 != nx.p0 || nd.np != nx.np || nd.nb > nx.nb || nd.nchild != nx.nchild) { from_dl = false; break; }
+          for (int j = 0; j < nd.nb; ++j)
+            if (PD.border[nd.border_off + j] != PX.border[nx.border_off + j]) { from_dl = false; break; }
+        }
+      }
+      if (from_dl) {
+        for (int q : dl_probs) {
+          const int i = H.probs[q].sub;
+          const int nn = (int)H.probs[q].nodes.size();
+          const int rd = b->h_probs[H.dir_prob[i]].root - nn + 1, rx = b->h_probs[q].root - nn + 1;
+          for (int k = 0; k < nn; ++k)
+            for (int c0 = 0; c0 < b->h_nodes[rd + k].np; c0 += 32) pcopy.push_back({rd + k, rx + k, c0});
+          pcopy_ptr.push_back((int64_t)pcopy.size());
+        }
+        if (b->prec == 0) b->bd.F.alloc(std::max<int64_t>(b->bd.nF, 1));
+        else b->bd.F32.alloc(std::max<int64_t>(b->bd.nF, 1));
+      } else {
+        pcopy_ptr.clear();
+        factor_batch(b, b->bd, V, status);
+        VB_CUDA(cudaStreamSynchronize(st));
+        b->bd.U.release();
+        b->bd.U32.release();
+      }
+    }
     mark("t_factor_dirichlet_ms");
     factor_batch(b, b->bn, V, status);
     VB_CUDA(cudaStreamSynchronize(st));
@@ -2596,6 +2695,16 @@ static void setup_core(bddc* b, const int32_t* part) {
         upload_levels(b, Bc);
         V = make_view(b);
         factor_batch(b, Bc, V, status);
+        if (!pcopy_ptr.empty() && pcopy_ptr[t1c] > pcopy_ptr[t0c]) {
+          DBuf<PanelCopyTask> dpc;
+          std::vector<PanelCopyTask> pc(pcopy.begin() + pcopy_ptr[t0c], pcopy.begin() + pcopy_ptr[t1c]);
+          upload_vec(dpc, pc, st);
+          if (b->prec == 0)
+            launch(KPanelCopy<double>{V, dpc.p, Bc.F.p, b->bd.F.p}, (int64_t)pc.size(), 256, 0, st);
+          else
+            launch(KPanelCopy<float>{V, dpc.p, Bc.F32.p, b->bd.F32.p}, (int64_t)pc.size(), 256, 0, st);
+          VB_CUDA(cudaStreamSynchronize(st));
+        }
         DBuf<DeluxeTask> dct;
         upload_vec(dct, ct, st);
         DBuf<double> work(std::max<int64_t>(w, 1));

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <map>
 #include <numeric>
@@ -414,6 +415,13 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
   const int nE = t.nE;
   const int np = d.np;
   const int64_t nvf = d.nvf;
+  H.times.clear();
+  auto t0 = std::chrono::steady_clock::now();
+  auto mark = [&](const char* name) {
+    const auto t1 = std::chrono::steady_clock::now();
+    H.times.push_back({name, std::chrono::duration<double, std::milli>(t1 - t0).count()});
+    t0 = t1;
+  };
   H.part.assign(part, part + nE);
   int N = 0;
   for (int e = 0; e < nE; ++e) {
@@ -435,6 +443,7 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
     sv.erase(std::unique(sv.begin(), sv.end()), sv.end());
     H.mult[r] = (int)sv.size();
   }
+  mark("t_sym_share_ms");
   // ---- macro entities: interface mesh entities grouped by sharing set and connectivity
   // entity (type, id) -> interface entity number, through one flat table
   // over vertices, edges, faces and elements
@@ -553,7 +562,9 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
     }
     H.macros.push_back(std::move(G));
   }
+  mark("t_sym_macros_ms");
   if (!(o.constraints & 16)) check_rigid_modes(s, part, o, H);
+  mark("t_sym_rigid_ms");
   // coarse numbering
   int64_t cc = 0;
   for (auto& G : H.macros) {
@@ -579,6 +590,7 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
   for (int gi = 0; gi < (int)H.macros.size(); ++gi)
     for (int i : H.macros[gi].share) sub_macros[i].push_back(gi);
 
+  mark("t_sym_neighbours_ms");
   const bool all_primal = (o.constraints & 16) != 0;
   H.probs.clear();
   std::vector<std::vector<Problem>> sub_probs(N);
@@ -957,6 +969,7 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
       errors[i] = e.what();
     }
   }
+  mark("t_sym_subdomains_ms");
   for (int i = 0; i < N; ++i) VB_CHECK(errors[i].empty(), VEM_EINVAL, errors[i]);
   H.dir_prob.assign(N, -1);
   H.neu_prob.assign(N, -1);
@@ -966,6 +979,7 @@ void bddc_host_setup(const vem_system* s, const int32_t* part, const SetupOption
       if (P.kind == PK_NEUMANN) H.neu_prob[i] = (int)H.probs.size();
       H.probs.push_back(std::move(P));
     }
+  mark("t_sym_collect_ms");
 }
 
 }  // namespace vb

@@ -4,6 +4,10 @@
 #pragma once
 #include "system.h"
 
+#include <string>
+#include <utility>
+#include <vector>
+
 namespace vb {
 
 enum ProbKind { PK_DIRICHLET = 0, PK_NEUMANN = 1, PK_DELUXE = 2 };
@@ -80,6 +84,7 @@ struct BddcHost {
   int64_t ncoarse_vel = 0, ncoarse = 0;
   std::vector<Problem> probs;          // Dirichlet(i), Neumann(i), deluxe(i, F)
   std::vector<int> dir_prob, neu_prob; // per subdomain
+  std::vector<std::pair<std::string, double>> times;   // host phase times (ms)
 };
 
 struct SetupOptions {
