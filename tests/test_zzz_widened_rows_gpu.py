@@ -18,9 +18,12 @@ against the CPU oracle:
   the velocity against the full scheme's direct solve.
 
 Tolerances as in the other parity tests: element matrices and assembly to
-rounding; PCG within +-1 iteration and, at equal iteration counts, the
-velocity and the zero-mean pressure within 1e-10 of the oracle's iterate,
-lambda_max within 1e-6.
+rounding; PCG by the shared rule of oracle_cache.check_pcg_parity
+(iterations within +-1 of the oracle's, or of its own range under
+rounding-level perturbation; lambda_max within 1e-6; at equal iteration
+counts the velocity and the whole zero-mean solution within 1e-10, and at
+rtol 1e-11 within 1e-10 wherever the oracle cannot reproduce its own
+iterate to 1e-11).
 """
 import numpy as np
 import pytest
