@@ -2379,51 +2379,81 @@ static void setup_core(bddc* b, const int32_t* part) {
       D.loc_off = loc;
       loc += D.nv + D.npress;
     }
-    // problems and nodes
+    // problems and nodes: offsets and node records in one pass, then the
+    // per-problem tables copied into place in parallel
     b->h_probs.assign(H.probs.size(), ProbDev{});
     b->h_nodes.clear();
-    for (size_t q = 0; q < H.probs.size(); ++q) {
-      const Problem& P = H.probs[q];
-      ProbDev& D = b->h_probs[q];
-      D.sub = P.sub;
-      D.kind = P.kind;
-      D.n = P.n;
-      D.npiv = P.npiv;
-      D.mult0 = P.mult0;
-      D.nmult = P.nmult;
-      D.macro = P.macro;
-      D.pos_off = (int64_t)dtype.size();
-      dtype.insert(dtype.end(), P.dtype.begin(), P.dtype.end());
-      bgrp.insert(bgrp.end(), P.bgrp.begin(), P.bgrp.end());
-      for (int64_t x : P.dsrc) dsrc.push_back((int)x);
-      D.elpos_off = (int64_t)elpos.size();
-      elpos.insert(elpos.end(), P.elpos.begin(), P.elpos.end());
-      D.elptr_off = (int64_t)elptr.size();
-      elptr.insert(elptr.end(), P.elpos_off.begin(), P.elpos_off.end());
-      D.pv_off = (int64_t)pv.size();
-      pv.insert(pv.end(), P.pos_of_vdof.begin(), P.pos_of_vdof.end());
-      const int base = (int)b->h_nodes.size();
-      const int64_t border_base = (int64_t)border.size(), rel_base = (int64_t)rel.size();
-      const int child_base = (int)children.size();
-      border.insert(border.end(), P.border.begin(), P.border.end());
-      rel.insert(rel.end(), P.rel.begin(), P.rel.end());
-      for (int c : P.children) children.push_back(base + c);
-      for (const Node& Nd : P.nodes) {
-        NodeDev N{};
-        N.prob = (int)q;
-        N.p0 = Nd.p0;
-        N.np = Nd.np;
-        N.nb = Nd.nb;
-        N.parent = Nd.parent >= 0 ? base + Nd.parent : -1;
-        N.height = Nd.height;
-        N.first_child = child_base + Nd.first_child;
-        N.nchild = Nd.nchild;
-        N.flags = Nd.flags;
-        N.border_off = border_base + Nd.border_off;
-        N.rel_off = rel_base + Nd.rel_off;
-        b->h_nodes.push_back(N);
+    {
+      const size_t nq = H.probs.size();
+      std::vector<int64_t> o_pos(nq), o_elpos(nq), o_elptr(nq), o_pv(nq), o_bord(nq), o_rel(nq), o_child(nq);
+      int64_t n_pos = 0, n_elpos = 0, n_elptr = 0, n_pv = 0, n_bord = 0, n_rel = 0, n_child = 0;
+      std::vector<int> nbase(nq);
+      for (size_t q = 0; q < nq; ++q) {
+        const Problem& P = H.probs[q];
+        ProbDev& D = b->h_probs[q];
+        D.sub = P.sub;
+        D.kind = P.kind;
+        D.n = P.n;
+        D.npiv = P.npiv;
+        D.mult0 = P.mult0;
+        D.nmult = P.nmult;
+        D.macro = P.macro;
+        VB_CHECK(P.bgrp.size() == P.dtype.size() && P.dsrc.size() == P.dtype.size(), VEM_EINVAL,
+                 "setup: position tables of a local problem differ in length");
+        o_pos[q] = D.pos_off = n_pos;
+        n_pos += (int64_t)P.dtype.size();
+        o_elpos[q] = D.elpos_off = n_elpos;
+        n_elpos += (int64_t)P.elpos.size();
+        o_elptr[q] = D.elptr_off = n_elptr;
+        n_elptr += (int64_t)P.elpos_off.size();
+        o_pv[q] = D.pv_off = n_pv;
+        n_pv += (int64_t)P.pos_of_vdof.size();
+        o_bord[q] = n_bord;
+        n_bord += (int64_t)P.border.size();
+        o_rel[q] = n_rel;
+        n_rel += (int64_t)P.rel.size();
+        o_child[q] = n_child;
+        n_child += (int64_t)P.children.size();
+        const int base = nbase[q] = (int)b->h_nodes.size();
+        for (const Node& Nd : P.nodes) {
+          NodeDev N{};
+          N.prob = (int)q;
+          N.p0 = Nd.p0;
+          N.np = Nd.np;
+          N.nb = Nd.nb;
+          N.parent = Nd.parent >= 0 ? base + Nd.parent : -1;
+          N.height = Nd.height;
+          N.first_child = (int)o_child[q] + Nd.first_child;
+          N.nchild = Nd.nchild;
+          N.flags = Nd.flags;
+          N.border_off = o_bord[q] + Nd.border_off;
+          N.rel_off = o_rel[q] + Nd.rel_off;
+          b->h_nodes.push_back(N);
+        }
+        D.root = (int)b->h_nodes.size() - 1;
       }
-      D.root = (int)b->h_nodes.size() - 1;
+      dtype.resize(n_pos);
+      bgrp.resize(n_pos);
+      dsrc.resize(n_pos);
+      elpos.resize(n_elpos);
+      elptr.resize(n_elptr);
+      pv.resize(n_pv);
+      border.resize(n_bord);
+      rel.resize(n_rel);
+      children.resize(n_child);
+#pragma omp parallel for schedule(dynamic)
+      for (int64_t q = 0; q < (int64_t)nq; ++q) {
+        const Problem& P = H.probs[q];
+        std::copy(P.dtype.begin(), P.dtype.end(), dtype.begin() + o_pos[q]);
+        std::copy(P.bgrp.begin(), P.bgrp.end(), bgrp.begin() + o_pos[q]);
+        for (size_t i = 0; i < P.dsrc.size(); ++i) dsrc[o_pos[q] + i] = (int)P.dsrc[i];
+        std::copy(P.elpos.begin(), P.elpos.end(), elpos.begin() + o_elpos[q]);
+        std::copy(P.elpos_off.begin(), P.elpos_off.end(), elptr.begin() + o_elptr[q]);
+        std::copy(P.pos_of_vdof.begin(), P.pos_of_vdof.end(), pv.begin() + o_pv[q]);
+        std::copy(P.border.begin(), P.border.end(), border.begin() + o_bord[q]);
+        std::copy(P.rel.begin(), P.rel.end(), rel.begin() + o_rel[q]);
+        for (size_t i = 0; i < P.children.size(); ++i) children[o_child[q] + i] = nbase[q] + P.children[i];
+      }
     }
     // macro entities; the (entity, sharing subdomain) position and interface
     // index tables need searches and are built in parallel
