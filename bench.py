@@ -33,12 +33,13 @@ METRIC = "BDDC-PCG time-to-solution at rtol 1e-8 and BDDC applies/s, FP32-local 
 WORKLOAD = "tri32_k2"
 LOAD_DEGREE = 11            # k + 9: exact for the degree-9 manufactured load at k = 2
 ORACLE_WORKLOAD = "tri8_k2"
-# DRAM bytes the sweep kernels move per algorithmic factor byte: 1,931.7 MB
-# against 1.79 GB in one ncu capture of an apply on the 16^3 member
+# DRAM bytes the sweep kernels (with the FP32 conversions of their vectors)
+# move per algorithmic factor byte: 1,910.2 MB against 1.79 GB in one ncu
+# capture of an apply on the 16^3 member
 # (profiles/bddc_apply_tri16_k2_fp32local_dram.md); the traffic scales with
 # the factor bytes, so the 32^3 sweep pair's traffic is this ratio times its
 # algorithmic bytes
-SWEEP_TRAFFIC_RATIO = 1931.7 / 1790.0
+SWEEP_TRAFFIC_RATIO = 1910.2 / 1790.0
 
 
 def peaks():
