@@ -222,7 +222,7 @@ def measure(pkg, torch, cfg, fq_host, precision, steps, warmup, stream, with_e2e
             g, bd, u, rhs, res = step(host_u)
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
-    keys = ("factor_bytes_dirichlet", "factor_bytes_neumann", "deluxe_bytes", "t_symbolic_ms", "t_upload_ms",
+    keys = ("factor_bytes_dirichlet", "factor_bytes_neumann", "deluxe_bytes", "t_symbolic_ms", "t_flatten_ms", "t_upload_ms",
             "t_factor_dirichlet_ms", "t_factor_neumann_ms", "t_factor_deluxe_ms", "t_deluxe_combine_ms",
             "t_coarse_rhs_ms", "t_coarse_solves_ms", "t_coarse_gram_ms", "t_coarse_inverse_ms",
             "gflop_factor_dirichlet", "gflop_factor_neumann", "gflop_factor_deluxe")
