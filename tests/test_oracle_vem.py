@@ -184,3 +184,43 @@ def test_convergence_rate_cubic_solution():
         errs.append(np.sqrt(e2 / n2))
     rate = np.log(errs[0] / errs[1]) / np.log(2.0)
     assert 2.7 < rate < 3.3
+
+
+def test_convergence_rates_manufactured_solution():
+    """The manufactured solution of the benchmark load (u = curl psi,
+    vanishing on the boundary, p = 0), k = 2, on 2^3, 4^3 and 8^3 cubes: the
+    H^1 error of Pi^nabla_k u_h decays like h^k and the L^2 error of
+    Pi^0_k u_h like h^{k+1} (convergence theorem, Sec. 3); the rates are
+    taken between 4^3 and 8^3 (2^3 is still pre-asymptotic).  The gradient
+    of u is taken by central differences of step 1e-6 (error ~1e-12)."""
+    from oracle_cache import oracle_system
+    from oracle.poly import dmono3
+    from synth.fields import manufactured_u
+    Nk = dim3(2)
+    errs = []
+    for n in (2, 4, 8):
+        _, S = oracle_system("cube4_k2", n=n)
+        uh, _ = S.solve_direct()
+        e1 = n1 = e0 = n0 = 0.0
+        d = 1e-6
+        for e, el in S.elements.items():
+            x = el.vq_pts
+            ue = manufactured_u(x)
+            gu = np.stack([(manufactured_u(x + d * np.eye(3)[j]) - manufactured_u(x - d * np.eye(3)[j])) / (2 * d)
+                           for j in range(3)], 2)
+            cN = el.PiN @ uh[el.dofs]
+            g = np.stack([np.stack([dmono3(2, el.xi, j) @ cN[c * Nk:(c + 1) * Nk] / el.hK for j in range(3)], 1)
+                          for c in range(3)], 1)
+            e1 += el.vq_w @ np.sum((g - gu) ** 2, (1, 2))
+            n1 += el.vq_w @ np.sum(gu ** 2, (1, 2))
+            c0 = el.Pi0 @ uh[el.dofs]
+            M = mono3(2, el.xi)
+            v = np.stack([M @ c0[j * Nk:(j + 1) * Nk] for j in range(3)], 1)
+            e0 += el.vq_w @ np.sum((v - ue) ** 2, 1)
+            n0 += el.vq_w @ np.sum(ue ** 2, 1)
+        errs.append((np.sqrt(e1 / n1), np.sqrt(e0 / n0)))
+    assert errs[0][0] > errs[1][0] > errs[2][0] and errs[0][1] > errs[1][1] > errs[2][1]
+    h1 = np.log(errs[1][0] / errs[2][0]) / np.log(2.0)
+    l2 = np.log(errs[1][1] / errs[2][1]) / np.log(2.0)
+    assert 1.8 < h1 < 2.2, h1
+    assert 2.8 < l2 < 3.3, l2
